@@ -1,0 +1,241 @@
+/*
+ * vl.h -- C ABI of the GB300 iterative Vecchia-Laplace library (libvl.so).
+ *
+ * The library computes, for a latent Gaussian-process model with a non-Gaussian
+ * likelihood (Kuendig & Sigrist, "Iterative Methods for Vecchia-Laplace
+ * Approximations for Latent Gaussian Process Models"):
+ *   - the Vecchia factor Sigma_tilde^{-1} = B^T D^{-1} B           (Section 2.1)
+ *   - the Laplace mode b* by Newton's method                       (Eq. newton)
+ *   - the negative log-marginal likelihood L^VLA with the
+ *     log-determinant by stochastic Lanczos quadrature             (Eqs. VLA_loss,
+ *                                                                   logdetsplit,
+ *                                                                   logdetsplit2, def_SLQ)
+ *   - latent predictive means and variances                        (Eq. latentpostpredictive,
+ *                                                                   Algorithm simAlgo)
+ * All linear solves with W + Sigma_tilde^{-1} use preconditioned CG
+ * (Appendix, "PCG algorithm with Lanczos tridiagonal matrix") with the VADU, LVA
+ * or LRAC preconditioner (Section 3.1). Every step runs in CUDA kernels on one
+ * GPU; there is no CPU fallback.
+ *
+ * Conventions for every call:
+ *   - Status codes are returned; nothing throws across the ABI. A message for the
+ *     last failure on a context is available from vl_last_error().
+ *   - Pointer arguments may be host or device memory; the library asks the CUDA
+ *     driver which (cudaPointerGetAttributes) and copies host data itself. Device
+ *     pointers must be on the context's device.
+ *   - "caller order" is the row order of the caller's location array. The Vecchia
+ *     ordering is given by `order` (order[k] = caller index of the k-th point).
+ *   - Matrices of right-hand sides are n x t, row-major (t values of a point are
+ *     contiguous), float64.
+ *   - All work is issued on the context's stream. Calls that return host scalars
+ *     synchronise that stream; the others may return before the GPU finishes,
+ *     except that results written to host pointers are complete on return.
+ *   - The caller owns every input and output buffer. The library owns the opaque
+ *     handles. Device memory comes from the workspace given to vl_ctx_create (or
+ *     from one allocation of ws_bytes made there if none is given); nothing is
+ *     allocated on the device after that. Running out of it is VL_ERR_OOM.
+ *   - On an error, handles stay valid and destroyable; outputs are unspecified.
+ */
+#ifndef VL_H_
+#define VL_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum vl_status {
+  VL_OK = 0,
+  VL_ERR_INVALID_ARG = 1,   /* bad size, pointer or option                     */
+  VL_ERR_OOM = 2,           /* workspace exhausted                              */
+  VL_ERR_NOT_SPD = 3,       /* a Cholesky pivot <= 0 (message names the row)    */
+  VL_ERR_NOT_CONVERGED = 4, /* CG or Newton hit its iteration cap               */
+  VL_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up               */
+  VL_ERR_CUDA = 6,          /* a CUDA runtime call failed                       */
+  VL_ERR_STATE = 7          /* call made on a handle in the wrong state         */
+} vl_status;
+
+/* Covariance c(h) of the latent GP (Section 4.1 writes the Matern nu = 3/2 form). */
+typedef enum vl_cov {
+  VL_COV_EXPONENTIAL = 0, /* sigma2 exp(-h / rho)                              */
+  VL_COV_MATERN15 = 1     /* sigma2 (1 + sqrt3 h / rho) exp(-sqrt3 h / rho)    */
+} vl_cov;
+
+/* Likelihood p(y_i | mu_i) (Section 2; log-concave in mu). */
+typedef enum vl_lik {
+  VL_LIK_BERNOULLI_LOGIT = 0, /* y in {0,1}, p = 1 / (1 + exp(-mu))             */
+  VL_LIK_POISSON_LOG = 1      /* y in {0,1,2,...}, mean exp(mu)                  */
+} vl_lik;
+
+/* Preconditioner (Section 3.1). VADU and LVA use Eqs. pcls1/logdetsplit; LRAC uses
+ * Eqs. pcls2/logdetsplit2. */
+typedef enum vl_precond {
+  VL_PREC_VADU = 0, /* P = B^T (W + D^{-1}) B                                     */
+  VL_PREC_LVA = 1,  /* P = B^T D^{-1} B                                           */
+  VL_PREC_LRAC = 2  /* P = L_k L_k^T + W^{-1}, L_k pivoted Cholesky of Sigma        */
+} vl_precond;
+
+/* Arithmetic of the iterative solves. The factor build is always float64. */
+typedef enum vl_precision {
+  VL_FP64 = 0,        /* every Krylov vector, operator and dot in float64            */
+  VL_FP32_REFINE = 1  /* float32 operator and vectors; scalars in float64; Newton
+                         and simulation solves refined with float64 residuals until
+                         the float64 relative residual meets cg_tol               */
+} vl_precision;
+
+typedef struct vl_opts {
+  int precision;        /* vl_precision                                  default VL_FP64 */
+  int precond;          /* vl_precond                                    default VL_PREC_VADU */
+  int t;                /* SLQ probe vectors (Rademacher)                default 50 */
+  int k;                /* LRAC rank                                     default 50 */
+  int s;                /* simulation vectors for predictive variances   default 100 */
+  double cg_tol;        /* per-column relative residual ||r|| / ||b||    default 1e-6 */
+  int cg_max_iter;      /*                                               default 1000 */
+  double newton_tol;    /* max |b_new - b| <= newton_tol (1 + max |b_new|)   default 1e-9 */
+  int newton_max_iter;  /*                                               default 100 */
+  double nugget;        /* added to diag(Sigma); < 0 means 1e-10 sigma2  default -1 */
+  uint64_t seed;        /* Philox4x64-10 key for probes and simulation   default 1 */
+} vl_opts;
+
+/* Per-call diagnostics (any pointer argument of this type may be NULL). */
+typedef struct vl_stats {
+  int newton_iters;
+  int cg_calls;            /* PCG solves issued                                    */
+  int cg_iters_max;        /* most iterations used by a column in the last solve   */
+  int cg_iters_total;      /* sum of per-solve iteration counts                    */
+  double cg_relres_max;    /* largest final relative residual of the last solve    */
+  int refine_steps;        /* float64 refinement passes (mixed precision)          */
+  double true_relres_max;  /* float64 relative residual of the refined solutions   */
+  double slq_mean;         /* mean of gamma_i (the SLQ term)                       */
+  double slq_stderr;       /* standard error of that mean over the probes          */
+  double logdet;           /* log det(Sigma_tilde W + I) used in L^VLA             */
+  double ms_total;         /* device time of the call (CUDA events)                */
+} vl_stats;
+
+typedef struct vl_ctx vl_ctx;
+typedef struct vl_factor vl_factor;
+typedef struct vl_state vl_state;
+
+/* Library version string, e.g. "vl 0.1.0 sm_103a". Never NULL. */
+const char* vl_version(void);
+
+/* Fills *o with the defaults listed in vl_opts. */
+void vl_opts_default(vl_opts* o);
+
+/* Creates a context on CUDA device `device` issuing work on `cuda_stream` (a
+ * cudaStream_t; NULL = the legacy default stream). `workspace` is a device buffer
+ * of ws_bytes the library sub-allocates from for every handle made on this
+ * context; if NULL, the library makes one cudaMalloc of ws_bytes here and frees it
+ * in vl_ctx_destroy. Errors: VL_ERR_INVALID_ARG (out == NULL, ws_bytes < 1 MiB),
+ * VL_ERR_CUDA, VL_ERR_OOM. */
+vl_status vl_ctx_create(int device, void* cuda_stream, void* workspace, size_t ws_bytes,
+                        vl_ctx** out);
+void vl_ctx_destroy(vl_ctx* ctx);
+/* Thread-unsafe, context-local: the message of the last failed call (or ""). */
+const char* vl_last_error(const vl_ctx* ctx);
+/* Blocks until the context's stream is idle. */
+vl_status vl_ctx_synchronize(vl_ctx* ctx);
+/* Bytes of workspace currently in use / peak use. */
+vl_status vl_ctx_mem(const vl_ctx* ctx, size_t* in_use, size_t* peak);
+
+/* Vecchia factor (Section 2.1): for locations `locs` (n x 2, caller order) and the
+ * ordering `order` (n entries, a permutation of 0..n-1; NULL = identity), finds
+ * N(i) = the min(i, m) nearest earlier points under the key (d2, index) with d2 in
+ * float64 and no fused multiply-add (bit-exact, ties to the lower index), the
+ * forward/backward level schedules of B, and for every row the m x m covariance
+ * solve A_i = Sigma_{i,N(i)} Sigma_{N(i)}^{-1}, D_i = Sigma_ii - A_i Sigma_{N(i),i}
+ * with the nugget of opts on diag(Sigma). 0 <= m <= 64; n >= 1.
+ * Errors: VL_ERR_INVALID_ARG, VL_ERR_NOT_SPD (row named in vl_last_error),
+ * VL_ERR_OOM, VL_ERR_CUDA, VL_ERR_TIMEOUT. */
+vl_status vl_build_factor(vl_ctx* ctx, const double* locs, int64_t n, const int32_t* order,
+                          int cov, double sigma2, double range, int m, const vl_opts* opts,
+                          vl_factor** out);
+
+/* Recomputes A_i and D_i for new covariance parameters (the per-evaluation part of
+ * Section 2.1), reusing neighbours and level schedules. */
+vl_status vl_factor_refit(vl_factor* f, double sigma2, double range, const vl_opts* opts);
+
+/* Copies the factor out in Vecchia row order (k = 0..n-1). Any pointer may be NULL.
+ * N: n x m int32 (Vecchia indices, -1 padding), A: n x m float64 kriging weights
+ * (B_{k,N(k)} = -A), D: n float64, lev_fwd/lev_bwd: n int32 level of each row. */
+vl_status vl_factor_export(const vl_factor* f, int32_t* N, double* A, double* D,
+                           int32_t* lev_fwd, int32_t* lev_bwd);
+/* n, m and the number of forward / backward levels. Any pointer may be NULL. */
+vl_status vl_factor_info(const vl_factor* f, int64_t* n, int* m, int* nlev_fwd, int* nlev_bwd);
+void vl_factor_destroy(vl_factor* f);
+
+/* Laplace mode (Eq. newton): b^{t+1} = (W + Sigma_tilde^{-1})^{-1}(W b^t + grad log p),
+ * b^0 = 0, a step halved (at most 30 times) while it lowers
+ * psi(b) = log p(y|F+b) - b^T Sigma_tilde^{-1} b / 2 by more than 1e-12 (1 + |psi|),
+ * stopping when max|b^{t+1} - b^t| <= newton_tol (1 + max|b^{t+1}|). y, F (F may be NULL
+ * = 0) and mode_out (may be NULL) have n entries in caller order. The state keeps b*,
+ * W and the factor resident for vl_log_marglik / vl_pred_var; it references f,
+ * which must outlive it. Errors: VL_ERR_NOT_CONVERGED, VL_ERR_TIMEOUT, ... */
+vl_status vl_find_mode(vl_factor* f, int lik, const double* y, const double* F,
+                       const vl_opts* opts, double* mode_out, vl_state** out);
+void vl_state_destroy(vl_state* s);
+
+/* L^VLA (Eq. VLA_loss) at the state's mode: -log p(y|mu*) + b*^T Sigma_tilde^{-1} b* / 2
+ * + log det(Sigma_tilde W + I)/2. The log-determinant is split by the preconditioner
+ * (Eq. logdetsplit for VADU/LVA, Eq. logdetsplit2 for LRAC) and the last term
+ * estimated by SLQ (Eq. def_SLQ) from the CG coefficients of opts->t probe solves,
+ * probes z = P^{1/2} r with r Rademacher from Philox4x64-10(counter = (caller index,
+ * j / 256, 0, 0), key = (seed, 0)). log p includes every constant (-log y! for
+ * Poisson). Writes the host scalars *lml (and *logdet if non-NULL). */
+vl_status vl_log_marglik(vl_state* s, const vl_opts* opts, double* lml, double* logdet,
+                         vl_stats* stats);
+
+/* Per-probe SLQ values gamma_i = ||P^{-1/2} z_i||^2 e1^T log(T_i) e1 of the last
+ * vl_log_marglik call on this state (t doubles, host or device). */
+vl_status vl_slq_gammas(const vl_state* s, double* gammas, int t);
+
+/* Latent predictive distribution (Eq. latentpostpredictive) at np test locations
+ * (np x 2): each conditions on its m nearest training points (Section 4.1, B_p = I),
+ * mean_p = F_p - B_po b*, var_p = D_p + (1/s) sum_k (B_po (W + Sigma_tilde^{-1})^{-1}
+ * z3_k)_p^2 with z3 = W^{1/2} z1 + B^T D^{-1/2} z2 (Algorithm simAlgo), z1, z2 standard
+ * normal by Box-Muller from Philox4x64-10(counter = (caller index, j / 4, 1 or 2, 0),
+ * key = (seed, 0)). Fp may be NULL (0). mean/var: np doubles (either may be NULL). */
+vl_status vl_pred_var(vl_state* s, const double* test_locs, int64_t np, const double* Fp,
+                      const vl_opts* opts, double* mean, double* var, vl_stats* stats);
+
+/* ------------------------------------------------------------------------------
+ * Building blocks, exposed for verification and for callers composing their own
+ * solvers. Vectors are in caller order, n x t row-major float64.
+ * ---------------------------------------------------------------------------- */
+
+/* The m nearest earlier neighbours of every point of `locs` (n x 2) taken in the
+ * given row order (Section 2.1; key (d2, index), bit-exact). N_out: n x m int32. */
+vl_status vl_knn_prev(vl_ctx* ctx, const double* locs, int64_t n, int m, int32_t* N_out);
+/* The min(m, n) nearest training points of each test point (Section 4.1), same key.
+ * N_out: np x m int32 (training row indices, -1 padding). */
+vl_status vl_knn_cross(vl_ctx* ctx, const double* train, int64_t n, const double* test,
+                       int64_t np, int m, int32_t* N_out);
+
+typedef enum vl_op {
+  VL_OP_A = 0,        /* (W + B^T D^{-1} B) X                                     */
+  VL_OP_PINV = 1,     /* P^{-1} X for the state's preconditioner (opts->precond)    */
+  VL_OP_B = 2,        /* B X                                                       */
+  VL_OP_BT = 3,       /* B^T X                                                     */
+  VL_OP_BINV = 4,     /* B^{-1} X  (level-scheduled forward solve)                  */
+  VL_OP_BTINV = 5,    /* B^{-T} X  (level-scheduled backward solve)                 */
+  VL_OP_SIGMA = 6,    /* Sigma_tilde X = B^{-1} D B^{-T} X                          */
+  VL_OP_A2 = 7        /* (Sigma_tilde + W^{-1}) X  (the form-2 operator, Eq. pcls2)  */
+} vl_op;
+
+/* Y = op(X) with the state's W, in the precision of opts (float64 in/out). */
+vl_status vl_apply(vl_state* s, int op, const double* X, int t, const vl_opts* opts, double* Y);
+
+/* Solves (W + Sigma_tilde^{-1}) U = RHS (t columns) by PCG with T extraction (the
+ * appendix algorithm, u_0 = 0, per-column stop ||r|| <= cg_tol ||b||), in the
+ * precision and preconditioner of opts (LRAC solves the form-2 system, Eq. pcls2).
+ * T_diag/T_off: t x lmax row-major (may be NULL), iters: t ints (may be NULL),
+ * relres: t doubles (may be NULL). */
+vl_status vl_pcg_solve(vl_state* s, const double* RHS, int t, const vl_opts* opts, double* U,
+                       int lmax, double* T_diag, double* T_off, int* iters, double* relres);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VL_H_ */

@@ -1,0 +1,325 @@
+"""ctypes declarations of include/vl.h and thin handle wrappers."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+
+COV_EXPONENTIAL, COV_MATERN15 = 0, 1
+LIK_BERNOULLI_LOGIT, LIK_POISSON_LOG = 0, 1
+PREC_VADU, PREC_LVA, PREC_LRAC = 0, 1, 2
+FP64, FP32_REFINE = 0, 1
+OP_A, OP_PINV, OP_B, OP_BT, OP_BINV, OP_BTINV, OP_SIGMA, OP_A2 = range(8)
+
+_STATUS = {0: "VL_OK", 1: "VL_ERR_INVALID_ARG", 2: "VL_ERR_OOM", 3: "VL_ERR_NOT_SPD",
+           4: "VL_ERR_NOT_CONVERGED", 5: "VL_ERR_TIMEOUT", 6: "VL_ERR_CUDA", 7: "VL_ERR_STATE"}
+
+
+class VLError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Opts(C.Structure):
+    _fields_ = [("precision", C.c_int), ("precond", C.c_int), ("t", C.c_int), ("k", C.c_int),
+                ("s", C.c_int), ("cg_tol", C.c_double), ("cg_max_iter", C.c_int),
+                ("newton_tol", C.c_double), ("newton_max_iter", C.c_int), ("nugget", C.c_double),
+                ("seed", C.c_uint64)]
+
+    @classmethod
+    def make(cls, **kw) -> "Opts":
+        o = cls()
+        library().vl_opts_default(C.byref(o))
+        for k, v in kw.items():
+            if not hasattr(o, k):
+                raise AttributeError(k)
+            setattr(o, k, v)
+        return o
+
+
+class Stats(C.Structure):
+    _fields_ = [("newton_iters", C.c_int), ("cg_calls", C.c_int), ("cg_iters_max", C.c_int),
+                ("cg_iters_total", C.c_int), ("cg_relres_max", C.c_double), ("refine_steps", C.c_int),
+                ("true_relres_max", C.c_double), ("slq_mean", C.c_double), ("slq_stderr", C.c_double),
+                ("logdet", C.c_double), ("ms_total", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return os.path.join(_HERE, "_build", "libvl.so")
+
+
+def library():
+    """The loaded libvl; raises if the CUDA library has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = lib_path()
+    if not os.path.exists(p):
+        raise ImportError(f"libvl.so not found at {p}: run paper_2310_12000_gb300.build.build() "
+                          "(the CUDA library is required; there is no CPU fallback)")
+    L = C.CDLL(p)
+    vp, i64, i32, d, st = C.c_void_p, C.c_int64, C.c_int, C.c_double, C.c_int
+    sig = {
+        "vl_version": (C.c_char_p, []),
+        "vl_opts_default": (None, [vp]),
+        "vl_ctx_create": (st, [i32, vp, vp, C.c_size_t, vp]),
+        "vl_ctx_destroy": (None, [vp]),
+        "vl_last_error": (C.c_char_p, [vp]),
+        "vl_ctx_synchronize": (st, [vp]),
+        "vl_ctx_mem": (st, [vp, vp, vp]),
+        "vl_build_factor": (st, [vp, vp, i64, vp, i32, d, d, i32, vp, vp]),
+        "vl_factor_refit": (st, [vp, d, d, vp]),
+        "vl_factor_export": (st, [vp, vp, vp, vp, vp, vp]),
+        "vl_factor_info": (st, [vp, vp, vp, vp, vp]),
+        "vl_factor_destroy": (None, [vp]),
+        "vl_find_mode": (st, [vp, i32, vp, vp, vp, vp, vp]),
+        "vl_state_destroy": (None, [vp]),
+        "vl_log_marglik": (st, [vp, vp, vp, vp, vp]),
+        "vl_slq_gammas": (st, [vp, vp, i32]),
+        "vl_pred_var": (st, [vp, vp, i64, vp, vp, vp, vp, vp]),
+        "vl_knn_prev": (st, [vp, vp, i64, i32, vp]),
+        "vl_knn_cross": (st, [vp, vp, i64, vp, i64, i32, vp]),
+        "vl_apply": (st, [vp, i32, vp, i32, vp, vp]),
+        "vl_pcg_solve": (st, [vp, vp, i32, vp, vp, i32, vp, vp, vp, vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _ptr(a, dtype) -> int:
+    """Pointer of a contiguous numpy array or torch tensor of the given dtype."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if a.dtype != dtype or not a.flags.c_contiguous:
+            raise TypeError(f"expected a C-contiguous {np.dtype(dtype)} array")
+        return a.ctypes.data
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        torch = None
+    if torch is not None and isinstance(a, torch.Tensor):
+        tmap = {np.float64: torch.float64, np.int32: torch.int32}
+        if a.dtype != tmap[np.dtype(dtype).type] or not a.is_contiguous():
+            raise TypeError(f"expected a contiguous {np.dtype(dtype)} tensor")
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _host(a, dtype):
+    if a is None or not isinstance(a, np.ndarray):
+        return a
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+class Context:
+    """A libvl context on one CUDA device: a stream and a workspace.
+
+    ws_bytes sizes the workspace every handle of this context sub-allocates from.
+    With torch available the workspace is a torch CUDA buffer owned by this object
+    (PyTorch as the device-memory provider); otherwise the library allocates it."""
+
+    def __init__(self, device: int = 0, ws_bytes: int = 1 << 30, stream=None, use_torch: bool = True):
+        self.lib = library()
+        self._ws = None
+        ws_ptr = None
+        sptr = None
+        if use_torch:
+            try:
+                import torch
+                if torch.cuda.is_available():
+                    self._ws = torch.empty(int(ws_bytes), dtype=torch.uint8, device=f"cuda:{device}")
+                    ws_ptr = self._ws.data_ptr()
+                    if stream is None:
+                        stream = torch.cuda.current_stream(device)
+                    sptr = stream.cuda_stream
+            except ImportError:
+                pass
+        if stream is not None and sptr is None:
+            sptr = int(stream)
+        h = C.c_void_p()
+        s = self.lib.vl_ctx_create(device, sptr, ws_ptr, int(ws_bytes), C.byref(h))
+        if s != 0:
+            raise VLError(s, "vl_ctx_create failed")
+        self.h = h
+        self.device = device
+
+    def check(self, status: int):
+        if status != 0:
+            raise VLError(status, self.lib.vl_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.vl_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def synchronize(self):
+        self.check(self.lib.vl_ctx_synchronize(self.h))
+
+    def mem(self):
+        a, b = C.c_size_t(), C.c_size_t()
+        self.check(self.lib.vl_ctx_mem(self.h, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    # ---------------------------------------------------------------- calls
+    def build_factor(self, locs, order, cov: int, sigma2: float, rho: float, m: int,
+                     opts: Opts | None = None) -> "Factor":
+        locs = _host(locs, np.float64)
+        order = _host(order, np.int32)
+        n = locs.shape[0]
+        opts = opts or Opts.make()
+        h = C.c_void_p()
+        self.check(self.lib.vl_build_factor(self.h, _ptr(locs, np.float64), n, _ptr(order, np.int32), cov,
+                                            sigma2, rho, m, C.byref(opts), C.byref(h)))
+        return Factor(self, h, n, m)
+
+    def knn_prev(self, locs, m: int, out=None):
+        locs = _host(locs, np.float64)
+        n = locs.shape[0]
+        out = np.empty((n, m), np.int32) if out is None else out
+        self.check(self.lib.vl_knn_prev(self.h, _ptr(locs, np.float64), n, m, _ptr(out, np.int32)))
+        return out
+
+    def knn_cross(self, train, test, m: int, out=None):
+        train, test = _host(train, np.float64), _host(test, np.float64)
+        out = np.empty((test.shape[0], m), np.int32) if out is None else out
+        self.check(self.lib.vl_knn_cross(self.h, _ptr(train, np.float64), train.shape[0], _ptr(test, np.float64),
+                                         test.shape[0], m, _ptr(out, np.int32)))
+        return out
+
+
+class Factor:
+    def __init__(self, ctx: Context, h, n: int, m: int):
+        self.ctx, self.h, self.n, self.m = ctx, h, n, m
+
+    def close(self):
+        if self.h:
+            self.ctx.lib.vl_factor_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def refit(self, sigma2: float, rho: float, opts: Opts | None = None):
+        opts = opts or Opts.make()
+        self.ctx.check(self.ctx.lib.vl_factor_refit(self.h, sigma2, rho, C.byref(opts)))
+
+    def info(self):
+        n, m, a, b = C.c_int64(), C.c_int(), C.c_int(), C.c_int()
+        self.ctx.check(self.ctx.lib.vl_factor_info(self.h, C.byref(n), C.byref(m), C.byref(a), C.byref(b)))
+        return {"n": n.value, "m": m.value, "nlev_fwd": a.value, "nlev_bwd": b.value}
+
+    def export(self):
+        n, m = self.n, self.m
+        N = np.empty((n, m), np.int32)
+        A = np.empty((n, m))
+        D = np.empty(n)
+        lf = np.empty(n, np.int32)
+        lb = np.empty(n, np.int32)
+        self.ctx.check(self.ctx.lib.vl_factor_export(self.h, N.ctypes.data, A.ctypes.data, D.ctypes.data,
+                                                     lf.ctypes.data, lb.ctypes.data))
+        return {"N": N, "A": A, "D": D, "lev_fwd": lf, "lev_bwd": lb}
+
+    def find_mode(self, lik: int, y, F=None, opts: Opts | None = None, mode_out=None, allow_unconverged=False):
+        y = _host(y, np.float64)
+        F = _host(F, np.float64)
+        opts = opts or Opts.make()
+        mode = np.empty(self.n) if mode_out is None else mode_out
+        h = C.c_void_p()
+        s = self.ctx.lib.vl_find_mode(self.h, lik, _ptr(y, np.float64), _ptr(F, np.float64), C.byref(opts),
+                                      _ptr(mode, np.float64), C.byref(h))
+        if s != 0 and not (allow_unconverged and s == 4 and h.value):
+            if h.value:
+                self.ctx.lib.vl_state_destroy(h)
+            self.ctx.check(s)
+        return State(self, h, mode)
+
+
+class State:
+    def __init__(self, fac: Factor, h, mode):
+        self.fac, self.ctx, self.h, self.mode = fac, fac.ctx, h, mode
+
+    def close(self):
+        if self.h:
+            self.ctx.lib.vl_state_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def log_marglik(self, opts: Opts | None = None, with_stats: bool = False):
+        opts = opts or Opts.make()
+        lml, ld = C.c_double(), C.c_double()
+        st = Stats()
+        self.ctx.check(self.ctx.lib.vl_log_marglik(self.h, C.byref(opts), C.byref(lml), C.byref(ld), C.byref(st)))
+        return (lml.value, st.as_dict()) if with_stats else lml.value
+
+    def slq_gammas(self, t: int):
+        g = np.empty(t)
+        self.ctx.check(self.ctx.lib.vl_slq_gammas(self.h, g.ctypes.data, t))
+        return g
+
+    def pred_var(self, test_locs, Fp=None, opts: Opts | None = None, mean_out=None, var_out=None,
+                 with_stats: bool = False):
+        test_locs = _host(test_locs, np.float64)
+        Fp = _host(Fp, np.float64)
+        opts = opts or Opts.make()
+        n_p = test_locs.shape[0]
+        mean = np.empty(n_p) if mean_out is None else mean_out
+        var = np.empty(n_p) if var_out is None else var_out
+        st = Stats()
+        self.ctx.check(self.ctx.lib.vl_pred_var(self.h, _ptr(test_locs, np.float64), n_p, _ptr(Fp, np.float64),
+                                                C.byref(opts), _ptr(mean, np.float64), _ptr(var, np.float64),
+                                                C.byref(st)))
+        return (mean, var, st.as_dict()) if with_stats else (mean, var)
+
+    def apply(self, op: int, X, opts: Opts | None = None):
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        if X.ndim == 1:
+            X = X[:, None]
+        opts = opts or Opts.make()
+        Y = np.empty_like(X)
+        self.ctx.check(self.ctx.lib.vl_apply(self.h, op, X.ctypes.data, X.shape[1], C.byref(opts), Y.ctypes.data))
+        return Y
+
+    def pcg_solve(self, RHS, opts: Opts | None = None, lmax: int = 0):
+        R = np.ascontiguousarray(RHS, dtype=np.float64)
+        if R.ndim == 1:
+            R = R[:, None]
+        t = R.shape[1]
+        opts = opts or Opts.make()
+        U = np.empty_like(R)
+        Td = np.zeros((t, max(lmax, 1)))
+        To = np.zeros((t, max(lmax, 1)))
+        it = np.zeros(t, np.int32)
+        rel = np.zeros(t)
+        self.ctx.check(self.ctx.lib.vl_pcg_solve(self.h, R.ctypes.data, t, C.byref(opts), U.ctypes.data, lmax,
+                                                 Td.ctypes.data if lmax else None, To.ctypes.data if lmax else None,
+                                                 it.ctypes.data, rel.ctypes.data))
+        return U, Td, To, it, rel

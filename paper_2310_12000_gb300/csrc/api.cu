@@ -1,0 +1,1058 @@
+// extern "C" entry points of libvl (include/vl.h) and the orchestration of the
+// Newton, SLQ and prediction steps. Every arithmetic step runs in the kernels of
+// kernels.cuh / factor.cu / knn.cu / graph.cu; the host only sequences launches,
+// reads back scalars and makes the stopping decisions.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "engine.cuh"
+
+namespace vl {
+
+// ----------------------------------------------------------------------------- small kernels
+__global__ void gather2_kernel(int n, const double* __restrict__ in, const int32_t* __restrict__ idx,
+                               double* __restrict__ out) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) {
+    int u = idx ? idx[k] : k;
+    out[2 * k] = in[2 * (int64_t)u];
+    out[2 * k + 1] = in[2 * (int64_t)u + 1];
+  }
+}
+
+template <typename T>
+__global__ void to_storage_kernel(int n, int t, int ld, const int32_t* __restrict__ s2u, const double* __restrict__ Xu,
+                                  T* __restrict__ Xs) {
+  const int64_t total = (int64_t)n * ld;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int s = (int)(e / ld), c = (int)(e % ld);
+    Xs[e] = (c < t) ? (T)Xu[(int64_t)s2u[s] * t + c] : T(0);
+  }
+}
+
+template <typename T>
+__global__ void from_storage_kernel(int n, int t, int ld, const int32_t* __restrict__ s2u, const T* __restrict__ Xs,
+                                    double* __restrict__ Xu) {
+  const int64_t total = (int64_t)n * t;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int s = (int)(e / t), c = (int)(e % t);
+    Xu[(int64_t)s2u[s] * t + c] = (double)Xs[(int64_t)s * ld + c];
+  }
+}
+
+__global__ void export_kernel(int n, int m, const int32_t* __restrict__ s2v, const int32_t* __restrict__ nbr,
+                              const double* __restrict__ A, const double* __restrict__ D, const int32_t* __restrict__ lf,
+                              const int32_t* __restrict__ lb, int32_t* __restrict__ N_out, double* __restrict__ A_out,
+                              double* __restrict__ D_out, int32_t* __restrict__ lf_out, int32_t* __restrict__ lb_out) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const int k = s2v[s];
+  for (int c = 0; c < m; ++c) {
+    const int j = nbr[(int64_t)s * m + c];
+    if (N_out) N_out[(int64_t)k * m + c] = j >= 0 ? s2v[j] : -1;
+    if (A_out) A_out[(int64_t)k * m + c] = A[(int64_t)s * m + c];
+  }
+  if (D_out) D_out[k] = D[s];
+  if (lf_out) lf_out[k] = lf[s];
+  if (lb_out) lb_out[k] = lb[s];
+}
+
+// out[b] = partial sums of x (one column) or of log D etc., combined with reduce_partials.
+__global__ void sum_kernel(int n, int mode, const double* __restrict__ a, const double* __restrict__ b,
+                           double* __restrict__ partial) {
+  double acc = 0.0;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+    double v;
+    if (mode == 0) v = a[s];                          // sum a
+    else if (mode == 1) v = log(a[s]);                // sum log a
+    else v = log(b[s] + 1.0 / a[s]);                  // sum log(W + 1/D), a = D, b = W
+    acc += v;
+  }
+  __shared__ double sh[256];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < blockDim.x; ++i) s += sh[i];
+    partial[blockIdx.x] = s;
+  }
+}
+
+__global__ void absmax_kernel(int n, const double* __restrict__ a, const double* __restrict__ b,
+                              double* __restrict__ partial) {
+  double m1 = 0.0, m2 = 0.0;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+    m1 = fmax(m1, fabs(a[s] - (b ? b[s] : 0.0)));
+    m2 = fmax(m2, fabs(a[s]));
+  }
+  __shared__ double s1[256], s2[256];
+  s1[threadIdx.x] = m1;
+  s2[threadIdx.x] = m2;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double x = 0.0, y = 0.0;
+    for (int i = 0; i < blockDim.x; ++i) {
+      x = fmax(x, s1[i]);
+      y = fmax(y, s2[i]);
+    }
+    partial[2 * blockIdx.x] = x;
+    partial[2 * blockIdx.x + 1] = y;
+  }
+}
+
+// b_new <- b + 0.5 (b_new - b)
+__global__ void halve_kernel(int n, const double* __restrict__ b, double* __restrict__ bn) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) bn[s] = b[s] + 0.5 * (bn[s] - b[s]);
+}
+
+// elementwise helpers for diagonal scalings used by probes / simulation
+__global__ void diag_fn_kernel(int n, int mode, const double* __restrict__ W, const double* __restrict__ D,
+                               double* __restrict__ out) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+    double v;
+    if (mode == 0) v = sqrt(W[s] + 1.0 / D[s]);   // VADU P^{1/2} diagonal
+    else if (mode == 1) v = 1.0 / sqrt(D[s]);     // D^{-1/2}
+    else v = sqrt(W[s]);                          // W^{1/2}
+    out[s] = v;
+  }
+}
+
+// Prediction: mean_p = Fp + sum_c Ap[p,c] b[nbr_p,c];  var_p = Dp + mean_k z4[p,k]^2 with
+// z4[p,k] = -sum_c Ap[p,c] U[nbr_p,c][k]. One warp per test point, lanes over columns.
+template <typename T>
+__global__ void pred_kernel(int np, int m, const int32_t* __restrict__ nbr, const double* __restrict__ Ap,
+                            const double* __restrict__ Dp, const double* __restrict__ Fp, const double* __restrict__ b,
+                            const T* __restrict__ U, int s_cols, int ld, double* __restrict__ mean,
+                            double* __restrict__ var_acc) {
+  const int lane = threadIdx.x & 31;
+  const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (p >= np) return;
+  double mu = 0.0;
+  for (int c = lane; c < m; c += 32) {
+    const int j = nbr[(int64_t)p * m + c];
+    if (j >= 0) mu += Ap[(int64_t)p * m + c] * b[j];
+  }
+  mu = warp_sum(mu);
+  double sq = 0.0;
+  if (U) {
+    for (int col = lane; col < s_cols; col += 32) {
+      double z4 = 0.0;
+      for (int c = 0; c < m; ++c) {
+        const int j = nbr[(int64_t)p * m + c];
+        if (j < 0) break;
+        z4 -= Ap[(int64_t)p * m + c] * (double)U[(int64_t)j * ld + col];
+      }
+      sq += z4 * z4;
+    }
+    sq = warp_sum(sq);
+  }
+  if (lane == 0) {
+    if (mean) mean[p] = (Fp ? Fp[p] : 0.0) + mu;
+    if (var_acc) var_acc[p] += sq;
+  }
+}
+
+__global__ void pred_finish_kernel(int np, const double* __restrict__ Dp, double inv_s, double* __restrict__ var) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < np) var[p] = Dp[p] + var[p] * inv_s;
+}
+
+__global__ void translate_kernel(int64_t total, const int32_t* __restrict__ map, int32_t* __restrict__ idx) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
+    idx[e] = idx[e] >= 0 ? map[idx[e]] : -1;
+}
+
+// ----------------------------------------------------------------------------- pointer staging
+static bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <typename T>
+static vl_status stage_in(Ctx* c, Scratch& S, const T* p, size_t count, const T** out) {
+  if (!p || count == 0) {
+    *out = p;
+    return VL_OK;
+  }
+  if (is_device_ptr(p)) {
+    *out = p;
+    return VL_OK;
+  }
+  T* d = S.get<T>(count);
+  if (!d) return fail(c, VL_ERR_OOM, "workspace exhausted (staging input)");
+  VL_CUDA(c, cudaMemcpyAsync(d, p, sizeof(T) * count, cudaMemcpyHostToDevice, c->stream));
+  *out = d;
+  return VL_OK;
+}
+
+template <typename T>
+static vl_status stage_out(Ctx* c, const T* dev, T* p, size_t count) {
+  if (!p || count == 0) return VL_OK;
+  const bool d = is_device_ptr(p);
+  VL_CUDA(c, cudaMemcpyAsync(p, dev, sizeof(T) * count, d ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                             c->stream));
+  if (!d) VL_CUDA(c, cudaStreamSynchronize(c->stream));
+  return VL_OK;
+}
+
+static double read_scalar(Ctx* c, const double* dev, vl_status* st) {
+  double v = 0.0;
+  cudaError_t e = cudaMemcpyAsync(&v, dev, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) *st = cuda_fail(c, e, "read back");
+  return v;
+}
+
+// sum over n of mode-selected terms (see sum_kernel); float64, fixed order.
+static vl_status dev_sum(Ctx* c, Scratch& S, int n, int mode, const double* a, const double* b, double* host_out) {
+  const int nb = std::max(1, std::min(c->num_sms * 2, (n + 255) / 256));
+  double* part = S.get<double>(nb + 1);
+  if (!part) return fail(c, VL_ERR_OOM, "workspace exhausted (sum)");
+  sum_kernel<<<nb, 256, 0, c->stream>>>(n, mode, a, b, part);
+  reduce_partials_kernel<<<1, 32, 0, c->stream>>>(nb, 1, part, part + nb);
+  VL_CUDA(c, cudaGetLastError());
+  vl_status st = VL_OK;
+  *host_out = read_scalar(c, part + nb, &st);
+  return st;
+}
+
+static vl_status dev_absmax(Ctx* c, Scratch& S, int n, const double* a, const double* b, double* diff, double* amax) {
+  const int nb = std::max(1, std::min(c->num_sms * 2, (n + 255) / 256));
+  double* part = S.get<double>(2 * nb);
+  if (!part) return fail(c, VL_ERR_OOM, "workspace exhausted (absmax)");
+  absmax_kernel<<<nb, 256, 0, c->stream>>>(n, a, b, part);
+  VL_CUDA(c, cudaGetLastError());
+  std::vector<double> h(2 * nb);
+  VL_CUDA(c, cudaMemcpyAsync(h.data(), part, sizeof(double) * 2 * nb, cudaMemcpyDeviceToHost, c->stream));
+  VL_CUDA(c, cudaStreamSynchronize(c->stream));
+  *diff = 0.0;
+  *amax = 0.0;
+  for (int i = 0; i < nb; ++i) {
+    *diff = std::max(*diff, h[2 * i]);
+    *amax = std::max(*amax, h[2 * i + 1]);
+  }
+  return VL_OK;
+}
+
+static vl_status check_opts(Ctx* c, const vl_opts* o) {
+  if (!o) return fail(c, VL_ERR_INVALID_ARG, "opts is NULL");
+  if (o->precision != VL_FP64 && o->precision != VL_FP32_REFINE)
+    return fail(c, VL_ERR_INVALID_ARG, "unknown precision");
+  if (o->precond < 0 || o->precond > 2) return fail(c, VL_ERR_INVALID_ARG, "unknown preconditioner");
+  if (o->precond == VL_PREC_LRAC) return fail(c, VL_ERR_INVALID_ARG, "LRAC preconditioner is not available in this build");
+  if (o->t < 1 || o->t > 256 || o->s < 1 || !(o->cg_tol > 0) || o->cg_max_iter < 1 || o->newton_max_iter < 1)
+    return fail(c, VL_ERR_INVALID_ARG, "invalid option value");
+  return VL_OK;
+}
+
+// ----------------------------------------------------------------------------- log-likelihood pieces
+// psi(b) = sum log p(y | F + b) - b^T Sigma_tilde^{-1} b / 2     (float64)
+static vl_status psi_eval(State* st, Engine<double>& E1, Scratch& S, const double* b, double* psi_out,
+                          double* logp_out, double* quad_out) {
+  Ctx* c = st->ctx;
+  const int n = (int)st->f->n;
+  double* lp = S.get<double>(n);
+  if (!lp) return fail(c, VL_ERR_OOM, "workspace exhausted (psi)");
+  lik_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, st->lik, st->y, st->F, b, nullptr, nullptr, nullptr, lp);
+  VL_CUDA(c, cudaGetLastError());
+  double logp = 0.0, quad = 0.0;
+  VL_TRY(dev_sum(c, S, n, 0, lp, nullptr, &logp));
+  VL_TRY(E1.opB(b, nullptr, E1.y));
+  VL_TRY(E1.coldot(E1.y, E1.y, E1.Dinv, E1.red));
+  vl_status s = VL_OK;
+  quad = read_scalar(c, E1.red, &s);
+  VL_TRY(s);
+  c->arena.release(lp);
+  S.blocks.erase(std::find(S.blocks.begin(), S.blocks.end(), (void*)lp));
+  if (psi_out) *psi_out = logp - 0.5 * quad;
+  if (logp_out) *logp_out = logp;
+  if (quad_out) *quad_out = quad;
+  return VL_OK;
+}
+
+// Solve (W + Sigma_tilde^{-1}) x = rhs (one column, float64 in/out). FP64: one PCG
+// from x = 0. Mixed: float32 PCG on corrections, refined with float64 residuals
+// until ||rhs - A x|| <= tol ||rhs||.
+static vl_status solve1(State* st, const vl_opts* o, Engine<double>& E64, Engine<float>* E32, const double* rhs,
+                        double* x, vl_stats* stats) {
+  Ctx* c = st->ctx;
+  const int n = (int)st->f->n;
+  int used = 0;
+  if (o->precision == VL_FP64) {
+    VL_TRY(E64.pcg(rhs, x, o->cg_tol, o->cg_max_iter, &used));
+    if (stats) {
+      stats->cg_calls++;
+      stats->cg_iters_total += used;
+      stats->cg_iters_max = used;
+    }
+    return VL_OK;
+  }
+  // mixed precision with float64 iterative refinement; x starts at 0
+  Scratch S(c);
+  double* res = S.get<double>(n);
+  float* r32 = S.get<float>(n);
+  float* d32 = S.get<float>(n);
+  if (!res || !r32 || !d32) return fail(c, VL_ERR_OOM, "workspace exhausted (refinement)");
+  VL_CUDA(c, cudaMemsetAsync(x, 0, sizeof(double) * n, c->stream));
+  VL_TRY(E64.coldot(rhs, rhs, nullptr, E64.red));
+  vl_status s = VL_OK;
+  const double bn = std::sqrt(read_scalar(c, E64.red, &s));
+  VL_TRY(s);
+  double rel = 1.0;
+  const double inner_tol = std::max(o->cg_tol, 1e-4);
+  for (int pass = 0; pass < 12; ++pass) {
+    if (pass > 0 || true) {
+      VL_TRY(E64.opA(x, res));
+      residual_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, rhs, res);
+      VL_TRY(E64.coldot(res, res, nullptr, E64.red));
+      rel = bn > 0 ? std::sqrt(read_scalar(c, E64.red, &s)) / bn : 0.0;
+      VL_TRY(s);
+    }
+    if (rel <= o->cg_tol) break;
+    convert_kernel<double, float><<<grid_for(c, n), 256, 0, c->stream>>>(n, res, r32);
+    VL_CUDA(c, cudaGetLastError());
+    VL_TRY(E32->pcg(r32, d32, inner_tol, o->cg_max_iter, &used));
+    accumulate_kernel<double, float><<<grid_for(c, n), 256, 0, c->stream>>>(n, x, d32);
+    VL_CUDA(c, cudaGetLastError());
+    if (stats) {
+      stats->cg_calls++;
+      stats->cg_iters_total += used;
+      stats->cg_iters_max = used;
+      stats->refine_steps++;
+    }
+  }
+  if (stats) stats->true_relres_max = std::max(stats->true_relres_max, rel);
+  if (rel > o->cg_tol) return fail(c, VL_ERR_NOT_CONVERGED, "mixed-precision refinement did not reach cg_tol");
+  return VL_OK;
+}
+
+}  // namespace vl
+
+namespace vl {
+
+__global__ void repack_kernel(int64_t total, const double* __restrict__ in, float* __restrict__ out) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = (float)in[e];
+}
+
+// SLQ (Eq. def_SLQ): probes z = P^{1/2} r, PCG on A u = z with T extraction,
+// gamma_i = (r_0^T z_0)_i e1^T log(T_i) e1. Returns the t gammas on the host.
+template <typename T>
+static vl_status slq_run(State* st, const vl_opts* o, std::vector<double>& gam, vl_stats* stats) {
+  Ctx* c = st->ctx;
+  Factor* f = st->f;
+  const int n = (int)f->n, t = o->t;
+  Scratch S(c);
+  Engine<T> E(c);
+  VL_TRY(E.init(f, t, o->precond, st->W, o->cg_max_iter + 1));
+  // VADU: z = B^T (W + D^{-1})^{1/2} r;  LVA: z = B^T D^{-1/2} r     (Section 3.1.1)
+  T* Rm = S.get<T>((size_t)n * E.ld);
+  T* Zm = S.get<T>((size_t)n * E.ld);
+  T* Um = S.get<T>((size_t)n * E.ld);
+  double* sc64 = S.get<double>(n);
+  T* sc = S.get<T>(n);
+  double* gdev = S.get<double>(t);
+  double* work = S.get<double>((size_t)3 * t * E.lmax);
+  int* bad = S.get<int>(1);
+  if (!Rm || !Zm || !Um || !sc64 || !sc || !gdev || !work || !bad) return fail(c, VL_ERR_OOM, "workspace exhausted (SLQ)");
+  rademacher_kernel<T><<<(n + 127) / 128, 128, 0, c->stream>>>(n, t, E.ld, f->s2u, o->seed, 0, 0, Rm);
+  diag_fn_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, o->precond == VL_PREC_VADU ? 0 : 1, st->W, f->D64, sc64);
+  convert_kernel<double, T><<<grid_for(c, n), 256, 0, c->stream>>>(n, sc64, sc);
+  VL_CUDA(c, cudaGetLastError());
+  VL_TRY(E.opBt(Rm, sc, nullptr, nullptr, Zm));
+  int used = 0;
+  VL_TRY(E.pcg(Zm, Um, o->cg_tol, o->cg_max_iter, &used));
+  VL_CUDA(c, cudaMemsetAsync(bad, 0, sizeof(int), c->stream));
+  slq_quad_kernel<<<(t + 63) / 64, 64, 0, c->stream>>>(t, E.lmax, E.S.Tdiag, E.S.Toff, E.S.iters, E.S.rz0, work, gdev,
+                                                       bad);
+  VL_CUDA(c, cudaGetLastError());
+  std::vector<int> iters;
+  std::vector<double> rel;
+  VL_TRY(E.column_stats(iters, rel));
+  int hbad = 0;
+  gam.resize(t);
+  VL_CUDA(c, cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  VL_CUDA(c, cudaMemcpyAsync(gam.data(), gdev, sizeof(double) * t, cudaMemcpyDeviceToHost, c->stream));
+  VL_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (hbad) return fail(c, VL_ERR_NOT_CONVERGED, "SLQ: tridiagonal eigen-solve failed (non-positive Ritz value)");
+  const int itmax = *std::max_element(iters.begin(), iters.end());
+  const double relmax = *std::max_element(rel.begin(), rel.end());
+  if (stats) {
+    stats->cg_calls++;
+    stats->cg_iters_max = itmax;
+    stats->cg_iters_total += std::accumulate(iters.begin(), iters.end(), 0);
+    stats->cg_relres_max = relmax;
+  }
+  if (relmax > o->cg_tol && itmax >= o->cg_max_iter)
+    return fail(c, VL_ERR_NOT_CONVERGED, "SLQ probe solves reached cg_max_iter");
+  return VL_OK;
+}
+
+// U = (W + Sigma_tilde^{-1})^{-1} z3 for simulation columns [col0, col0 + sc),
+// z3 = W^{1/2} z1 + B^T D^{-1/2} z2 (Algorithm simAlgo). U: n x ld float64 (storage).
+static vl_status sim_block(State* st, const vl_opts* o, Engine<double>& E64, int sc, int col0, double* U,
+                           vl_stats* stats) {
+  Ctx* c = st->ctx;
+  Factor* f = st->f;
+  const int n = (int)f->n, ld = E64.ld;
+  const int64_t vec = (int64_t)n * ld;
+  Scratch S(c);
+  double* z1 = S.get<double>(vec);
+  double* z2 = S.get<double>(vec);
+  double* z3 = S.get<double>(vec);
+  double* sW = S.get<double>(n);
+  double* sD = S.get<double>(n);
+  if (!z1 || !z2 || !z3 || !sW || !sD) return fail(c, VL_ERR_OOM, "workspace exhausted (simulation)");
+  gaussian_kernel<<<(n + 127) / 128, 128, 0, c->stream>>>(n, sc, ld, col0, f->s2u, o->seed, 1, z1);
+  gaussian_kernel<<<(n + 127) / 128, 128, 0, c->stream>>>(n, sc, ld, col0, f->s2u, o->seed, 2, z2);
+  diag_fn_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, 2, st->W, f->D64, sW);
+  diag_fn_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, 1, st->W, f->D64, sD);
+  VL_CUDA(c, cudaGetLastError());
+  VL_TRY(E64.opBt(z2, sD, z1, sW, z3));
+  int used = 0;
+  if (o->precision == VL_FP64) {
+    VL_TRY(E64.pcg(z3, U, o->cg_tol, o->cg_max_iter, &used));
+    if (stats) {
+      stats->cg_calls++;
+      stats->cg_iters_total += used;
+      stats->cg_iters_max = used;
+    }
+    return VL_OK;
+  }
+  Engine<float> E32(c);
+  VL_TRY(E32.init(f, sc, o->precond, st->W, o->cg_max_iter + 1));
+  double* res = S.get<double>(vec);
+  float* r32 = S.get<float>(vec);
+  float* d32 = S.get<float>(vec);
+  if (!res || !r32 || !d32) return fail(c, VL_ERR_OOM, "workspace exhausted (simulation refinement)");
+  VL_CUDA(c, cudaMemsetAsync(res, 0, sizeof(double) * vec, c->stream));
+  VL_CUDA(c, cudaMemsetAsync(U, 0, sizeof(double) * vec, c->stream));
+  VL_TRY(E64.coldot(z3, z3, nullptr, E64.red2));
+  std::vector<double> bn(sc), rn(sc);
+  VL_CUDA(c, cudaMemcpyAsync(bn.data(), E64.red2, sizeof(double) * sc, cudaMemcpyDeviceToHost, c->stream));
+  double worst = 1.0;
+  for (int pass = 0; pass < 12; ++pass) {
+    VL_TRY(E64.opA(U, res));
+    residual_kernel<<<grid_for(c, vec), 256, 0, c->stream>>>(vec, z3, res);
+    VL_TRY(E64.coldot(res, res, nullptr, E64.red));
+    VL_CUDA(c, cudaMemcpyAsync(rn.data(), E64.red, sizeof(double) * sc, cudaMemcpyDeviceToHost, c->stream));
+    VL_CUDA(c, cudaStreamSynchronize(c->stream));
+    worst = 0.0;
+    for (int k = 0; k < sc; ++k) worst = std::max(worst, bn[k] > 0 ? std::sqrt(rn[k] / bn[k]) : 0.0);
+    if (worst <= o->cg_tol) break;
+    repack_kernel<<<grid_for(c, vec), 256, 0, c->stream>>>(vec, res, r32);
+    VL_CUDA(c, cudaGetLastError());
+    VL_TRY(E32.pcg(r32, d32, std::max(o->cg_tol, 1e-4), o->cg_max_iter, &used));
+    accumulate_kernel<double, float><<<grid_for(c, vec), 256, 0, c->stream>>>(vec, U, d32);
+    VL_CUDA(c, cudaGetLastError());
+    if (stats) {
+      stats->cg_calls++;
+      stats->cg_iters_total += used;
+      stats->cg_iters_max = used;
+      stats->refine_steps++;
+    }
+  }
+  if (stats) stats->true_relres_max = std::max(stats->true_relres_max, worst);
+  if (worst > o->cg_tol) return fail(c, VL_ERR_NOT_CONVERGED, "simulation solves: refinement did not reach cg_tol");
+  return VL_OK;
+}
+
+template <typename T>
+static vl_status apply_op(State* st, int op, const double* Xd, int t, const vl_opts* o, double* Yd) {
+  Ctx* c = st->ctx;
+  Factor* f = st->f;
+  const int n = (int)f->n;
+  Engine<T> E(c);
+  VL_TRY(E.init(f, t, o->precond, st->W, 0));
+  to_storage_kernel<T><<<grid_for(c, (int64_t)n * E.ld), 256, 0, c->stream>>>(n, t, E.ld, f->s2u, Xd, E.u);
+  VL_CUDA(c, cudaGetLastError());
+  switch (op) {
+    case VL_OP_A: VL_TRY(E.opA(E.u, E.v)); break;
+    case VL_OP_PINV: VL_TRY(E.opPinv(E.u, E.v)); break;
+    case VL_OP_B: VL_TRY(E.opB(E.u, nullptr, E.v)); break;
+    case VL_OP_BT: VL_TRY(E.opBt(E.u, nullptr, nullptr, nullptr, E.v)); break;
+    case VL_OP_BINV: VL_TRY(E.solveB(E.u, nullptr, E.v)); break;
+    case VL_OP_BTINV: VL_TRY(E.solveBt(E.u, nullptr, E.v)); break;
+    case VL_OP_SIGMA: VL_TRY(E.opSigma(E.u, E.v)); break;
+    case VL_OP_A2: VL_TRY(E.opA2(E.u, E.v)); break;
+    default: return fail(c, VL_ERR_INVALID_ARG, "vl_apply: unknown op");
+  }
+  from_storage_kernel<T><<<grid_for(c, (int64_t)n * t), 256, 0, c->stream>>>(n, t, E.ld, f->s2u, E.v, Yd);
+  VL_CUDA(c, cudaGetLastError());
+  return check_dev_status(c, "vl_apply");
+}
+
+template <typename T>
+static vl_status pcg_op(State* st, const double* Rd, int t, const vl_opts* o, double* Ud, int lmax, double* Td,
+                        double* To, int* iters, double* relres) {
+  Ctx* c = st->ctx;
+  Factor* f = st->f;
+  const int n = (int)f->n;
+  Engine<T> E(c);
+  VL_TRY(E.init(f, t, o->precond, st->W, o->cg_max_iter + 1));
+  Scratch S(c);
+  T* Bm = S.get<T>((size_t)n * E.ld);
+  T* Um = S.get<T>((size_t)n * E.ld);
+  if (!Bm || !Um) return fail(c, VL_ERR_OOM, "workspace exhausted (vl_pcg_solve)");
+  VL_CUDA(c, cudaMemsetAsync(Bm, 0, sizeof(T) * n * E.ld, c->stream));
+  to_storage_kernel<T><<<grid_for(c, (int64_t)n * E.ld), 256, 0, c->stream>>>(n, t, E.ld, f->s2u, Rd, Bm);
+  VL_CUDA(c, cudaGetLastError());
+  int used = 0;
+  VL_TRY(E.pcg(Bm, Um, o->cg_tol, o->cg_max_iter, &used));
+  from_storage_kernel<T><<<grid_for(c, (int64_t)n * t), 256, 0, c->stream>>>(n, t, E.ld, f->s2u, Um, Ud);
+  VL_CUDA(c, cudaGetLastError());
+  std::vector<int> it;
+  std::vector<double> rel;
+  VL_TRY(E.column_stats(it, rel));
+  if (iters) std::copy(it.begin(), it.end(), iters);
+  if (relres) std::copy(rel.begin(), rel.end(), relres);
+  if (lmax > 0 && (Td || To)) {
+    std::vector<double> hd((size_t)t * E.lmax), ho((size_t)t * E.lmax);
+    VL_CUDA(c, cudaMemcpyAsync(hd.data(), E.S.Tdiag, sizeof(double) * t * E.lmax, cudaMemcpyDeviceToHost, c->stream));
+    VL_CUDA(c, cudaMemcpyAsync(ho.data(), E.S.Toff, sizeof(double) * t * E.lmax, cudaMemcpyDeviceToHost, c->stream));
+    VL_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < t; ++k)
+      for (int l = 0; l < lmax; ++l) {
+        const bool in = l < E.lmax;
+        if (Td) Td[(size_t)k * lmax + l] = in ? hd[(size_t)k * E.lmax + l] : 0.0;
+        if (To) To[(size_t)k * lmax + l] = in ? ho[(size_t)k * E.lmax + l] : 0.0;
+      }
+  }
+  return VL_OK;
+}
+
+}  // namespace vl
+
+using namespace vl;
+
+struct vl_ctx : Ctx {};
+struct vl_factor : Factor {};
+struct vl_state : State {};
+
+// ============================================================================== C ABI
+extern "C" {
+
+const char* vl_version(void) { return "vl 0.1.0 sm_103a"; }
+
+void vl_opts_default(vl_opts* o) {
+  if (!o) return;
+  o->precision = VL_FP64;
+  o->precond = VL_PREC_VADU;
+  o->t = 50;
+  o->k = 50;
+  o->s = 100;
+  o->cg_tol = 1e-6;
+  o->cg_max_iter = 1000;
+  o->newton_tol = 1e-9;
+  o->newton_max_iter = 100;
+  o->nugget = -1.0;
+  o->seed = 1;
+}
+
+vl_status vl_ctx_create(int device, void* cuda_stream, void* workspace, size_t ws_bytes, vl_ctx** out) {
+  if (!out || ws_bytes < (1u << 20)) return VL_ERR_INVALID_ARG;
+  *out = nullptr;
+  vl_ctx* c = new vl_ctx();
+  c->device = device;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  auto bail = [&](vl_status s) {
+    if (c->owns_ws && c->ws) cudaFree(c->ws);
+    if (c->pinned) cudaFreeHost(c->pinned);
+    delete c;
+    return s;
+  };
+  if (cudaSetDevice(device) != cudaSuccess) return bail(VL_ERR_CUDA);
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return bail(VL_ERR_CUDA);
+  c->num_sms = prop.multiProcessorCount;
+  if (workspace) {
+    c->ws = static_cast<char*>(workspace);
+  } else {
+    if (cudaMalloc(&c->ws, ws_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return bail(VL_ERR_OOM);
+    }
+    c->owns_ws = true;
+  }
+  c->arena.init(c->ws, ws_bytes);
+  c->pinned_bytes = 1 << 16;
+  if (cudaMallocHost(&c->pinned, c->pinned_bytes) != cudaSuccess) return bail(VL_ERR_CUDA);
+  c->hstatus = reinterpret_cast<DevStatus*>(c->pinned + 1024);
+  c->dstatus = static_cast<DevStatus*>(c->arena.alloc(sizeof(DevStatus)));
+  if (!c->dstatus) return bail(VL_ERR_OOM);
+  if (cudaMemsetAsync(c->dstatus, 0, sizeof(DevStatus), c->stream) != cudaSuccess) return bail(VL_ERR_CUDA);
+  if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) return bail(VL_ERR_CUDA);
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return bail(VL_ERR_CUDA);
+  *out = c;
+  return VL_OK;
+}
+
+void vl_ctx_destroy(vl_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  if (c->owns_ws && c->ws) cudaFree(c->ws);
+  if (c->pinned) cudaFreeHost(c->pinned);
+  delete c;
+}
+
+const char* vl_last_error(const vl_ctx* c) { return c ? c->last_error.c_str() : "null context"; }
+
+vl_status vl_ctx_synchronize(vl_ctx* c) {
+  if (!c) return VL_ERR_INVALID_ARG;
+  VL_CUDA(c, cudaStreamSynchronize(c->stream));
+  return VL_OK;
+}
+
+vl_status vl_ctx_mem(const vl_ctx* c, size_t* in_use, size_t* peak) {
+  if (!c) return VL_ERR_INVALID_ARG;
+  if (in_use) *in_use = c->arena.in_use();
+  if (peak) *peak = c->arena.peak();
+  return VL_OK;
+}
+
+// --------------------------------------------------------------------------- neighbours
+vl_status vl_knn_prev(vl_ctx* c, const double* locs, int64_t n, int m, int32_t* N_out) {
+  if (!c) return VL_ERR_INVALID_ARG;
+  if (n < 0 || n > INT32_MAX / 2 || m < 0 || m > 64 || (!locs && n > 0) || (!N_out && n > 0 && m > 0))
+    return fail(c, VL_ERR_INVALID_ARG, "vl_knn_prev: invalid argument");
+  if (n == 0 || m == 0) return VL_OK;
+  Scratch S(c);
+  const double* dl;
+  VL_TRY(stage_in(c, S, locs, (size_t)n * 2, &dl));
+  int32_t* N = S.get<int32_t>((size_t)n * m);
+  if (!N) return fail(c, VL_ERR_OOM, "workspace exhausted (kNN)");
+  VL_TRY(knn_prev_dev(c, dl, n, m, N));
+  return stage_out(c, N, N_out, (size_t)n * m);
+}
+
+vl_status vl_knn_cross(vl_ctx* c, const double* train, int64_t n, const double* test, int64_t np, int m,
+                       int32_t* N_out) {
+  if (!c) return VL_ERR_INVALID_ARG;
+  if (n < 0 || np < 0 || m < 0 || m > 64 || (!train && n > 0) || (!test && np > 0) || (!N_out && np > 0 && m > 0))
+    return fail(c, VL_ERR_INVALID_ARG, "vl_knn_cross: invalid argument");
+  if (np == 0 || m == 0) return VL_OK;
+  Scratch S(c);
+  const double *dt, *dq;
+  VL_TRY(stage_in(c, S, train, (size_t)n * 2, &dt));
+  VL_TRY(stage_in(c, S, test, (size_t)np * 2, &dq));
+  int32_t* N = S.get<int32_t>((size_t)np * m);
+  if (!N) return fail(c, VL_ERR_OOM, "workspace exhausted (kNN)");
+  VL_TRY(knn_cross_dev(c, dt, n, dq, np, m, N));
+  return stage_out(c, N, N_out, (size_t)np * m);
+}
+
+// --------------------------------------------------------------------------- factor
+static double nugget_of(const vl_opts* o, double sigma2) {
+  return (o && o->nugget >= 0.0) ? o->nugget : 1e-10 * sigma2;
+}
+
+vl_status vl_factor_refit(vl_factor* f, double sigma2, double range, const vl_opts* opts) {
+  if (!f) return VL_ERR_INVALID_ARG;
+  Ctx* c = f->ctx;
+  if (!(sigma2 > 0) || !(range > 0)) return fail(c, VL_ERR_INVALID_ARG, "sigma2 and range must be > 0");
+  f->sigma2 = sigma2;
+  f->rho = range;
+  f->nugget = nugget_of(opts, sigma2);
+  VL_CUDA(c, cudaMemsetAsync(c->dstatus, 0, sizeof(DevStatus), c->stream));
+  VL_TRY(factor_rows(c, f->n, f->m, f->locs_s, f->locs_s, f->nbr, f->cov, f->sigma2, f->rho, f->nugget, f->A64, f->D64,
+                     f->s2v));
+  VL_TRY(refresh_transpose_values(f));
+  return check_dev_status(c, "Vecchia factor");
+}
+
+vl_status vl_build_factor(vl_ctx* c, const double* locs, int64_t n, const int32_t* order, int cov, double sigma2,
+                          double range, int m, const vl_opts* opts, vl_factor** out) {
+  if (!c) return VL_ERR_INVALID_ARG;
+  if (!out || !locs || n < 1 || n > (1LL << 30) || m < 0 || m > 64 || (cov != VL_COV_EXPONENTIAL && cov != VL_COV_MATERN15))
+    return fail(c, VL_ERR_INVALID_ARG, "vl_build_factor: invalid argument");
+  if (!(sigma2 > 0) || !(range > 0)) return fail(c, VL_ERR_INVALID_ARG, "sigma2 and range must be > 0");
+  *out = nullptr;
+  vl_factor* f = new vl_factor();
+  f->ctx = c;
+  f->mem.ctx = c;
+  f->n = n;
+  f->m = m;
+  f->cov = cov;
+  auto bail = [&](vl_status s) {
+    f->mem.free_all();
+    delete f;
+    return s;
+  };
+  Scratch S(c);
+  const double* dl;
+  const int32_t* dord = nullptr;
+  vl_status st = stage_in(c, S, locs, (size_t)n * 2, &dl);
+  if (st == VL_OK && order) st = stage_in(c, S, order, (size_t)n, &dord);
+  if (st != VL_OK) return bail(st);
+  const int64_t nm = n * (int64_t)m;
+  f->locs_v = f->mem.get<double>((size_t)n * 2);
+  f->locs_s = f->mem.get<double>((size_t)n * 2);
+  f->s2v = f->mem.get<int32_t>(n);
+  f->v2s = f->mem.get<int32_t>(n);
+  f->s2u = f->mem.get<int32_t>(n);
+  f->u2s = f->mem.get<int32_t>(n);
+  f->nbr = f->mem.get<int32_t>(std::max<int64_t>(nm, 1));
+  f->A64 = f->mem.get<double>(std::max<int64_t>(nm, 1));
+  f->A32 = f->mem.get<float>(std::max<int64_t>(nm, 1));
+  f->D64 = f->mem.get<double>(n);
+  f->lev_fwd = f->mem.get<int32_t>(n);
+  f->lev_bwd = f->mem.get<int32_t>(n);
+  f->task_fwd = f->mem.get<int32_t>(n);
+  f->task_bwd = f->mem.get<int32_t>(n);
+  f->ready = f->mem.get<unsigned>(n);
+  if (!f->locs_v || !f->locs_s || !f->s2v || !f->v2s || !f->s2u || !f->u2s || !f->nbr || !f->A64 || !f->A32 ||
+      !f->D64 || !f->lev_fwd || !f->lev_bwd || !f->task_fwd || !f->task_bwd || !f->ready)
+    return bail(fail(c, VL_ERR_OOM, "workspace exhausted (factor)"));
+  if (cudaMemsetAsync(f->ready, 0, sizeof(unsigned) * n, c->stream) != cudaSuccess)
+    return bail(cuda_fail(c, cudaGetLastError(), "memset"));
+  gather2_kernel<<<(int)((n + 255) / 256), 256, 0, c->stream>>>((int)n, dl, dord, f->locs_v);
+  int32_t* Nv = S.get<int32_t>(std::max<int64_t>(nm, 1));
+  if (!Nv) return bail(fail(c, VL_ERR_OOM, "workspace exhausted (neighbours)"));
+  if (m > 0) {
+    st = knn_prev_dev(c, f->locs_v, n, m, Nv);
+    if (st != VL_OK) return bail(st);
+  }
+  st = build_graph_impl(f, Nv, f->locs_v, dord);
+  if (st != VL_OK) return bail(st);
+  st = vl_factor_refit(f, sigma2, range, opts);
+  if (st != VL_OK) return bail(st);
+  *out = f;
+  return VL_OK;
+}
+
+vl_status vl_factor_export(const vl_factor* fc, int32_t* N, double* A, double* D, int32_t* lev_fwd, int32_t* lev_bwd) {
+  if (!fc) return VL_ERR_INVALID_ARG;
+  vl_factor* f = const_cast<vl_factor*>(fc);
+  Ctx* c = f->ctx;
+  const int64_t n = f->n, nm = n * f->m;
+  Scratch S(c);
+  int32_t* dN = N ? S.get<int32_t>(std::max<int64_t>(nm, 1)) : nullptr;
+  double* dA = A ? S.get<double>(std::max<int64_t>(nm, 1)) : nullptr;
+  double* dD = D ? S.get<double>(n) : nullptr;
+  int32_t* dlf = lev_fwd ? S.get<int32_t>(n) : nullptr;
+  int32_t* dlb = lev_bwd ? S.get<int32_t>(n) : nullptr;
+  if ((N && !dN) || (A && !dA) || (D && !dD) || (lev_fwd && !dlf) || (lev_bwd && !dlb))
+    return fail(c, VL_ERR_OOM, "workspace exhausted (export)");
+  export_kernel<<<(int)((n + 255) / 256), 256, 0, c->stream>>>((int)n, f->m, f->s2v, f->nbr, f->A64, f->D64,
+                                                               f->lev_fwd, f->lev_bwd, dN, dA, dD, dlf, dlb);
+  VL_CUDA(c, cudaGetLastError());
+  VL_TRY(stage_out(c, dN, N, nm));
+  VL_TRY(stage_out(c, dA, A, nm));
+  VL_TRY(stage_out(c, dD, D, n));
+  VL_TRY(stage_out(c, dlf, lev_fwd, n));
+  VL_TRY(stage_out(c, dlb, lev_bwd, n));
+  VL_CUDA(c, cudaStreamSynchronize(c->stream));
+  return VL_OK;
+}
+
+vl_status vl_factor_info(const vl_factor* f, int64_t* n, int* m, int* nf, int* nb) {
+  if (!f) return VL_ERR_INVALID_ARG;
+  if (n) *n = f->n;
+  if (m) *m = f->m;
+  if (nf) *nf = f->nlev_fwd;
+  if (nb) *nb = f->nlev_bwd;
+  return VL_OK;
+}
+
+void vl_factor_destroy(vl_factor* f) {
+  if (!f) return;
+  cudaStreamSynchronize(f->ctx->stream);
+  f->mem.free_all();
+  delete f;
+}
+
+// --------------------------------------------------------------------------- mode
+vl_status vl_find_mode(vl_factor* f, int lik, const double* y, const double* F, const vl_opts* opts,
+                       double* mode_out, vl_state** out) {
+  if (!f) return VL_ERR_INVALID_ARG;
+  Ctx* c = f->ctx;
+  if (!out || !y || (lik != VL_LIK_BERNOULLI_LOGIT && lik != VL_LIK_POISSON_LOG))
+    return fail(c, VL_ERR_INVALID_ARG, "vl_find_mode: invalid argument");
+  VL_TRY(check_opts(c, opts));
+  *out = nullptr;
+  const int n = (int)f->n;
+  cudaEventRecord(c->ev0, c->stream);
+  vl_state* st = new vl_state();
+  st->f = f;
+  st->ctx = c;
+  st->mem.ctx = c;
+  st->lik = lik;
+  auto bail = [&](vl_status s) {
+    st->mem.free_all();
+    delete st;
+    return s;
+  };
+  st->y = st->mem.get<double>(n);
+  st->F = st->mem.get<double>(n);
+  st->b = st->mem.get<double>(n);
+  st->W = st->mem.get<double>(n);
+  if (!st->y || !st->F || !st->b || !st->W) return bail(fail(c, VL_ERR_OOM, "workspace exhausted (state)"));
+  vl_status s;
+  {
+    Scratch S(c);
+    const double *dy, *dF = nullptr;
+    s = stage_in(c, S, y, n, &dy);
+    if (s == VL_OK && F) s = stage_in(c, S, F, n, &dF);
+    if (s != VL_OK) return bail(s);
+    to_storage_kernel<double><<<grid_for(c, n), 256, 0, c->stream>>>(n, 1, 1, f->s2u, dy, st->y);
+    if (dF)
+      to_storage_kernel<double><<<grid_for(c, n), 256, 0, c->stream>>>(n, 1, 1, f->s2u, dF, st->F);
+    else
+      cudaMemsetAsync(st->F, 0, sizeof(double) * n, c->stream);
+    cudaMemsetAsync(st->b, 0, sizeof(double) * n, c->stream);
+    if (cudaGetLastError() != cudaSuccess) return bail(fail(c, VL_ERR_CUDA, "staging y/F"));
+  }
+  // Newton iterations (Eq. newton)
+  Scratch S(c);
+  double* g = S.get<double>(n);
+  double* rhs = S.get<double>(n);
+  double* bn = S.get<double>(n);
+  if (!g || !rhs || !bn) return bail(fail(c, VL_ERR_OOM, "workspace exhausted (Newton)"));
+  const bool mixed = opts->precision == VL_FP32_REFINE;
+  Engine<double> E64(c);
+  Engine<float> E32(c);
+  vl_stats stats{};
+  double psi = 0.0;
+  int it = 0;
+  bool converged = false;
+  s = E64.init(f, 1, opts->precond, st->W, mixed ? 0 : opts->cg_max_iter + 1);
+  if (s != VL_OK) return bail(s);
+  s = psi_eval(st, E64, S, st->b, &psi, nullptr, nullptr);
+  if (s != VL_OK) return bail(s);
+  for (it = 1; it <= opts->newton_max_iter; ++it) {
+    lik_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, lik, st->y, st->F, st->b, st->W, g, rhs, nullptr);
+    diag_prep_kernel<double><<<grid_for(c, n), 256, 0, c->stream>>>(n, opts->precond, st->W, f->D64, E64.W, E64.Dinv,
+                                                                    E64.dsc, E64.Dt, E64.Winv);
+    if (mixed) {
+      if (!E32.W) {
+        s = E32.init(f, 1, opts->precond, st->W, opts->cg_max_iter + 1);
+        if (s != VL_OK) return bail(s);
+      } else {
+        diag_prep_kernel<float><<<grid_for(c, n), 256, 0, c->stream>>>(n, opts->precond, st->W, f->D64, E32.W,
+                                                                       E32.Dinv, E32.dsc, E32.Dt, E32.Winv);
+      }
+    }
+    if (cudaGetLastError() != cudaSuccess) return bail(fail(c, VL_ERR_CUDA, "Newton setup"));
+    s = solve1(st, opts, E64, mixed ? &E32 : nullptr, rhs, bn, &stats);
+    if (s != VL_OK) return bail(s);
+    double psi_new = 0.0;
+    s = psi_eval(st, E64, S, bn, &psi_new, nullptr, nullptr);
+    if (s != VL_OK) return bail(s);
+    for (int hlv = 0; hlv < 30 && psi_new < psi - 1e-12 * (1.0 + std::fabs(psi)); ++hlv) {
+      halve_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, st->b, bn);
+      s = psi_eval(st, E64, S, bn, &psi_new, nullptr, nullptr);
+      if (s != VL_OK) return bail(s);
+    }
+    double step = 0.0, bmax = 0.0;
+    s = dev_absmax(c, S, n, bn, st->b, &step, &bmax);
+    if (s != VL_OK) return bail(s);
+    cudaMemcpyAsync(st->b, bn, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream);
+    psi = psi_new;
+    if (!std::isfinite(psi)) return bail(fail(c, VL_ERR_NOT_CONVERGED, "Newton: non-finite objective"));
+    if (step <= opts->newton_tol * (1.0 + bmax)) {
+      converged = true;
+      break;
+    }
+  }
+  // W at the mode
+  lik_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, lik, st->y, st->F, st->b, st->W, nullptr, nullptr, nullptr);
+  if (cudaGetLastError() != cudaSuccess) return bail(fail(c, VL_ERR_CUDA, "lik"));
+  if (mode_out) {
+    double* mu = S.get<double>(n);
+    if (!mu) return bail(fail(c, VL_ERR_OOM, "workspace exhausted (mode out)"));
+    from_storage_kernel<double><<<grid_for(c, n), 256, 0, c->stream>>>(n, 1, 1, f->s2u, st->b, mu);
+    s = stage_out(c, mu, mode_out, n);
+    if (s != VL_OK) return bail(s);
+  }
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return bail(fail(c, VL_ERR_CUDA, "sync"));
+  *out = st;
+  if (!converged) return fail(c, VL_ERR_NOT_CONVERGED, "Newton reached newton_max_iter");
+  return VL_OK;
+}
+
+void vl_state_destroy(vl_state* s) {
+  if (!s) return;
+  cudaStreamSynchronize(s->ctx->stream);
+  s->mem.free_all();
+  delete s;
+}
+
+// --------------------------------------------------------------------------- L^VLA
+vl_status vl_log_marglik(vl_state* st, const vl_opts* o, double* lml, double* logdet, vl_stats* stats) {
+  if (!st) return VL_ERR_INVALID_ARG;
+  Ctx* c = st->ctx;
+  VL_TRY(check_opts(c, o));
+  if (!lml) return fail(c, VL_ERR_INVALID_ARG, "lml is NULL");
+  Factor* f = st->f;
+  const int n = (int)f->n, t = o->t;
+  VL_CUDA(c, cudaEventRecord(c->ev0, c->stream));
+  vl_stats loc{};
+  std::vector<double> g;
+  if (o->precision == VL_FP64)
+    VL_TRY(slq_run<double>(st, o, g, &loc));
+  else
+    VL_TRY(slq_run<float>(st, o, g, &loc));
+  double mean = 0.0;
+  for (double v : g) mean += v;
+  mean /= t;
+  double var = 0.0;
+  for (double v : g) var += (v - mean) * (v - mean);
+  const double se = t > 1 ? std::sqrt(var / (t - 1) / t) : 0.0;
+  Scratch S(c);
+  Engine<double> E1(c);
+  VL_TRY(E1.init(f, 1, o->precond, st->W, 0));
+  double logp = 0.0, quad = 0.0;
+  VL_TRY(psi_eval(st, E1, S, st->b, nullptr, &logp, &quad));
+  double sum_log_D = 0.0, sum_log_P = 0.0;
+  VL_TRY(dev_sum(c, S, n, 1, f->D64, nullptr, &sum_log_D));
+  if (o->precond == VL_PREC_VADU)
+    VL_TRY(dev_sum(c, S, n, 2, f->D64, st->W, &sum_log_P));   // log det P = log det(W + D^{-1})
+  else
+    sum_log_P = -sum_log_D;                                   // log det P = log det D^{-1}
+  const double ld = sum_log_D + sum_log_P + mean;             // Eq. logdetsplit
+  *lml = -logp + 0.5 * quad + 0.5 * ld;                       // Eq. VLA_loss
+  if (logdet) *logdet = ld;
+  st->h_gammas = g;
+  st->last_t = t;
+  VL_CUDA(c, cudaEventRecord(c->ev1, c->stream));
+  VL_CUDA(c, cudaEventSynchronize(c->ev1));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+  if (stats) {
+    *stats = loc;
+    stats->slq_mean = mean;
+    stats->slq_stderr = se;
+    stats->logdet = ld;
+    stats->ms_total = ms;
+  }
+  return VL_OK;
+}
+
+vl_status vl_slq_gammas(const vl_state* st, double* gammas, int t) {
+  if (!st) return VL_ERR_INVALID_ARG;
+  Ctx* c = st->ctx;
+  if (!gammas || t != st->last_t || (int)st->h_gammas.size() != t)
+    return fail(c, VL_ERR_STATE, "vl_slq_gammas: no SLQ result of that size");
+  if (is_device_ptr(gammas)) {
+    VL_CUDA(c, cudaMemcpyAsync(gammas, st->h_gammas.data(), sizeof(double) * t, cudaMemcpyHostToDevice, c->stream));
+    VL_CUDA(c, cudaStreamSynchronize(c->stream));
+  } else {
+    std::memcpy(gammas, st->h_gammas.data(), sizeof(double) * t);
+  }
+  return VL_OK;
+}
+
+// --------------------------------------------------------------------------- prediction
+vl_status vl_pred_var(vl_state* st, const double* test_locs, int64_t np, const double* Fp, const vl_opts* o,
+                      double* mean, double* var, vl_stats* stats) {
+  if (!st) return VL_ERR_INVALID_ARG;
+  Ctx* c = st->ctx;
+  VL_TRY(check_opts(c, o));
+  if (np < 0 || (np > 0 && !test_locs) || np > (1LL << 30)) return fail(c, VL_ERR_INVALID_ARG, "vl_pred_var: invalid argument");
+  if (np == 0) return VL_OK;
+  Factor* f = st->f;
+  const int m = f->m, n = (int)f->n;
+  VL_CUDA(c, cudaEventRecord(c->ev0, c->stream));
+  vl_stats loc{};
+  Scratch S(c);
+  const double *dq, *dF = nullptr;
+  VL_TRY(stage_in(c, S, test_locs, (size_t)np * 2, &dq));
+  if (Fp) VL_TRY(stage_in(c, S, Fp, (size_t)np, &dF));
+  const int64_t npm = np * (int64_t)std::max(m, 1);
+  int32_t* Np = S.get<int32_t>(npm);
+  double* Ap = S.get<double>(npm);
+  double* Dp = S.get<double>(np);
+  double* dmean = S.get<double>(np);
+  double* dvar = S.get<double>(np);
+  if (!Np || !Ap || !Dp || !dmean || !dvar) return fail(c, VL_ERR_OOM, "workspace exhausted (prediction)");
+  if (m > 0) {
+    VL_TRY(knn_cross_dev(c, f->locs_v, n, dq, np, m, Np));   // Vecchia indices, Section 4.1
+    translate_kernel<<<grid_for(c, npm), 256, 0, c->stream>>>(npm, f->v2s, Np);
+    VL_CUDA(c, cudaGetLastError());
+  }
+  VL_CUDA(c, cudaMemsetAsync(c->dstatus, 0, sizeof(DevStatus), c->stream));
+  VL_TRY(factor_rows(c, np, m, dq, f->locs_s, Np, f->cov, f->sigma2, f->rho, f->nugget, Ap, Dp, nullptr));
+  VL_TRY(check_dev_status(c, "prediction rows"));
+  VL_CUDA(c, cudaMemsetAsync(dvar, 0, sizeof(double) * np, c->stream));
+  const int pg = (int)((np * 32 + 255) / 256);
+  pred_kernel<double><<<pg, 256, 0, c->stream>>>((int)np, m, Np, Ap, Dp, dF, st->b, nullptr, 0, 1, dmean, nullptr);
+  VL_CUDA(c, cudaGetLastError());
+  if (var) {
+    for (int col0 = 0; col0 < o->s; col0 += 128) {
+      const int sc = std::min(128, o->s - col0);
+      Engine<double> E64(c);
+      VL_TRY(E64.init(f, sc, o->precond, st->W, o->precision == VL_FP64 ? o->cg_max_iter + 1 : 0));
+      double* U = S.get<double>((size_t)n * E64.ld);
+      if (!U) return fail(c, VL_ERR_OOM, "workspace exhausted (simulation)");
+      VL_TRY(sim_block(st, o, E64, sc, col0, U, &loc));
+      pred_kernel<double><<<pg, 256, 0, c->stream>>>((int)np, m, Np, Ap, Dp, nullptr, st->b, U, sc, E64.ld, nullptr,
+                                                      dvar);
+      VL_CUDA(c, cudaGetLastError());
+      VL_CUDA(c, cudaStreamSynchronize(c->stream));
+      c->arena.release(U);
+      S.blocks.erase(std::find(S.blocks.begin(), S.blocks.end(), (void*)U));
+    }
+    pred_finish_kernel<<<(int)((np + 255) / 256), 256, 0, c->stream>>>((int)np, Dp, 1.0 / o->s, dvar);
+    VL_CUDA(c, cudaGetLastError());
+  }
+  VL_TRY(stage_out(c, dmean, mean, np));
+  VL_TRY(stage_out(c, dvar, var, np));
+  VL_CUDA(c, cudaEventRecord(c->ev1, c->stream));
+  VL_CUDA(c, cudaEventSynchronize(c->ev1));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+  loc.ms_total = ms;
+  if (stats) *stats = loc;
+  return VL_OK;
+}
+
+// --------------------------------------------------------------------------- building blocks
+vl_status vl_apply(vl_state* st, int op, const double* X, int t, const vl_opts* o, double* Y) {
+  if (!st) return VL_ERR_INVALID_ARG;
+  Ctx* c = st->ctx;
+  VL_TRY(check_opts(c, o));
+  if (!X || !Y || t < 1 || t > 256) return fail(c, VL_ERR_INVALID_ARG, "vl_apply: invalid argument");
+  const int64_t nt = st->f->n * (int64_t)t;
+  Scratch S(c);
+  const double* dX;
+  VL_TRY(stage_in(c, S, X, nt, &dX));
+  double* dY = S.get<double>(nt);
+  if (!dY) return fail(c, VL_ERR_OOM, "workspace exhausted (vl_apply)");
+  if (o->precision == VL_FP64)
+    VL_TRY(apply_op<double>(st, op, dX, t, o, dY));
+  else
+    VL_TRY(apply_op<float>(st, op, dX, t, o, dY));
+  return stage_out(c, dY, Y, nt);
+}
+
+vl_status vl_pcg_solve(vl_state* st, const double* RHS, int t, const vl_opts* o, double* U, int lmax, double* T_diag,
+                       double* T_off, int* iters, double* relres) {
+  if (!st) return VL_ERR_INVALID_ARG;
+  Ctx* c = st->ctx;
+  VL_TRY(check_opts(c, o));
+  if (!RHS || !U || t < 1 || t > 256 || lmax < 0) return fail(c, VL_ERR_INVALID_ARG, "vl_pcg_solve: invalid argument");
+  const int64_t nt = st->f->n * (int64_t)t;
+  Scratch S(c);
+  const double* dR;
+  VL_TRY(stage_in(c, S, RHS, nt, &dR));
+  double* dU = S.get<double>(nt);
+  if (!dU) return fail(c, VL_ERR_OOM, "workspace exhausted (vl_pcg_solve)");
+  if (o->precision == VL_FP64)
+    VL_TRY(pcg_op<double>(st, dR, t, o, dU, lmax, T_diag, T_off, iters, relres));
+  else
+    VL_TRY(pcg_op<float>(st, dR, t, o, dU, lmax, T_diag, T_off, iters, relres));
+  return stage_out(c, dU, U, nt);
+}
+
+}  // extern "C"

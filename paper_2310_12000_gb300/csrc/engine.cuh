@@ -1,0 +1,297 @@
+// Krylov engine: the operators of Eqs. pcls1/pcls2 and the preconditioners of
+// Section 3.1 on a block of t right-hand sides, and the PCG loop of the appendix
+// algorithm with per-column freezing and Lanczos T extraction.
+#pragma once
+
+#include <vector>
+
+#include "kernels.cuh"
+
+namespace vl {
+
+struct Scratch {
+  Ctx* c = nullptr;
+  std::vector<void*> blocks;
+  explicit Scratch(Ctx* ctx) : c(ctx) {}
+  Scratch(const Scratch&) = delete;
+  template <typename T>
+  T* get(size_t count) {
+    void* p = c->arena.alloc(count * sizeof(T) + 16);
+    if (p) blocks.push_back(p);
+    return static_cast<T*>(p);
+  }
+  ~Scratch() {
+    for (void* p : blocks) c->arena.release(p);
+  }
+};
+
+// ----------------------------------------------------------------------------- small kernels
+template <typename T>
+__global__ void diag_prep_kernel(int n, int prec, const double* __restrict__ W, const double* __restrict__ D,
+                                 T* __restrict__ Wt, T* __restrict__ Dinv, T* __restrict__ dsc, T* __restrict__ Dt,
+                                 T* __restrict__ Winv) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+    const double w = W ? W[s] : 0.0, d = D[s];
+    Wt[s] = (T)w;
+    Dinv[s] = (T)(1.0 / d);
+    Dt[s] = (T)d;
+    // VADU: (W + D^{-1})^{-1}; LVA: D; LRAC uses W^{-1} and Sigma_tilde = B^{-1} D B^{-T}
+    dsc[s] = (prec == VL_PREC_VADU) ? (T)(1.0 / (w + 1.0 / d)) : (T)d;
+    Winv[s] = (T)(W ? 1.0 / w : 0.0);
+  }
+}
+
+template <typename T>
+__global__ void fill_kernel(int64_t total, T v, T* __restrict__ x) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
+    x[e] = v;
+}
+
+// Z = Y + w o X  (row scale)
+template <typename T>
+__global__ void add_diag_kernel(int n, int t, int ld, const T* __restrict__ Y, const T* __restrict__ w,
+                                const T* __restrict__ X, T* __restrict__ Z) {
+  const int64_t total = (int64_t)n * ld;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int s = (int)(e / ld), c = (int)(e % ld);
+    if (c < t) Z[e] = Y[e] + w[s] * X[e];
+  }
+}
+
+template <typename TI, typename TO>
+__global__ void convert_kernel(int64_t total, const TI* __restrict__ a, TO* __restrict__ b) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
+    b[e] = (TO)a[e];
+}
+
+// x += y (mixed types)
+template <typename TX, typename TY>
+__global__ void accumulate_kernel(int64_t total, TX* __restrict__ x, const TY* __restrict__ y) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
+    x[e] += (TX)y[e];
+}
+
+// r = b - r (in place on r holding A x)
+__global__ void residual_kernel(int64_t total, const double* __restrict__ b, double* __restrict__ r) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
+    r[e] = b[e] - r[e];
+}
+
+inline int grid_for(Ctx* c, int64_t work, int block = 256) {
+  int64_t g = (work + block - 1) / block;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(g, (int64_t)c->num_sms * 16));
+}
+
+// ----------------------------------------------------------------------------- engine
+template <typename T>
+struct Engine {
+  Ctx* c = nullptr;
+  Factor* f = nullptr;
+  int n = 0, m = 0, t = 0, ld = 0, prec = VL_PREC_VADU;
+  Scratch mem;
+  const T* Aval = nullptr;
+  const T* valT = nullptr;
+  T *W = nullptr, *Dinv = nullptr, *dsc = nullptr, *Dt = nullptr, *Winv = nullptr;
+  T *u = nullptr, *r = nullptr, *z = nullptr, *h = nullptr, *v = nullptr, *y = nullptr, *sv = nullptr;
+  double *partial = nullptr, *red = nullptr, *red2 = nullptr;
+  int nblk = 1, rpb = 1;
+  dim3 cb;
+  size_t csh = 0;
+  PcgScalars S{};
+  int lmax = 0;
+  int* d_count = nullptr;
+  int* h_count = nullptr;
+
+  explicit Engine(Ctx* ctx) : c(ctx), mem(ctx) {}
+
+  // Leading dimension: 1 for a single column, else a multiple of 8 (the same for
+  // float32 and float64 blocks, so mixed-precision refinement converts in place).
+  static int lead(int t_) { return t_ == 1 ? 1 : (t_ + 7) / 8 * 8; }
+
+  vl_status init(Factor* fac, int t_, int prec_, const double* W64, int lmax_) {
+    f = fac;
+    n = (int)f->n;
+    m = f->m;
+    t = t_;
+    prec = prec_;
+    if (t < 1 || t > 32 * kMaxChunks) return fail(c, VL_ERR_INVALID_ARG, "block width t must be in [1, 256]");
+    ld = lead(t);
+    Aval = std::is_same<T, double>::value ? (const T*)f->A64 : (const T*)f->A32;
+    valT = std::is_same<T, double>::value ? (const T*)f->valT64 : (const T*)f->valT32;
+    W = mem.get<T>(n);
+    Dinv = mem.get<T>(n);
+    dsc = mem.get<T>(n);
+    Dt = mem.get<T>(n);
+    Winv = mem.get<T>(n);
+    if (!W || !Dinv || !dsc || !Dt || !Winv) return fail(c, VL_ERR_OOM, "workspace exhausted (engine diagonals)");
+    diag_prep_kernel<T><<<grid_for(c, n), 256, 0, c->stream>>>(n, prec, W64, f->D64, W, Dinv, dsc, Dt, Winv);
+    VL_CUDA(c, cudaGetLastError());
+    const size_t vec = (size_t)n * ld;
+    T** vs[] = {&u, &r, &z, &h, &v, &y, &sv};
+    for (T** p : vs) {
+      *p = mem.get<T>(vec);
+      if (!*p) return fail(c, VL_ERR_OOM, "workspace exhausted (Krylov vectors)");
+      VL_CUDA(c, cudaMemsetAsync(*p, 0, sizeof(T) * vec, c->stream));
+    }
+    const int cx = (t == 1) ? 1 : (t + 31) / 32 * 32;
+    cb = dim3(cx, 256 / cx);
+    csh = sizeof(double) * 256;
+    const int64_t want = (n + (int64_t)cb.y * 8 - 1) / ((int64_t)cb.y * 8);
+    nblk = (int)std::max<int64_t>(1, std::min<int64_t>(want, 4LL * c->num_sms));
+    rpb = (n + nblk - 1) / nblk;
+    partial = mem.get<double>((size_t)nblk * t);
+    red = mem.get<double>(t);
+    red2 = mem.get<double>(t);
+    if (!partial || !red || !red2) return fail(c, VL_ERR_OOM, "workspace exhausted (reductions)");
+    lmax = lmax_;
+    if (lmax > 0) {
+      double** ds[] = {&S.rz, &S.rz0, &S.alpha, &S.beta, &S.alpha_prev, &S.beta_prev, &S.bnorm2, &S.rnorm2, &S.relres};
+      for (double** p : ds) {
+        *p = mem.get<double>(t);
+        if (!*p) return fail(c, VL_ERR_OOM, "workspace exhausted (PCG scalars)");
+      }
+      S.active = mem.get<int>(t);
+      S.stop = mem.get<int>(t);
+      S.iters = mem.get<int>(t);
+      S.Tdiag = mem.get<double>((size_t)t * lmax);
+      S.Toff = mem.get<double>((size_t)t * lmax);
+      d_count = mem.get<int>(1);
+      S.count = d_count;
+      S.lmax = lmax;
+      if (!S.active || !S.stop || !S.iters || !S.Tdiag || !S.Toff || !d_count)
+        return fail(c, VL_ERR_OOM, "workspace exhausted (PCG state)");
+      VL_CUDA(c, cudaMemsetAsync(S.Tdiag, 0, sizeof(double) * t * lmax, c->stream));
+      VL_CUDA(c, cudaMemsetAsync(S.Toff, 0, sizeof(double) * t * lmax, c->stream));
+    }
+    h_count = reinterpret_cast<int*>(c->pinned);
+    return VL_OK;
+  }
+
+  // ------------------------------------------------------------------ primitives
+  vl_status coldot(const T* X, const T* Y, const T* w, double* out) {
+    coldot_kernel<T><<<nblk, cb, csh, c->stream>>>(n, t, ld, rpb, X, Y, w, partial);
+    reduce_partials_kernel<<<1, 256, 0, c->stream>>>(nblk, t, partial, out);
+    VL_CUDA(c, cudaGetLastError());
+    return VL_OK;
+  }
+
+  int spmv_grid() const { return std::max(1, std::min((n + 7) / 8, c->num_sms * 8)); }
+
+  // Y = ys o (B X)
+  vl_status opB(const T* X, const T* ys, T* Yo) {
+    if (t == 1)
+      spmv_B_kernel<T, true><<<spmv_grid(), 256, 0, c->stream>>>(n, m, f->nbr, Aval, X, t, ld, ys, Yo);
+    else
+      spmv_B_kernel<T, false><<<spmv_grid(), 256, 0, c->stream>>>(n, m, f->nbr, Aval, X, t, ld, ys, Yo);
+    VL_CUDA(c, cudaGetLastError());
+    return VL_OK;
+  }
+  // Z = wx o X + B^T (ys o Y)
+  vl_status opBt(const T* Y, const T* ys, const T* X, const T* wx, T* Zo) {
+    if (t == 1)
+      spmv_Bt_kernel<T, true><<<spmv_grid(), 256, 0, c->stream>>>(n, f->rowptrT, f->colT, valT, Y, ys, X, wx, t, ld, Zo);
+    else
+      spmv_Bt_kernel<T, false><<<spmv_grid(), 256, 0, c->stream>>>(n, f->rowptrT, f->colT, valT, Y, ys, X, wx, t, ld,
+                                                                   Zo);
+    VL_CUDA(c, cudaGetLastError());
+    return VL_OK;
+  }
+  // A X = W X + B^T D^{-1} B X      (Eq. pcls1 operator)
+  vl_status opA(const T* X, T* Z) {
+    VL_TRY(opB(X, Dinv, y));
+    return opBt(y, nullptr, X, W, Z);
+  }
+
+  template <bool FWD, bool T1>
+  vl_status solve_launch(const T* rhs, const T* q, T* x) {
+    auto fn = sptrsv_kernel<T, FWD, T1>;
+    int nn = n, mm = m, tt = t, l = ld;
+    const int32_t* task = FWD ? f->task_fwd : f->task_bwd;
+    const int32_t* idx = FWD ? f->nbr : f->colT;
+    const T* val = FWD ? Aval : valT;
+    const int32_t* rp = FWD ? nullptr : f->rowptrT;
+    unsigned* ready = f->ready;
+    unsigned ep = ++c->epoch;
+    DevStatus* st = c->dstatus;
+    void* args[] = {&nn, &mm, &task, &idx, &val, &rp, &rhs, &q, &x, &tt, &l, &ready, &ep, &st};
+    const int grid = std::max(1, std::min(resident_blocks(c, (const void*)fn, 256, 0), (n + 7) / 8));
+    VL_CUDA(c, cudaLaunchCooperativeKernel((const void*)fn, grid, 256, args, 0, c->stream));
+    return VL_OK;
+  }
+  // x = B^{-1} (q o rhs)
+  vl_status solveB(const T* rhs, const T* q, T* x) {
+    return t == 1 ? solve_launch<true, true>(rhs, q, x) : solve_launch<true, false>(rhs, q, x);
+  }
+  // x = B^{-T} (q o rhs)
+  vl_status solveBt(const T* rhs, const T* q, T* x) {
+    return t == 1 ? solve_launch<false, true>(rhs, q, x) : solve_launch<false, false>(rhs, q, x);
+  }
+  // P^{-1} R for VADU / LVA: B^{-1} dsc B^{-T} R     (Section 3.1.1)
+  vl_status opPinv(const T* R, T* Zo) {
+    VL_TRY(solveBt(R, nullptr, sv));
+    return solveB(sv, dsc, Zo);
+  }
+  // Sigma_tilde X = B^{-1} D B^{-T} X
+  vl_status opSigma(const T* X, T* Zo) {
+    VL_TRY(solveBt(X, nullptr, sv));
+    return solveB(sv, Dt, Zo);
+  }
+  // (Sigma_tilde + W^{-1}) X       (Eq. pcls2 operator)
+  vl_status opA2(const T* X, T* Zo) {
+    VL_TRY(opSigma(X, y));
+    add_diag_kernel<T><<<grid_for(c, (int64_t)n * ld), 256, 0, c->stream>>>(n, t, ld, y, Winv, X, Zo);
+    VL_CUDA(c, cudaGetLastError());
+    return VL_OK;
+  }
+
+  // ------------------------------------------------------------------ PCG
+  // Solves A U = Bm column by column (u_0 = 0), stopping a column when
+  // ||r|| <= tol ||b||; records T (Lanczos) per column. Operators: form 1.
+  vl_status pcg(const T* Bm, T* U, double tol, int max_iter, int* iters_used) {
+    const int64_t vec = (int64_t)n * ld;
+    VL_CUDA(c, cudaMemsetAsync(U, 0, sizeof(T) * vec, c->stream));
+    VL_CUDA(c, cudaMemcpyAsync(r, Bm, sizeof(T) * vec, cudaMemcpyDeviceToDevice, c->stream));
+    VL_TRY(opPinv(r, z));
+    VL_CUDA(c, cudaMemcpyAsync(h, z, sizeof(T) * vec, cudaMemcpyDeviceToDevice, c->stream));
+    VL_TRY(coldot(r, z, nullptr, S.rz));
+    VL_TRY(coldot(Bm, Bm, nullptr, S.bnorm2));
+    pcg_init_kernel<<<1, 256, 0, c->stream>>>(t, S);
+    VL_CUDA(c, cudaGetLastError());
+    const double tol2 = tol * tol;
+    int it = 0;
+    for (; it < max_iter; ++it) {
+      VL_TRY(opA(h, v));
+      VL_TRY(coldot(h, v, nullptr, red));
+      pcg_alpha_kernel<<<1, 256, 0, c->stream>>>(t, red, S);
+      pcg_update1_kernel<T><<<nblk, cb, csh, c->stream>>>(n, t, ld, rpb, S.alpha, U, r, h, v, partial);
+      reduce_partials_kernel<<<1, 256, 0, c->stream>>>(nblk, t, partial, S.rnorm2);
+      pcg_stop_kernel<<<1, 256, 0, c->stream>>>(t, tol2, S);
+      VL_CUDA(c, cudaGetLastError());
+      VL_TRY(opPinv(r, z));
+      VL_TRY(coldot(r, z, nullptr, red2));
+      pcg_beta_kernel<<<1, 256, 0, c->stream>>>(t, red2, max_iter, S);
+      pcg_update2_kernel<T><<<grid_for(c, vec), 256, 0, c->stream>>>(vec, t, ld, S.beta, S.active, z, h);
+      VL_CUDA(c, cudaGetLastError());
+      VL_CUDA(c, cudaMemcpyAsync(h_count, d_count, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+      VL_TRY(check_dev_status(c, "PCG"));
+      if (*h_count == 0) {
+        ++it;
+        break;
+      }
+    }
+    if (iters_used) *iters_used = it;
+    return VL_OK;
+  }
+
+  // Host copies of per-column results.
+  vl_status column_stats(std::vector<int>& iters, std::vector<double>& relres) {
+    iters.resize(t);
+    relres.resize(t);
+    VL_CUDA(c, cudaMemcpyAsync(iters.data(), S.iters, sizeof(int) * t, cudaMemcpyDeviceToHost, c->stream));
+    VL_CUDA(c, cudaMemcpyAsync(relres.data(), S.relres, sizeof(double) * t, cudaMemcpyDeviceToHost, c->stream));
+    VL_CUDA(c, cudaStreamSynchronize(c->stream));
+    return VL_OK;
+  }
+};
+
+}  // namespace vl

@@ -1,0 +1,540 @@
+// Kernels of the Krylov hot path (Section 3): products with B, B^T and the
+// diagonals, sync-free level-ordered triangular solves with B and B^T, the
+// per-column PCG scalar recurrences with Lanczos T extraction (Appendix, PCG
+// algorithm), the SLQ quadrature e1^T log(T) e1, likelihood terms and probes.
+//
+// Right-hand-side blocks are n x ld row-major (ld >= t, the columns of one point
+// contiguous) in storage order. One warp owns one row; for t = 1 its lanes split
+// the row's m neighbours, otherwise they split the columns.
+#pragma once
+
+#include "vl_device.cuh"
+
+namespace vl {
+
+constexpr int kMaxChunks = 8;   // t <= 256 columns per block
+
+template <typename T>
+__device__ __forceinline__ T ldcg(const T* p) {
+  return __ldcg(p);
+}
+
+// ----------------------------------------------------------------------------- B X
+// Y_s = ys_s (X_s - sum_c A[s,c] X_{nbr[s,c]})   (ys == nullptr: 1)
+template <typename T, bool T1>
+__global__ void __launch_bounds__(256) spmv_B_kernel(int n, int m, const int32_t* __restrict__ nbr,
+                                                     const T* __restrict__ A, const T* __restrict__ X, int t, int ld,
+                                                     const T* __restrict__ ys, T* __restrict__ Y) {
+  const int lane = threadIdx.x & 31;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < n; s += nw) {
+    const T sc = ys ? ys[s] : T(1);
+    const int64_t base = (int64_t)s * m;
+    if (T1) {
+      T acc = T(0);
+      for (int c = lane; c < m; c += 32) {
+        const int j = nbr[base + c];
+        if (j >= 0) acc += A[base + c] * __ldg(&X[j]);
+      }
+      acc = warp_sum(acc);
+      if (lane == 0) Y[s] = sc * (X[s] - acc);
+    } else {
+      T acc[kMaxChunks];
+#pragma unroll
+      for (int k = 0; k < kMaxChunks; ++k) {
+        const int col = lane + 32 * k;
+        acc[k] = (col < t) ? __ldg(&X[(int64_t)s * ld + col]) : T(0);
+      }
+      for (int c0 = 0; c0 < m; c0 += 32) {
+        const int jl = (c0 + lane < m) ? nbr[base + c0 + lane] : -1;
+        const T al = (c0 + lane < m) ? A[base + c0 + lane] : T(0);
+        const int cnt = min(32, m - c0);
+        for (int q = 0; q < cnt; ++q) {
+          const int j = __shfl_sync(0xffffffffu, jl, q);
+          const T a = __shfl_sync(0xffffffffu, al, q);
+          if (j < 0) break;
+          const T* xr = X + (int64_t)j * ld;
+#pragma unroll
+          for (int k = 0; k < kMaxChunks; ++k) {
+            const int col = lane + 32 * k;
+            if (col < t) acc[k] -= a * __ldg(&xr[col]);
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < kMaxChunks; ++k) {
+        const int col = lane + 32 * k;
+        if (col < t) Y[(int64_t)s * ld + col] = sc * acc[k];
+      }
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------- W X + B^T Y
+// Z_s = wx_s X_s + ys_s Y_s - sum_{e in row s of B^T} valT[e] ys_{i} Y_{i},  i = colT[e]
+// (X == nullptr: no diagonal term; ys == nullptr: 1)
+template <typename T, bool T1>
+__global__ void __launch_bounds__(256) spmv_Bt_kernel(int n, const int32_t* __restrict__ rowptrT,
+                                                      const int32_t* __restrict__ colT, const T* __restrict__ valT,
+                                                      const T* __restrict__ Y, const T* __restrict__ ys,
+                                                      const T* __restrict__ X, const T* __restrict__ wx, int t, int ld,
+                                                      T* __restrict__ Z) {
+  const int lane = threadIdx.x & 31;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < n; s += nw) {
+    const int beg = rowptrT[s], end = rowptrT[s + 1];
+    const T yss = ys ? ys[s] : T(1);
+    const T wxs = X ? wx[s] : T(0);
+    if (T1) {
+      T acc = T(0);
+      for (int e = beg + lane; e < end; e += 32) {
+        const int i = colT[e];
+        acc += valT[e] * (ys ? ys[i] : T(1)) * __ldg(&Y[i]);
+      }
+      acc = warp_sum(acc);
+      if (lane == 0) Z[s] = (X ? wxs * X[s] : T(0)) + yss * Y[s] - acc;
+    } else {
+      T acc[kMaxChunks];
+#pragma unroll
+      for (int k = 0; k < kMaxChunks; ++k) {
+        const int col = lane + 32 * k;
+        T v = T(0);
+        if (col < t) {
+          v = yss * __ldg(&Y[(int64_t)s * ld + col]);
+          if (X) v += wxs * __ldg(&X[(int64_t)s * ld + col]);
+        }
+        acc[k] = v;
+      }
+      for (int e0 = beg; e0 < end; e0 += 32) {
+        const int cnt = min(32, end - e0);
+        int il = 0;
+        T al = T(0);
+        if (lane < cnt) {
+          il = colT[e0 + lane];
+          al = valT[e0 + lane] * (ys ? ys[il] : T(1));
+        }
+        for (int q = 0; q < cnt; ++q) {
+          const int i = __shfl_sync(0xffffffffu, il, q);
+          const T a = __shfl_sync(0xffffffffu, al, q);
+          const T* yr = Y + (int64_t)i * ld;
+#pragma unroll
+          for (int k = 0; k < kMaxChunks; ++k) {
+            const int col = lane + 32 * k;
+            if (col < t) acc[k] -= a * __ldg(&yr[col]);
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < kMaxChunks; ++k) {
+        const int col = lane + 32 * k;
+        if (col < t) Z[(int64_t)s * ld + col] = acc[k];
+      }
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------- solves
+// Sync-free level-ordered triangular solve, one row per warp, rows taken in the
+// topological task order (w, w + W, ...). Every warp is resident (cooperative
+// launch), so the earliest unfinished task always has its inputs and the walk
+// cannot deadlock; each wait is bounded and a timeout aborts the whole solve.
+//   FWD (B^{-1}):   x_s = q_s r_s + sum_{c} A[s,c] x_{nbr[s,c]}
+//   BWD (B^{-T}):   x_s = q_s r_s + sum_{e in row s of B^T} valT[e] x_{colT[e]}
+// Values produced in this launch are read through L2 (ld.global.cg).
+template <typename T, bool FWD, bool T1>
+__global__ void __launch_bounds__(256) sptrsv_kernel(int n, int m, const int32_t* __restrict__ task,
+                                                     const int32_t* __restrict__ idx, const T* __restrict__ val,
+                                                     const int32_t* __restrict__ rowptr, const T* __restrict__ rhs,
+                                                     const T* __restrict__ q, T* x, int t, int ld, unsigned* ready,
+                                                     unsigned epoch, DevStatus* st) {
+  const int lane = threadIdx.x & 31;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < n; p += nw) {
+    const int s = task[p];
+    int beg, end;
+    if (FWD) {
+      beg = s * m;
+      end = beg + m;
+    } else {
+      beg = rowptr[s];
+      end = rowptr[s + 1];
+    }
+    for (int e = beg + lane; e < end; e += 32) {
+      const int j = idx[e];
+      if (j >= 0) bounded_wait([&] { return ld_acquire(&ready[j]) == epoch; }, st, s);
+    }
+    __syncwarp();
+    const T qs = q ? q[s] : T(1);
+    if (T1) {
+      T acc = T(0);
+      for (int e = beg + lane; e < end; e += 32) {
+        const int j = idx[e];
+        if (j >= 0) acc += val[e] * ldcg(&x[j]);
+      }
+      acc = warp_sum(acc);
+      if (lane == 0) x[s] = qs * rhs[s] + acc;
+    } else {
+      T acc[kMaxChunks];
+#pragma unroll
+      for (int k = 0; k < kMaxChunks; ++k) {
+        const int col = lane + 32 * k;
+        acc[k] = (col < t) ? qs * rhs[(int64_t)s * ld + col] : T(0);
+      }
+      for (int e0 = beg; e0 < end; e0 += 32) {
+        const int cnt = min(32, end - e0);
+        const int jl = lane < cnt ? idx[e0 + lane] : -1;
+        const T al = lane < cnt ? val[e0 + lane] : T(0);
+        for (int qq = 0; qq < cnt; ++qq) {
+          const int j = __shfl_sync(0xffffffffu, jl, qq);
+          const T a = __shfl_sync(0xffffffffu, al, qq);
+          if (j < 0) continue;
+          const T* xr = x + (int64_t)j * ld;
+#pragma unroll
+          for (int k = 0; k < kMaxChunks; ++k) {
+            const int col = lane + 32 * k;
+            if (col < t) acc[k] += a * ldcg(&xr[col]);
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < kMaxChunks; ++k) {
+        const int col = lane + 32 * k;
+        if (col < t) x[(int64_t)s * ld + col] = acc[k];
+      }
+    }
+    __syncwarp();
+    if (lane == 0) {
+      __threadfence();
+      st_release(&ready[s], epoch);
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------- column reductions
+// Block layout for column sweeps: blockDim = (cx, 256 / cx) with cx = 1 for t == 1
+// and a multiple of 32 covering t otherwise. Block b owns rows [b*rpb, (b+1)*rpb).
+// partial[b * t + c] = sum over its rows of w_s X[s,c] Y[s,c] (w == nullptr: 1),
+// accumulated in Acc (float64 for float64 data; float32 per thread then float64).
+template <typename T>
+__global__ void coldot_kernel(int n, int t, int ld, int rpb, const T* __restrict__ X, const T* __restrict__ Y,
+                              const T* __restrict__ w, double* __restrict__ partial) {
+  const int cx = blockDim.x, ry = blockDim.y;
+  const int c = threadIdx.x;
+  const int r0 = blockIdx.x * rpb, r1 = min(n, r0 + rpb);
+  double acc = 0.0;
+  if (c < t) {
+    T a = T(0);
+    int cntf = 0;
+    for (int s = r0 + threadIdx.y; s < r1; s += ry) {
+      const int64_t o = (int64_t)s * ld + c;
+      T v = X[o] * Y[o];
+      if (w) v *= w[s];
+      a += v;
+      if (++cntf == 16) {   // flush the working-precision partial every 16 rows
+        acc += (double)a;
+        a = T(0);
+        cntf = 0;
+      }
+    }
+    acc += (double)a;
+  }
+  extern __shared__ double sh[];
+  sh[threadIdx.y * cx + c] = acc;
+  __syncthreads();
+  if (threadIdx.y == 0 && c < t) {
+    double sum = 0.0;
+    for (int y = 0; y < ry; ++y) sum += sh[y * cx + c];
+    partial[(int64_t)blockIdx.x * t + c] = sum;
+  }
+}
+
+// out[c] = sum_b partial[b * t + c] (fixed order)
+__global__ void reduce_partials_kernel(int nblk, int t, const double* __restrict__ partial, double* __restrict__ out) {
+  for (int c = threadIdx.x; c < t; c += blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += partial[(int64_t)b * t + c];
+    out[c] = s;
+  }
+}
+
+// ----------------------------------------------------------------------------- PCG scalars
+struct PcgScalars {
+  double* rz;          // r_l^T z_l
+  double* rz0;         // r_0^T z_0 = ||P^{-1/2} b||^2
+  double* alpha;       // alpha_{l+1}
+  double* beta;        // beta_{l+1}
+  double* alpha_prev;  // alpha_l   (alpha_0 = 1)
+  double* beta_prev;   // beta_l    (beta_0 = 0)
+  double* bnorm2;
+  double* rnorm2;
+  double* relres;
+  int* active;
+  int* stop;
+  int* iters;
+  double* Tdiag;       // t x lmax
+  double* Toff;        // t x lmax
+  int lmax;
+  int* count;          // number of active columns after the update
+};
+
+// r_0 = b, z_0 = P^{-1} r_0: set rz, rz0, bnorm2 (already reduced into rz/bnorm2) and flags.
+__global__ void pcg_init_kernel(int t, PcgScalars S) {
+  for (int c = threadIdx.x; c < t; c += blockDim.x) {
+    S.rz0[c] = S.rz[c];
+    S.alpha_prev[c] = 1.0;
+    S.beta_prev[c] = 0.0;
+    S.iters[c] = 0;
+    S.stop[c] = 0;
+    S.alpha[c] = 0.0;
+    S.beta[c] = 0.0;
+    const bool act = S.bnorm2[c] > 0.0 && S.rz[c] > 0.0;
+    S.active[c] = act ? 1 : 0;
+    S.relres[c] = act ? 1.0 : 0.0;
+  }
+}
+
+// alpha_{l+1} = r_l^T z_l / h_l^T v_l for active columns (0 otherwise).
+__global__ void pcg_alpha_kernel(int t, const double* __restrict__ hv, PcgScalars S) {
+  for (int c = threadIdx.x; c < t; c += blockDim.x) {
+    const double a = S.active[c] ? S.rz[c] / hv[c] : 0.0;
+    S.alpha[c] = (S.active[c] && isfinite(a)) ? a : 0.0;
+  }
+}
+
+// early-stopping test on ||r_{l+1}|| (before the T update, as in the algorithm).
+__global__ void pcg_stop_kernel(int t, double tol2, PcgScalars S) {
+  for (int c = threadIdx.x; c < t; c += blockDim.x) {
+    if (!S.active[c]) continue;
+    const double rn = S.rnorm2[c];
+    S.relres[c] = sqrt(rn / S.bnorm2[c]);
+    S.stop[c] = (rn <= tol2 * S.bnorm2[c]) ? 1 : 0;
+  }
+}
+
+// beta_{l+1}, the T update, and the freeze of converged columns.
+__global__ void pcg_beta_kernel(int t, const double* __restrict__ rz_new, int max_iter, PcgScalars S) {
+  __shared__ int cnt;
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  int local = 0;
+  for (int c = threadIdx.x; c < t; c += blockDim.x) {
+    if (!S.active[c]) continue;
+    const int l = S.iters[c];
+    const double a = S.alpha[c], ap = S.alpha_prev[c], bp = S.beta_prev[c];
+    const double b = rz_new[c] / S.rz[c];
+    if (l < S.lmax) {
+      S.Tdiag[(int64_t)c * S.lmax + l] = 1.0 / a + bp / ap;
+      if (l > 0) S.Toff[(int64_t)c * S.lmax + l - 1] = sqrt(bp) / ap;
+    }
+    S.beta[c] = b;
+    S.alpha_prev[c] = a;
+    S.beta_prev[c] = b;
+    S.rz[c] = rz_new[c];
+    S.iters[c] = l + 1;
+    if (S.stop[c] || l + 1 >= max_iter || l + 1 >= S.lmax || !(a > 0.0) || !isfinite(b)) {
+      S.active[c] = 0;
+    } else {
+      ++local;
+    }
+  }
+  atomicAdd(&cnt, local);
+  __syncthreads();
+  if (threadIdx.x == 0) *S.count = cnt;
+}
+
+// u += alpha h, r -= alpha v  (alpha = 0 for frozen columns); fused ||r||^2 partials.
+template <typename T>
+__global__ void pcg_update1_kernel(int n, int t, int ld, int rpb, const double* __restrict__ alpha, T* __restrict__ u,
+                                   T* __restrict__ r, const T* __restrict__ h, const T* __restrict__ v,
+                                   double* __restrict__ partial) {
+  const int cx = blockDim.x, ry = blockDim.y;
+  const int c = threadIdx.x;
+  const int r0 = blockIdx.x * rpb, r1 = min(n, r0 + rpb);
+  double acc = 0.0;
+  if (c < t) {
+    const T a = (T)alpha[c];
+    T part = T(0);
+    int cntf = 0;
+    for (int s = r0 + threadIdx.y; s < r1; s += ry) {
+      const int64_t o = (int64_t)s * ld + c;
+      if (a != T(0)) {
+        u[o] += a * h[o];
+        r[o] -= a * v[o];
+      }
+      const T rv = r[o];
+      part += rv * rv;
+      if (++cntf == 16) {
+        acc += (double)part;
+        part = T(0);
+        cntf = 0;
+      }
+    }
+    acc += (double)part;
+  }
+  extern __shared__ double sh[];
+  sh[threadIdx.y * cx + c] = acc;
+  __syncthreads();
+  if (threadIdx.y == 0 && c < t) {
+    double sum = 0.0;
+    for (int y = 0; y < ry; ++y) sum += sh[y * cx + c];
+    partial[(int64_t)blockIdx.x * t + c] = sum;
+  }
+}
+
+// h = z + beta h for active columns.
+template <typename T>
+__global__ void pcg_update2_kernel(int64_t total, int t, int ld, const double* __restrict__ beta,
+                                   const int* __restrict__ active, const T* __restrict__ z, T* __restrict__ h) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e % ld);
+    if (c < t && active[c]) h[e] = z[e] + (T)beta[c] * h[e];
+  }
+}
+
+// ----------------------------------------------------------------------------- SLQ quadrature
+// gamma_c = w_c * e1^T log(T_c) e1 = w_c * sum_j q_{1j}^2 log(theta_j) for the
+// symmetric tridiagonal T_c (size iters[c]), by implicit symmetric QR steps with
+// Wilkinson shifts (Golub & Van Loan, Sec. 8.3) while rotating only the first
+// row of the eigenvector matrix. One thread per column, float64.
+__global__ void slq_quad_kernel(int t, int lmax, const double* __restrict__ Tdiag, const double* __restrict__ Toff,
+                                const int* __restrict__ iters, const double* __restrict__ w,
+                                double* __restrict__ work, double* __restrict__ gamma, int* __restrict__ bad) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= t) return;
+  const int l = iters[c];
+  double* d = work + (int64_t)c * 3 * lmax;
+  double* e = d + lmax;
+  double* z = e + lmax;
+  for (int i = 0; i < l; ++i) {
+    d[i] = Tdiag[(int64_t)c * lmax + i];
+    e[i] = (i + 1 < l) ? Toff[(int64_t)c * lmax + i] : 0.0;
+    z[i] = (i == 0) ? 1.0 : 0.0;
+  }
+  const double eps = 2.220446049250313e-16;
+  int hi = l - 1;
+  int guard = 0;
+  while (hi > 0 && guard < 60 * l + 60) {
+    if (fabs(e[hi - 1]) <= eps * (fabs(d[hi - 1]) + fabs(d[hi]))) {
+      e[hi - 1] = 0.0;
+      --hi;
+      continue;
+    }
+    int lo = hi - 1;
+    while (lo > 0 && fabs(e[lo - 1]) > eps * (fabs(d[lo - 1]) + fabs(d[lo]))) --lo;
+    if (lo > 0) e[lo - 1] = 0.0;
+    const double dd = 0.5 * (d[hi - 1] - d[hi]);
+    const double ee = e[hi - 1];
+    const double sg = dd >= 0.0 ? 1.0 : -1.0;
+    const double mu = d[hi] - ee * ee / (dd + sg * hypot(dd, ee));
+    double x = d[lo] - mu, y = e[lo];
+    for (int k = lo; k < hi; ++k) {
+      const double rr = hypot(x, y);
+      double cs = 1.0, sn = 0.0;
+      if (rr > 0.0) {
+        cs = x / rr;
+        sn = y / rr;
+      }
+      if (k > lo) e[k - 1] = rr;
+      const double dk = d[k], dk1 = d[k + 1], ek = e[k];
+      d[k] = cs * cs * dk + 2.0 * cs * sn * ek + sn * sn * dk1;
+      d[k + 1] = sn * sn * dk - 2.0 * cs * sn * ek + cs * cs * dk1;
+      e[k] = cs * sn * (dk1 - dk) + (cs * cs - sn * sn) * ek;
+      if (k + 1 < hi) {
+        y = sn * e[k + 1];
+        e[k + 1] = cs * e[k + 1];
+        x = e[k];
+      }
+      const double zk = z[k], zk1 = z[k + 1];
+      z[k] = cs * zk + sn * zk1;
+      z[k + 1] = -sn * zk + cs * zk1;
+    }
+    ++guard;
+  }
+  double g = 0.0;
+  int nb = 0;
+  for (int i = 0; i < l; ++i) {
+    if (!(d[i] > 0.0)) ++nb;
+    g += z[i] * z[i] * log(d[i]);
+  }
+  if (hi > 0 || nb) atomicAdd(bad, 1);
+  gamma[c] = (l > 0) ? w[c] * g : 0.0;
+}
+
+// ----------------------------------------------------------------------------- likelihood
+// mu = F + b; g = d log p / d mu; W = -d^2 log p / d mu^2; logp; rhs = W b + g.
+__device__ __forceinline__ void lik_terms(int lik, double y, double mu, double& lp, double& g, double& W) {
+  if (lik == VL_LIK_BERNOULLI_LOGIT) {
+    const double p = 1.0 / (1.0 + exp(-mu));
+    g = y - p;
+    W = p * (1.0 - p);
+    const double sp = fmax(mu, 0.0) + log1p(exp(-fabs(mu)));   // log(1 + e^mu)
+    lp = y * mu - sp;
+  } else {
+    const double lam = exp(mu);
+    g = y - lam;
+    W = lam;
+    lp = y * mu - lam - lgamma(y + 1.0);
+  }
+}
+
+__global__ void lik_kernel(int n, int lik, const double* __restrict__ y, const double* __restrict__ F,
+                           const double* __restrict__ b, double* __restrict__ W, double* __restrict__ g,
+                           double* __restrict__ rhs, double* __restrict__ logp) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+    double lp, gg, ww;
+    lik_terms(lik, y[s], F[s] + b[s], lp, gg, ww);
+    if (W) W[s] = ww;
+    if (g) g[s] = gg;
+    if (rhs) rhs[s] = ww * b[s] + gg;
+    if (logp) logp[s] = lp;
+  }
+}
+
+// ----------------------------------------------------------------------------- probes
+// Rademacher r[s, j] = 1 - 2 * bit j of Philox4x64-10(counter = (p, j / 256, stream, 0),
+// key = (seed, 0)), p = the caller index of storage row s; bit j % 256 is bit
+// (j % 64) of output word (j % 256) / 64.
+template <typename T>
+__global__ void rademacher_kernel(int n, int t, int ld, const int32_t* __restrict__ s2u, uint64_t seed, int stream,
+                                  int64_t idx_offset, T* __restrict__ R) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const uint64_t p = s2u ? (uint64_t)s2u[s] : (uint64_t)(s + idx_offset);
+  for (int blk = 0; blk * 256 < ld; ++blk) {
+    const Philox4 w = philox4x64_10(p, (uint64_t)blk, (uint64_t)stream, 0, seed, 0);
+    for (int j = blk * 256; j < min(ld, blk * 256 + 256); ++j) {
+      const int bit = j - blk * 256;
+      const uint64_t v = (w.v[bit >> 6] >> (bit & 63)) & 1ULL;
+      R[(int64_t)s * ld + j] = (j < t) ? (T)(1.0 - 2.0 * (double)v) : T(0);
+    }
+  }
+}
+
+// Gaussian z[s, j] by Box-Muller: block j / 4, words (2q, 2q + 1), q = (j % 4) / 2:
+// u1 = ((w >> 11) + 1) 2^-53, u2 = (w >> 11) 2^-53, sqrt(-2 ln u1) cos / sin (2 pi u2).
+// Fills columns j = col0 .. col0 + t - 1 into Z[s, j - col0]; padding columns get 0.
+__global__ void gaussian_kernel(int n, int t, int ld, int col0, const int32_t* __restrict__ s2u, uint64_t seed,
+                                int stream, double* __restrict__ Z) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const uint64_t p = (uint64_t)s2u[s];
+  const double two_m53 = 1.1102230246251565e-16;
+  const double two_pi = 6.283185307179586;
+  for (int k = t; k < ld; ++k) Z[(int64_t)s * ld + k] = 0.0;
+  if (t <= 0) return;
+  for (int blk = col0 / 4; blk <= (col0 + t - 1) / 4; ++blk) {
+    const Philox4 w = philox4x64_10(p, (uint64_t)blk, (uint64_t)stream, 0, seed, 0);
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const double u1 = ((double)(w.v[2 * q] >> 11) + 1.0) * two_m53;
+      const double u2 = (double)(w.v[2 * q + 1] >> 11) * two_m53;
+      const double rad = sqrt(-2.0 * log(u1));
+      const double ang = two_pi * u2;
+      const int j0 = blk * 4 + 2 * q;
+      if (j0 >= col0 && j0 < col0 + t) Z[(int64_t)s * ld + (j0 - col0)] = rad * cos(ang);
+      if (j0 + 1 >= col0 && j0 + 1 < col0 + t) Z[(int64_t)s * ld + (j0 + 1 - col0)] = rad * sin(ang);
+    }
+  }
+}
+
+}  // namespace vl

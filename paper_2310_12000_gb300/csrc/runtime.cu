@@ -1,0 +1,99 @@
+// Runtime pieces of libvl: workspace arena, error plumbing, occupancy queries.
+#include <cstdio>
+#include <cstring>
+
+#include "vl_internal.h"
+
+namespace vl {
+
+static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+void Arena::init(char* base, size_t size) {
+  base_ = base;
+  size_ = size;
+  free_.clear();
+  used_.clear();
+  in_use_ = peak_ = 0;
+  free_[0] = size;
+}
+
+void* Arena::alloc(size_t bytes) {
+  bytes = align_up(bytes ? bytes : 1, 256);
+  for (auto it = free_.begin(); it != free_.end(); ++it) {
+    if (it->second >= bytes) {
+      size_t off = it->first, sz = it->second;
+      free_.erase(it);
+      if (sz > bytes) free_[off + bytes] = sz - bytes;
+      used_[off] = bytes;
+      in_use_ += bytes;
+      if (in_use_ > peak_) peak_ = in_use_;
+      return base_ + off;
+    }
+  }
+  return nullptr;
+}
+
+void Arena::release(void* p) {
+  if (!p) return;
+  size_t off = static_cast<char*>(p) - base_;
+  auto u = used_.find(off);
+  if (u == used_.end()) return;
+  size_t sz = u->second;
+  used_.erase(u);
+  in_use_ -= sz;
+  auto nx = free_.lower_bound(off);
+  if (nx != free_.end() && nx->first == off + sz) {   // merge with the next block
+    sz += nx->second;
+    free_.erase(nx);
+  }
+  auto pv = free_.lower_bound(off);
+  if (pv != free_.begin()) {
+    --pv;
+    if (pv->first + pv->second == off) {   // merge with the previous block
+      pv->second += sz;
+      return;
+    }
+  }
+  free_[off] = sz;
+}
+
+vl_status cuda_fail(Ctx* c, cudaError_t e, const char* what) {
+  if (c) {
+    char buf[512];
+    snprintf(buf, sizeof buf, "CUDA error in %s: %s", what, cudaGetErrorString(e));
+    c->last_error = buf;
+  }
+  return VL_ERR_CUDA;
+}
+
+vl_status fail(Ctx* c, vl_status s, const std::string& msg) {
+  if (c) c->last_error = msg;
+  return s;
+}
+
+vl_status check_dev_status(Ctx* c, const char* what) {
+  VL_CUDA(c, cudaMemcpyAsync(c->hstatus, c->dstatus, sizeof(DevStatus), cudaMemcpyDeviceToHost, c->stream));
+  VL_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (c->hstatus->code != 0) {
+    const int code = c->hstatus->code, row = c->hstatus->row;
+    VL_CUDA(c, cudaMemsetAsync(c->dstatus, 0, sizeof(DevStatus), c->stream));
+    VL_CUDA(c, cudaStreamSynchronize(c->stream));
+    char buf[256];
+    if (code == VL_ERR_NOT_SPD)
+      snprintf(buf, sizeof buf, "%s: NOT_SPD at row %d", what, row);
+    else if (code == VL_ERR_TIMEOUT)
+      snprintf(buf, sizeof buf, "%s: bounded device wait timed out at row %d", what, row);
+    else
+      snprintf(buf, sizeof buf, "%s: device error %d at row %d", what, code, row);
+    return fail(c, (vl_status)code, buf);
+  }
+  return VL_OK;
+}
+
+int resident_blocks(Ctx* c, const void* kernel, int block, size_t smem) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem) != cudaSuccess) per_sm = 1;
+  return std::max(1, per_sm) * c->num_sms;
+}
+
+}  // namespace vl

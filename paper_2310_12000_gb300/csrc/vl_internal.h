@@ -1,0 +1,160 @@
+// Internal declarations of libvl: context, workspace arena, handles, launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <map>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/vl.h"
+
+namespace vl {
+
+// ----------------------------------------------------------------------------- status
+// Device-side status block: the first error code/row wins; `abort` tells every
+// bounded wait in a running kernel to give up at once.
+struct DevStatus {
+  int code;
+  int row;
+  int abort;
+  int pad;
+};
+
+// ----------------------------------------------------------------------------- arena
+// First-fit sub-allocator over one device buffer (the caller's workspace).
+class Arena {
+ public:
+  void init(char* base, size_t size);
+  void* alloc(size_t bytes);   // nullptr when exhausted
+  void release(void* p);
+  size_t in_use() const { return in_use_; }
+  size_t peak() const { return peak_; }
+  size_t size() const { return size_; }
+
+ private:
+  char* base_ = nullptr;
+  size_t size_ = 0, in_use_ = 0, peak_ = 0;
+  std::map<size_t, size_t> free_;            // offset -> bytes
+  std::unordered_map<size_t, size_t> used_;  // offset -> bytes
+};
+
+struct Ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool owns_ws = false;
+  char* ws = nullptr;
+  Arena arena;
+  std::string last_error;
+  DevStatus* dstatus = nullptr;   // device
+  DevStatus* hstatus = nullptr;   // pinned host mirror
+  char* pinned = nullptr;         // pinned scratch for small read-backs
+  size_t pinned_bytes = 0;
+  int num_sms = 0;
+  unsigned epoch = 0;             // sync-free solve flag generation
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+// RAII list of arena blocks owned by a handle.
+struct Owned {
+  Ctx* ctx = nullptr;
+  std::vector<void*> blocks;
+  template <typename T>
+  T* get(size_t count) {
+    void* p = ctx->arena.alloc(count * sizeof(T) + 16);
+    if (p) blocks.push_back(p);
+    return static_cast<T*>(p);
+  }
+  void free_all() {
+    for (void* p : blocks) ctx->arena.release(p);
+    blocks.clear();
+  }
+};
+
+struct Factor {
+  Ctx* ctx = nullptr;
+  Owned mem;
+  int64_t n = 0;
+  int m = 0;
+  int cov = 0;
+  double sigma2 = 1.0, rho = 1.0, nugget = 0.0;
+  int64_t nnz = 0;            // off-diagonal entries of B
+  int nlev_fwd = 0, nlev_bwd = 0;
+  // storage order = Morton order of the locations
+  double* locs_s = nullptr;   // n x 2
+  double* locs_v = nullptr;   // n x 2, Vecchia order
+  int32_t* s2v = nullptr;     // storage -> Vecchia index
+  int32_t* v2s = nullptr;
+  int32_t* s2u = nullptr;     // storage -> caller index
+  int32_t* u2s = nullptr;
+  int32_t* nbr = nullptr;     // n x m storage indices, -1 padding (ELL of B)
+  double* A64 = nullptr;      // n x m kriging weights, B_{i,N(i)} = -A
+  float* A32 = nullptr;
+  double* D64 = nullptr;      // n
+  int32_t* rowptrT = nullptr; // n + 1  (CSR of the transpose pattern)
+  int32_t* colT = nullptr;    // nnz: storage row i listing j
+  int32_t* permT = nullptr;   // nnz: ELL flat index of the entry
+  double* valT64 = nullptr;   // nnz
+  float* valT32 = nullptr;
+  int32_t* lev_fwd = nullptr; // n (storage order)
+  int32_t* lev_bwd = nullptr;
+  int32_t* task_fwd = nullptr;  // storage rows sorted by (lev_fwd, s)
+  int32_t* task_bwd = nullptr;
+  unsigned* ready = nullptr;    // n flags for the sync-free solves
+};
+
+struct State {
+  Factor* f = nullptr;
+  Ctx* ctx = nullptr;
+  Owned mem;
+  int lik = 0;
+  double* y = nullptr;     // storage order
+  double* F = nullptr;
+  double* b = nullptr;     // mode
+  double* W = nullptr;
+  int last_t = 0;
+  std::vector<double> h_gammas;   // last SLQ gammas
+};
+
+// ----------------------------------------------------------------------------- helpers
+vl_status cuda_fail(Ctx* c, cudaError_t e, const char* what);
+vl_status fail(Ctx* c, vl_status s, const std::string& msg);
+vl_status check_dev_status(Ctx* c, const char* what);   // syncs the stream
+int resident_blocks(Ctx* c, const void* kernel, int block, size_t smem);
+
+#define VL_CUDA(ctx, call)                                                 \
+  do {                                                                     \
+    cudaError_t e_ = (call);                                               \
+    if (e_ != cudaSuccess) return ::vl::cuda_fail((ctx), e_, #call);       \
+  } while (0)
+
+#define VL_TRY(call)                    \
+  do {                                  \
+    vl_status s_ = (call);              \
+    if (s_ != VL_OK) return s_;         \
+  } while (0)
+
+// ----------------------------------------------------------------------------- launchers
+// knn.cu
+vl_status knn_prev_dev(Ctx* c, const double* locs_v, int64_t n, int m, int32_t* N_out);
+vl_status knn_cross_dev(Ctx* c, const double* train, int64_t n, const double* test, int64_t np,
+                        int m, int32_t* N_out);
+vl_status morton_perm(Ctx* c, const double* locs, int64_t n, int32_t* perm_out);
+vl_status bbox(Ctx* c, const double* locs, int64_t n, const double* extra, int64_t n_extra,
+               double out[4]);
+
+// graph.cu: storage order, ELL/transpose patterns, levels and task orders from
+// the Vecchia-order neighbour table N_v and locations locs_v (both device).
+vl_status build_graph_impl(Factor* f, const int32_t* N_v, const double* locs_v, const int32_t* order_dev);
+vl_status refresh_transpose_values(Factor* f);
+
+// factor.cu: A (rows x m) and D (rows) of the Vecchia rows; row_ids (optional)
+// name rows in error messages.
+vl_status factor_rows(Ctx* c, int64_t rows, int m, const double* self_locs, const double* ref_locs,
+                      const int32_t* nbr, int cov, double sigma2, double rho, double nugget,
+                      double* A, double* D, const int32_t* row_ids);
+
+}  // namespace vl
