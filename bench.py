@@ -1,0 +1,386 @@
+"""Benchmark of the iterative Vecchia-Laplace hot path on GB300.
+
+One step = one evaluation of the Vecchia-Laplace negative log-marginal likelihood
+at fixed covariance parameters and fixed locations: the Vecchia factor rows (A_i,
+D_i), Newton's mode with PCG solves, the SLQ probe solves and the L^VLA
+assembly. Neighbour sets and level schedules depend only on the locations; they
+are built once before timing and reported separately (graph_ms).
+
+Workload (default): n = 1,000,000 points of a 1250 x 1000 grid over the unit
+square with 20% removed in rectangular gaps, Matern-1.5 covariance (sigma2 = 1,
+range 0.02), m = 20, Poisson-log responses with offset 1.0, t = 50 Rademacher
+probes, VADU preconditioner, float32 Krylov path with float64 refinement.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU (torchrun, one rank per GPU): independent replicas, each rank solving its
+own seeded problem of the same shape (weak scaling); no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "n=1M log-marglik evals/s (mixed vs FP64) at stated err; PCG HBM GB/s; p99 latency"
+UNIT = "evals/s"
+WORKLOAD = "c3_grid1m"
+CPU_SAMPLE_N = 20000
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def _nnz(n: int, m: int) -> int:
+    return sum(min(k, m) for k in range(min(n, m))) + max(0, n - m) * m
+
+
+def algorithmic_bytes(cls: str, n: int, m: int, t: int, e: int) -> float:
+    """Bytes one launch of kernel class `cls` must move (each operand once)."""
+    nnz = _nnz(n, m)
+    vec = n * t * e
+    if cls == "sptrsv_fwd":     # ELL (idx + val), task list, rhs, row scale, solution
+        return nnz * (4 + e) + 4 * n + vec + n * e + vec
+    if cls == "sptrsv_bwd":     # CSR (idx + val + row pointers), task list, rhs, solution
+        return nnz * (4 + e) + 4 * (n + 1) + 4 * n + vec + vec
+    if cls == "spmv_B":         # ELL, X, row scale, Y
+        return nnz * (4 + e) + vec + n * e + vec
+    if cls == "spmv_Bt":        # CSR, Y, X, diagonal, Z
+        return nnz * (4 + e) + 4 * (n + 1) + 3 * vec + n * e
+    if cls == "coldot":
+        return 2 * vec
+    return float("nan")
+
+
+def _kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("kernels.cuh", "engine.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2310_12000_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(cls: str, t: int):
+    """Per-launch DRAM bytes from the committed ncu summary, if it matches the kernels."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("kernel_hash") != _kernel_hash():
+        return None
+    ent = d.get("per_launch_bytes", {}).get(f"{cls}/t={t}")
+    return ent
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.out = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out = ""
+
+    def summary(self):
+        if not self.out:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- CPU oracle timing
+def _oracle_eval_seconds(n_sub: int, seed: int) -> tuple[float, float]:
+    """One oracle LML evaluation (factor rows, Newton with sparse LU, exact log-det)
+    on the same recipe at n_sub points; neighbours built before timing."""
+    import workloads as wl
+    from oracle import laplace as la
+    P = wl.make_problem(WORKLOAD, seed=seed, n=n_sub)
+    f = la.build_factor(P.locs, P.order, P.cov, P.sigma2, P.rho, P.m, P.nugget)
+    t0 = time.perf_counter()
+    f = la.refit(f, P.sigma2, P.rho, P.nugget)
+    md = la.find_mode(f, P.y, P.F, P.lik)
+    L, _ = la.lml_exact(f, md)
+    return time.perf_counter() - t0, L
+
+
+def cpu_baseline(n_full: int, steps: int = 1) -> dict:
+    """The oracle timed on this host in a single-threaded child process."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = (f"import sys; sys.path.insert(0, {ROOT!r}); import bench, json; "
+            f"r = [bench._oracle_eval_seconds({CPU_SAMPLE_N}, 1) for _ in range({steps})]; "
+            f"print(json.dumps([x[0] for x in r]))")
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=1800)
+    if out.returncode != 0:
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": out.stderr[-400:]}
+    secs = json.loads(out.stdout.strip().splitlines()[-1])
+    s = statistics.median(secs)
+    return {"value": (1.0 / s) * (CPU_SAMPLE_N / n_full), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "seconds_per_eval_at_sample": s,
+            "sample": f"one LML evaluation (factor rows + Newton with sparse-LU solves + exact log-det) of the "
+                      f"same grid-with-gaps recipe at n={CPU_SAMPLE_N}, single thread, scaled to n={n_full} "
+                      f"by n_sample/n (linear; flatters the CPU since sparse LU grows faster than n)"}
+
+
+# ----------------------------------------------------------------------------- distributed
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    n_full = 1_000_000
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = (f"import sys; sys.path.insert(0, {ROOT!r}); import bench, json; "
+            f"[bench._oracle_eval_seconds({CPU_SAMPLE_N}, 1) for _ in range({args.warmup})]; "
+            f"r = [bench._oracle_eval_seconds({CPU_SAMPLE_N}, 1)[0] for _ in range({args.steps})]; "
+            f"print(json.dumps(r))")
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=3600)
+    if out.returncode != 0:
+        print(json.dumps({"impl": "reference", "unavailable": "oracle run failed: " + out.stderr[-200:]}))
+        return 0
+    secs = json.loads(out.stdout.strip().splitlines()[-1])
+    total = sum(secs)
+    value = args.steps / total * (CPU_SAMPLE_N / n_full)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{WORKLOAD}: grid 1250x1000 minus 20% gaps, n=1,000,000, Matern-1.5 rho=0.02, "
+                               f"m=20, Poisson offset 1.0; each step a bounded sample at n={CPU_SAMPLE_N} "
+                               f"scaled by n_sample/n"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"the CPU oracle (float64, sparse-LU Laplace) on the same recipe at "
+                                   f"n={CPU_SAMPLE_N}, single thread, scaled linearly to n=1,000,000"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = local
+    torch.cuda.set_device(dev)
+    import paper_2310_12000_gb300 as vl
+    import workloads as wl
+
+    P = wl.make_problem(WORKLOAD, seed=1 + rank)
+    n = P.n
+    ws_bytes = int(min(torch.cuda.mem_get_info(dev)[0] * 0.6, 120 << 30))
+    ctx = vl.Context(dev, ws_bytes=ws_bytes)
+    stream = torch.cuda.current_stream(dev)
+    o32 = vl.Opts.make(precision=vl.FP32_REFINE, t=50, cg_tol=1e-6, newton_tol=1e-7, cg_max_iter=2000)
+    o64 = vl.Opts.make(precision=vl.FP64, t=50, cg_tol=1e-6, newton_tol=1e-7, cg_max_iter=2000)
+
+    # neighbours + levels + factor, once per location set
+    t0 = time.perf_counter()
+    fac = ctx.build_factor(P.locs, P.order, P.cov, P.sigma2, P.rho, P.m, o32)
+    torch.cuda.synchronize(dev)
+    graph_ms = 1000 * (time.perf_counter() - t0)
+    info = fac.info()
+
+    y_d = torch.from_numpy(P.y).to(f"cuda:{dev}")
+    F_d = torch.from_numpy(P.F).to(f"cuda:{dev}")
+    mode_d = torch.empty(n, dtype=torch.float64, device=f"cuda:{dev}")
+    y_h = torch.from_numpy(P.y).pin_memory()
+    F_h = torch.from_numpy(P.F).pin_memory()
+    mode_h = torch.empty(n, dtype=torch.float64).pin_memory()
+
+    def step(opts, host=False):
+        fac.refit(P.sigma2, P.rho, opts)
+        if host:
+            st = fac.find_mode(P.lik, y_h.numpy(), F_h.numpy(), opts, mode_out=mode_h.numpy())
+        else:
+            st = fac.find_mode(P.lik, y_d, F_d, opts, mode_out=mode_d)
+        val = st.log_marglik(opts, with_stats=True)
+        st.close()
+        return val
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    def max_over_ranks(x: float) -> float:
+        if ws == 1:
+            return x
+        tt = torch.tensor([x], dtype=torch.float64, device=f"cuda:{dev}")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        return float(tt.item())
+
+    for _ in range(args.warmup):
+        step(o32)
+
+    # ---------------- timed: device-resident inputs, kernel profiling on
+    ctx.profile(True)
+    ctx.profile_read("all", reset=True)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    lmls, stats = [], []
+    with ClockSampler(dev) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            L, s = step(o32)
+            lmls.append(L)
+            stats.append(s)
+        e1.record(stream)
+        barrier()
+    elapsed_s = max_over_ranks(e0.elapsed_time(e1) / 1000.0)
+    launches = ctx.profile_read("all")[1]
+    classes = ["sptrsv_fwd", "sptrsv_bwd", "spmv_B", "spmv_Bt", "coldot", "pcg_update", "factor"]
+    prof = {}
+    for cls in classes:
+        for t in (1, 50):
+            ms, cnt = ctx.profile_read(cls, t)
+            if cnt:
+                prof[f"{cls}/t={t}"] = {"ms": ms, "launches": cnt}
+        if cls == "factor":
+            ms, cnt = ctx.profile_read(cls, 0)
+            if cnt:
+                prof["factor"] = {"ms": ms, "launches": cnt}
+    ctx.profile(False)
+    value = ws * args.steps / elapsed_s
+
+    # roofline for the dominant HBM-bound kernel class
+    hbm_peak, peak_kind = _peaks()
+    dom_key = max((k for k in prof if k.split("/")[0] in ("sptrsv_fwd", "sptrsv_bwd", "spmv_B", "spmv_Bt", "coldot")),
+                  key=lambda k: prof[k]["ms"])
+    dcls, dt = dom_key.split("/")[0], int(dom_key.split("=")[1])
+    avg_ms = prof[dom_key]["ms"] / prof[dom_key]["launches"]
+    bytes_launch = algorithmic_bytes(dcls, n, P.m, dt, 4)
+    achieved = bytes_launch / (avg_ms / 1000.0) / 1e9
+    total_prof_ms = sum(v["ms"] for v in prof.values())
+    roofline = {"bound": "hbm", "kernel": dom_key, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
+                if peak_kind == "measured" else "fallback 6.8 TB/s",
+                "traffic": _traffic(dcls, dt), "algorithmic_bytes_per_launch": bytes_launch,
+                "avg_launch_ms": avg_ms,
+                "share_of_profiled_time": prof[dom_key]["ms"] / total_prof_ms if total_prof_ms else None}
+
+    # ---------------- e2e: host buffers, copies inside the timed region
+    barrier()
+    t0 = time.perf_counter()
+    e2e_steps = max(1, min(args.steps, 3))
+    for _ in range(e2e_steps):
+        step(o32, host=True)
+    barrier()
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e = {"value": ws * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 2 * n * 8,
+           "d2h_bytes_per_step": n * 8 + 8}
+
+    # ---------------- FP64 reference on the GPU (the "vs FP64" part of the metric)
+    fp64 = None
+    if not args.no_fp64:
+        barrier()
+        t0 = time.perf_counter()
+        L64, s64 = step(o64)
+        barrier()
+        fp64 = {"evals_per_s": ws / max_over_ranks(time.perf_counter() - t0), "lml": L64,
+                "rel_diff_mixed_vs_fp64": abs(lmls[-1] - L64) / abs(L64),
+                "newton_cg_iters_total": s64.get("cg_iters_total")}
+
+    out = None
+    if rank == 0:
+        cb = cpu_baseline(n) if (ws == 1 and not args.no_cpu) else None
+        s_last = stats[-1]
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000 * elapsed_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{WORKLOAD}: 1250x1000 grid on [0,1]^2 minus 20% rectangular gaps, "
+                                   f"n={n}, Matern-1.5 sigma2=1 rho=0.02, m=20, Poisson-log offset 1.0, "
+                                   f"t=50 Rademacher probes, VADU, float32 Krylov + float64 refinement, "
+                                   f"cg_tol 1e-6",
+                       "step": "factor rows + Newton mode + SLQ log-marglik (neighbours/levels once, excluded)",
+                       "l2": "inputs larger than L2 (probe block 1e6 x 56 float32 = 224 MB per vector)",
+                       "graph_ms": graph_ms, "levels_fwd": info["nlev_fwd"], "levels_bwd": info["nlev_bwd"]},
+            "lml": lmls[-1], "newton_cg_iters_total": s_last.get("cg_iters_total"),
+            "slq_cg_iters_max": s_last.get("cg_iters_max"), "slq_stderr": s_last.get("slq_stderr"),
+            "fp64": fp64, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
+            "kernel_profile_ms": prof, "clocks": clk.summary(), "cpu_baseline": cb,
+            "p99_latency_ms": None,
+        }
+        print(json.dumps(out))
+    if ws > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -176,6 +176,9 @@ void vl_factor_destroy(vl_factor* f);
 vl_status vl_find_mode(vl_factor* f, int lik, const double* y, const double* F,
                        const vl_opts* opts, double* mode_out, vl_state** out);
 void vl_state_destroy(vl_state* s);
+/* Diagnostics of the Newton solve that made the state (iterations, PCG solves and
+ * iterations, refinement passes, final float64 relative residual). */
+vl_status vl_state_stats(const vl_state* s, vl_stats* out);
 
 /* L^VLA (Eq. VLA_loss) at the state's mode: -log p(y|mu*) + b*^T Sigma_tilde^{-1} b* / 2
  * + log det(Sigma_tilde W + I)/2. The log-determinant is split by the preconditioner
@@ -199,6 +202,18 @@ vl_status vl_slq_gammas(const vl_state* s, double* gammas, int t);
  * key = (seed, 0)). Fp may be NULL (0). mean/var: np doubles (either may be NULL). */
 vl_status vl_pred_var(vl_state* s, const double* test_locs, int64_t np, const double* Fp,
                       const vl_opts* opts, double* mean, double* var, vl_stats* stats);
+
+/* Kernel timing. While enabled, every launch of the library's hot kernels is
+ * bracketed by a pair of CUDA events on the context's stream, grouped by kernel
+ * class and block width: "sptrsv_fwd", "sptrsv_bwd", "spmv_B", "spmv_Bt",
+ * "pcg_update", "coldot", "factor", "knn". Costs two event records per launch. */
+vl_status vl_profile_enable(vl_ctx* ctx, int enable);
+/* Device time (ms, summed) and launch count of class `cls` at block width t
+ * (t = 0: all widths) since the last reset; reset != 0 clears every class.
+ * cls = "all" gives the number of kernels launched on the context (counted
+ * whether or not profiling is enabled) and zero time. Synchronises the stream.
+ * Unknown class: zero time and count. */
+vl_status vl_profile_read(vl_ctx* ctx, const char* cls, int t, double* ms, int64_t* launches, int reset);
 
 /* ------------------------------------------------------------------------------
  * Building blocks, exposed for verification and for callers composing their own

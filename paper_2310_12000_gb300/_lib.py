@@ -52,6 +52,28 @@ class Stats(C.Structure):
 
 
 _lib = None
+_live = []   # weak references to open handles, closed children-first at exit
+
+
+def _track(obj):
+    import weakref
+    _live.append(weakref.ref(obj))
+
+
+def _close_all():
+    for kind in (State, Factor, Context):
+        for r in list(_live):
+            o = r()
+            if isinstance(o, kind):
+                try:
+                    o.close()
+                except Exception:
+                    pass
+
+
+import atexit  # noqa: E402
+
+atexit.register(_close_all)
 
 
 def lib_path() -> str:
@@ -77,6 +99,8 @@ def library():
         "vl_last_error": (C.c_char_p, [vp]),
         "vl_ctx_synchronize": (st, [vp]),
         "vl_ctx_mem": (st, [vp, vp, vp]),
+        "vl_profile_enable": (st, [vp, i32]),
+        "vl_profile_read": (st, [vp, C.c_char_p, i32, vp, vp, i32]),
         "vl_build_factor": (st, [vp, vp, i64, vp, i32, d, d, i32, vp, vp]),
         "vl_factor_refit": (st, [vp, d, d, vp]),
         "vl_factor_export": (st, [vp, vp, vp, vp, vp, vp]),
@@ -84,6 +108,7 @@ def library():
         "vl_factor_destroy": (None, [vp]),
         "vl_find_mode": (st, [vp, i32, vp, vp, vp, vp, vp]),
         "vl_state_destroy": (None, [vp]),
+        "vl_state_stats": (st, [vp, vp]),
         "vl_log_marglik": (st, [vp, vp, vp, vp, vp]),
         "vl_slq_gammas": (st, [vp, vp, i32]),
         "vl_pred_var": (st, [vp, vp, i64, vp, vp, vp, vp, vp]),
@@ -157,6 +182,7 @@ class Context:
             raise VLError(s, "vl_ctx_create failed")
         self.h = h
         self.device = device
+        _track(self)
 
     def check(self, status: int):
         if status != 0:
@@ -164,6 +190,10 @@ class Context:
 
     def close(self):
         if getattr(self, "h", None):
+            for r in list(_live):          # children first: they reference this context
+                o = r()
+                if o is not None and o is not self and getattr(o, "ctx", None) is self:
+                    o.close()
             self.lib.vl_ctx_destroy(self.h)
             self.h = None
 
@@ -180,6 +210,14 @@ class Context:
         a, b = C.c_size_t(), C.c_size_t()
         self.check(self.lib.vl_ctx_mem(self.h, C.byref(a), C.byref(b)))
         return a.value, b.value
+
+    def profile(self, enable: bool = True):
+        self.check(self.lib.vl_profile_enable(self.h, 1 if enable else 0))
+
+    def profile_read(self, cls: str, t: int = 0, reset: bool = False):
+        ms, cnt = C.c_double(), C.c_int64()
+        self.check(self.lib.vl_profile_read(self.h, cls.encode(), t, C.byref(ms), C.byref(cnt), 1 if reset else 0))
+        return ms.value, cnt.value
 
     # ---------------------------------------------------------------- calls
     def build_factor(self, locs, order, cov: int, sigma2: float, rho: float, m: int,
@@ -211,6 +249,7 @@ class Context:
 class Factor:
     def __init__(self, ctx: Context, h, n: int, m: int):
         self.ctx, self.h, self.n, self.m = ctx, h, n, m
+        _track(self)
 
     def close(self):
         if self.h:
@@ -261,6 +300,7 @@ class Factor:
 class State:
     def __init__(self, fac: Factor, h, mode):
         self.fac, self.ctx, self.h, self.mode = fac, fac.ctx, h, mode
+        _track(self)
 
     def close(self):
         if self.h:
@@ -272,6 +312,11 @@ class State:
             self.close()
         except Exception:
             pass
+
+    def mode_stats(self) -> dict:
+        st = Stats()
+        self.ctx.check(self.ctx.lib.vl_state_stats(self.h, C.byref(st)))
+        return st.as_dict()
 
     def log_marglik(self, opts: Opts | None = None, with_stats: bool = False):
         opts = opts or Opts.make()

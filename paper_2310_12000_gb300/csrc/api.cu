@@ -217,8 +217,8 @@ static vl_status dev_sum(Ctx* c, Scratch& S, int n, int mode, const double* a, c
   const int nb = std::max(1, std::min(c->num_sms * 2, (n + 255) / 256));
   double* part = S.get<double>(nb + 1);
   if (!part) return fail(c, VL_ERR_OOM, "workspace exhausted (sum)");
-  sum_kernel<<<nb, 256, 0, c->stream>>>(n, mode, a, b, part);
-  reduce_partials_kernel<<<1, 32, 0, c->stream>>>(nb, 1, part, part + nb);
+  sum_kernel<<<nb, 256, 0, VL_STREAM(c)>>>(n, mode, a, b, part);
+  reduce_partials_kernel<<<1, 32, 0, VL_STREAM(c)>>>(nb, 1, part, part + nb);
   VL_CUDA(c, cudaGetLastError());
   vl_status st = VL_OK;
   *host_out = read_scalar(c, part + nb, &st);
@@ -229,7 +229,7 @@ static vl_status dev_absmax(Ctx* c, Scratch& S, int n, const double* a, const do
   const int nb = std::max(1, std::min(c->num_sms * 2, (n + 255) / 256));
   double* part = S.get<double>(2 * nb);
   if (!part) return fail(c, VL_ERR_OOM, "workspace exhausted (absmax)");
-  absmax_kernel<<<nb, 256, 0, c->stream>>>(n, a, b, part);
+  absmax_kernel<<<nb, 256, 0, VL_STREAM(c)>>>(n, a, b, part);
   VL_CUDA(c, cudaGetLastError());
   std::vector<double> h(2 * nb);
   VL_CUDA(c, cudaMemcpyAsync(h.data(), part, sizeof(double) * 2 * nb, cudaMemcpyDeviceToHost, c->stream));
@@ -262,7 +262,7 @@ static vl_status psi_eval(State* st, Engine<double>& E1, Scratch& S, const doubl
   const int n = (int)st->f->n;
   double* lp = S.get<double>(n);
   if (!lp) return fail(c, VL_ERR_OOM, "workspace exhausted (psi)");
-  lik_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, st->lik, st->y, st->F, b, nullptr, nullptr, nullptr, lp);
+  lik_kernel<<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, st->lik, st->y, st->F, b, nullptr, nullptr, nullptr, lp);
   VL_CUDA(c, cudaGetLastError());
   double logp = 0.0, quad = 0.0;
   VL_TRY(dev_sum(c, S, n, 0, lp, nullptr, &logp));
@@ -279,9 +279,11 @@ static vl_status psi_eval(State* st, Engine<double>& E1, Scratch& S, const doubl
   return VL_OK;
 }
 
-// Solve (W + Sigma_tilde^{-1}) x = rhs (one column, float64 in/out). FP64: one PCG
-// from x = 0. Mixed: float32 PCG on corrections, refined with float64 residuals
-// until ||rhs - A x|| <= tol ||rhs||.
+// Solve (W + Sigma_tilde^{-1}) x = rhs (one column, float64 in/out).
+// FP64: one PCG from x = 0 (the appendix algorithm). Mixed: x enters holding a
+// starting guess (the current Newton iterate); float32 PCG solves for corrections
+// d of the float64 residual, each to the relative accuracy still missing
+// (0.5 tol ||rhs|| / ||res||, at least 1e-6), until ||rhs - A x|| <= tol ||rhs||.
 static vl_status solve1(State* st, const vl_opts* o, Engine<double>& E64, Engine<float>* E32, const double* rhs,
                         double* x, vl_stats* stats) {
   Ctx* c = st->ctx;
@@ -296,32 +298,29 @@ static vl_status solve1(State* st, const vl_opts* o, Engine<double>& E64, Engine
     }
     return VL_OK;
   }
-  // mixed precision with float64 iterative refinement; x starts at 0
   Scratch S(c);
   double* res = S.get<double>(n);
   float* r32 = S.get<float>(n);
   float* d32 = S.get<float>(n);
   if (!res || !r32 || !d32) return fail(c, VL_ERR_OOM, "workspace exhausted (refinement)");
-  VL_CUDA(c, cudaMemsetAsync(x, 0, sizeof(double) * n, c->stream));
   VL_TRY(E64.coldot(rhs, rhs, nullptr, E64.red));
   vl_status s = VL_OK;
   const double bn = std::sqrt(read_scalar(c, E64.red, &s));
   VL_TRY(s);
   double rel = 1.0;
-  const double inner_tol = std::max(o->cg_tol, 1e-4);
   for (int pass = 0; pass < 12; ++pass) {
-    if (pass > 0 || true) {
-      VL_TRY(E64.opA(x, res));
-      residual_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, rhs, res);
-      VL_TRY(E64.coldot(res, res, nullptr, E64.red));
-      rel = bn > 0 ? std::sqrt(read_scalar(c, E64.red, &s)) / bn : 0.0;
-      VL_TRY(s);
-    }
+    VL_TRY(E64.opA(x, res));
+    residual_kernel<<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, rhs, res);
+    VL_TRY(E64.coldot(res, res, nullptr, E64.red));
+    const double rn = std::sqrt(read_scalar(c, E64.red, &s));
+    VL_TRY(s);
+    rel = bn > 0 ? rn / bn : 0.0;
     if (rel <= o->cg_tol) break;
-    convert_kernel<double, float><<<grid_for(c, n), 256, 0, c->stream>>>(n, res, r32);
+    const double inner = std::min(0.1, std::max(1e-6, 0.5 * o->cg_tol * bn / rn));
+    convert_kernel<double, float><<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, res, r32);
     VL_CUDA(c, cudaGetLastError());
-    VL_TRY(E32->pcg(r32, d32, inner_tol, o->cg_max_iter, &used));
-    accumulate_kernel<double, float><<<grid_for(c, n), 256, 0, c->stream>>>(n, x, d32);
+    VL_TRY(E32->pcg(r32, d32, inner, o->cg_max_iter, &used));
+    accumulate_kernel<double, float><<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, x, d32);
     VL_CUDA(c, cudaGetLastError());
     if (stats) {
       stats->cg_calls++;
@@ -364,15 +363,15 @@ static vl_status slq_run(State* st, const vl_opts* o, std::vector<double>& gam, 
   double* work = S.get<double>((size_t)3 * t * E.lmax);
   int* bad = S.get<int>(1);
   if (!Rm || !Zm || !Um || !sc64 || !sc || !gdev || !work || !bad) return fail(c, VL_ERR_OOM, "workspace exhausted (SLQ)");
-  rademacher_kernel<T><<<(n + 127) / 128, 128, 0, c->stream>>>(n, t, E.ld, f->s2u, o->seed, 0, 0, Rm);
-  diag_fn_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, o->precond == VL_PREC_VADU ? 0 : 1, st->W, f->D64, sc64);
-  convert_kernel<double, T><<<grid_for(c, n), 256, 0, c->stream>>>(n, sc64, sc);
+  rademacher_kernel<T><<<(n + 127) / 128, 128, 0, VL_STREAM(c)>>>(n, t, E.ld, f->s2u, o->seed, 0, 0, Rm);
+  diag_fn_kernel<<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, o->precond == VL_PREC_VADU ? 0 : 1, st->W, f->D64, sc64);
+  convert_kernel<double, T><<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, sc64, sc);
   VL_CUDA(c, cudaGetLastError());
   VL_TRY(E.opBt(Rm, sc, nullptr, nullptr, Zm));
   int used = 0;
   VL_TRY(E.pcg(Zm, Um, o->cg_tol, o->cg_max_iter, &used));
   VL_CUDA(c, cudaMemsetAsync(bad, 0, sizeof(int), c->stream));
-  slq_quad_kernel<<<(t + 63) / 64, 64, 0, c->stream>>>(t, E.lmax, E.S.Tdiag, E.S.Toff, E.S.iters, E.S.rz0, work, gdev,
+  slq_quad_kernel<<<(t + 63) / 64, 64, 0, VL_STREAM(c)>>>(t, E.lmax, E.S.Tdiag, E.S.Toff, E.S.iters, E.S.rz0, work, gdev,
                                                        bad);
   VL_CUDA(c, cudaGetLastError());
   std::vector<int> iters;
@@ -412,10 +411,10 @@ static vl_status sim_block(State* st, const vl_opts* o, Engine<double>& E64, int
   double* sW = S.get<double>(n);
   double* sD = S.get<double>(n);
   if (!z1 || !z2 || !z3 || !sW || !sD) return fail(c, VL_ERR_OOM, "workspace exhausted (simulation)");
-  gaussian_kernel<<<(n + 127) / 128, 128, 0, c->stream>>>(n, sc, ld, col0, f->s2u, o->seed, 1, z1);
-  gaussian_kernel<<<(n + 127) / 128, 128, 0, c->stream>>>(n, sc, ld, col0, f->s2u, o->seed, 2, z2);
-  diag_fn_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, 2, st->W, f->D64, sW);
-  diag_fn_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, 1, st->W, f->D64, sD);
+  gaussian_kernel<<<(n + 127) / 128, 128, 0, VL_STREAM(c)>>>(n, sc, ld, col0, f->s2u, o->seed, 1, z1);
+  gaussian_kernel<<<(n + 127) / 128, 128, 0, VL_STREAM(c)>>>(n, sc, ld, col0, f->s2u, o->seed, 2, z2);
+  diag_fn_kernel<<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, 2, st->W, f->D64, sW);
+  diag_fn_kernel<<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, 1, st->W, f->D64, sD);
   VL_CUDA(c, cudaGetLastError());
   VL_TRY(E64.opBt(z2, sD, z1, sW, z3));
   int used = 0;
@@ -442,17 +441,17 @@ static vl_status sim_block(State* st, const vl_opts* o, Engine<double>& E64, int
   double worst = 1.0;
   for (int pass = 0; pass < 12; ++pass) {
     VL_TRY(E64.opA(U, res));
-    residual_kernel<<<grid_for(c, vec), 256, 0, c->stream>>>(vec, z3, res);
+    residual_kernel<<<grid_for(c, vec), 256, 0, VL_STREAM(c)>>>(vec, z3, res);
     VL_TRY(E64.coldot(res, res, nullptr, E64.red));
     VL_CUDA(c, cudaMemcpyAsync(rn.data(), E64.red, sizeof(double) * sc, cudaMemcpyDeviceToHost, c->stream));
     VL_CUDA(c, cudaStreamSynchronize(c->stream));
     worst = 0.0;
     for (int k = 0; k < sc; ++k) worst = std::max(worst, bn[k] > 0 ? std::sqrt(rn[k] / bn[k]) : 0.0);
     if (worst <= o->cg_tol) break;
-    repack_kernel<<<grid_for(c, vec), 256, 0, c->stream>>>(vec, res, r32);
+    repack_kernel<<<grid_for(c, vec), 256, 0, VL_STREAM(c)>>>(vec, res, r32);
     VL_CUDA(c, cudaGetLastError());
     VL_TRY(E32.pcg(r32, d32, std::max(o->cg_tol, 1e-4), o->cg_max_iter, &used));
-    accumulate_kernel<double, float><<<grid_for(c, vec), 256, 0, c->stream>>>(vec, U, d32);
+    accumulate_kernel<double, float><<<grid_for(c, vec), 256, 0, VL_STREAM(c)>>>(vec, U, d32);
     VL_CUDA(c, cudaGetLastError());
     if (stats) {
       stats->cg_calls++;
@@ -473,7 +472,7 @@ static vl_status apply_op(State* st, int op, const double* Xd, int t, const vl_o
   const int n = (int)f->n;
   Engine<T> E(c);
   VL_TRY(E.init(f, t, o->precond, st->W, 0));
-  to_storage_kernel<T><<<grid_for(c, (int64_t)n * E.ld), 256, 0, c->stream>>>(n, t, E.ld, f->s2u, Xd, E.u);
+  to_storage_kernel<T><<<grid_for(c, (int64_t)n * E.ld), 256, 0, VL_STREAM(c)>>>(n, t, E.ld, f->s2u, Xd, E.u);
   VL_CUDA(c, cudaGetLastError());
   switch (op) {
     case VL_OP_A: VL_TRY(E.opA(E.u, E.v)); break;
@@ -486,7 +485,7 @@ static vl_status apply_op(State* st, int op, const double* Xd, int t, const vl_o
     case VL_OP_A2: VL_TRY(E.opA2(E.u, E.v)); break;
     default: return fail(c, VL_ERR_INVALID_ARG, "vl_apply: unknown op");
   }
-  from_storage_kernel<T><<<grid_for(c, (int64_t)n * t), 256, 0, c->stream>>>(n, t, E.ld, f->s2u, E.v, Yd);
+  from_storage_kernel<T><<<grid_for(c, (int64_t)n * t), 256, 0, VL_STREAM(c)>>>(n, t, E.ld, f->s2u, E.v, Yd);
   VL_CUDA(c, cudaGetLastError());
   return check_dev_status(c, "vl_apply");
 }
@@ -504,11 +503,11 @@ static vl_status pcg_op(State* st, const double* Rd, int t, const vl_opts* o, do
   T* Um = S.get<T>((size_t)n * E.ld);
   if (!Bm || !Um) return fail(c, VL_ERR_OOM, "workspace exhausted (vl_pcg_solve)");
   VL_CUDA(c, cudaMemsetAsync(Bm, 0, sizeof(T) * n * E.ld, c->stream));
-  to_storage_kernel<T><<<grid_for(c, (int64_t)n * E.ld), 256, 0, c->stream>>>(n, t, E.ld, f->s2u, Rd, Bm);
+  to_storage_kernel<T><<<grid_for(c, (int64_t)n * E.ld), 256, 0, VL_STREAM(c)>>>(n, t, E.ld, f->s2u, Rd, Bm);
   VL_CUDA(c, cudaGetLastError());
   int used = 0;
   VL_TRY(E.pcg(Bm, Um, o->cg_tol, o->cg_max_iter, &used));
-  from_storage_kernel<T><<<grid_for(c, (int64_t)n * t), 256, 0, c->stream>>>(n, t, E.ld, f->s2u, Um, Ud);
+  from_storage_kernel<T><<<grid_for(c, (int64_t)n * t), 256, 0, VL_STREAM(c)>>>(n, t, E.ld, f->s2u, Um, Ud);
   VL_CUDA(c, cudaGetLastError());
   std::vector<int> it;
   std::vector<double> rel;
@@ -599,6 +598,7 @@ vl_status vl_ctx_create(int device, void* cuda_stream, void* workspace, size_t w
 void vl_ctx_destroy(vl_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
+  prof_release(c);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   if (c->owns_ws && c->ws) cudaFree(c->ws);
@@ -611,6 +611,39 @@ const char* vl_last_error(const vl_ctx* c) { return c ? c->last_error.c_str() : 
 vl_status vl_ctx_synchronize(vl_ctx* c) {
   if (!c) return VL_ERR_INVALID_ARG;
   VL_CUDA(c, cudaStreamSynchronize(c->stream));
+  return VL_OK;
+}
+
+vl_status vl_profile_enable(vl_ctx* c, int enable) {
+  if (!c) return VL_ERR_INVALID_ARG;
+  VL_CUDA(c, cudaStreamSynchronize(c->stream));
+  prof_drain(c);
+  c->prof.on = enable != 0;
+  return VL_OK;
+}
+
+vl_status vl_profile_read(vl_ctx* c, const char* cls, int t, double* ms, int64_t* launches, int reset) {
+  if (!c) return VL_ERR_INVALID_ARG;
+  VL_CUDA(c, cudaStreamSynchronize(c->stream));
+  prof_drain(c);
+  double tot = 0.0;
+  int64_t cnt = 0;
+  if (cls && std::string(cls) == "all") {
+    cnt = c->launches;
+  } else if (cls) {
+    for (auto& kv : c->prof.acc) {
+      if (kv.first.first == cls && (t == 0 || kv.first.second == t)) {
+        tot += kv.second.ms;
+        cnt += kv.second.launches;
+      }
+    }
+  }
+  if (ms) *ms = tot;
+  if (launches) *launches = cnt;
+  if (reset) {
+    c->prof.acc.clear();
+    c->launches = 0;
+  }
   return VL_OK;
 }
 
@@ -716,7 +749,7 @@ vl_status vl_build_factor(vl_ctx* c, const double* locs, int64_t n, const int32_
     return bail(fail(c, VL_ERR_OOM, "workspace exhausted (factor)"));
   if (cudaMemsetAsync(f->ready, 0, sizeof(unsigned) * n, c->stream) != cudaSuccess)
     return bail(cuda_fail(c, cudaGetLastError(), "memset"));
-  gather2_kernel<<<(int)((n + 255) / 256), 256, 0, c->stream>>>((int)n, dl, dord, f->locs_v);
+  gather2_kernel<<<(int)((n + 255) / 256), 256, 0, VL_STREAM(c)>>>((int)n, dl, dord, f->locs_v);
   int32_t* Nv = S.get<int32_t>(std::max<int64_t>(nm, 1));
   if (!Nv) return bail(fail(c, VL_ERR_OOM, "workspace exhausted (neighbours)"));
   if (m > 0) {
@@ -744,7 +777,7 @@ vl_status vl_factor_export(const vl_factor* fc, int32_t* N, double* A, double* D
   int32_t* dlb = lev_bwd ? S.get<int32_t>(n) : nullptr;
   if ((N && !dN) || (A && !dA) || (D && !dD) || (lev_fwd && !dlf) || (lev_bwd && !dlb))
     return fail(c, VL_ERR_OOM, "workspace exhausted (export)");
-  export_kernel<<<(int)((n + 255) / 256), 256, 0, c->stream>>>((int)n, f->m, f->s2v, f->nbr, f->A64, f->D64,
+  export_kernel<<<(int)((n + 255) / 256), 256, 0, VL_STREAM(c)>>>((int)n, f->m, f->s2v, f->nbr, f->A64, f->D64,
                                                                f->lev_fwd, f->lev_bwd, dN, dA, dD, dlf, dlb);
   VL_CUDA(c, cudaGetLastError());
   VL_TRY(stage_out(c, dN, N, nm));
@@ -805,9 +838,9 @@ vl_status vl_find_mode(vl_factor* f, int lik, const double* y, const double* F, 
     s = stage_in(c, S, y, n, &dy);
     if (s == VL_OK && F) s = stage_in(c, S, F, n, &dF);
     if (s != VL_OK) return bail(s);
-    to_storage_kernel<double><<<grid_for(c, n), 256, 0, c->stream>>>(n, 1, 1, f->s2u, dy, st->y);
+    to_storage_kernel<double><<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, 1, 1, f->s2u, dy, st->y);
     if (dF)
-      to_storage_kernel<double><<<grid_for(c, n), 256, 0, c->stream>>>(n, 1, 1, f->s2u, dF, st->F);
+      to_storage_kernel<double><<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, 1, 1, f->s2u, dF, st->F);
     else
       cudaMemsetAsync(st->F, 0, sizeof(double) * n, c->stream);
     cudaMemsetAsync(st->b, 0, sizeof(double) * n, c->stream);
@@ -831,26 +864,27 @@ vl_status vl_find_mode(vl_factor* f, int lik, const double* y, const double* F, 
   s = psi_eval(st, E64, S, st->b, &psi, nullptr, nullptr);
   if (s != VL_OK) return bail(s);
   for (it = 1; it <= opts->newton_max_iter; ++it) {
-    lik_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, lik, st->y, st->F, st->b, st->W, g, rhs, nullptr);
-    diag_prep_kernel<double><<<grid_for(c, n), 256, 0, c->stream>>>(n, opts->precond, st->W, f->D64, E64.W, E64.Dinv,
+    lik_kernel<<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, lik, st->y, st->F, st->b, st->W, g, rhs, nullptr);
+    diag_prep_kernel<double><<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, opts->precond, st->W, f->D64, E64.W, E64.Dinv,
                                                                     E64.dsc, E64.Dt, E64.Winv);
     if (mixed) {
       if (!E32.W) {
         s = E32.init(f, 1, opts->precond, st->W, opts->cg_max_iter + 1);
         if (s != VL_OK) return bail(s);
       } else {
-        diag_prep_kernel<float><<<grid_for(c, n), 256, 0, c->stream>>>(n, opts->precond, st->W, f->D64, E32.W,
+        diag_prep_kernel<float><<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, opts->precond, st->W, f->D64, E32.W,
                                                                        E32.Dinv, E32.dsc, E32.Dt, E32.Winv);
       }
     }
     if (cudaGetLastError() != cudaSuccess) return bail(fail(c, VL_ERR_CUDA, "Newton setup"));
+    if (mixed) cudaMemcpyAsync(bn, st->b, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream);  // warm start
     s = solve1(st, opts, E64, mixed ? &E32 : nullptr, rhs, bn, &stats);
     if (s != VL_OK) return bail(s);
     double psi_new = 0.0;
     s = psi_eval(st, E64, S, bn, &psi_new, nullptr, nullptr);
     if (s != VL_OK) return bail(s);
     for (int hlv = 0; hlv < 30 && psi_new < psi - 1e-12 * (1.0 + std::fabs(psi)); ++hlv) {
-      halve_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, st->b, bn);
+      halve_kernel<<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, st->b, bn);
       s = psi_eval(st, E64, S, bn, &psi_new, nullptr, nullptr);
       if (s != VL_OK) return bail(s);
     }
@@ -866,18 +900,26 @@ vl_status vl_find_mode(vl_factor* f, int lik, const double* y, const double* F, 
     }
   }
   // W at the mode
-  lik_kernel<<<grid_for(c, n), 256, 0, c->stream>>>(n, lik, st->y, st->F, st->b, st->W, nullptr, nullptr, nullptr);
+  lik_kernel<<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, lik, st->y, st->F, st->b, st->W, nullptr, nullptr, nullptr);
   if (cudaGetLastError() != cudaSuccess) return bail(fail(c, VL_ERR_CUDA, "lik"));
   if (mode_out) {
     double* mu = S.get<double>(n);
     if (!mu) return bail(fail(c, VL_ERR_OOM, "workspace exhausted (mode out)"));
-    from_storage_kernel<double><<<grid_for(c, n), 256, 0, c->stream>>>(n, 1, 1, f->s2u, st->b, mu);
+    from_storage_kernel<double><<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, 1, 1, f->s2u, st->b, mu);
     s = stage_out(c, mu, mode_out, n);
     if (s != VL_OK) return bail(s);
   }
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return bail(fail(c, VL_ERR_CUDA, "sync"));
+  stats.newton_iters = it;
+  st->mode_stats = stats;
   *out = st;
   if (!converged) return fail(c, VL_ERR_NOT_CONVERGED, "Newton reached newton_max_iter");
+  return VL_OK;
+}
+
+vl_status vl_state_stats(const vl_state* s, vl_stats* out) {
+  if (!s || !out) return VL_ERR_INVALID_ARG;
+  *out = s->mode_stats;
   return VL_OK;
 }
 
@@ -978,7 +1020,7 @@ vl_status vl_pred_var(vl_state* st, const double* test_locs, int64_t np, const d
   if (!Np || !Ap || !Dp || !dmean || !dvar) return fail(c, VL_ERR_OOM, "workspace exhausted (prediction)");
   if (m > 0) {
     VL_TRY(knn_cross_dev(c, f->locs_v, n, dq, np, m, Np));   // Vecchia indices, Section 4.1
-    translate_kernel<<<grid_for(c, npm), 256, 0, c->stream>>>(npm, f->v2s, Np);
+    translate_kernel<<<grid_for(c, npm), 256, 0, VL_STREAM(c)>>>(npm, f->v2s, Np);
     VL_CUDA(c, cudaGetLastError());
   }
   VL_CUDA(c, cudaMemsetAsync(c->dstatus, 0, sizeof(DevStatus), c->stream));
@@ -986,7 +1028,7 @@ vl_status vl_pred_var(vl_state* st, const double* test_locs, int64_t np, const d
   VL_TRY(check_dev_status(c, "prediction rows"));
   VL_CUDA(c, cudaMemsetAsync(dvar, 0, sizeof(double) * np, c->stream));
   const int pg = (int)((np * 32 + 255) / 256);
-  pred_kernel<double><<<pg, 256, 0, c->stream>>>((int)np, m, Np, Ap, Dp, dF, st->b, nullptr, 0, 1, dmean, nullptr);
+  pred_kernel<double><<<pg, 256, 0, VL_STREAM(c)>>>((int)np, m, Np, Ap, Dp, dF, st->b, nullptr, 0, 1, dmean, nullptr);
   VL_CUDA(c, cudaGetLastError());
   if (var) {
     for (int col0 = 0; col0 < o->s; col0 += 128) {
@@ -996,14 +1038,14 @@ vl_status vl_pred_var(vl_state* st, const double* test_locs, int64_t np, const d
       double* U = S.get<double>((size_t)n * E64.ld);
       if (!U) return fail(c, VL_ERR_OOM, "workspace exhausted (simulation)");
       VL_TRY(sim_block(st, o, E64, sc, col0, U, &loc));
-      pred_kernel<double><<<pg, 256, 0, c->stream>>>((int)np, m, Np, Ap, Dp, nullptr, st->b, U, sc, E64.ld, nullptr,
+      pred_kernel<double><<<pg, 256, 0, VL_STREAM(c)>>>((int)np, m, Np, Ap, Dp, nullptr, st->b, U, sc, E64.ld, nullptr,
                                                       dvar);
       VL_CUDA(c, cudaGetLastError());
       VL_CUDA(c, cudaStreamSynchronize(c->stream));
       c->arena.release(U);
       S.blocks.erase(std::find(S.blocks.begin(), S.blocks.end(), (void*)U));
     }
-    pred_finish_kernel<<<(int)((np + 255) / 256), 256, 0, c->stream>>>((int)np, Dp, 1.0 / o->s, dvar);
+    pred_finish_kernel<<<(int)((np + 255) / 256), 256, 0, VL_STREAM(c)>>>((int)np, Dp, 1.0 / o->s, dvar);
     VL_CUDA(c, cudaGetLastError());
   }
   VL_TRY(stage_out(c, dmean, mean, np));

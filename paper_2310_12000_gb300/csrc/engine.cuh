@@ -77,6 +77,25 @@ __global__ void residual_kernel(int64_t total, const double* __restrict__ b, dou
     r[e] = b[e] - r[e];
 }
 
+// Calls f(LPV, NV, UNR) (as integral constants) for the row-gather shape that
+// covers ld columns: LPV lanes per row, NV vector words per lane, UNR dependency
+// rows in flight per lane.
+template <typename T, typename F>
+vl_status with_shape(int ld, F&& f) {
+  using I8 = std::integral_constant<int, 8>;
+  using I16 = std::integral_constant<int, 16>;
+  using I32 = std::integral_constant<int, 32>;
+  using I1 = std::integral_constant<int, 1>;
+  using I2 = std::integral_constant<int, 2>;
+  using I4 = std::integral_constant<int, 4>;
+  const int nvec = ld / VecT<T>::n;
+  if (nvec <= 8) return f(I8{}, I1{}, I8{});
+  if (nvec <= 16) return f(I16{}, I1{}, I8{});
+  if (nvec <= 32) return f(I32{}, I1{}, I8{});
+  if (nvec <= 64) return f(I32{}, I2{}, I4{});
+  return f(I32{}, I4{}, I2{});
+}
+
 inline int grid_for(Ctx* c, int64_t work, int block = 256) {
   int64_t g = (work + block - 1) / block;
   return (int)std::max<int64_t>(1, std::min<int64_t>(g, (int64_t)c->num_sms * 16));
@@ -114,7 +133,7 @@ struct Engine {
     m = f->m;
     t = t_;
     prec = prec_;
-    if (t < 1 || t > 32 * kMaxChunks) return fail(c, VL_ERR_INVALID_ARG, "block width t must be in [1, 256]");
+    if (t < 1 || t > 256) return fail(c, VL_ERR_INVALID_ARG, "block width t must be in [1, 256]");
     ld = lead(t);
     Aval = std::is_same<T, double>::value ? (const T*)f->A64 : (const T*)f->A32;
     valT = std::is_same<T, double>::value ? (const T*)f->valT64 : (const T*)f->valT32;
@@ -124,7 +143,7 @@ struct Engine {
     Dt = mem.get<T>(n);
     Winv = mem.get<T>(n);
     if (!W || !Dinv || !dsc || !Dt || !Winv) return fail(c, VL_ERR_OOM, "workspace exhausted (engine diagonals)");
-    diag_prep_kernel<T><<<grid_for(c, n), 256, 0, c->stream>>>(n, prec, W64, f->D64, W, Dinv, dsc, Dt, Winv);
+    diag_prep_kernel<T><<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, prec, W64, f->D64, W, Dinv, dsc, Dt, Winv);
     VL_CUDA(c, cudaGetLastError());
     const size_t vec = (size_t)n * ld;
     T** vs[] = {&u, &r, &z, &h, &v, &y, &sv};
@@ -169,8 +188,9 @@ struct Engine {
 
   // ------------------------------------------------------------------ primitives
   vl_status coldot(const T* X, const T* Y, const T* w, double* out) {
-    coldot_kernel<T><<<nblk, cb, csh, c->stream>>>(n, t, ld, rpb, X, Y, w, partial);
-    reduce_partials_kernel<<<1, 256, 0, c->stream>>>(nblk, t, partial, out);
+    ProfScope ps(c, "coldot", t);
+    coldot_kernel<T><<<nblk, cb, csh, VL_STREAM(c)>>>(n, t, ld, rpb, X, Y, w, partial);
+    reduce_partials_kernel<<<1, 256, 0, VL_STREAM(c)>>>(nblk, t, partial, out);
     VL_CUDA(c, cudaGetLastError());
     return VL_OK;
   }
@@ -179,20 +199,31 @@ struct Engine {
 
   // Y = ys o (B X)
   vl_status opB(const T* X, const T* ys, T* Yo) {
-    if (t == 1)
-      spmv_B_kernel<T, true><<<spmv_grid(), 256, 0, c->stream>>>(n, m, f->nbr, Aval, X, t, ld, ys, Yo);
-    else
-      spmv_B_kernel<T, false><<<spmv_grid(), 256, 0, c->stream>>>(n, m, f->nbr, Aval, X, t, ld, ys, Yo);
+    ProfScope ps(c, "spmv_B", t);
+    if (t == 1) {
+      spmv_B_t1_kernel<T><<<spmv_grid(), 256, 0, VL_STREAM(c)>>>(n, m, f->nbr, Aval, X, ys, Yo);
+    } else {
+      with_shape<T>(ld, [&](auto L, auto N, auto U) {
+        spmv_B_kernel<T, decltype(L)::value, decltype(N)::value, decltype(U)::value>
+            <<<spmv_grid(), 256, 0, VL_STREAM(c)>>>(n, m, f->nbr, Aval, X, ld, ys, Yo);
+        return VL_OK;
+      });
+    }
     VL_CUDA(c, cudaGetLastError());
     return VL_OK;
   }
   // Z = wx o X + B^T (ys o Y)
   vl_status opBt(const T* Y, const T* ys, const T* X, const T* wx, T* Zo) {
-    if (t == 1)
-      spmv_Bt_kernel<T, true><<<spmv_grid(), 256, 0, c->stream>>>(n, f->rowptrT, f->colT, valT, Y, ys, X, wx, t, ld, Zo);
-    else
-      spmv_Bt_kernel<T, false><<<spmv_grid(), 256, 0, c->stream>>>(n, f->rowptrT, f->colT, valT, Y, ys, X, wx, t, ld,
-                                                                   Zo);
+    ProfScope ps(c, "spmv_Bt", t);
+    if (t == 1) {
+      spmv_Bt_t1_kernel<T><<<spmv_grid(), 256, 0, VL_STREAM(c)>>>(n, f->rowptrT, f->colT, valT, Y, ys, X, wx, Zo);
+    } else {
+      with_shape<T>(ld, [&](auto L, auto N, auto U) {
+        spmv_Bt_kernel<T, decltype(L)::value, decltype(N)::value, decltype(U)::value>
+            <<<spmv_grid(), 256, 0, VL_STREAM(c)>>>(n, f->rowptrT, f->colT, valT, Y, ys, X, wx, ld, Zo);
+        return VL_OK;
+      });
+    }
     VL_CUDA(c, cudaGetLastError());
     return VL_OK;
   }
@@ -202,10 +233,9 @@ struct Engine {
     return opBt(y, nullptr, X, W, Z);
   }
 
-  template <bool FWD, bool T1>
+  template <bool FWD>
   vl_status solve_launch(const T* rhs, const T* q, T* x) {
-    auto fn = sptrsv_kernel<T, FWD, T1>;
-    int nn = n, mm = m, tt = t, l = ld;
+    int nn = n, mm = m, l = ld;
     const int32_t* task = FWD ? f->task_fwd : f->task_bwd;
     const int32_t* idx = FWD ? f->nbr : f->colT;
     const T* val = FWD ? Aval : valT;
@@ -213,19 +243,27 @@ struct Engine {
     unsigned* ready = f->ready;
     unsigned ep = ++c->epoch;
     DevStatus* st = c->dstatus;
-    void* args[] = {&nn, &mm, &task, &idx, &val, &rp, &rhs, &q, &x, &tt, &l, &ready, &ep, &st};
-    const int grid = std::max(1, std::min(resident_blocks(c, (const void*)fn, 256, 0), (n + 7) / 8));
-    VL_CUDA(c, cudaLaunchCooperativeKernel((const void*)fn, grid, 256, args, 0, c->stream));
-    return VL_OK;
+    auto launch = [&](const void* fn, void** args) -> vl_status {
+      const int grid = std::max(1, std::min(resident_blocks(c, fn, 256, 0), (n + 7) / 8));
+      ProfScope ps(c, FWD ? "sptrsv_fwd" : "sptrsv_bwd", t);
+      ++c->launches;
+      VL_CUDA(c, cudaLaunchCooperativeKernel(fn, grid, 256, args, 0, c->stream));
+      return VL_OK;
+    };
+    if (t == 1) {
+      void* args[] = {&nn, &mm, &task, &idx, &val, &rp, &rhs, &q, &x, &ready, &ep, &st};
+      return launch((const void*)sptrsv_t1_kernel<T, FWD>, args);
+    }
+    void* args[] = {&nn, &mm, &task, &idx, &val, &rp, &rhs, &q, &x, &l, &ready, &ep, &st};
+    return with_shape<T>(ld, [&](auto L, auto N, auto U) {
+      return launch((const void*)sptrsv_kernel<T, FWD, decltype(L)::value, decltype(N)::value, decltype(U)::value>,
+                    args);
+    });
   }
   // x = B^{-1} (q o rhs)
-  vl_status solveB(const T* rhs, const T* q, T* x) {
-    return t == 1 ? solve_launch<true, true>(rhs, q, x) : solve_launch<true, false>(rhs, q, x);
-  }
+  vl_status solveB(const T* rhs, const T* q, T* x) { return solve_launch<true>(rhs, q, x); }
   // x = B^{-T} (q o rhs)
-  vl_status solveBt(const T* rhs, const T* q, T* x) {
-    return t == 1 ? solve_launch<false, true>(rhs, q, x) : solve_launch<false, false>(rhs, q, x);
-  }
+  vl_status solveBt(const T* rhs, const T* q, T* x) { return solve_launch<false>(rhs, q, x); }
   // P^{-1} R for VADU / LVA: B^{-1} dsc B^{-T} R     (Section 3.1.1)
   vl_status opPinv(const T* R, T* Zo) {
     VL_TRY(solveBt(R, nullptr, sv));
@@ -239,7 +277,7 @@ struct Engine {
   // (Sigma_tilde + W^{-1}) X       (Eq. pcls2 operator)
   vl_status opA2(const T* X, T* Zo) {
     VL_TRY(opSigma(X, y));
-    add_diag_kernel<T><<<grid_for(c, (int64_t)n * ld), 256, 0, c->stream>>>(n, t, ld, y, Winv, X, Zo);
+    add_diag_kernel<T><<<grid_for(c, (int64_t)n * ld), 256, 0, VL_STREAM(c)>>>(n, t, ld, y, Winv, X, Zo);
     VL_CUDA(c, cudaGetLastError());
     return VL_OK;
   }
@@ -255,22 +293,28 @@ struct Engine {
     VL_CUDA(c, cudaMemcpyAsync(h, z, sizeof(T) * vec, cudaMemcpyDeviceToDevice, c->stream));
     VL_TRY(coldot(r, z, nullptr, S.rz));
     VL_TRY(coldot(Bm, Bm, nullptr, S.bnorm2));
-    pcg_init_kernel<<<1, 256, 0, c->stream>>>(t, S);
+    pcg_init_kernel<<<1, 256, 0, VL_STREAM(c)>>>(t, S);
     VL_CUDA(c, cudaGetLastError());
     const double tol2 = tol * tol;
     int it = 0;
     for (; it < max_iter; ++it) {
       VL_TRY(opA(h, v));
       VL_TRY(coldot(h, v, nullptr, red));
-      pcg_alpha_kernel<<<1, 256, 0, c->stream>>>(t, red, S);
-      pcg_update1_kernel<T><<<nblk, cb, csh, c->stream>>>(n, t, ld, rpb, S.alpha, U, r, h, v, partial);
-      reduce_partials_kernel<<<1, 256, 0, c->stream>>>(nblk, t, partial, S.rnorm2);
-      pcg_stop_kernel<<<1, 256, 0, c->stream>>>(t, tol2, S);
+      pcg_alpha_kernel<<<1, 256, 0, VL_STREAM(c)>>>(t, red, S);
+      {
+        ProfScope ps(c, "pcg_update", t);
+        pcg_update1_kernel<T><<<nblk, cb, csh, VL_STREAM(c)>>>(n, t, ld, rpb, S.alpha, U, r, h, v, partial);
+      }
+      reduce_partials_kernel<<<1, 256, 0, VL_STREAM(c)>>>(nblk, t, partial, S.rnorm2);
+      pcg_stop_kernel<<<1, 256, 0, VL_STREAM(c)>>>(t, tol2, S);
       VL_CUDA(c, cudaGetLastError());
       VL_TRY(opPinv(r, z));
       VL_TRY(coldot(r, z, nullptr, red2));
-      pcg_beta_kernel<<<1, 256, 0, c->stream>>>(t, red2, max_iter, S);
-      pcg_update2_kernel<T><<<grid_for(c, vec), 256, 0, c->stream>>>(vec, t, ld, S.beta, S.active, z, h);
+      pcg_beta_kernel<<<1, 256, 0, VL_STREAM(c)>>>(t, red2, max_iter, S);
+      {
+        ProfScope ps(c, "pcg_update", t);
+        pcg_update2_kernel<T><<<grid_for(c, vec), 256, 0, VL_STREAM(c)>>>(vec, t, ld, S.beta, S.active, z, h);
+      }
       VL_CUDA(c, cudaGetLastError());
       VL_CUDA(c, cudaMemcpyAsync(h_count, d_count, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
       VL_TRY(check_dev_status(c, "PCG"));

@@ -117,7 +117,8 @@ vl_status factor_rows(Ctx* c, int64_t rows, int m, const double* self_locs, cons
   const size_t smem = sizeof(double) * (size_t)kFactorWarps * (m * (m + 1) + 3 * m + 1);
   VL_CUDA(c, cudaFuncSetAttribute(factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int grid = (int)((rows + kFactorWarps - 1) / kFactorWarps);
-  factor_kernel<<<grid, 32 * kFactorWarps, smem, c->stream>>>((int)rows, m, self_locs, ref_locs, nbr, cov, sigma2, rho,
+  ProfScope ps(c, "factor", m);
+  factor_kernel<<<grid, 32 * kFactorWarps, smem, VL_STREAM(c)>>>((int)rows, m, self_locs, ref_locs, nbr, cov, sigma2, rho,
                                                               nugget, A, D, row_ids, c->dstatus);
   VL_CUDA(c, cudaGetLastError());
   return VL_OK;

@@ -142,7 +142,8 @@ struct Scratch {
 vl_status launch_coop(Ctx* c, const void* fn, int want_blocks, int block, void** args) {
   int maxb = resident_blocks(c, fn, block, 0);
   int grid = std::max(1, std::min(want_blocks, maxb));
-  VL_CUDA(c, cudaLaunchCooperativeKernel(fn, grid, block, args, 0, c->stream));
+  ++c->launches;
+    VL_CUDA(c, cudaLaunchCooperativeKernel(fn, grid, block, args, 0, c->stream));
   return VL_OK;
 }
 
@@ -151,14 +152,14 @@ vl_status task_order(Ctx* c, Scratch& S, int n, const int* lev, int32_t* task, i
   auto* k2 = (unsigned long long*)S.get(sizeof(unsigned long long) * n);
   if (!k1 || !k2) return fail(c, VL_ERR_OOM, "workspace exhausted (task order)");
   const int T = 256;
-  level_keys_kernel<<<(n + T - 1) / T, T, 0, c->stream>>>(n, lev, k1);
+  level_keys_kernel<<<(n + T - 1) / T, T, 0, VL_STREAM(c)>>>(n, lev, k1);
   VL_CUDA(c, cudaGetLastError());
   size_t tb = 0;
   cub::DeviceRadixSort::SortKeys(nullptr, tb, k1, k2, n, 0, 64, c->stream);
   void* tmp = S.get(tb);
   if (!tmp) return fail(c, VL_ERR_OOM, "workspace exhausted (task sort)");
   VL_CUDA(c, cub::DeviceRadixSort::SortKeys(tmp, tb, k1, k2, n, 0, 64, c->stream));
-  unpack_tasks_kernel<<<(n + T - 1) / T, T, 0, c->stream>>>(n, k2, task);
+  unpack_tasks_kernel<<<(n + T - 1) / T, T, 0, VL_STREAM(c)>>>(n, k2, task);
   VL_CUDA(c, cudaGetLastError());
   unsigned long long last = 0;
   VL_CUDA(c, cudaMemcpyAsync(&last, k2 + (n - 1), sizeof(last), cudaMemcpyDeviceToHost, c->stream));
@@ -180,7 +181,7 @@ vl_status build_graph_impl(Factor* f, const int32_t* N_v, const double* locs_v, 
   if (!perm) return fail(c, VL_ERR_OOM, "workspace exhausted (graph)");
   VL_TRY(morton_perm(c, locs_v, n, perm));
   const int T = 256;
-  storage_maps_kernel<<<(n + T - 1) / T, T, 0, c->stream>>>(n, m, perm, order_dev, locs_v, f->s2v, f->v2s, f->s2u,
+  storage_maps_kernel<<<(n + T - 1) / T, T, 0, VL_STREAM(c)>>>(n, m, perm, order_dev, locs_v, f->s2v, f->v2s, f->s2u,
                                                               f->u2s, f->locs_s);
   VL_CUDA(c, cudaGetLastError());
   f->nnz = 0;
@@ -202,7 +203,7 @@ vl_status build_graph_impl(Factor* f, const int32_t* N_v, const double* locs_v, 
     int32_t* tv = (int32_t*)S.get(sizeof(int32_t) * nm);
     int32_t* tv2 = (int32_t*)S.get(sizeof(int32_t) * nm);
     if (!tk || !tk2 || !tv || !tv2) return fail(c, VL_ERR_OOM, "workspace exhausted (transpose sort)");
-    translate_nbr_kernel<<<(int)((nm + T - 1) / T), T, 0, c->stream>>>(n, m, f->s2v, f->v2s, N_v, f->nbr, tk, tv,
+    translate_nbr_kernel<<<(int)((nm + T - 1) / T), T, 0, VL_STREAM(c)>>>(n, m, f->s2v, f->v2s, N_v, f->nbr, tk, tv,
                                                                         count);
     VL_CUDA(c, cudaGetLastError());
     size_t tb = 0;
@@ -211,7 +212,7 @@ vl_status build_graph_impl(Factor* f, const int32_t* N_v, const double* locs_v, 
     if (!tmp) return fail(c, VL_ERR_OOM, "workspace exhausted (transpose sort)");
     VL_CUDA(c, cub::DeviceRadixSort::SortPairs(tmp, tb, tk, tk2, tv, tv2, (int)nm, 0, 64, c->stream));
     if (nnz > 0) {
-      unpack_transpose_kernel<<<(int)((nnz + T - 1) / T), T, 0, c->stream>>>(nnz, tk2, f->colT);
+      unpack_transpose_kernel<<<(int)((nnz + T - 1) / T), T, 0, VL_STREAM(c)>>>(nnz, tk2, f->colT);
       VL_CUDA(c, cudaMemcpyAsync(f->permT, tv2, sizeof(int32_t) * nnz, cudaMemcpyDeviceToDevice, c->stream));
     }
   }
@@ -256,7 +257,7 @@ vl_status refresh_transpose_values(Factor* f) {
   const int64_t nm = f->n * (int64_t)f->m;
   const int64_t work = std::max<int64_t>(std::max<int64_t>(f->nnz, nm), 1);
   const int T = 256;
-  gather_vals_kernel<<<(int)((work + T - 1) / T), T, 0, c->stream>>>(f->nnz, f->permT, f->A64, f->valT64,
+  gather_vals_kernel<<<(int)((work + T - 1) / T), T, 0, VL_STREAM(c)>>>(f->nnz, f->permT, f->A64, f->valT64,
                                                                      f->valT32, nm, f->A32);
   VL_CUDA(c, cudaGetLastError());
   return VL_OK;

@@ -12,124 +12,206 @@
 
 namespace vl {
 
-constexpr int kMaxChunks = 8;   // t <= 256 columns per block
 
+// ----------------------------------------------------------------------------- row gathers
+// Vector word of a row block: float4 for float32, double2 for float64. Rows of a
+// block (ld columns, ld a multiple of 8) are split into ld / VEC words; LPV lanes
+// cover one row (NV words each), so a warp holds SUB = 32 / LPV dependency rows
+// in flight at once, each lane with UNR rows' loads outstanding before it
+// accumulates. Padding columns are computed too; they stay zero.
 template <typename T>
-__device__ __forceinline__ T ldcg(const T* p) {
-  return __ldcg(p);
+struct VecT;
+template <>
+struct VecT<float> {
+  using type = float4;
+  static constexpr int n = 4;
+};
+template <>
+struct VecT<double> {
+  using type = double2;
+  static constexpr int n = 2;
+};
+
+template <typename T, bool CG>
+__device__ __forceinline__ typename VecT<T>::type load_vec(const T* p) {
+  using V = typename VecT<T>::type;
+  return CG ? __ldcg(reinterpret_cast<const V*>(p)) : __ldg(reinterpret_cast<const V*>(p));
+}
+__device__ __forceinline__ void fma_vec(float* a, float s, float4 v) {
+  a[0] += s * v.x;
+  a[1] += s * v.y;
+  a[2] += s * v.z;
+  a[3] += s * v.w;
+}
+__device__ __forceinline__ void fma_vec(double* a, double s, double2 v) {
+  a[0] += s * v.x;
+  a[1] += s * v.y;
+}
+__device__ __forceinline__ void store_vec(float* p, const float* a) {
+  *reinterpret_cast<float4*>(p) = make_float4(a[0], a[1], a[2], a[3]);
+}
+__device__ __forceinline__ void store_vec(double* p, const double* a) {
+  *reinterpret_cast<double2*>(p) = make_double2(a[0], a[1]);
+}
+
+// acc (this lane's NV words of the row) += sum_e coef_e * X[idx_e, :], e in [beg, end),
+// coef_e = sgn * val[e] * (dscale ? dscale[idx_e] : 1); idx_e < 0 entries are skipped.
+template <typename T, int LPV, int NV, int UNR, bool CG>
+__device__ __forceinline__ void gather_rows(T* acc, const int32_t* __restrict__ idx, const T* __restrict__ val,
+                                            const T* __restrict__ dscale, T sgn, int beg, int end, const T* X,
+                                            int ld) {
+  constexpr int VEC = VecT<T>::n;
+  constexpr int SUB = 32 / LPV;
+  const int lane = threadIdx.x & 31;
+  const int sub = lane / LPV, sl = lane % LPV;
+  for (int e0 = beg; e0 < end; e0 += 32) {
+    const int cnt = min(32, end - e0);
+    int jl = -1;
+    T al = T(0);
+    if (lane < cnt) {
+      jl = idx[e0 + lane];
+      if (jl >= 0) al = sgn * val[e0 + lane] * (dscale ? dscale[jl] : T(1));
+    }
+    for (int q0 = 0; q0 < cnt; q0 += SUB * UNR) {
+      int j[UNR];
+      T a[UNR];
+#pragma unroll
+      for (int u = 0; u < UNR; ++u) {
+        const int q = q0 + sub + SUB * u;
+        const int src = q < 31 ? q : 31;
+        const int jj = __shfl_sync(0xffffffffu, jl, src);
+        const T aa = __shfl_sync(0xffffffffu, al, src);
+        j[u] = (q < cnt) ? jj : -1;
+        a[u] = aa;
+      }
+      typename VecT<T>::type xv[UNR][NV];
+#pragma unroll
+      for (int u = 0; u < UNR; ++u)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const int col = (sl + LPV * v) * VEC;
+          if (j[u] >= 0 && col < ld)
+            xv[u][v] = load_vec<T, CG>(X + (int64_t)j[u] * ld + col);
+          else
+            xv[u][v] = typename VecT<T>::type{};
+        }
+#pragma unroll
+      for (int u = 0; u < UNR; ++u)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) fma_vec(acc + v * VEC, j[u] >= 0 ? a[u] : T(0), xv[u][v]);
+    }
+  }
+  // combine the sub-warps' partial rows
+#pragma unroll
+  for (int off = 16; off >= LPV; off >>= 1)
+#pragma unroll
+    for (int i = 0; i < NV * VEC; ++i) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], off);
+}
+
+// acc = s1 * A[row] + s2 * Bm[row] (either pointer may be null), for lanes of sub-warp 0.
+template <typename T, int LPV, int NV>
+__device__ __forceinline__ void init_row(T* acc, int64_t row, int ld, T s1, const T* __restrict__ A1, T s2,
+                                         const T* __restrict__ A2) {
+  constexpr int VEC = VecT<T>::n;
+  const int lane = threadIdx.x & 31;
+  const int sub = lane / LPV, sl = lane % LPV;
+#pragma unroll
+  for (int i = 0; i < NV * VEC; ++i) acc[i] = T(0);
+  if (sub != 0) return;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const int col = (sl + LPV * v) * VEC;
+    if (col < ld) {
+      if (A1) fma_vec(acc + v * VEC, s1, load_vec<T, false>(A1 + row * ld + col));
+      if (A2) fma_vec(acc + v * VEC, s2, load_vec<T, false>(A2 + row * ld + col));
+    }
+  }
+}
+
+template <typename T, int LPV, int NV>
+__device__ __forceinline__ void store_row(T* Y, int64_t row, int ld, T scale, T* acc) {
+  constexpr int VEC = VecT<T>::n;
+  const int lane = threadIdx.x & 31;
+  const int sub = lane / LPV, sl = lane % LPV;
+  if (sub != 0) return;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const int col = (sl + LPV * v) * VEC;
+    if (col < ld) {
+#pragma unroll
+      for (int i = 0; i < VEC; ++i) acc[v * VEC + i] *= scale;
+      store_vec(Y + row * ld + col, acc + v * VEC);
+    }
+  }
 }
 
 // ----------------------------------------------------------------------------- B X
 // Y_s = ys_s (X_s - sum_c A[s,c] X_{nbr[s,c]})   (ys == nullptr: 1)
-template <typename T, bool T1>
-__global__ void __launch_bounds__(256) spmv_B_kernel(int n, int m, const int32_t* __restrict__ nbr,
-                                                     const T* __restrict__ A, const T* __restrict__ X, int t, int ld,
-                                                     const T* __restrict__ ys, T* __restrict__ Y) {
+template <typename T>
+__global__ void __launch_bounds__(256) spmv_B_t1_kernel(int n, int m, const int32_t* __restrict__ nbr,
+                                                        const T* __restrict__ A, const T* __restrict__ X,
+                                                        const T* __restrict__ ys, T* __restrict__ Y) {
   const int lane = threadIdx.x & 31;
   const int nw = (gridDim.x * blockDim.x) >> 5;
   for (int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < n; s += nw) {
-    const T sc = ys ? ys[s] : T(1);
     const int64_t base = (int64_t)s * m;
-    if (T1) {
-      T acc = T(0);
-      for (int c = lane; c < m; c += 32) {
-        const int j = nbr[base + c];
-        if (j >= 0) acc += A[base + c] * __ldg(&X[j]);
-      }
-      acc = warp_sum(acc);
-      if (lane == 0) Y[s] = sc * (X[s] - acc);
-    } else {
-      T acc[kMaxChunks];
-#pragma unroll
-      for (int k = 0; k < kMaxChunks; ++k) {
-        const int col = lane + 32 * k;
-        acc[k] = (col < t) ? __ldg(&X[(int64_t)s * ld + col]) : T(0);
-      }
-      for (int c0 = 0; c0 < m; c0 += 32) {
-        const int jl = (c0 + lane < m) ? nbr[base + c0 + lane] : -1;
-        const T al = (c0 + lane < m) ? A[base + c0 + lane] : T(0);
-        const int cnt = min(32, m - c0);
-        for (int q = 0; q < cnt; ++q) {
-          const int j = __shfl_sync(0xffffffffu, jl, q);
-          const T a = __shfl_sync(0xffffffffu, al, q);
-          if (j < 0) break;
-          const T* xr = X + (int64_t)j * ld;
-#pragma unroll
-          for (int k = 0; k < kMaxChunks; ++k) {
-            const int col = lane + 32 * k;
-            if (col < t) acc[k] -= a * __ldg(&xr[col]);
-          }
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < kMaxChunks; ++k) {
-        const int col = lane + 32 * k;
-        if (col < t) Y[(int64_t)s * ld + col] = sc * acc[k];
-      }
+    T acc = T(0);
+    for (int c = lane; c < m; c += 32) {
+      const int j = nbr[base + c];
+      if (j >= 0) acc += A[base + c] * __ldg(&X[j]);
     }
+    acc = warp_sum(acc);
+    if (lane == 0) Y[s] = (ys ? ys[s] : T(1)) * (X[s] - acc);
+  }
+}
+
+template <typename T, int LPV, int NV, int UNR>
+__global__ void __launch_bounds__(256) spmv_B_kernel(int n, int m, const int32_t* __restrict__ nbr,
+                                                     const T* __restrict__ A, const T* __restrict__ X, int ld,
+                                                     const T* __restrict__ ys, T* __restrict__ Y) {
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  T acc[NV * VecT<T>::n];
+  for (int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < n; s += nw) {
+    init_row<T, LPV, NV>(acc, s, ld, T(1), X, T(0), nullptr);
+    gather_rows<T, LPV, NV, UNR, false>(acc, nbr, A, nullptr, T(-1), s * m, s * m + m, X, ld);
+    store_row<T, LPV, NV>(Y, s, ld, ys ? ys[s] : T(1), acc);
   }
 }
 
 // ----------------------------------------------------------------------------- W X + B^T Y
 // Z_s = wx_s X_s + ys_s Y_s - sum_{e in row s of B^T} valT[e] ys_{i} Y_{i},  i = colT[e]
 // (X == nullptr: no diagonal term; ys == nullptr: 1)
-template <typename T, bool T1>
-__global__ void __launch_bounds__(256) spmv_Bt_kernel(int n, const int32_t* __restrict__ rowptrT,
-                                                      const int32_t* __restrict__ colT, const T* __restrict__ valT,
-                                                      const T* __restrict__ Y, const T* __restrict__ ys,
-                                                      const T* __restrict__ X, const T* __restrict__ wx, int t, int ld,
-                                                      T* __restrict__ Z) {
+template <typename T>
+__global__ void __launch_bounds__(256) spmv_Bt_t1_kernel(int n, const int32_t* __restrict__ rowptrT,
+                                                         const int32_t* __restrict__ colT, const T* __restrict__ valT,
+                                                         const T* __restrict__ Y, const T* __restrict__ ys,
+                                                         const T* __restrict__ X, const T* __restrict__ wx,
+                                                         T* __restrict__ Z) {
   const int lane = threadIdx.x & 31;
   const int nw = (gridDim.x * blockDim.x) >> 5;
   for (int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < n; s += nw) {
-    const int beg = rowptrT[s], end = rowptrT[s + 1];
-    const T yss = ys ? ys[s] : T(1);
-    const T wxs = X ? wx[s] : T(0);
-    if (T1) {
-      T acc = T(0);
-      for (int e = beg + lane; e < end; e += 32) {
-        const int i = colT[e];
-        acc += valT[e] * (ys ? ys[i] : T(1)) * __ldg(&Y[i]);
-      }
-      acc = warp_sum(acc);
-      if (lane == 0) Z[s] = (X ? wxs * X[s] : T(0)) + yss * Y[s] - acc;
-    } else {
-      T acc[kMaxChunks];
-#pragma unroll
-      for (int k = 0; k < kMaxChunks; ++k) {
-        const int col = lane + 32 * k;
-        T v = T(0);
-        if (col < t) {
-          v = yss * __ldg(&Y[(int64_t)s * ld + col]);
-          if (X) v += wxs * __ldg(&X[(int64_t)s * ld + col]);
-        }
-        acc[k] = v;
-      }
-      for (int e0 = beg; e0 < end; e0 += 32) {
-        const int cnt = min(32, end - e0);
-        int il = 0;
-        T al = T(0);
-        if (lane < cnt) {
-          il = colT[e0 + lane];
-          al = valT[e0 + lane] * (ys ? ys[il] : T(1));
-        }
-        for (int q = 0; q < cnt; ++q) {
-          const int i = __shfl_sync(0xffffffffu, il, q);
-          const T a = __shfl_sync(0xffffffffu, al, q);
-          const T* yr = Y + (int64_t)i * ld;
-#pragma unroll
-          for (int k = 0; k < kMaxChunks; ++k) {
-            const int col = lane + 32 * k;
-            if (col < t) acc[k] -= a * __ldg(&yr[col]);
-          }
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < kMaxChunks; ++k) {
-        const int col = lane + 32 * k;
-        if (col < t) Z[(int64_t)s * ld + col] = acc[k];
-      }
+    T acc = T(0);
+    for (int e = rowptrT[s] + lane; e < rowptrT[s + 1]; e += 32) {
+      const int i = colT[e];
+      acc += valT[e] * (ys ? ys[i] : T(1)) * __ldg(&Y[i]);
     }
+    acc = warp_sum(acc);
+    if (lane == 0) Z[s] = (X ? wx[s] * X[s] : T(0)) + (ys ? ys[s] : T(1)) * Y[s] - acc;
+  }
+}
+
+template <typename T, int LPV, int NV, int UNR>
+__global__ void __launch_bounds__(256) spmv_Bt_kernel(int n, const int32_t* __restrict__ rowptrT,
+                                                      const int32_t* __restrict__ colT, const T* __restrict__ valT,
+                                                      const T* __restrict__ Y, const T* __restrict__ ys,
+                                                      const T* __restrict__ X, const T* __restrict__ wx, int ld,
+                                                      T* __restrict__ Z) {
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  T acc[NV * VecT<T>::n];
+  for (int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < n; s += nw) {
+    init_row<T, LPV, NV>(acc, s, ld, ys ? ys[s] : T(1), Y, X ? wx[s] : T(0), X);
+    gather_rows<T, LPV, NV, UNR, false>(acc, colT, valT, ys, T(-1), rowptrT[s], rowptrT[s + 1], Y, ld);
+    store_row<T, LPV, NV>(Z, s, ld, T(1), acc);
   }
 }
 
@@ -140,73 +222,71 @@ __global__ void __launch_bounds__(256) spmv_Bt_kernel(int n, const int32_t* __re
 // cannot deadlock; each wait is bounded and a timeout aborts the whole solve.
 //   FWD (B^{-1}):   x_s = q_s r_s + sum_{c} A[s,c] x_{nbr[s,c]}
 //   BWD (B^{-T}):   x_s = q_s r_s + sum_{e in row s of B^T} valT[e] x_{colT[e]}
-// Values produced in this launch are read through L2 (ld.global.cg).
-template <typename T, bool FWD, bool T1>
-__global__ void __launch_bounds__(256) sptrsv_kernel(int n, int m, const int32_t* __restrict__ task,
-                                                     const int32_t* __restrict__ idx, const T* __restrict__ val,
-                                                     const int32_t* __restrict__ rowptr, const T* __restrict__ rhs,
-                                                     const T* __restrict__ q, T* x, int t, int ld, unsigned* ready,
-                                                     unsigned epoch, DevStatus* st) {
+// Flags are polled with relaxed loads and backoff; one acquire fence follows the
+// waits, and values produced in this launch are read through L2 (ld.global.cg).
+__device__ __forceinline__ unsigned ld_relaxed(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
+__device__ __forceinline__ void wait_deps(const int32_t* __restrict__ idx, int beg, int end, const unsigned* ready,
+                                          unsigned epoch, DevStatus* st, int s) {
+  const int lane = threadIdx.x & 31;
+  for (int e = beg + lane; e < end; e += 32) {
+    const int j = idx[e];
+    if (j >= 0) bounded_wait([&] { return ld_relaxed(&ready[j]) == epoch; }, st, s);
+  }
+  __syncwarp();
+  fence_acq_rel();
+}
+
+template <typename T, bool FWD>
+__global__ void __launch_bounds__(256) sptrsv_t1_kernel(int n, int m, const int32_t* __restrict__ task,
+                                                        const int32_t* __restrict__ idx, const T* __restrict__ val,
+                                                        const int32_t* __restrict__ rowptr, const T* __restrict__ rhs,
+                                                        const T* __restrict__ q, T* x, unsigned* ready,
+                                                        unsigned epoch, DevStatus* st) {
   const int lane = threadIdx.x & 31;
   const int nw = (gridDim.x * blockDim.x) >> 5;
   for (int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < n; p += nw) {
     const int s = task[p];
-    int beg, end;
-    if (FWD) {
-      beg = s * m;
-      end = beg + m;
-    } else {
-      beg = rowptr[s];
-      end = rowptr[s + 1];
-    }
+    const int beg = FWD ? s * m : rowptr[s];
+    const int end = FWD ? s * m + m : rowptr[s + 1];
+    wait_deps(idx, beg, end, ready, epoch, st, s);
+    T acc = T(0);
     for (int e = beg + lane; e < end; e += 32) {
       const int j = idx[e];
-      if (j >= 0) bounded_wait([&] { return ld_acquire(&ready[j]) == epoch; }, st, s);
+      if (j >= 0) acc += val[e] * __ldcg(&x[j]);
     }
-    __syncwarp();
-    const T qs = q ? q[s] : T(1);
-    if (T1) {
-      T acc = T(0);
-      for (int e = beg + lane; e < end; e += 32) {
-        const int j = idx[e];
-        if (j >= 0) acc += val[e] * ldcg(&x[j]);
-      }
-      acc = warp_sum(acc);
-      if (lane == 0) x[s] = qs * rhs[s] + acc;
-    } else {
-      T acc[kMaxChunks];
-#pragma unroll
-      for (int k = 0; k < kMaxChunks; ++k) {
-        const int col = lane + 32 * k;
-        acc[k] = (col < t) ? qs * rhs[(int64_t)s * ld + col] : T(0);
-      }
-      for (int e0 = beg; e0 < end; e0 += 32) {
-        const int cnt = min(32, end - e0);
-        const int jl = lane < cnt ? idx[e0 + lane] : -1;
-        const T al = lane < cnt ? val[e0 + lane] : T(0);
-        for (int qq = 0; qq < cnt; ++qq) {
-          const int j = __shfl_sync(0xffffffffu, jl, qq);
-          const T a = __shfl_sync(0xffffffffu, al, qq);
-          if (j < 0) continue;
-          const T* xr = x + (int64_t)j * ld;
-#pragma unroll
-          for (int k = 0; k < kMaxChunks; ++k) {
-            const int col = lane + 32 * k;
-            if (col < t) acc[k] += a * ldcg(&xr[col]);
-          }
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < kMaxChunks; ++k) {
-        const int col = lane + 32 * k;
-        if (col < t) x[(int64_t)s * ld + col] = acc[k];
-      }
-    }
-    __syncwarp();
+    acc = warp_sum(acc);
     if (lane == 0) {
-      __threadfence();
+      x[s] = (q ? q[s] : T(1)) * rhs[s] + acc;
       st_release(&ready[s], epoch);
     }
+  }
+}
+
+template <typename T, bool FWD, int LPV, int NV, int UNR>
+__global__ void __launch_bounds__(256) sptrsv_kernel(int n, int m, const int32_t* __restrict__ task,
+                                                     const int32_t* __restrict__ idx, const T* __restrict__ val,
+                                                     const int32_t* __restrict__ rowptr, const T* __restrict__ rhs,
+                                                     const T* __restrict__ q, T* x, int ld, unsigned* ready,
+                                                     unsigned epoch, DevStatus* st) {
+  const int lane = threadIdx.x & 31;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  T acc[NV * VecT<T>::n];
+  for (int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < n; p += nw) {
+    const int s = task[p];
+    const int beg = FWD ? s * m : rowptr[s];
+    const int end = FWD ? s * m + m : rowptr[s + 1];
+    init_row<T, LPV, NV>(acc, s, ld, q ? q[s] : T(1), rhs, T(0), nullptr);
+    wait_deps(idx, beg, end, ready, epoch, st, s);
+    gather_rows<T, LPV, NV, UNR, true>(acc, idx, val, nullptr, T(1), beg, end, x, ld);
+    store_row<T, LPV, NV>(x, s, ld, T(1), acc);
+    __syncwarp();
+    if (lane == 0) st_release(&ready[s], epoch);
   }
 }
 

@@ -161,11 +161,11 @@ vl_status bbox(Ctx* c, const double* locs, int64_t n, const double* extra, int64
   if (!part) return fail(c, VL_ERR_OOM, "workspace exhausted (bbox)");
   int used = 0;
   if (n > 0) {
-    minmax_kernel<<<nb, 256, 0, c->stream>>>(reinterpret_cast<const double2*>(locs), (int)n, part);
+    minmax_kernel<<<nb, 256, 0, VL_STREAM(c)>>>(reinterpret_cast<const double2*>(locs), (int)n, part);
     used += nb;
   }
   if (n_extra > 0) {
-    minmax_kernel<<<nb, 256, 0, c->stream>>>(reinterpret_cast<const double2*>(extra), (int)n_extra, part + used);
+    minmax_kernel<<<nb, 256, 0, VL_STREAM(c)>>>(reinterpret_cast<const double2*>(extra), (int)n_extra, part + used);
     used += nb;
   }
   std::vector<double4> h(used);
@@ -256,7 +256,7 @@ static vl_status build_grid(Ctx* c, GridMem& gm, const double2* pts, int n, cons
   VL_CUDA(c, cudaMemsetAsync(count, 0, sizeof(int) * (ncell + 1), c->stream));
   const int T = 256;
   if (n > 0)
-    cell_keys_kernel<<<(n + T - 1) / T, T, 0, c->stream>>>(pts, n, G.x0, G.y0, G.inv_h, G.gx, G.gy, key, val, count);
+    cell_keys_kernel<<<(n + T - 1) / T, T, 0, VL_STREAM(c)>>>(pts, n, G.x0, G.y0, G.inv_h, G.gx, G.gy, key, val, count);
   VL_CUDA(c, cudaGetLastError());
   size_t tb1 = 0, tb2 = 0;
   int bits = 1;
@@ -267,7 +267,7 @@ static vl_status build_grid(Ctx* c, GridMem& gm, const double2* pts, int n, cons
   if (!tmp) return fail(c, VL_ERR_OOM, "workspace exhausted (kNN sort)");
   VL_CUDA(c, cub::DeviceRadixSort::SortPairs(tmp, tb1, key, key2, val, val2, n, 0, bits, c->stream));
   VL_CUDA(c, cub::DeviceScan::ExclusiveSum(tmp, tb2, count, start, ncell + 1, c->stream));
-  if (n > 0) gather_pts_kernel<<<(n + T - 1) / T, T, 0, c->stream>>>(pts, val2, n, cpts);
+  if (n > 0) gather_pts_kernel<<<(n + T - 1) / T, T, 0, VL_STREAM(c)>>>(pts, val2, n, cpts);
   VL_CUDA(c, cudaGetLastError());
   G.cell_start = start;
   G.cell_idx = val2;
@@ -287,7 +287,8 @@ vl_status knn_prev_dev(Ctx* c, const double* locs_v, int64_t n, int m, int32_t* 
   Grid G;
   VL_TRY(build_grid(c, gm, reinterpret_cast<const double2*>(locs_v), (int)n, bb, G));
   const int T = 128;
-  knn_prev_kernel<<<(int)((n + T - 1) / T), T, 0, c->stream>>>(reinterpret_cast<const double2*>(locs_v), (int)n, m, G, N_out);
+  ProfScope ps(c, "knn", m);
+  knn_prev_kernel<<<(int)((n + T - 1) / T), T, 0, VL_STREAM(c)>>>(reinterpret_cast<const double2*>(locs_v), (int)n, m, G, N_out);
   VL_CUDA(c, cudaGetLastError());
   VL_CUDA(c, cudaStreamSynchronize(c->stream));  // the grid lives in scratch
   return VL_OK;
@@ -307,7 +308,7 @@ vl_status knn_cross_dev(Ctx* c, const double* train, int64_t n, const double* te
   Grid G;
   VL_TRY(build_grid(c, gm, reinterpret_cast<const double2*>(train), (int)n, bb, G));
   const int T = 128;
-  knn_cross_kernel<<<(int)((np + T - 1) / T), T, 0, c->stream>>>(reinterpret_cast<const double2*>(test), (int)np,
+  knn_cross_kernel<<<(int)((np + T - 1) / T), T, 0, VL_STREAM(c)>>>(reinterpret_cast<const double2*>(test), (int)np,
                                                                    (int)n, m, G, N_out);
   VL_CUDA(c, cudaGetLastError());
   VL_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -348,7 +349,7 @@ vl_status morton_perm(Ctx* c, const double* locs, int64_t n, int32_t* perm_out) 
   int* val = (int*)gm.get(sizeof(int) * n);
   if (!key || !key2 || !val) return fail(c, VL_ERR_OOM, "workspace exhausted (Morton)");
   const int T = 256;
-  morton_kernel<<<(int)((n + T - 1) / T), T, 0, c->stream>>>(reinterpret_cast<const double2*>(locs), (int)n, bb[0], sx,
+  morton_kernel<<<(int)((n + T - 1) / T), T, 0, VL_STREAM(c)>>>(reinterpret_cast<const double2*>(locs), (int)n, bb[0], sx,
                                                             bb[2], sy, key, val);
   VL_CUDA(c, cudaGetLastError());
   size_t tb = 0;

@@ -74,6 +74,7 @@ vl_status fail(Ctx* c, vl_status s, const std::string& msg) {
 vl_status check_dev_status(Ctx* c, const char* what) {
   VL_CUDA(c, cudaMemcpyAsync(c->hstatus, c->dstatus, sizeof(DevStatus), cudaMemcpyDeviceToHost, c->stream));
   VL_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (c->prof.on && c->prof.pending.size() > 256) prof_drain(c);
   if (c->hstatus->code != 0) {
     const int code = c->hstatus->code, row = c->hstatus->row;
     VL_CUDA(c, cudaMemsetAsync(c->dstatus, 0, sizeof(DevStatus), c->stream));
@@ -88,6 +89,52 @@ vl_status check_dev_status(Ctx* c, const char* what) {
     return fail(c, (vl_status)code, buf);
   }
   return VL_OK;
+}
+
+static cudaEvent_t pool_get(Ctx* c) {
+  if (!c->prof.pool.empty()) {
+    cudaEvent_t e = c->prof.pool.back();
+    c->prof.pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+ProfScope::ProfScope(Ctx* ctx, const char* key, int t) : c(ctx) {
+  if (!c->prof.on) return;
+  Profiler::Pending p{key, t, pool_get(c), pool_get(c)};
+  cudaEventRecord(p.a, c->stream);
+  c->prof.pending.push_back(p);
+  idx = (int)c->prof.pending.size() - 1;
+}
+
+ProfScope::~ProfScope() {
+  if (idx < 0) return;
+  cudaEventRecord(c->prof.pending[idx].b, c->stream);
+}
+
+void prof_drain(Ctx* c) {
+  for (auto& p : c->prof.pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      auto& a = c->prof.acc[{p.key, p.t}];
+      a.ms += ms;
+      a.launches += 1;
+    } else {
+      cudaGetLastError();
+    }
+    c->prof.pool.push_back(p.a);
+    c->prof.pool.push_back(p.b);
+  }
+  c->prof.pending.clear();
+}
+
+void prof_release(Ctx* c) {
+  prof_drain(c);
+  for (cudaEvent_t e : c->prof.pool) cudaEventDestroy(e);
+  c->prof.pool.clear();
 }
 
 int resident_blocks(Ctx* c, const void* kernel, int block, size_t smem) {

@@ -52,7 +52,7 @@ __device__ __forceinline__ bool bounded_wait(Pred pred, DevStatus* st, int row) 
         return false;
       }
     }
-    if (it > 64) __nanosleep(64);
+    __nanosleep(it < 4 ? 32 : (it < 16 ? 64 : 256));
   }
 }
 

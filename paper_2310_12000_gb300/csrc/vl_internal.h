@@ -42,6 +42,23 @@ class Arena {
   std::unordered_map<size_t, size_t> used_;  // offset -> bytes
 };
 
+// Kernel-class timing with CUDA events (enabled by vl_profile_enable).
+struct Profiler {
+  bool on = false;
+  struct Pending {
+    std::string key;
+    int t;
+    cudaEvent_t a, b;
+  };
+  struct Acc {
+    double ms = 0.0;
+    int64_t launches = 0;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> pool;
+  std::map<std::pair<std::string, int>, Acc> acc;
+};
+
 struct Ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -56,7 +73,22 @@ struct Ctx {
   int num_sms = 0;
   unsigned epoch = 0;             // sync-free solve flag generation
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  Profiler prof;
+  int64_t launches = 0;           // kernels launched on this context
 };
+
+// Launch-configuration stream argument that also counts the launch.
+#define VL_STREAM(c) (++(c)->launches, (c)->stream)
+
+// Brackets the launches issued in its lifetime when profiling is on.
+struct ProfScope {
+  Ctx* c;
+  int idx = -1;
+  ProfScope(Ctx* ctx, const char* key, int t);
+  ~ProfScope();
+};
+void prof_drain(Ctx* c);   // resolve finished event pairs (stream must be idle)
+void prof_release(Ctx* c); // destroy all events
 
 // RAII list of arena blocks owned by a handle.
 struct Owned {
@@ -117,6 +149,7 @@ struct State {
   double* W = nullptr;
   int last_t = 0;
   std::vector<double> h_gammas;   // last SLQ gammas
+  vl_stats mode_stats{};          // diagnostics of the Newton solve
 };
 
 // ----------------------------------------------------------------------------- helpers

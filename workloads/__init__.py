@@ -80,7 +80,8 @@ def latent_exact(locs: np.ndarray, cov: int, sigma2: float, rho: float, rng) -> 
     return np.linalg.cholesky(K) @ rng.standard_normal(len(locs))
 
 
-def latent_rff(locs: np.ndarray, cov: int, sigma2: float, rho: float, rng, K: int = 512) -> np.ndarray:
+def latent_rff(locs: np.ndarray, cov: int, sigma2: float, rho: float, rng, K: int = 0) -> np.ndarray:
+    K = K or (512 if len(locs) <= 200_000 else 256)
     nu = 0.5 if cov == COV_EXPONENTIAL else 1.5
     g = rng.standard_normal((K, 2))
     u = rng.chisquare(2.0 * nu, size=K)
@@ -113,8 +114,12 @@ def grid_with_gaps(nx: int, ny: int, remove: int, rng) -> np.ndarray:
     while removed < remove:
         w, h = rng.uniform(0.01, 0.15, size=2)
         cx, cy = rng.uniform(0.0, 1.0, size=2)
-        inside = keep & (np.abs(pts[:, 0] - cx) <= w / 2) & (np.abs(pts[:, 1] - cy) <= h / 2)
-        idx = np.nonzero(inside)[0]
+        # candidate grid block (one cell of slack), then the exact membership test
+        i0, i1 = max(0, int((cx - w / 2) * nx) - 1), min(nx, int((cx + w / 2) * nx) + 2)
+        j0, j1 = max(0, int((cy - h / 2) * ny) - 1), min(ny, int((cy + h / 2) * ny) + 2)
+        cand = (np.arange(i0, i1)[:, None] * ny + np.arange(j0, j1)[None, :]).ravel()
+        inside = keep[cand] & (np.abs(pts[cand, 0] - cx) <= w / 2) & (np.abs(pts[cand, 1] - cy) <= h / 2)
+        idx = cand[inside]
         take = idx[: remove - removed]
         keep[take] = False
         removed += len(take)
