@@ -203,11 +203,18 @@ vl_status vl_slq_gammas(const vl_state* s, double* gammas, int t);
 vl_status vl_pred_var(vl_state* s, const double* test_locs, int64_t np, const double* Fp,
                       const vl_opts* opts, double* mean, double* var, vl_stats* stats);
 
-/* Kernel timing. While enabled, every launch of the library's hot kernels is
+/* Kernel timing. While enabled (enable >= 1), every launch of the library's hot kernels is
  * bracketed by a pair of CUDA events on the context's stream, grouped by kernel
  * class and block width: "sptrsv_fwd", "sptrsv_bwd", "spmv_B", "spmv_Bt",
  * "pcg_update", "coldot", "factor", "knn". Costs two event records per launch. */
 vl_status vl_profile_enable(vl_ctx* ctx, int enable);
+/* With enable >= 2 every triangular solve also records block 0's SM clock at each
+ * level boundary; this returns the last such trace of class `cls` ("sptrsv_fwd" /
+ * "sptrsv_bwd") at block width t: *len = levels + 1 clock values (cycles), and the
+ * head / tail level cut used (levels [0, l_head) and [l_tail, nlev) ran in block 0
+ * alone). Costs a stream synchronisation per solve. */
+vl_status vl_profile_trace(vl_ctx* ctx, const char* cls, int t, long long* out, int cap, int* len,
+                           int* l_head, int* l_tail);
 /* Device time (ms, summed) and launch count of class `cls` at block width t
  * (t = 0: all widths) since the last reset; reset != 0 clears every class.
  * cls = "all" gives the number of kernels launched on the context (counted

@@ -101,6 +101,7 @@ def library():
         "vl_ctx_mem": (st, [vp, vp, vp]),
         "vl_profile_enable": (st, [vp, i32]),
         "vl_profile_read": (st, [vp, C.c_char_p, i32, vp, vp, i32]),
+        "vl_profile_trace": (st, [vp, C.c_char_p, i32, vp, i32, vp, vp, vp]),
         "vl_build_factor": (st, [vp, vp, i64, vp, i32, d, d, i32, vp, vp]),
         "vl_factor_refit": (st, [vp, d, d, vp]),
         "vl_factor_export": (st, [vp, vp, vp, vp, vp, vp]),
@@ -211,8 +212,17 @@ class Context:
         self.check(self.lib.vl_ctx_mem(self.h, C.byref(a), C.byref(b)))
         return a.value, b.value
 
-    def profile(self, enable: bool = True):
-        self.check(self.lib.vl_profile_enable(self.h, 1 if enable else 0))
+    def profile(self, enable=True):
+        """enable: False/0 off, True/1 kernel timing, 2 also per-level solve traces."""
+        self.check(self.lib.vl_profile_enable(self.h, int(enable)))
+
+    def profile_trace(self, cls: str, t: int):
+        cap = 1 << 16
+        buf = np.zeros(cap, np.int64)
+        ln, lh, lt = C.c_int(), C.c_int(), C.c_int()
+        self.check(self.lib.vl_profile_trace(self.h, cls.encode(), t, buf.ctypes.data, cap, C.byref(ln),
+                                             C.byref(lh), C.byref(lt)))
+        return buf[:ln.value].copy(), lh.value, lt.value
 
     def profile_read(self, cls: str, t: int = 0, reset: bool = False):
         ms, cnt = C.c_double(), C.c_int64()

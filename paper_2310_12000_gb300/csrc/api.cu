@@ -587,7 +587,8 @@ vl_status vl_ctx_create(int device, void* cuda_stream, void* workspace, size_t w
   if (cudaMallocHost(&c->pinned, c->pinned_bytes) != cudaSuccess) return bail(VL_ERR_CUDA);
   c->hstatus = reinterpret_cast<DevStatus*>(c->pinned + 1024);
   c->dstatus = static_cast<DevStatus*>(c->arena.alloc(sizeof(DevStatus)));
-  if (!c->dstatus) return bail(VL_ERR_OOM);
+  c->gbar = static_cast<unsigned*>(c->arena.alloc(2 * sizeof(unsigned)));
+  if (!c->dstatus || !c->gbar) return bail(VL_ERR_OOM);
   if (cudaMemsetAsync(c->dstatus, 0, sizeof(DevStatus), c->stream) != cudaSuccess) return bail(VL_ERR_CUDA);
   if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) return bail(VL_ERR_CUDA);
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return bail(VL_ERR_CUDA);
@@ -619,6 +620,25 @@ vl_status vl_profile_enable(vl_ctx* c, int enable) {
   VL_CUDA(c, cudaStreamSynchronize(c->stream));
   prof_drain(c);
   c->prof.on = enable != 0;
+  c->prof.trace = enable >= 2;
+  return VL_OK;
+}
+
+vl_status vl_profile_trace(vl_ctx* c, const char* cls, int t, long long* out, int cap, int* len, int* l_head,
+                           int* l_tail) {
+  if (!c || !cls) return VL_ERR_INVALID_ARG;
+  auto it = c->prof.traces.find({cls, t});
+  if (it == c->prof.traces.end()) {
+    if (len) *len = 0;
+    return VL_OK;
+  }
+  const int n = (int)it->second.size();
+  if (len) *len = n;
+  if (out)
+    for (int i = 0; i < std::min(n, cap); ++i) out[i] = it->second[i];
+  auto ct = c->prof.cuts[{cls, t}];
+  if (l_head) *l_head = ct.first;
+  if (l_tail) *l_tail = ct.second;
   return VL_OK;
 }
 
@@ -743,12 +763,9 @@ vl_status vl_build_factor(vl_ctx* c, const double* locs, int64_t n, const int32_
   f->lev_bwd = f->mem.get<int32_t>(n);
   f->task_fwd = f->mem.get<int32_t>(n);
   f->task_bwd = f->mem.get<int32_t>(n);
-  f->ready = f->mem.get<unsigned>(n);
   if (!f->locs_v || !f->locs_s || !f->s2v || !f->v2s || !f->s2u || !f->u2s || !f->nbr || !f->A64 || !f->A32 ||
-      !f->D64 || !f->lev_fwd || !f->lev_bwd || !f->task_fwd || !f->task_bwd || !f->ready)
+      !f->D64 || !f->lev_fwd || !f->lev_bwd || !f->task_fwd || !f->task_bwd)
     return bail(fail(c, VL_ERR_OOM, "workspace exhausted (factor)"));
-  if (cudaMemsetAsync(f->ready, 0, sizeof(unsigned) * n, c->stream) != cudaSuccess)
-    return bail(cuda_fail(c, cudaGetLastError(), "memset"));
   gather2_kernel<<<(int)((n + 255) / 256), 256, 0, VL_STREAM(c)>>>((int)n, dl, dord, f->locs_v);
   int32_t* Nv = S.get<int32_t>(std::max<int64_t>(nm, 1));
   if (!Nv) return bail(fail(c, VL_ERR_OOM, "workspace exhausted (neighbours)"));

@@ -201,7 +201,7 @@ struct Engine {
   vl_status opB(const T* X, const T* ys, T* Yo) {
     ProfScope ps(c, "spmv_B", t);
     if (t == 1) {
-      spmv_B_t1_kernel<T><<<spmv_grid(), 256, 0, VL_STREAM(c)>>>(n, m, f->nbr, Aval, X, ys, Yo);
+      spmv_B_t1_kernel<T, 8><<<spmv_grid(), 256, 0, VL_STREAM(c)>>>(n, m, f->nbr, Aval, X, ys, Yo);
     } else {
       with_shape<T>(ld, [&](auto L, auto N, auto U) {
         spmv_B_kernel<T, decltype(L)::value, decltype(N)::value, decltype(U)::value>
@@ -216,7 +216,7 @@ struct Engine {
   vl_status opBt(const T* Y, const T* ys, const T* X, const T* wx, T* Zo) {
     ProfScope ps(c, "spmv_Bt", t);
     if (t == 1) {
-      spmv_Bt_t1_kernel<T><<<spmv_grid(), 256, 0, VL_STREAM(c)>>>(n, f->rowptrT, f->colT, valT, Y, ys, X, wx, Zo);
+      spmv_Bt_t1_kernel<T, 8><<<spmv_grid(), 256, 0, VL_STREAM(c)>>>(n, f->rowptrT, f->colT, valT, Y, ys, X, wx, Zo);
     } else {
       with_shape<T>(ld, [&](auto L, auto N, auto U) {
         spmv_Bt_kernel<T, decltype(L)::value, decltype(N)::value, decltype(U)::value>
@@ -233,31 +233,71 @@ struct Engine {
     return opBt(y, nullptr, X, W, Z);
   }
 
+  // Head/tail cut of the level profile: leading and trailing levels whose gathers
+  // (rows + dependencies, in vector words) fit one block's round of loads run in
+  // block 0 alone; the rest use the whole grid with a barrier per level.
+  static void level_cut(const std::vector<int32_t>& lp, const std::vector<int64_t>& work, int words, int* l_head,
+                        int* l_tail) {
+    const int nlev = (int)lp.size() - 1;
+    const int64_t cap = 4096;   // vector loads one 512-thread block issues in ~one round trip
+    auto narrow = [&](int l) { return (work[l] + (lp[l + 1] - lp[l])) * (int64_t)words <= cap; };
+    int h = 0;
+    while (h < nlev && narrow(h)) ++h;
+    int tl = nlev;
+    while (tl > h && narrow(tl - 1)) --tl;
+    *l_head = h;
+    *l_tail = tl;
+  }
+
   template <bool FWD>
   vl_status solve_launch(const T* rhs, const T* q, T* x) {
-    int nn = n, mm = m, l = ld;
-    const int32_t* task = FWD ? f->task_fwd : f->task_bwd;
+    const std::vector<int32_t>& hl = FWD ? f->h_lptr_fwd : f->h_lptr_bwd;
+    const std::vector<int64_t>& hw = FWD ? f->h_lwork_fwd : f->h_lwork_bwd;
+    LevelPlan L{FWD ? f->task_fwd : f->task_bwd, FWD ? f->lptr_fwd : f->lptr_bwd, 0, 0, (int)hl.size() - 1, c->gbar,
+                c->dstatus, nullptr};
+    const char* cls = FWD ? "sptrsv_fwd" : "sptrsv_bwd";
+    if (c->prof.trace) {
+      if (c->prof.dtrace_len < hl.size()) {
+        if (c->prof.dtrace) c->arena.release(c->prof.dtrace);
+        c->prof.dtrace = static_cast<long long*>(c->arena.alloc(sizeof(long long) * hl.size()));
+        c->prof.dtrace_len = c->prof.dtrace ? hl.size() : 0;
+      }
+      L.trace = c->prof.dtrace;
+    }
+    int mm = m, l = ld;
     const int32_t* idx = FWD ? f->nbr : f->colT;
     const T* val = FWD ? Aval : valT;
     const int32_t* rp = FWD ? nullptr : f->rowptrT;
-    unsigned* ready = f->ready;
-    unsigned ep = ++c->epoch;
-    DevStatus* st = c->dstatus;
-    auto launch = [&](const void* fn, void** args) -> vl_status {
-      const int grid = std::max(1, std::min(resident_blocks(c, fn, 256, 0), (n + 7) / 8));
-      ProfScope ps(c, FWD ? "sptrsv_fwd" : "sptrsv_bwd", t);
-      ++c->launches;
-      VL_CUDA(c, cudaLaunchCooperativeKernel(fn, grid, 256, args, 0, c->stream));
+    VL_CUDA(c, cudaMemsetAsync(c->gbar, 0, 2 * sizeof(unsigned), c->stream));
+    auto launch = [&](const void* fn, void** args, int lpv) -> vl_status {
+      const int tpb = 16 * (32 / lpv);   // row teams per 512-thread block
+      level_cut(hl, hw, t == 1 ? 1 : ld / VecT<T>::n, &L.l_head, &L.l_tail);
+      const int body_rows = hl[L.l_tail] - hl[L.l_head];
+      // at most two blocks per SM: fewer arrivals per grid barrier
+      const int maxb = std::min(resident_blocks(c, fn, 512, 0), 2 * c->num_sms);
+      const int grid = std::max(1, std::min(maxb, (body_rows + tpb - 1) / tpb));
+      {
+        ProfScope ps(c, cls, t);
+        ++c->launches;
+        VL_CUDA(c, cudaLaunchCooperativeKernel(fn, grid, 512, args, 0, c->stream));
+      }
+      if (L.trace) {
+        std::vector<long long>& h = c->prof.traces[{cls, t}];
+        h.resize(hl.size());
+        VL_CUDA(c, cudaMemcpyAsync(h.data(), L.trace, sizeof(long long) * h.size(), cudaMemcpyDeviceToHost, c->stream));
+        VL_CUDA(c, cudaStreamSynchronize(c->stream));
+        c->prof.cuts[{cls, t}] = {L.l_head, L.l_tail};
+      }
       return VL_OK;
     };
     if (t == 1) {
-      void* args[] = {&nn, &mm, &task, &idx, &val, &rp, &rhs, &q, &x, &ready, &ep, &st};
-      return launch((const void*)sptrsv_t1_kernel<T, FWD>, args);
+      void* args[] = {&L, &mm, &idx, &val, &rp, &rhs, &q, &x};
+      return launch((const void*)sptrsv_t1_kernel<T, FWD, 8>, args, 8);
     }
-    void* args[] = {&nn, &mm, &task, &idx, &val, &rp, &rhs, &q, &x, &l, &ready, &ep, &st};
-    return with_shape<T>(ld, [&](auto L, auto N, auto U) {
-      return launch((const void*)sptrsv_kernel<T, FWD, decltype(L)::value, decltype(N)::value, decltype(U)::value>,
-                    args);
+    void* args[] = {&L, &mm, &idx, &val, &rp, &rhs, &q, &x, &l};
+    return with_shape<T>(ld, [&](auto Lc, auto N, auto U) {
+      constexpr int LPV = decltype(Lc)::value;
+      return launch((const void*)sptrsv_kernel<T, FWD, LPV, decltype(N)::value, decltype(U)::value>, args, LPV);
     });
   }
   // x = B^{-1} (q o rhs)

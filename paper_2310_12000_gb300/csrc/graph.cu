@@ -115,14 +115,34 @@ __global__ void levels_bwd_kernel(int n, const int32_t* __restrict__ rowptrT, co
   }
 }
 
+// work[lev(s)] += number of dependencies of row s
+__global__ void level_work_kernel(int n, int m, const int* __restrict__ lev, const int32_t* __restrict__ nbr,
+                                  const int32_t* __restrict__ rowptrT, unsigned long long* __restrict__ work) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  int d = 0;
+  if (nbr) {
+    for (int c = 0; c < m; ++c) d += nbr[(int64_t)s * m + c] >= 0;
+  } else {
+    d = rowptrT[s + 1] - rowptrT[s];
+  }
+  atomicAdd(&work[lev[s]], (unsigned long long)d);
+}
+
 __global__ void level_keys_kernel(int n, const int* __restrict__ lev, unsigned long long* __restrict__ key) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s < n) key[s] = ((unsigned long long)(unsigned)lev[s] << 32) | (unsigned)s;
 }
 
-__global__ void unpack_tasks_kernel(int n, const unsigned long long* __restrict__ key, int32_t* __restrict__ task) {
+__global__ void unpack_tasks_kernel(int n, const unsigned long long* __restrict__ key, int32_t* __restrict__ task,
+                                    int32_t* __restrict__ lptr) {
   int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p < n) task[p] = (int32_t)(key[p] & 0xffffffffULL);
+  if (p >= n) return;
+  task[p] = (int32_t)(key[p] & 0xffffffffULL);
+  const int l = (int)(key[p] >> 32);
+  // levels are dense (0..nlev-1), so each level starts where the key's level changes
+  if (p == 0 || (int)(key[p - 1] >> 32) != l) lptr[l] = p;
+  if (p == n - 1) lptr[l + 1] = n;
 }
 
 namespace {
@@ -147,7 +167,8 @@ vl_status launch_coop(Ctx* c, const void* fn, int want_blocks, int block, void**
   return VL_OK;
 }
 
-vl_status task_order(Ctx* c, Scratch& S, int n, const int* lev, int32_t* task, int* nlev) {
+vl_status task_order(Ctx* c, Scratch& S, int n, const int* lev, int32_t* task, int* nlev, int32_t** lptr,
+                     std::vector<int32_t>& h_lptr, Owned& own) {
   auto* k1 = (unsigned long long*)S.get(sizeof(unsigned long long) * n);
   auto* k2 = (unsigned long long*)S.get(sizeof(unsigned long long) * n);
   if (!k1 || !k2) return fail(c, VL_ERR_OOM, "workspace exhausted (task order)");
@@ -159,12 +180,17 @@ vl_status task_order(Ctx* c, Scratch& S, int n, const int* lev, int32_t* task, i
   void* tmp = S.get(tb);
   if (!tmp) return fail(c, VL_ERR_OOM, "workspace exhausted (task sort)");
   VL_CUDA(c, cub::DeviceRadixSort::SortKeys(tmp, tb, k1, k2, n, 0, 64, c->stream));
-  unpack_tasks_kernel<<<(n + T - 1) / T, T, 0, VL_STREAM(c)>>>(n, k2, task);
-  VL_CUDA(c, cudaGetLastError());
   unsigned long long last = 0;
   VL_CUDA(c, cudaMemcpyAsync(&last, k2 + (n - 1), sizeof(last), cudaMemcpyDeviceToHost, c->stream));
   VL_CUDA(c, cudaStreamSynchronize(c->stream));
   *nlev = (int)(last >> 32) + 1;
+  *lptr = own.get<int32_t>(*nlev + 1);
+  if (!*lptr) return fail(c, VL_ERR_OOM, "workspace exhausted (level pointers)");
+  unpack_tasks_kernel<<<(n + T - 1) / T, T, 0, VL_STREAM(c)>>>(n, k2, task, *lptr);
+  VL_CUDA(c, cudaGetLastError());
+  h_lptr.resize(*nlev + 1);
+  VL_CUDA(c, cudaMemcpyAsync(h_lptr.data(), *lptr, sizeof(int32_t) * (*nlev + 1), cudaMemcpyDeviceToHost, c->stream));
+  VL_CUDA(c, cudaStreamSynchronize(c->stream));
   return VL_OK;
 }
 }  // namespace
@@ -247,8 +273,21 @@ vl_status build_graph_impl(Factor* f, const int32_t* N_v, const double* locs_v, 
     VL_TRY(launch_coop(c, (const void*)levels_bwd_kernel, (n + 7) / 8, 256, args));
   }
   VL_TRY(check_dev_status(c, "level schedule"));
-  VL_TRY(task_order(c, S, n, f->lev_fwd, f->task_fwd, &f->nlev_fwd));
-  VL_TRY(task_order(c, S, n, f->lev_bwd, f->task_bwd, &f->nlev_bwd));
+  VL_TRY(task_order(c, S, n, f->lev_fwd, f->task_fwd, &f->nlev_fwd, &f->lptr_fwd, f->h_lptr_fwd, f->mem));
+  VL_TRY(task_order(c, S, n, f->lev_bwd, f->task_bwd, &f->nlev_bwd, &f->lptr_bwd, f->h_lptr_bwd, f->mem));
+  for (int dir = 0; dir < 2; ++dir) {
+    const int nl = dir == 0 ? f->nlev_fwd : f->nlev_bwd;
+    auto* w = (unsigned long long*)S.get(sizeof(unsigned long long) * nl);
+    if (!w) return fail(c, VL_ERR_OOM, "workspace exhausted (level work)");
+    VL_CUDA(c, cudaMemsetAsync(w, 0, sizeof(unsigned long long) * nl, c->stream));
+    level_work_kernel<<<(n + T - 1) / T, T, 0, VL_STREAM(c)>>>(n, m, dir == 0 ? f->lev_fwd : f->lev_bwd,
+                                                              dir == 0 ? f->nbr : nullptr, f->rowptrT, w);
+    VL_CUDA(c, cudaGetLastError());
+    std::vector<int64_t>& hw = dir == 0 ? f->h_lwork_fwd : f->h_lwork_bwd;
+    hw.resize(nl);
+    VL_CUDA(c, cudaMemcpyAsync(hw.data(), w, sizeof(int64_t) * nl, cudaMemcpyDeviceToHost, c->stream));
+  }
+  VL_CUDA(c, cudaStreamSynchronize(c->stream));
   return VL_OK;
 }
 

@@ -13,12 +13,15 @@
 namespace vl {
 
 
-// ----------------------------------------------------------------------------- row gathers
-// Vector word of a row block: float4 for float32, double2 for float64. Rows of a
-// block (ld columns, ld a multiple of 8) are split into ld / VEC words; LPV lanes
-// cover one row (NV words each), so a warp holds SUB = 32 / LPV dependency rows
-// in flight at once, each lane with UNR rows' loads outstanding before it
-// accumulates. Padding columns are computed too; they stay zero.
+// ----------------------------------------------------------------------------- row teams
+// A team of LPV lanes (LPV in {8, 16, 32}) owns one row; a warp runs 32 / LPV
+// teams on different rows at once. Teams synchronise only within their own lane
+// segment (masked shuffles), so teams of one warp never wait on each other.
+// Row blocks (ld columns, ld a multiple of 8) are read as float4 / double2 words,
+// NV words per lane; dependency rows are broadcast inside the team UNR at a time,
+// so each lane has UNR row loads outstanding before it accumulates. Padding
+// columns are computed too and stay zero. For t = 1 the team's lanes split the
+// row's dependencies instead and reduce at the end.
 template <typename T>
 struct VecT;
 template <>
@@ -32,11 +35,19 @@ struct VecT<double> {
   static constexpr int n = 2;
 };
 
-template <typename T, bool CG>
-__device__ __forceinline__ typename VecT<T>::type load_vec(const T* p) {
-  using V = typename VecT<T>::type;
-  return CG ? __ldcg(reinterpret_cast<const V*>(p)) : __ldg(reinterpret_cast<const V*>(p));
+template <int LPV>
+__device__ __forceinline__ unsigned team_mask() {
+  const int lane = threadIdx.x & 31;
+  return LPV == 32 ? 0xffffffffu : (((1u << LPV) - 1u) << (lane / LPV * LPV));
 }
+
+__device__ __forceinline__ float4 ldg_vec(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+__device__ __forceinline__ double2 ldg_vec(const double* p) { return __ldg(reinterpret_cast<const double2*>(p)); }
+
+// L2 (not L1) vector loads for values written earlier in the same launch.
+__device__ __forceinline__ float4 ldcg_vec(const float* p) { return __ldcg(reinterpret_cast<const float4*>(p)); }
+__device__ __forceinline__ double2 ldcg_vec(const double* p) { return __ldcg(reinterpret_cast<const double2*>(p)); }
+
 __device__ __forceinline__ void fma_vec(float* a, float s, float4 v) {
   a[0] += s * v.x;
   a[1] += s * v.y;
@@ -53,47 +64,49 @@ __device__ __forceinline__ void store_vec(float* p, const float* a) {
 __device__ __forceinline__ void store_vec(double* p, const double* a) {
   *reinterpret_cast<double2*>(p) = make_double2(a[0], a[1]);
 }
-
-// acc (this lane's NV words of the row) += sum_e coef_e * X[idx_e, :], e in [beg, end),
-// coef_e = sgn * val[e] * (dscale ? dscale[idx_e] : 1); idx_e < 0 entries are skipped.
-template <typename T, int LPV, int NV, int UNR, bool CG>
-__device__ __forceinline__ void gather_rows(T* acc, const int32_t* __restrict__ idx, const T* __restrict__ val,
+// acc (this lane's NV words of the row) += sum_e coef_e * X[idx_e, :] over e in [beg, end),
+// coef_e = sgn * val[e] * (dscale ? dscale[idx_e] : 1); negative indices are skipped.
+// PRODUCED: X rows were written earlier in the same launch (read through L2).
+template <typename T, int LPV, int NV, int UNR, bool PRODUCED>
+__device__ __forceinline__ void team_gather(T* acc, const int32_t* __restrict__ idx, const T* __restrict__ val,
                                             const T* __restrict__ dscale, T sgn, int beg, int end, const T* X,
-                                            int ld) {
+                                            int ld, DevStatus* st, int row) {
   constexpr int VEC = VecT<T>::n;
-  constexpr int SUB = 32 / LPV;
-  const int lane = threadIdx.x & 31;
-  const int sub = lane / LPV, sl = lane % LPV;
-  for (int e0 = beg; e0 < end; e0 += 32) {
-    const int cnt = min(32, end - e0);
+  using V = typename VecT<T>::type;
+  const unsigned mask = team_mask<LPV>();
+  const int sl = (threadIdx.x & 31) % LPV;
+  for (int e0 = beg; e0 < end; e0 += LPV) {
+    const int cnt = min(LPV, end - e0);
     int jl = -1;
     T al = T(0);
-    if (lane < cnt) {
-      jl = idx[e0 + lane];
-      if (jl >= 0) al = sgn * val[e0 + lane] * (dscale ? dscale[jl] : T(1));
+    if (sl < cnt) {
+      jl = idx[e0 + sl];
+      if (jl >= 0) al = sgn * val[e0 + sl] * (dscale ? dscale[jl] : T(1));
     }
-    for (int q0 = 0; q0 < cnt; q0 += SUB * UNR) {
+    for (int q0 = 0; q0 < cnt; q0 += UNR) {
       int j[UNR];
       T a[UNR];
 #pragma unroll
       for (int u = 0; u < UNR; ++u) {
-        const int q = q0 + sub + SUB * u;
-        const int src = q < 31 ? q : 31;
-        const int jj = __shfl_sync(0xffffffffu, jl, src);
-        const T aa = __shfl_sync(0xffffffffu, al, src);
+        const int q = q0 + u;
+        const int src = q < LPV ? q : LPV - 1;
+        const int jj = __shfl_sync(mask, jl, src, LPV);
+        const T aa = __shfl_sync(mask, al, src, LPV);
         j[u] = (q < cnt) ? jj : -1;
         a[u] = aa;
       }
-      typename VecT<T>::type xv[UNR][NV];
+      V xv[UNR][NV];
 #pragma unroll
       for (int u = 0; u < UNR; ++u)
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
           const int col = (sl + LPV * v) * VEC;
-          if (j[u] >= 0 && col < ld)
-            xv[u][v] = load_vec<T, CG>(X + (int64_t)j[u] * ld + col);
-          else
-            xv[u][v] = typename VecT<T>::type{};
+          if (j[u] >= 0 && col < ld) {
+            const T* p = X + (int64_t)j[u] * ld + col;
+            xv[u][v] = PRODUCED ? ldcg_vec(p) : ldg_vec(p);
+          } else {
+            xv[u][v] = V{};
+          }
         }
 #pragma unroll
       for (int u = 0; u < UNR; ++u)
@@ -101,39 +114,30 @@ __device__ __forceinline__ void gather_rows(T* acc, const int32_t* __restrict__ 
         for (int v = 0; v < NV; ++v) fma_vec(acc + v * VEC, j[u] >= 0 ? a[u] : T(0), xv[u][v]);
     }
   }
-  // combine the sub-warps' partial rows
-#pragma unroll
-  for (int off = 16; off >= LPV; off >>= 1)
-#pragma unroll
-    for (int i = 0; i < NV * VEC; ++i) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], off);
 }
 
-// acc = s1 * A[row] + s2 * Bm[row] (either pointer may be null), for lanes of sub-warp 0.
+// acc = s1 * A1[row] + s2 * A2[row] (either array may be null) for the lane's words.
 template <typename T, int LPV, int NV>
-__device__ __forceinline__ void init_row(T* acc, int64_t row, int ld, T s1, const T* __restrict__ A1, T s2,
-                                         const T* __restrict__ A2) {
+__device__ __forceinline__ void team_init(T* acc, int64_t row, int ld, T s1, const T* __restrict__ A1, T s2,
+                                          const T* __restrict__ A2) {
   constexpr int VEC = VecT<T>::n;
-  const int lane = threadIdx.x & 31;
-  const int sub = lane / LPV, sl = lane % LPV;
+  const int sl = (threadIdx.x & 31) % LPV;
 #pragma unroll
   for (int i = 0; i < NV * VEC; ++i) acc[i] = T(0);
-  if (sub != 0) return;
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
     const int col = (sl + LPV * v) * VEC;
     if (col < ld) {
-      if (A1) fma_vec(acc + v * VEC, s1, load_vec<T, false>(A1 + row * ld + col));
-      if (A2) fma_vec(acc + v * VEC, s2, load_vec<T, false>(A2 + row * ld + col));
+      if (A1) fma_vec(acc + v * VEC, s1, ldg_vec(A1 + row * ld + col));
+      if (A2) fma_vec(acc + v * VEC, s2, ldg_vec(A2 + row * ld + col));
     }
   }
 }
 
 template <typename T, int LPV, int NV>
-__device__ __forceinline__ void store_row(T* Y, int64_t row, int ld, T scale, T* acc) {
+__device__ __forceinline__ void team_store(T* Y, int64_t row, int ld, T scale, T* acc) {
   constexpr int VEC = VecT<T>::n;
-  const int lane = threadIdx.x & 31;
-  const int sub = lane / LPV, sl = lane % LPV;
-  if (sub != 0) return;
+  const int sl = (threadIdx.x & 31) % LPV;
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
     const int col = (sl + LPV * v) * VEC;
@@ -145,149 +149,347 @@ __device__ __forceinline__ void store_row(T* Y, int64_t row, int ld, T scale, T*
   }
 }
 
-// ----------------------------------------------------------------------------- B X
-// Y_s = ys_s (X_s - sum_c A[s,c] X_{nbr[s,c]})   (ys == nullptr: 1)
-template <typename T>
-__global__ void __launch_bounds__(256) spmv_B_t1_kernel(int n, int m, const int32_t* __restrict__ nbr,
-                                                        const T* __restrict__ A, const T* __restrict__ X,
-                                                        const T* __restrict__ ys, T* __restrict__ Y) {
-  const int lane = threadIdx.x & 31;
-  const int nw = (gridDim.x * blockDim.x) >> 5;
-  for (int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < n; s += nw) {
-    const int64_t base = (int64_t)s * m;
-    T acc = T(0);
-    for (int c = lane; c < m; c += 32) {
-      const int j = nbr[base + c];
-      if (j >= 0) acc += A[base + c] * __ldg(&X[j]);
+// Scalar rows (t = 1): the team's lanes split the dependencies; returns the team sum
+// of coef_e * X[idx_e] on every lane of the team.
+template <typename T, int LPV, bool PRODUCED>
+__device__ __forceinline__ T team_dot1(const int32_t* __restrict__ idx, const T* __restrict__ val,
+                                       const T* __restrict__ dscale, int beg, int end, const T* X, DevStatus* st,
+                                       int row) {
+  const unsigned mask = team_mask<LPV>();
+  const int sl = (threadIdx.x & 31) % LPV;
+  T acc = T(0);
+  constexpr int K = 4;   // loads in flight per lane
+  for (int e0 = beg + sl; e0 < end; e0 += LPV * K) {
+    int j[K];
+    T xv[K];
+#pragma unroll
+    for (int u = 0; u < K; ++u) {
+      const int e = e0 + u * LPV;
+      j[u] = e < end ? idx[e] : -1;
+      xv[u] = j[u] >= 0 ? (PRODUCED ? __ldcg(&X[j[u]]) : __ldg(&X[j[u]])) : T(0);
     }
-    acc = warp_sum(acc);
-    if (lane == 0) Y[s] = (ys ? ys[s] : T(1)) * (X[s] - acc);
+#pragma unroll
+    for (int u = 0; u < K; ++u) {
+      if (j[u] < 0) continue;
+      acc += val[e0 + u * LPV] * (dscale ? dscale[j[u]] : T(1)) * xv[u];
+    }
   }
+#pragma unroll
+  for (int off = LPV / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(mask, acc, off, LPV);
+  return acc;
 }
 
+// ----------------------------------------------------------------------------- B X
+// Y_s = ys_s (X_s - sum_c A[s,c] X_{nbr[s,c]})   (ys == nullptr: 1)
 template <typename T, int LPV, int NV, int UNR>
 __global__ void __launch_bounds__(256) spmv_B_kernel(int n, int m, const int32_t* __restrict__ nbr,
                                                      const T* __restrict__ A, const T* __restrict__ X, int ld,
                                                      const T* __restrict__ ys, T* __restrict__ Y) {
-  const int nw = (gridDim.x * blockDim.x) >> 5;
+  constexpr int RPW = 32 / LPV;
+  const int G = ((gridDim.x * blockDim.x) >> 5) * RPW;
+  const int g = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * RPW + (threadIdx.x & 31) / LPV;
   T acc[NV * VecT<T>::n];
-  for (int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < n; s += nw) {
-    init_row<T, LPV, NV>(acc, s, ld, T(1), X, T(0), nullptr);
-    gather_rows<T, LPV, NV, UNR, false>(acc, nbr, A, nullptr, T(-1), s * m, s * m + m, X, ld);
-    store_row<T, LPV, NV>(Y, s, ld, ys ? ys[s] : T(1), acc);
+  for (int s = g; s < n; s += G) {
+    team_init<T, LPV, NV>(acc, s, ld, T(1), X, T(0), nullptr);
+    team_gather<T, LPV, NV, UNR, false>(acc, nbr, A, nullptr, T(-1), s * m, s * m + m, X, ld, nullptr, s);
+    team_store<T, LPV, NV>(Y, s, ld, ys ? ys[s] : T(1), acc);
+  }
+}
+
+template <typename T, int LPV>
+__global__ void __launch_bounds__(256) spmv_B_t1_kernel(int n, int m, const int32_t* __restrict__ nbr,
+                                                        const T* __restrict__ A, const T* __restrict__ X,
+                                                        const T* __restrict__ ys, T* __restrict__ Y) {
+  constexpr int RPW = 32 / LPV;
+  const int G = ((gridDim.x * blockDim.x) >> 5) * RPW;
+  const int g = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * RPW + (threadIdx.x & 31) / LPV;
+  for (int s = g; s < n; s += G) {
+    const T acc = team_dot1<T, LPV, false>(nbr, A, nullptr, s * m, s * m + m, X, nullptr, s);
+    if ((threadIdx.x & 31) % LPV == 0) Y[s] = (ys ? ys[s] : T(1)) * (X[s] - acc);
   }
 }
 
 // ----------------------------------------------------------------------------- W X + B^T Y
 // Z_s = wx_s X_s + ys_s Y_s - sum_{e in row s of B^T} valT[e] ys_{i} Y_{i},  i = colT[e]
 // (X == nullptr: no diagonal term; ys == nullptr: 1)
-template <typename T>
-__global__ void __launch_bounds__(256) spmv_Bt_t1_kernel(int n, const int32_t* __restrict__ rowptrT,
-                                                         const int32_t* __restrict__ colT, const T* __restrict__ valT,
-                                                         const T* __restrict__ Y, const T* __restrict__ ys,
-                                                         const T* __restrict__ X, const T* __restrict__ wx,
-                                                         T* __restrict__ Z) {
-  const int lane = threadIdx.x & 31;
-  const int nw = (gridDim.x * blockDim.x) >> 5;
-  for (int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < n; s += nw) {
-    T acc = T(0);
-    for (int e = rowptrT[s] + lane; e < rowptrT[s + 1]; e += 32) {
-      const int i = colT[e];
-      acc += valT[e] * (ys ? ys[i] : T(1)) * __ldg(&Y[i]);
-    }
-    acc = warp_sum(acc);
-    if (lane == 0) Z[s] = (X ? wx[s] * X[s] : T(0)) + (ys ? ys[s] : T(1)) * Y[s] - acc;
-  }
-}
-
 template <typename T, int LPV, int NV, int UNR>
 __global__ void __launch_bounds__(256) spmv_Bt_kernel(int n, const int32_t* __restrict__ rowptrT,
                                                       const int32_t* __restrict__ colT, const T* __restrict__ valT,
                                                       const T* __restrict__ Y, const T* __restrict__ ys,
                                                       const T* __restrict__ X, const T* __restrict__ wx, int ld,
                                                       T* __restrict__ Z) {
-  const int nw = (gridDim.x * blockDim.x) >> 5;
+  constexpr int RPW = 32 / LPV;
+  const int G = ((gridDim.x * blockDim.x) >> 5) * RPW;
+  const int g = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * RPW + (threadIdx.x & 31) / LPV;
   T acc[NV * VecT<T>::n];
-  for (int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < n; s += nw) {
-    init_row<T, LPV, NV>(acc, s, ld, ys ? ys[s] : T(1), Y, X ? wx[s] : T(0), X);
-    gather_rows<T, LPV, NV, UNR, false>(acc, colT, valT, ys, T(-1), rowptrT[s], rowptrT[s + 1], Y, ld);
-    store_row<T, LPV, NV>(Z, s, ld, T(1), acc);
+  for (int s = g; s < n; s += G) {
+    team_init<T, LPV, NV>(acc, s, ld, ys ? ys[s] : T(1), Y, X ? wx[s] : T(0), X);
+    team_gather<T, LPV, NV, UNR, false>(acc, colT, valT, ys, T(-1), rowptrT[s], rowptrT[s + 1], Y, ld, nullptr, s);
+    team_store<T, LPV, NV>(Z, s, ld, T(1), acc);
+  }
+}
+
+template <typename T, int LPV>
+__global__ void __launch_bounds__(256) spmv_Bt_t1_kernel(int n, const int32_t* __restrict__ rowptrT,
+                                                         const int32_t* __restrict__ colT, const T* __restrict__ valT,
+                                                         const T* __restrict__ Y, const T* __restrict__ ys,
+                                                         const T* __restrict__ X, const T* __restrict__ wx,
+                                                         T* __restrict__ Z) {
+  constexpr int RPW = 32 / LPV;
+  const int G = ((gridDim.x * blockDim.x) >> 5) * RPW;
+  const int g = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * RPW + (threadIdx.x & 31) / LPV;
+  for (int s = g; s < n; s += G) {
+    const T acc = team_dot1<T, LPV, false>(colT, valT, ys, rowptrT[s], rowptrT[s + 1], Y, nullptr, s);
+    if ((threadIdx.x & 31) % LPV == 0) Z[s] = (X ? wx[s] * X[s] : T(0)) + (ys ? ys[s] : T(1)) * Y[s] - acc;
   }
 }
 
 // ----------------------------------------------------------------------------- solves
-// Sync-free level-ordered triangular solve, one row per warp, rows taken in the
-// topological task order (w, w + W, ...). Every warp is resident (cooperative
-// launch), so the earliest unfinished task always has its inputs and the walk
-// cannot deadlock; each wait is bounded and a timeout aborts the whole solve.
+// Level-synchronous triangular solve in one cooperative launch. Rows are taken
+// in the level order of the task list (lptr[l] .. lptr[l+1] is level l); a row
+// only reads rows of earlier levels, so a level's rows are independent.
+//   head  levels [0, l_head):     block 0 alone, one __syncthreads per level
+//   body  levels [l_head, l_tail): every block, one grid barrier per level
+//   tail  levels [l_tail, nlev):   block 0 alone again
+// The head and tail are the narrow ends of the level profile (random orderings
+// give a long thin head), where a block barrier is far cheaper than a grid one.
+// Values of x produced in this launch are read through L2 (ld.global.cg).
 //   FWD (B^{-1}):   x_s = q_s r_s + sum_{c} A[s,c] x_{nbr[s,c]}
 //   BWD (B^{-T}):   x_s = q_s r_s + sum_{e in row s of B^T} valT[e] x_{colT[e]}
-// Flags are polled with relaxed loads and backoff; one acquire fence follows the
-// waits, and values produced in this launch are read through L2 (ld.global.cg).
-__device__ __forceinline__ unsigned ld_relaxed(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+struct LevelPlan {
+  const int32_t* task;
+  const int32_t* lptr;
+  int l_head, l_tail, nlev;
+  unsigned* bar;               // {count, generation}, count == 0 at launch
+  DevStatus* st;
+  long long* trace;            // optional: block 0's clock at each level boundary (nlev + 1)
+};
 
-__device__ __forceinline__ void wait_deps(const int32_t* __restrict__ idx, int beg, int end, const unsigned* ready,
-                                          unsigned epoch, DevStatus* st, int s) {
-  const int lane = threadIdx.x & 31;
-  for (int e = beg + lane; e < end; e += 32) {
-    const int j = idx[e];
-    if (j >= 0) bounded_wait([&] { return ld_relaxed(&ready[j]) == epoch; }, st, s);
-  }
-  __syncwarp();
-  fence_acq_rel();
-}
-
-template <typename T, bool FWD>
-__global__ void __launch_bounds__(256) sptrsv_t1_kernel(int n, int m, const int32_t* __restrict__ task,
-                                                        const int32_t* __restrict__ idx, const T* __restrict__ val,
-                                                        const int32_t* __restrict__ rowptr, const T* __restrict__ rhs,
-                                                        const T* __restrict__ q, T* x, unsigned* ready,
-                                                        unsigned epoch, DevStatus* st) {
-  const int lane = threadIdx.x & 31;
-  const int nw = (gridDim.x * blockDim.x) >> 5;
-  for (int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < n; p += nw) {
-    const int s = task[p];
-    const int beg = FWD ? s * m : rowptr[s];
-    const int end = FWD ? s * m + m : rowptr[s + 1];
-    wait_deps(idx, beg, end, ready, epoch, st, s);
-    T acc = T(0);
-    for (int e = beg + lane; e < end; e += 32) {
-      const int j = idx[e];
-      if (j >= 0) acc += val[e] * __ldcg(&x[j]);
-    }
-    acc = warp_sum(acc);
-    if (lane == 0) {
-      x[s] = (q ? q[s] : T(1)) * rhs[s] + acc;
-      st_release(&ready[s], epoch);
+// Grid barrier with a bounded wait: the last block to arrive bumps the
+// generation. A timeout records VL_ERR_TIMEOUT; after an abort every barrier
+// returns at once so the launch still ends.
+__device__ __forceinline__ void grid_barrier(unsigned* bar, DevStatus* st) {
+  __syncthreads();
+  if (threadIdx.x == 0 && !ld_volatile(&st->abort)) {
+    const unsigned gen = ld_acquire(&bar[1]);
+    __threadfence();
+    if (atomicAdd(&bar[0], 1u) == gridDim.x - 1) {
+      atomicExch(&bar[0], 0u);
+      st_release(&bar[1], gen + 1);
+    } else {
+      int spins = 0;
+      while (ld_acquire(&bar[1]) == gen && ++spins < 4096) {
+      }
+      if (spins >= 4096) bounded_wait([&] { return ld_acquire(&bar[1]) != gen; }, st, -1);
     }
   }
+  __syncthreads();
+}
+
+// Row state loaded ahead of time: everything a team needs before it reads x
+// (task, dependency range, its first chunk of dependency indices and weights,
+// the scaled right-hand side). Prefetching it for the next level before a
+// barrier leaves only the x gathers on the critical path.
+template <typename T, int LPV, int NV>
+struct RowPre {
+  int s, beg, end, jl;
+  T al;
+  T acc[NV * VecT<T>::n];
+};
+
+template <typename T, bool FWD, int LPV, int NV>
+__device__ __forceinline__ void row_pre(RowPre<T, LPV, NV>& r, int p, int m, const LevelPlan& L,
+                                        const int32_t* __restrict__ idx, const T* __restrict__ val,
+                                        const int32_t* __restrict__ rowptr, const T* __restrict__ rhs,
+                                        const T* __restrict__ q, int ld) {
+  const int sl = (threadIdx.x & 31) % LPV;
+  r.s = L.task[p];
+  r.beg = FWD ? r.s * m : rowptr[r.s];
+  r.end = FWD ? r.s * m + m : rowptr[r.s + 1];
+  const int e = r.beg + sl;
+  r.jl = e < r.end ? idx[e] : -1;
+  r.al = r.jl >= 0 ? val[e] : T(0);
+  team_init<T, LPV, NV>(r.acc, r.s, ld, q ? q[r.s] : T(1), rhs, T(0), nullptr);
+}
+
+// Finishes a prefetched row: gathers its dependencies (first chunk already in
+// registers) and stores x_s.
+template <typename T, int LPV, int NV, int UNR>
+__device__ __forceinline__ void row_run(RowPre<T, LPV, NV>& r, const int32_t* __restrict__ idx,
+                                        const T* __restrict__ val, T* x, int ld) {
+  constexpr int VEC = VecT<T>::n;
+  using V = typename VecT<T>::type;
+  const unsigned mask = team_mask<LPV>();
+  const int sl = (threadIdx.x & 31) % LPV;
+  for (int e0 = r.beg; e0 < r.end; e0 += LPV) {
+    const int cnt = min(LPV, r.end - e0);
+    int jl = r.jl;
+    T al = r.al;
+    if (e0 != r.beg) {
+      jl = sl < cnt ? idx[e0 + sl] : -1;
+      al = jl >= 0 ? val[e0 + sl] : T(0);
+    }
+    for (int q0 = 0; q0 < cnt; q0 += UNR) {
+      int j[UNR];
+      T a[UNR];
+#pragma unroll
+      for (int u = 0; u < UNR; ++u) {
+        const int qq = q0 + u;
+        const int src = qq < LPV ? qq : LPV - 1;
+        const int jj = __shfl_sync(mask, jl, src, LPV);
+        const T aa = __shfl_sync(mask, al, src, LPV);
+        j[u] = (qq < cnt) ? jj : -1;
+        a[u] = aa;
+      }
+      V xv[UNR][NV];
+#pragma unroll
+      for (int u = 0; u < UNR; ++u)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const int col = (sl + LPV * v) * VEC;
+          xv[u][v] = (j[u] >= 0 && col < ld) ? ldcg_vec(x + (int64_t)j[u] * ld + col) : V{};
+        }
+#pragma unroll
+      for (int u = 0; u < UNR; ++u)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) fma_vec(r.acc + v * VEC, j[u] >= 0 ? a[u] : T(0), xv[u][v]);
+    }
+  }
+  team_store<T, LPV, NV>(x, r.s, ld, T(1), r.acc);
+}
+
+// Scalar rows (t = 1): the team's lanes split the dependencies, K loads each in flight.
+template <typename T, int LPV>
+struct RowPre1 {
+  static constexpr int K = 4;
+  int s, beg, end;
+  int j[K];
+  T a[K];
+  T b;   // q_s r_s
+};
+
+template <typename T, bool FWD, int LPV>
+__device__ __forceinline__ void row_pre1(RowPre1<T, LPV>& r, int p, int m, const LevelPlan& L,
+                                         const int32_t* __restrict__ idx, const T* __restrict__ val,
+                                         const int32_t* __restrict__ rowptr, const T* __restrict__ rhs,
+                                         const T* __restrict__ q) {
+  const int sl = (threadIdx.x & 31) % LPV;
+  r.s = L.task[p];
+  r.beg = FWD ? r.s * m : rowptr[r.s];
+  r.end = FWD ? r.s * m + m : rowptr[r.s + 1];
+#pragma unroll
+  for (int u = 0; u < RowPre1<T, LPV>::K; ++u) {
+    const int e = r.beg + sl + u * LPV;
+    r.j[u] = e < r.end ? idx[e] : -1;
+    r.a[u] = r.j[u] >= 0 ? val[e] : T(0);
+  }
+  r.b = (q ? q[r.s] : T(1)) * rhs[r.s];
+}
+
+template <typename T, int LPV>
+__device__ __forceinline__ void row_run1(RowPre1<T, LPV>& r, const int32_t* __restrict__ idx,
+                                         const T* __restrict__ val, T* x) {
+  constexpr int K = RowPre1<T, LPV>::K;
+  const unsigned mask = team_mask<LPV>();
+  const int sl = (threadIdx.x & 31) % LPV;
+  T acc = T(0);
+  for (int e0 = r.beg + sl; e0 < r.end; e0 += LPV * K) {
+    int j[K];
+    T a[K], xv[K];
+#pragma unroll
+    for (int u = 0; u < K; ++u) {
+      const int e = e0 + u * LPV;
+      if (e0 == r.beg + sl) {
+        j[u] = r.j[u];
+        a[u] = r.a[u];
+      } else {
+        j[u] = e < r.end ? idx[e] : -1;
+        a[u] = j[u] >= 0 ? val[e] : T(0);
+      }
+      xv[u] = j[u] >= 0 ? __ldcg(&x[j[u]]) : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < K; ++u) acc += a[u] * xv[u];
+  }
+#pragma unroll
+  for (int off = LPV / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(mask, acc, off, LPV);
+  if (sl == 0) x[r.s] = r.b + acc;
+}
+
+// Walks the levels with the head/body/tail split; each team prefetches its next
+// row (pre) before the barrier that precedes it and finishes it after (run).
+template <int LPV, typename Pre, typename Run>
+__device__ __forceinline__ void level_walk(const LevelPlan& L, Pre pre, Run run) {
+  constexpr int RPW = 32 / LPV;
+  const int tpb = (blockDim.x >> 5) * RPW;
+  const int tib = (threadIdx.x >> 5) * RPW + (threadIdx.x & 31) / LPV;
+  const int G = gridDim.x * tpb, g = blockIdx.x * tpb + tib;
+  const bool tr = L.trace && blockIdx.x == 0 && threadIdx.x == 0;
+  // one block: levels [l0, l1) with a block barrier after each
+  auto solo = [&](int l0, int l1) {
+    int p = (l0 < l1) ? L.lptr[l0] + tib : 0;
+    bool has = l0 < l1 && p < L.lptr[l0 + 1];
+    if (has) pre(p);
+    for (int l = l0; l < l1; ++l) {
+      if (tr) L.trace[l] = clock64();
+      while (has) {
+        run();
+        p += tpb;
+        has = p < L.lptr[l + 1];
+        if (has) pre(p);
+      }
+      if (l + 1 < l1) {
+        p = L.lptr[l + 1] + tib;
+        has = p < L.lptr[l + 2];
+        if (has) pre(p);
+      }
+      __syncthreads();
+    }
+  };
+  if (blockIdx.x == 0) solo(0, L.l_head);
+  if (L.l_head > 0 && L.l_head < L.nlev) grid_barrier(L.bar, L.st);
+  {
+    int p = (L.l_head < L.l_tail) ? L.lptr[L.l_head] + g : 0;
+    bool has = L.l_head < L.l_tail && p < L.lptr[L.l_head + 1];
+    if (has) pre(p);
+    for (int l = L.l_head; l < L.l_tail; ++l) {
+      if (tr) L.trace[l] = clock64();
+      while (has) {
+        run();
+        p += G;
+        has = p < L.lptr[l + 1];
+        if (has) pre(p);
+      }
+      if (l + 1 < L.l_tail) {
+        p = L.lptr[l + 1] + g;
+        has = p < L.lptr[l + 2];
+        if (has) pre(p);
+      }
+      grid_barrier(L.bar, L.st);
+    }
+  }
+  if (blockIdx.x == 0) solo(L.l_tail, L.nlev);
+  if (tr) L.trace[L.nlev] = clock64();
 }
 
 template <typename T, bool FWD, int LPV, int NV, int UNR>
-__global__ void __launch_bounds__(256) sptrsv_kernel(int n, int m, const int32_t* __restrict__ task,
-                                                     const int32_t* __restrict__ idx, const T* __restrict__ val,
-                                                     const int32_t* __restrict__ rowptr, const T* __restrict__ rhs,
-                                                     const T* __restrict__ q, T* x, int ld, unsigned* ready,
-                                                     unsigned epoch, DevStatus* st) {
-  const int lane = threadIdx.x & 31;
-  const int nw = (gridDim.x * blockDim.x) >> 5;
-  T acc[NV * VecT<T>::n];
-  for (int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < n; p += nw) {
-    const int s = task[p];
-    const int beg = FWD ? s * m : rowptr[s];
-    const int end = FWD ? s * m + m : rowptr[s + 1];
-    init_row<T, LPV, NV>(acc, s, ld, q ? q[s] : T(1), rhs, T(0), nullptr);
-    wait_deps(idx, beg, end, ready, epoch, st, s);
-    gather_rows<T, LPV, NV, UNR, true>(acc, idx, val, nullptr, T(1), beg, end, x, ld);
-    store_row<T, LPV, NV>(x, s, ld, T(1), acc);
-    __syncwarp();
-    if (lane == 0) st_release(&ready[s], epoch);
-  }
+__global__ void __launch_bounds__(512) sptrsv_kernel(LevelPlan L, int m, const int32_t* __restrict__ idx,
+                                                     const T* __restrict__ val, const int32_t* __restrict__ rowptr,
+                                                     const T* __restrict__ rhs, const T* __restrict__ q, T* x, int ld) {
+  RowPre<T, LPV, NV> r;
+  level_walk<LPV>(
+      L, [&](int p) { row_pre<T, FWD, LPV, NV>(r, p, m, L, idx, val, rowptr, rhs, q, ld); },
+      [&]() { row_run<T, LPV, NV, UNR>(r, idx, val, x, ld); });
+}
+
+template <typename T, bool FWD, int LPV>
+__global__ void __launch_bounds__(512) sptrsv_t1_kernel(LevelPlan L, int m, const int32_t* __restrict__ idx,
+                                                        const T* __restrict__ val, const int32_t* __restrict__ rowptr,
+                                                        const T* __restrict__ rhs, const T* __restrict__ q, T* x) {
+  RowPre1<T, LPV> r;
+  level_walk<LPV>(
+      L, [&](int p) { row_pre1<T, FWD, LPV>(r, p, m, L, idx, val, rowptr, rhs, q); },
+      [&]() { row_run1<T, LPV>(r, idx, val, x); });
 }
 
 // ----------------------------------------------------------------------------- column reductions

@@ -57,6 +57,11 @@ struct Profiler {
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> pool;
   std::map<std::pair<std::string, int>, Acc> acc;
+  bool trace = false;                                   // record level traces of solves
+  long long* dtrace = nullptr;                          // device scratch for one trace
+  size_t dtrace_len = 0;
+  std::map<std::pair<std::string, int>, std::vector<long long>> traces;   // last per class
+  std::map<std::pair<std::string, int>, std::pair<int, int>> cuts;        // (l_head, l_tail)
 };
 
 struct Ctx {
@@ -71,10 +76,10 @@ struct Ctx {
   char* pinned = nullptr;         // pinned scratch for small read-backs
   size_t pinned_bytes = 0;
   int num_sms = 0;
-  unsigned epoch = 0;             // sync-free solve flag generation
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   Profiler prof;
   int64_t launches = 0;           // kernels launched on this context
+  unsigned* gbar = nullptr;       // grid-barrier state {count, generation} (device)
 };
 
 // Launch-configuration stream argument that also counts the launch.
@@ -135,7 +140,10 @@ struct Factor {
   int32_t* lev_bwd = nullptr;
   int32_t* task_fwd = nullptr;  // storage rows sorted by (lev_fwd, s)
   int32_t* task_bwd = nullptr;
-  unsigned* ready = nullptr;    // n flags for the sync-free solves
+  int32_t* lptr_fwd = nullptr;  // nlev_fwd + 1: first task of each level
+  int32_t* lptr_bwd = nullptr;
+  std::vector<int32_t> h_lptr_fwd, h_lptr_bwd;
+  std::vector<int64_t> h_lwork_fwd, h_lwork_bwd;   // dependencies per level
 };
 
 struct State {
