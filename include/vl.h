@@ -132,6 +132,9 @@ void vl_opts_default(vl_opts* o);
  * VL_ERR_CUDA, VL_ERR_OOM. */
 vl_status vl_ctx_create(int device, void* cuda_stream, void* workspace, size_t ws_bytes,
                         vl_ctx** out);
+/* Handles may be destroyed in any order: the context's stream, events and own
+ * workspace are released when the context and every factor and state made on it
+ * have been destroyed. A caller-provided workspace must stay allocated until then. */
 void vl_ctx_destroy(vl_ctx* ctx);
 /* Thread-unsafe, context-local: the message of the last failed call (or ""). */
 const char* vl_last_error(const vl_ctx* ctx);

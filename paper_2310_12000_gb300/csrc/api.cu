@@ -596,8 +596,11 @@ vl_status vl_ctx_create(int device, void* cuda_stream, void* workspace, size_t w
   return VL_OK;
 }
 
-void vl_ctx_destroy(vl_ctx* c) {
-  if (!c) return;
+// A context lives until it has been destroyed and every factor and state made on
+// it has been destroyed too, in whatever order those calls come.
+static void ctx_release(Ctx* cc) {
+  if (--cc->refs > 0) return;
+  vl_ctx* c = static_cast<vl_ctx*>(cc);
   cudaStreamSynchronize(c->stream);
   prof_release(c);
   if (c->ev0) cudaEventDestroy(c->ev0);
@@ -605,6 +608,12 @@ void vl_ctx_destroy(vl_ctx* c) {
   if (c->owns_ws && c->ws) cudaFree(c->ws);
   if (c->pinned) cudaFreeHost(c->pinned);
   delete c;
+}
+
+void vl_ctx_destroy(vl_ctx* c) {
+  if (!c || c->closed) return;
+  c->closed = true;
+  ctx_release(c);
 }
 
 const char* vl_last_error(const vl_ctx* c) { return c ? c->last_error.c_str() : "null context"; }
@@ -777,6 +786,7 @@ vl_status vl_build_factor(vl_ctx* c, const double* locs, int64_t n, const int32_
   if (st != VL_OK) return bail(st);
   st = vl_factor_refit(f, sigma2, range, opts);
   if (st != VL_OK) return bail(st);
+  ++c->refs;
   *out = f;
   return VL_OK;
 }
@@ -817,9 +827,11 @@ vl_status vl_factor_info(const vl_factor* f, int64_t* n, int* m, int* nf, int* n
 
 void vl_factor_destroy(vl_factor* f) {
   if (!f) return;
-  cudaStreamSynchronize(f->ctx->stream);
+  Ctx* c = f->ctx;
+  cudaStreamSynchronize(c->stream);
   f->mem.free_all();
   delete f;
+  ctx_release(c);
 }
 
 // --------------------------------------------------------------------------- mode
@@ -929,6 +941,7 @@ vl_status vl_find_mode(vl_factor* f, int lik, const double* y, const double* F, 
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return bail(fail(c, VL_ERR_CUDA, "sync"));
   stats.newton_iters = it;
   st->mode_stats = stats;
+  ++c->refs;
   *out = st;
   if (!converged) return fail(c, VL_ERR_NOT_CONVERGED, "Newton reached newton_max_iter");
   return VL_OK;
@@ -942,9 +955,11 @@ vl_status vl_state_stats(const vl_state* s, vl_stats* out) {
 
 void vl_state_destroy(vl_state* s) {
   if (!s) return;
-  cudaStreamSynchronize(s->ctx->stream);
+  Ctx* c = s->ctx;
+  cudaStreamSynchronize(c->stream);
   s->mem.free_all();
   delete s;
+  ctx_release(c);
 }
 
 // --------------------------------------------------------------------------- L^VLA

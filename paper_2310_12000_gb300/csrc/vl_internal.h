@@ -80,6 +80,8 @@ struct Ctx {
   Profiler prof;
   int64_t launches = 0;           // kernels launched on this context
   unsigned* gbar = nullptr;       // grid-barrier state {count, generation} (device)
+  int refs = 1;                   // the context itself + every live factor and state
+  bool closed = false;            // vl_ctx_destroy was called
 };
 
 // Launch-configuration stream argument that also counts the launch.
