@@ -252,6 +252,17 @@ typedef enum vl_op {
 /* Y = op(X) with the state's W, in the precision of opts (float64 in/out). */
 vl_status vl_apply(vl_state* s, int op, const double* X, int t, const vl_opts* opts, double* Y);
 
+/* Y = (W + B^T D^{-1} B) X in float64, like vl_apply(VL_OP_A), but without touching
+ * the context workspace or allocating device memory, for callers that cannot
+ * allocate when they call: its intermediates live in a fixed 64 MiB array built
+ * into the library (resident on every device that loads it), so it requires
+ * 3 * n * ld * 8 + n * 8 <= 64 MiB with ld = 1 for t = 1, else 8 * ceil(t / 8);
+ * larger requests fail with VL_ERR_INVALID_ARG and say so. X and Y must be device
+ * pointers (n x t, caller order). The first call on a device looks up the array's
+ * address, so make it before any stream capture. Calls share the array: calls that
+ * overlap on the GPU race. The paper has no counterpart; this is a deployment aid. */
+vl_status vl_apply_A_noalloc(vl_state* s, const double* X, int t, double* Y);
+
 /* Solves (W + Sigma_tilde^{-1}) U = RHS (t columns) by PCG with T extraction (the
  * appendix algorithm, u_0 = 0, per-column stop ||r|| <= cg_tol ||b||), in the
  * precision and preconditioner of opts (LRAC solves the form-2 system, Eq. pcls2).

@@ -117,6 +117,7 @@ def library():
         "vl_knn_cross": (st, [vp, vp, i64, vp, i64, i32, vp]),
         "vl_apply": (st, [vp, i32, vp, i32, vp, vp]),
         "vl_pcg_solve": (st, [vp, vp, i32, vp, vp, i32, vp, vp, vp, vp]),
+        "vl_apply_A_noalloc": (st, [vp, vp, i32, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -362,6 +363,13 @@ class State:
         Y = np.empty_like(X)
         self.ctx.check(self.ctx.lib.vl_apply(self.h, op, X.ctypes.data, X.shape[1], C.byref(opts), Y.ctypes.data))
         return Y
+
+    def apply_A_noalloc(self, X_dev, Y_dev):
+        """(W + B^T D^{-1} B) X for device tensors X, Y (n x t float64) without
+        allocating; see vl_apply_A_noalloc in include/vl.h."""
+        t = 1 if len(X_dev.shape) == 1 else X_dev.shape[1]
+        self.ctx.check(self.ctx.lib.vl_apply_A_noalloc(self.h, _ptr(X_dev, np.float64), t, _ptr(Y_dev, np.float64)))
+        return Y_dev
 
     def pcg_solve(self, RHS, opts: Opts | None = None, lmax: int = 0):
         R = np.ascontiguousarray(RHS, dtype=np.float64)

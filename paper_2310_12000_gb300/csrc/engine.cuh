@@ -72,7 +72,7 @@ __global__ void accumulate_kernel(int64_t total, TX* __restrict__ x, const TY* _
 }
 
 // r = b - r (in place on r holding A x)
-__global__ void residual_kernel(int64_t total, const double* __restrict__ b, double* __restrict__ r) {
+static __global__ void residual_kernel(int64_t total, const double* __restrict__ b, double* __restrict__ r) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
     r[e] = b[e] - r[e];
 }

@@ -531,7 +531,7 @@ __global__ void coldot_kernel(int n, int t, int ld, int rpb, const T* __restrict
 }
 
 // out[c] = sum_b partial[b * t + c] (fixed order)
-__global__ void reduce_partials_kernel(int nblk, int t, const double* __restrict__ partial, double* __restrict__ out) {
+static __global__ void reduce_partials_kernel(int nblk, int t, const double* __restrict__ partial, double* __restrict__ out) {
   for (int c = threadIdx.x; c < t; c += blockDim.x) {
     double s = 0.0;
     for (int b = 0; b < nblk; ++b) s += partial[(int64_t)b * t + c];
@@ -560,7 +560,7 @@ struct PcgScalars {
 };
 
 // r_0 = b, z_0 = P^{-1} r_0: set rz, rz0, bnorm2 (already reduced into rz/bnorm2) and flags.
-__global__ void pcg_init_kernel(int t, PcgScalars S) {
+static __global__ void pcg_init_kernel(int t, PcgScalars S) {
   for (int c = threadIdx.x; c < t; c += blockDim.x) {
     S.rz0[c] = S.rz[c];
     S.alpha_prev[c] = 1.0;
@@ -576,7 +576,7 @@ __global__ void pcg_init_kernel(int t, PcgScalars S) {
 }
 
 // alpha_{l+1} = r_l^T z_l / h_l^T v_l for active columns (0 otherwise).
-__global__ void pcg_alpha_kernel(int t, const double* __restrict__ hv, PcgScalars S) {
+static __global__ void pcg_alpha_kernel(int t, const double* __restrict__ hv, PcgScalars S) {
   for (int c = threadIdx.x; c < t; c += blockDim.x) {
     const double a = S.active[c] ? S.rz[c] / hv[c] : 0.0;
     S.alpha[c] = (S.active[c] && isfinite(a)) ? a : 0.0;
@@ -584,7 +584,7 @@ __global__ void pcg_alpha_kernel(int t, const double* __restrict__ hv, PcgScalar
 }
 
 // early-stopping test on ||r_{l+1}|| (before the T update, as in the algorithm).
-__global__ void pcg_stop_kernel(int t, double tol2, PcgScalars S) {
+static __global__ void pcg_stop_kernel(int t, double tol2, PcgScalars S) {
   for (int c = threadIdx.x; c < t; c += blockDim.x) {
     if (!S.active[c]) continue;
     const double rn = S.rnorm2[c];
@@ -594,7 +594,7 @@ __global__ void pcg_stop_kernel(int t, double tol2, PcgScalars S) {
 }
 
 // beta_{l+1}, the T update, and the freeze of converged columns.
-__global__ void pcg_beta_kernel(int t, const double* __restrict__ rz_new, int max_iter, PcgScalars S) {
+static __global__ void pcg_beta_kernel(int t, const double* __restrict__ rz_new, int max_iter, PcgScalars S) {
   __shared__ int cnt;
   if (threadIdx.x == 0) cnt = 0;
   __syncthreads();
@@ -678,7 +678,7 @@ __global__ void pcg_update2_kernel(int64_t total, int t, int ld, const double* _
 // symmetric tridiagonal T_c (size iters[c]), by implicit symmetric QR steps with
 // Wilkinson shifts (Golub & Van Loan, Sec. 8.3) while rotating only the first
 // row of the eigenvector matrix. One thread per column, float64.
-__global__ void slq_quad_kernel(int t, int lmax, const double* __restrict__ Tdiag, const double* __restrict__ Toff,
+static __global__ void slq_quad_kernel(int t, int lmax, const double* __restrict__ Tdiag, const double* __restrict__ Toff,
                                 const int* __restrict__ iters, const double* __restrict__ w,
                                 double* __restrict__ work, double* __restrict__ gamma, int* __restrict__ bad) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -759,7 +759,7 @@ __device__ __forceinline__ void lik_terms(int lik, double y, double mu, double& 
   }
 }
 
-__global__ void lik_kernel(int n, int lik, const double* __restrict__ y, const double* __restrict__ F,
+static __global__ void lik_kernel(int n, int lik, const double* __restrict__ y, const double* __restrict__ F,
                            const double* __restrict__ b, double* __restrict__ W, double* __restrict__ g,
                            double* __restrict__ rhs, double* __restrict__ logp) {
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
@@ -795,7 +795,7 @@ __global__ void rademacher_kernel(int n, int t, int ld, const int32_t* __restric
 // Gaussian z[s, j] by Box-Muller: block j / 4, words (2q, 2q + 1), q = (j % 4) / 2:
 // u1 = ((w >> 11) + 1) 2^-53, u2 = (w >> 11) 2^-53, sqrt(-2 ln u1) cos / sin (2 pi u2).
 // Fills columns j = col0 .. col0 + t - 1 into Z[s, j - col0]; padding columns get 0.
-__global__ void gaussian_kernel(int n, int t, int ld, int col0, const int32_t* __restrict__ s2u, uint64_t seed,
+static __global__ void gaussian_kernel(int n, int t, int ld, int col0, const int32_t* __restrict__ s2u, uint64_t seed,
                                 int stream, double* __restrict__ Z) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
