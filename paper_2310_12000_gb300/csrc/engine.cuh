@@ -236,11 +236,14 @@ struct Engine {
   // Head/tail cut of the level profile: leading and trailing levels whose gathers
   // (rows + dependencies, in vector words) fit one block's round of loads run in
   // block 0 alone; the rest use the whole grid with a barrier per level.
-  static void level_cut(const std::vector<int32_t>& lp, const std::vector<int64_t>& work, int words, int* l_head,
-                        int* l_tail) {
+  static void level_cut(const std::vector<int32_t>& lp, const std::vector<int32_t>& hp,
+                        const std::vector<int64_t>& work, int words, int* l_head, int* l_tail) {
     const int nlev = (int)lp.size() - 1;
     const int64_t cap = 4096;   // vector loads one 512-thread block issues in ~one round trip
-    auto narrow = [&](int l) { return (work[l] + (lp[l + 1] - lp[l])) * (int64_t)words <= cap; };
+    // block 0 runs heavy rows one after another, so a level with more than two goes to the grid
+    auto narrow = [&](int l) {
+      return (work[l] + (lp[l + 1] - lp[l])) * (int64_t)words <= cap && hp[l] - lp[l] <= 2;
+    };
     int h = 0;
     while (h < nlev && narrow(h)) ++h;
     int tl = nlev;
@@ -249,12 +252,36 @@ struct Engine {
     *l_tail = tl;
   }
 
+  // Largest cluster (<= 16 blocks of 1024 threads) the device can co-schedule for fn.
+  int cluster_size(const void* fn) {
+    static int cached[2][2] = {{-1, -1}, {-1, -1}};
+    (void)cached;
+    cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 1;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(16);
+    cfg.blockDim = dim3(1024);
+    cfg.attrs = at;
+    cfg.numAttrs = 0;
+    int cs = 0;
+    if (cudaOccupancyMaxPotentialClusterSize(&cs, fn, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    return std::min(cs, 16);
+  }
+
   template <bool FWD>
   vl_status solve_launch(const T* rhs, const T* q, T* x) {
     const std::vector<int32_t>& hl = FWD ? f->h_lptr_fwd : f->h_lptr_bwd;
     const std::vector<int64_t>& hw = FWD ? f->h_lwork_fwd : f->h_lwork_bwd;
-    LevelPlan L{FWD ? f->task_fwd : f->task_bwd, FWD ? f->lptr_fwd : f->lptr_bwd, 0, 0, (int)hl.size() - 1, c->gbar,
-                c->dstatus, nullptr};
+    const std::vector<int32_t>& hh = FWD ? f->h_hptr_fwd : f->h_hptr_bwd;
+    LevelPlan L{FWD ? f->task_fwd : f->task_bwd, FWD ? f->lptr_fwd : f->lptr_bwd, FWD ? f->hptr_fwd : f->hptr_bwd, 0, 0,
+                (int)hl.size() - 1, c->gbar, c->dstatus, nullptr};
     const char* cls = FWD ? "sptrsv_fwd" : "sptrsv_bwd";
     if (c->prof.trace) {
       if (c->prof.dtrace_len < hl.size()) {
@@ -271,15 +298,16 @@ struct Engine {
     VL_CUDA(c, cudaMemsetAsync(c->gbar, 0, 2 * sizeof(unsigned), c->stream));
     auto launch = [&](const void* fn, void** args, int lpv) -> vl_status {
       const int tpb = 16 * (32 / lpv);   // row teams per 512-thread block
-      level_cut(hl, hw, t == 1 ? 1 : ld / VecT<T>::n, &L.l_head, &L.l_tail);
+      const size_t smem = sizeof(T) * (size_t)tpb * (t == 1 ? 1 : ld);   // heavy-row partials
+      level_cut(hl, hh, hw, t == 1 ? 1 : ld / VecT<T>::n, &L.l_head, &L.l_tail);
       const int body_rows = hl[L.l_tail] - hl[L.l_head];
       // at most two blocks per SM: fewer arrivals per grid barrier
-      const int maxb = std::min(resident_blocks(c, fn, 512, 0), 2 * c->num_sms);
+      const int maxb = std::min(resident_blocks(c, fn, 512, smem), 2 * c->num_sms);
       const int grid = std::max(1, std::min(maxb, (body_rows + tpb - 1) / tpb));
       {
         ProfScope ps(c, cls, t);
         ++c->launches;
-        VL_CUDA(c, cudaLaunchCooperativeKernel(fn, grid, 512, args, 0, c->stream));
+        VL_CUDA(c, cudaLaunchCooperativeKernel(fn, grid, 512, args, smem, c->stream));
       }
       if (L.trace) {
         std::vector<long long>& h = c->prof.traces[{cls, t}];
@@ -291,6 +319,45 @@ struct Engine {
       return VL_OK;
     };
     if (t == 1) {
+      // one thread-block cluster walks all levels (see sptrsv_t1_cluster_kernel)
+      constexpr int LPV1 = FWD ? 8 : 16;   // backward rows can list hundreds of dependents
+      auto fn = sptrsv_t1_cluster_kernel<T, FWD, LPV1>;
+      const int cs = cluster_size((const void*)fn);
+      // one cluster only pays off while every level fits a few rounds of its teams;
+      // the widest levels of large problems need the whole grid
+      int widest = 0;
+      for (size_t l = 0; l + 1 < hl.size(); ++l) widest = std::max(widest, hl[l + 1] - hl[l]);
+      const int cluster_teams = cs * (1024 / 32) * (32 / LPV1);
+      if (cs >= 2 && widest <= 8 * cluster_teams) {
+        L.l_head = 0;
+        L.l_tail = L.nlev;
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = cs;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(cs);
+        cfg.blockDim = dim3(1024);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = c->stream;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        {
+          ProfScope ps(c, cls, t);
+          ++c->launches;
+          VL_CUDA(c, cudaLaunchKernelEx(&cfg, fn, L, mm, idx, val, rp, rhs, q, x));
+        }
+        if (L.trace) {
+          std::vector<long long>& h = c->prof.traces[{cls, t}];
+          h.resize(hl.size());
+          VL_CUDA(c, cudaMemcpyAsync(h.data(), L.trace, sizeof(long long) * h.size(), cudaMemcpyDeviceToHost,
+                                     c->stream));
+          VL_CUDA(c, cudaStreamSynchronize(c->stream));
+          c->prof.cuts[{cls, t}] = {L.l_head, L.l_tail};
+        }
+        return VL_OK;
+      }
       void* args[] = {&L, &mm, &idx, &val, &rp, &rhs, &q, &x};
       return launch((const void*)sptrsv_t1_kernel<T, FWD, 8>, args, 8);
     }

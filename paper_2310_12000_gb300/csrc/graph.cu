@@ -129,16 +129,34 @@ __global__ void level_work_kernel(int n, int m, const int* __restrict__ lev, con
   atomicAdd(&work[lev[s]], (unsigned long long)d);
 }
 
-__global__ void level_keys_kernel(int n, const int* __restrict__ lev, unsigned long long* __restrict__ key) {
+// Sort key (level, light, s): inside a level, rows with more than kHeavyDeps
+// dependencies come first (the solve gives each of them a whole block).
+constexpr int kHeavyDeps = 48;
+
+__device__ __forceinline__ int row_deps(int s, int m, const int32_t* nbr, const int32_t* rowptrT) {
+  if (nbr) {
+    int d = 0;
+    for (int c = 0; c < m; ++c) d += nbr[(int64_t)s * m + c] >= 0;
+    return d;
+  }
+  return rowptrT[s + 1] - rowptrT[s];
+}
+
+__global__ void level_keys_kernel(int n, int m, const int* __restrict__ lev, const int32_t* __restrict__ nbr,
+                                  const int32_t* __restrict__ rowptrT, unsigned long long* __restrict__ key,
+                                  unsigned* __restrict__ hcnt) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s < n) key[s] = ((unsigned long long)(unsigned)lev[s] << 32) | (unsigned)s;
+  if (s >= n) return;
+  const bool heavy = row_deps(s, m, nbr, rowptrT) > kHeavyDeps;
+  key[s] = ((unsigned long long)(unsigned)lev[s] << 32) | ((unsigned long long)(heavy ? 0u : 1u) << 31) | (unsigned)s;
+  if (heavy) atomicAdd(&hcnt[lev[s]], 1u);
 }
 
 __global__ void unpack_tasks_kernel(int n, const unsigned long long* __restrict__ key, int32_t* __restrict__ task,
                                     int32_t* __restrict__ lptr) {
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
-  task[p] = (int32_t)(key[p] & 0xffffffffULL);
+  task[p] = (int32_t)(key[p] & 0x7fffffffULL);
   const int l = (int)(key[p] >> 32);
   // levels are dense (0..nlev-1), so each level starts where the key's level changes
   if (p == 0 || (int)(key[p - 1] >> 32) != l) lptr[l] = p;
@@ -167,13 +185,16 @@ vl_status launch_coop(Ctx* c, const void* fn, int want_blocks, int block, void**
   return VL_OK;
 }
 
-vl_status task_order(Ctx* c, Scratch& S, int n, const int* lev, int32_t* task, int* nlev, int32_t** lptr,
-                     std::vector<int32_t>& h_lptr, Owned& own) {
+vl_status task_order(Ctx* c, Scratch& S, int n, int m, const int* lev, const int32_t* nbr, const int32_t* rowptrT,
+                     int32_t* task, int* nlev, int32_t** lptr, std::vector<int32_t>& h_lptr, int32_t** hptr,
+                     std::vector<int32_t>& h_hptr, Owned& own) {
   auto* k1 = (unsigned long long*)S.get(sizeof(unsigned long long) * n);
   auto* k2 = (unsigned long long*)S.get(sizeof(unsigned long long) * n);
-  if (!k1 || !k2) return fail(c, VL_ERR_OOM, "workspace exhausted (task order)");
+  auto* hc = (unsigned*)S.get(sizeof(unsigned) * (n + 1));
+  if (!k1 || !k2 || !hc) return fail(c, VL_ERR_OOM, "workspace exhausted (task order)");
   const int T = 256;
-  level_keys_kernel<<<(n + T - 1) / T, T, 0, VL_STREAM(c)>>>(n, lev, k1);
+  VL_CUDA(c, cudaMemsetAsync(hc, 0, sizeof(unsigned) * (n + 1), c->stream));
+  level_keys_kernel<<<(n + T - 1) / T, T, 0, VL_STREAM(c)>>>(n, m, lev, nbr, rowptrT, k1, hc);
   VL_CUDA(c, cudaGetLastError());
   size_t tb = 0;
   cub::DeviceRadixSort::SortKeys(nullptr, tb, k1, k2, n, 0, 64, c->stream);
@@ -189,7 +210,16 @@ vl_status task_order(Ctx* c, Scratch& S, int n, const int* lev, int32_t* task, i
   unpack_tasks_kernel<<<(n + T - 1) / T, T, 0, VL_STREAM(c)>>>(n, k2, task, *lptr);
   VL_CUDA(c, cudaGetLastError());
   h_lptr.resize(*nlev + 1);
+  std::vector<unsigned> h_hc(*nlev);
   VL_CUDA(c, cudaMemcpyAsync(h_lptr.data(), *lptr, sizeof(int32_t) * (*nlev + 1), cudaMemcpyDeviceToHost, c->stream));
+  VL_CUDA(c, cudaMemcpyAsync(h_hc.data(), hc, sizeof(unsigned) * (*nlev), cudaMemcpyDeviceToHost, c->stream));
+  VL_CUDA(c, cudaStreamSynchronize(c->stream));
+  // hptr[l] = end of the heavy rows of level l (they lead the level)
+  h_hptr.resize(*nlev);
+  for (int l = 0; l < *nlev; ++l) h_hptr[l] = h_lptr[l] + (int32_t)h_hc[l];
+  *hptr = own.get<int32_t>(*nlev);
+  if (!*hptr) return fail(c, VL_ERR_OOM, "workspace exhausted (level pointers)");
+  VL_CUDA(c, cudaMemcpyAsync(*hptr, h_hptr.data(), sizeof(int32_t) * (*nlev), cudaMemcpyHostToDevice, c->stream));
   VL_CUDA(c, cudaStreamSynchronize(c->stream));
   return VL_OK;
 }
@@ -273,8 +303,10 @@ vl_status build_graph_impl(Factor* f, const int32_t* N_v, const double* locs_v, 
     VL_TRY(launch_coop(c, (const void*)levels_bwd_kernel, (n + 7) / 8, 256, args));
   }
   VL_TRY(check_dev_status(c, "level schedule"));
-  VL_TRY(task_order(c, S, n, f->lev_fwd, f->task_fwd, &f->nlev_fwd, &f->lptr_fwd, f->h_lptr_fwd, f->mem));
-  VL_TRY(task_order(c, S, n, f->lev_bwd, f->task_bwd, &f->nlev_bwd, &f->lptr_bwd, f->h_lptr_bwd, f->mem));
+  VL_TRY(task_order(c, S, n, m, f->lev_fwd, f->nbr, nullptr, f->task_fwd, &f->nlev_fwd, &f->lptr_fwd, f->h_lptr_fwd,
+                    &f->hptr_fwd, f->h_hptr_fwd, f->mem));
+  VL_TRY(task_order(c, S, n, m, f->lev_bwd, nullptr, f->rowptrT, f->task_bwd, &f->nlev_bwd, &f->lptr_bwd,
+                    f->h_lptr_bwd, &f->hptr_bwd, f->h_hptr_bwd, f->mem));
   for (int dir = 0; dir < 2; ++dir) {
     const int nl = dir == 0 ? f->nlev_fwd : f->nlev_bwd;
     auto* w = (unsigned long long*)S.get(sizeof(unsigned long long) * nl);

@@ -8,6 +8,8 @@
 // the row's m neighbours, otherwise they split the columns.
 #pragma once
 
+#include <cooperative_groups.h>
+
 #include "vl_device.cuh"
 
 namespace vl {
@@ -259,6 +261,7 @@ __global__ void __launch_bounds__(256) spmv_Bt_t1_kernel(int n, const int32_t* _
 struct LevelPlan {
   const int32_t* task;
   const int32_t* lptr;
+  const int32_t* hptr;         // heavy rows of level l are task[lptr[l] .. hptr[l])
   int l_head, l_tail, nlev;
   unsigned* bar;               // {count, generation}, count == 0 at launch
   DevStatus* st;
@@ -314,12 +317,44 @@ __device__ __forceinline__ void row_pre(RowPre<T, LPV, NV>& r, int p, int m, con
 
 // Finishes a prefetched row: gathers its dependencies (first chunk already in
 // registers) and stores x_s.
+// acc += sum over one chunk of <= LPV dependencies (index jl / weight al held by
+// lane sl of the team) of al * x[jl, :], UNR rows' loads in flight per lane.
 template <typename T, int LPV, int NV, int UNR>
-__device__ __forceinline__ void row_run(RowPre<T, LPV, NV>& r, const int32_t* __restrict__ idx,
-                                        const T* __restrict__ val, T* x, int ld) {
+__device__ __forceinline__ void chunk_gather(T* acc, int jl, T al, int cnt, const T* x, int ld) {
   constexpr int VEC = VecT<T>::n;
   using V = typename VecT<T>::type;
   const unsigned mask = team_mask<LPV>();
+  const int sl = (threadIdx.x & 31) % LPV;
+  for (int q0 = 0; q0 < cnt; q0 += UNR) {
+    int j[UNR];
+    T a[UNR];
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) {
+      const int qq = q0 + u;
+      const int src = qq < LPV ? qq : LPV - 1;
+      const int jj = __shfl_sync(mask, jl, src, LPV);
+      const T aa = __shfl_sync(mask, al, src, LPV);
+      j[u] = (qq < cnt) ? jj : -1;
+      a[u] = aa;
+    }
+    V xv[UNR][NV];
+#pragma unroll
+    for (int u = 0; u < UNR; ++u)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const int col = (sl + LPV * v) * VEC;
+        xv[u][v] = (j[u] >= 0 && col < ld) ? ldcg_vec(x + (int64_t)j[u] * ld + col) : V{};
+      }
+#pragma unroll
+    for (int u = 0; u < UNR; ++u)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) fma_vec(acc + v * VEC, j[u] >= 0 ? a[u] : T(0), xv[u][v]);
+  }
+}
+
+template <typename T, int LPV, int NV, int UNR>
+__device__ __forceinline__ void row_run(RowPre<T, LPV, NV>& r, const int32_t* __restrict__ idx,
+                                        const T* __restrict__ val, T* x, int ld) {
   const int sl = (threadIdx.x & 31) % LPV;
   for (int e0 = r.beg; e0 < r.end; e0 += LPV) {
     const int cnt = min(LPV, r.end - e0);
@@ -329,33 +364,50 @@ __device__ __forceinline__ void row_run(RowPre<T, LPV, NV>& r, const int32_t* __
       jl = sl < cnt ? idx[e0 + sl] : -1;
       al = jl >= 0 ? val[e0 + sl] : T(0);
     }
-    for (int q0 = 0; q0 < cnt; q0 += UNR) {
-      int j[UNR];
-      T a[UNR];
-#pragma unroll
-      for (int u = 0; u < UNR; ++u) {
-        const int qq = q0 + u;
-        const int src = qq < LPV ? qq : LPV - 1;
-        const int jj = __shfl_sync(mask, jl, src, LPV);
-        const T aa = __shfl_sync(mask, al, src, LPV);
-        j[u] = (qq < cnt) ? jj : -1;
-        a[u] = aa;
-      }
-      V xv[UNR][NV];
-#pragma unroll
-      for (int u = 0; u < UNR; ++u)
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          const int col = (sl + LPV * v) * VEC;
-          xv[u][v] = (j[u] >= 0 && col < ld) ? ldcg_vec(x + (int64_t)j[u] * ld + col) : V{};
-        }
-#pragma unroll
-      for (int u = 0; u < UNR; ++u)
-#pragma unroll
-        for (int v = 0; v < NV; ++v) fma_vec(r.acc + v * VEC, j[u] >= 0 ? a[u] : T(0), xv[u][v]);
-    }
+    chunk_gather<T, LPV, NV, UNR>(r.acc, jl, al, cnt, x, ld);
   }
   team_store<T, LPV, NV>(x, r.s, ld, T(1), r.acc);
+}
+
+// A heavy row (many dependencies) by the whole block: team k takes dependency
+// chunks k, k + teams, ...; the teams' partial rows meet in shared memory and
+// are summed in team order (deterministic). Every thread of the block calls it.
+template <typename T, bool FWD, int LPV, int NV, int UNR>
+__device__ void heavy_row(int p, int m, const LevelPlan& L, const int32_t* __restrict__ idx, const T* __restrict__ val,
+                          const int32_t* __restrict__ rowptr, const T* __restrict__ rhs, const T* __restrict__ q, T* x,
+                          int ld, T* part) {
+  constexpr int VEC = VecT<T>::n;
+  constexpr int RPW = 32 / LPV;
+  const int tpb = (blockDim.x >> 5) * RPW;
+  const int tib = (threadIdx.x >> 5) * RPW + (threadIdx.x & 31) / LPV;
+  const int sl = (threadIdx.x & 31) % LPV;
+  const int s = L.task[p];
+  const int beg = FWD ? s * m : rowptr[s];
+  const int end = FWD ? s * m + m : rowptr[s + 1];
+  T acc[NV * VEC];
+#pragma unroll
+  for (int i = 0; i < NV * VEC; ++i) acc[i] = T(0);
+  for (int e0 = beg + tib * LPV; e0 < end; e0 += tpb * LPV) {
+    const int cnt = min(LPV, end - e0);
+    const int jl = sl < cnt ? idx[e0 + sl] : -1;
+    const T al = jl >= 0 ? val[e0 + sl] : T(0);
+    chunk_gather<T, LPV, NV, UNR>(acc, jl, al, cnt, x, ld);
+  }
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const int col = (sl + LPV * v) * VEC;
+    if (col < ld)
+#pragma unroll
+      for (int i = 0; i < VEC; ++i) part[tib * ld + col + i] = acc[v * VEC + i];
+  }
+  __syncthreads();
+  const T qs = q ? q[s] : T(1);
+  for (int col = threadIdx.x; col < ld; col += blockDim.x) {
+    T sum = qs * rhs[(int64_t)s * ld + col];
+    for (int k = 0; k < tpb; ++k) sum += part[k * ld + col];
+    x[(int64_t)s * ld + col] = sum;
+  }
+  __syncthreads();
 }
 
 // Scalar rows (t = 1): the team's lanes split the dependencies, K loads each in flight.
@@ -416,22 +468,70 @@ __device__ __forceinline__ void row_run1(RowPre1<T, LPV>& r, const int32_t* __re
   if (sl == 0) x[r.s] = r.b + acc;
 }
 
+// A heavy scalar row by the whole block: each team takes K dependency chunks of
+// LPV at a stride, reduces in registers, and thread 0 sums the team partials in
+// order (deterministic). Every thread of the block calls it.
+template <typename T, bool FWD, int LPV>
+__device__ void heavy_row1(int p, int m, const LevelPlan& L, const int32_t* __restrict__ idx,
+                           const T* __restrict__ val, const int32_t* __restrict__ rowptr, const T* __restrict__ rhs,
+                           const T* __restrict__ q, T* x, T* part) {
+  constexpr int RPW = 32 / LPV, K = 4;
+  const unsigned mask = team_mask<LPV>();
+  const int tpb = (blockDim.x >> 5) * RPW;
+  const int tib = (threadIdx.x >> 5) * RPW + (threadIdx.x & 31) / LPV;
+  const int sl = (threadIdx.x & 31) % LPV;
+  const int s = L.task[p];
+  const int beg = FWD ? s * m : rowptr[s];
+  const int end = FWD ? s * m + m : rowptr[s + 1];
+  T acc = T(0);
+  for (int e0 = beg + tib * LPV * K + sl; e0 < end; e0 += tpb * LPV * K) {
+    int j[K];
+    T a[K], xv[K];
+#pragma unroll
+    for (int u = 0; u < K; ++u) {
+      const int e = e0 + u * LPV;
+      j[u] = e < end ? idx[e] : -1;
+      a[u] = j[u] >= 0 ? val[e] : T(0);
+      xv[u] = j[u] >= 0 ? __ldcg(&x[j[u]]) : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < K; ++u) acc += a[u] * xv[u];
+  }
+#pragma unroll
+  for (int off = LPV / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(mask, acc, off, LPV);
+  if (sl == 0) part[tib] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    T sum = (q ? q[s] : T(1)) * rhs[s];
+    for (int k = 0; k < tpb; ++k) sum += part[k];
+    x[s] = sum;
+  }
+  __syncthreads();
+}
+
 // Walks the levels with the head/body/tail split; each team prefetches its next
-// row (pre) before the barrier that precedes it and finishes it after (run).
-template <int LPV, typename Pre, typename Run>
-__device__ __forceinline__ void level_walk(const LevelPlan& L, Pre pre, Run run) {
+// light row (pre) before the barrier that precedes it and finishes it after
+// (run); the heavy rows that lead each level are done first, a block per row
+// (heavy(p), called by every thread of the block).
+template <int LPV, typename Pre, typename Run, typename Heavy>
+__device__ __forceinline__ void level_walk(const LevelPlan& L, Pre pre, Run run, Heavy heavy) {
   constexpr int RPW = 32 / LPV;
   const int tpb = (blockDim.x >> 5) * RPW;
   const int tib = (threadIdx.x >> 5) * RPW + (threadIdx.x & 31) / LPV;
   const int G = gridDim.x * tpb, g = blockIdx.x * tpb + tib;
   const bool tr = L.trace && blockIdx.x == 0 && threadIdx.x == 0;
+  auto first_light = [&](int l, int start, int& p) {
+    p = L.hptr[l] + start;
+    return p < L.lptr[l + 1];
+  };
   // one block: levels [l0, l1) with a block barrier after each
   auto solo = [&](int l0, int l1) {
-    int p = (l0 < l1) ? L.lptr[l0] + tib : 0;
-    bool has = l0 < l1 && p < L.lptr[l0 + 1];
+    int p = 0;
+    bool has = l0 < l1 && first_light(l0, tib, p);
     if (has) pre(p);
     for (int l = l0; l < l1; ++l) {
       if (tr) L.trace[l] = clock64();
+      for (int h = L.lptr[l]; h < L.hptr[l]; ++h) heavy(h);
       while (has) {
         run();
         p += tpb;
@@ -439,8 +539,7 @@ __device__ __forceinline__ void level_walk(const LevelPlan& L, Pre pre, Run run)
         if (has) pre(p);
       }
       if (l + 1 < l1) {
-        p = L.lptr[l + 1] + tib;
-        has = p < L.lptr[l + 2];
+        has = first_light(l + 1, tib, p);
         if (has) pre(p);
       }
       __syncthreads();
@@ -449,11 +548,12 @@ __device__ __forceinline__ void level_walk(const LevelPlan& L, Pre pre, Run run)
   if (blockIdx.x == 0) solo(0, L.l_head);
   if (L.l_head > 0 && L.l_head < L.nlev) grid_barrier(L.bar, L.st);
   {
-    int p = (L.l_head < L.l_tail) ? L.lptr[L.l_head] + g : 0;
-    bool has = L.l_head < L.l_tail && p < L.lptr[L.l_head + 1];
+    int p = 0;
+    bool has = L.l_head < L.l_tail && first_light(L.l_head, g, p);
     if (has) pre(p);
     for (int l = L.l_head; l < L.l_tail; ++l) {
       if (tr) L.trace[l] = clock64();
+      for (int h = L.lptr[l] + blockIdx.x; h < L.hptr[l]; h += gridDim.x) heavy(h);
       while (has) {
         run();
         p += G;
@@ -461,8 +561,7 @@ __device__ __forceinline__ void level_walk(const LevelPlan& L, Pre pre, Run run)
         if (has) pre(p);
       }
       if (l + 1 < L.l_tail) {
-        p = L.lptr[l + 1] + g;
-        has = p < L.lptr[l + 2];
+        has = first_light(l + 1, g, p);
         if (has) pre(p);
       }
       grid_barrier(L.bar, L.st);
@@ -472,24 +571,70 @@ __device__ __forceinline__ void level_walk(const LevelPlan& L, Pre pre, Run run)
   if (tr) L.trace[L.nlev] = clock64();
 }
 
+// Scalar-row (t = 1) solve by one thread-block cluster: the cluster walks every
+// level with the hardware cluster barrier between levels (release/acquire at
+// cluster scope). A t = 1 solve moves a few megabytes, so its time is the level
+// chain; a cluster barrier is far cheaper than a grid-wide one, and the rest of
+// the GPU stays free. Each team prefetches its next row before the barrier.
+template <typename T, bool FWD, int LPV>
+__global__ void __launch_bounds__(1024) sptrsv_t1_cluster_kernel(LevelPlan L, int m, const int32_t* __restrict__ idx,
+                                                                 const T* __restrict__ val,
+                                                                 const int32_t* __restrict__ rowptr,
+                                                                 const T* __restrict__ rhs, const T* __restrict__ q,
+                                                                 T* x) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  constexpr int RPW = 32 / LPV;
+  const int tpb = (blockDim.x >> 5) * RPW;
+  const int tib = (threadIdx.x >> 5) * RPW + (threadIdx.x & 31) / LPV;
+  const int G = (int)cl.num_blocks() * tpb, g = (int)cl.block_rank() * tpb + tib;
+  const bool tr = L.trace && cl.block_rank() == 0 && threadIdx.x == 0;
+  RowPre1<T, LPV> r;
+  int p = L.lptr[0] + g;
+  bool has = L.nlev > 0 && p < L.lptr[1];
+  if (has) row_pre1<T, FWD, LPV>(r, p, m, L, idx, val, rowptr, rhs, q);
+  for (int l = 0; l < L.nlev; ++l) {
+    if (tr) L.trace[l] = clock64();
+    while (has) {
+      row_run1<T, LPV>(r, idx, val, x);
+      p += G;
+      has = p < L.lptr[l + 1];
+      if (has) row_pre1<T, FWD, LPV>(r, p, m, L, idx, val, rowptr, rhs, q);
+    }
+    if (l + 1 < L.nlev) {
+      p = L.lptr[l + 1] + g;
+      has = p < L.lptr[l + 2];
+      if (has) row_pre1<T, FWD, LPV>(r, p, m, L, idx, val, rowptr, rhs, q);
+    }
+    cl.sync();
+  }
+  if (tr) L.trace[L.nlev] = clock64();
+}
+
 template <typename T, bool FWD, int LPV, int NV, int UNR>
 __global__ void __launch_bounds__(512) sptrsv_kernel(LevelPlan L, int m, const int32_t* __restrict__ idx,
                                                      const T* __restrict__ val, const int32_t* __restrict__ rowptr,
                                                      const T* __restrict__ rhs, const T* __restrict__ q, T* x, int ld) {
+  extern __shared__ unsigned char vl_smem[];
+  T* part = reinterpret_cast<T*>(vl_smem);
   RowPre<T, LPV, NV> r;
   level_walk<LPV>(
       L, [&](int p) { row_pre<T, FWD, LPV, NV>(r, p, m, L, idx, val, rowptr, rhs, q, ld); },
-      [&]() { row_run<T, LPV, NV, UNR>(r, idx, val, x, ld); });
+      [&]() { row_run<T, LPV, NV, UNR>(r, idx, val, x, ld); },
+      [&](int p) { heavy_row<T, FWD, LPV, NV, UNR>(p, m, L, idx, val, rowptr, rhs, q, x, ld, part); });
 }
 
 template <typename T, bool FWD, int LPV>
 __global__ void __launch_bounds__(512) sptrsv_t1_kernel(LevelPlan L, int m, const int32_t* __restrict__ idx,
                                                         const T* __restrict__ val, const int32_t* __restrict__ rowptr,
                                                         const T* __restrict__ rhs, const T* __restrict__ q, T* x) {
+  extern __shared__ unsigned char vl_smem[];
+  T* part = reinterpret_cast<T*>(vl_smem);
   RowPre1<T, LPV> r;
   level_walk<LPV>(
       L, [&](int p) { row_pre1<T, FWD, LPV>(r, p, m, L, idx, val, rowptr, rhs, q); },
-      [&]() { row_run1<T, LPV>(r, idx, val, x); });
+      [&]() { row_run1<T, LPV>(r, idx, val, x); },
+      [&](int p) { heavy_row1<T, FWD, LPV>(p, m, L, idx, val, rowptr, rhs, q, x, part); });
 }
 
 // ----------------------------------------------------------------------------- column reductions

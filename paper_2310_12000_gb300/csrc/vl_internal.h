@@ -144,8 +144,11 @@ struct Factor {
   int32_t* task_bwd = nullptr;
   int32_t* lptr_fwd = nullptr;  // nlev_fwd + 1: first task of each level
   int32_t* lptr_bwd = nullptr;
+  int32_t* hptr_fwd = nullptr;  // nlev: end of the leading heavy rows of each level
+  int32_t* hptr_bwd = nullptr;
   std::vector<int32_t> h_lptr_fwd, h_lptr_bwd;
   std::vector<int64_t> h_lwork_fwd, h_lwork_bwd;   // dependencies per level
+  std::vector<int32_t> h_hptr_fwd, h_hptr_bwd;     // host copies of hptr
 };
 
 struct State {
