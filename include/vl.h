@@ -89,7 +89,7 @@ typedef struct vl_opts {
   int precision;        /* vl_precision                                  default VL_FP64 */
   int precond;          /* vl_precond                                    default VL_PREC_VADU */
   int t;                /* SLQ probe vectors (Rademacher)                default 50 */
-  int k;                /* LRAC rank                                     default 50 */
+  int k;                /* LRAC rank, 1 <= k <= min(n, 1024)              default 50 */
   int s;                /* simulation vectors for predictive variances   default 100 */
   double cg_tol;        /* per-column relative residual ||r|| / ||b||    default 1e-6 */
   int cg_max_iter;      /*                                               default 1000 */
@@ -188,8 +188,11 @@ vl_status vl_state_stats(const vl_state* s, vl_stats* out);
  * (Eq. logdetsplit for VADU/LVA, Eq. logdetsplit2 for LRAC) and the last term
  * estimated by SLQ (Eq. def_SLQ) from the CG coefficients of opts->t probe solves,
  * probes z = P^{1/2} r with r Rademacher from Philox4x64-10(counter = (caller index,
- * j / 256, 0, 0), key = (seed, 0)). log p includes every constant (-log y! for
- * Poisson). Writes the host scalars *lml (and *logdet if non-NULL). */
+ * j / 256, 0, 0), key = (seed, 0)). For LRAC the probe is z = L_k r1 + W^{-1/2} r2
+ * (E z z^T = P) with r2 as above and r1 in {+-1}^k from counter (rank index, j / 256,
+ * 3, 0), and log det(Sigma_tilde W + I) = log det(I_k + L_k^T W L_k) + SLQ term.
+ * log p includes every constant (-log y! for Poisson). Writes the host scalars *lml
+ * (and *logdet if non-NULL). */
 vl_status vl_log_marglik(vl_state* s, const vl_opts* opts, double* lml, double* logdet,
                          vl_stats* stats);
 
@@ -209,7 +212,10 @@ vl_status vl_pred_var(vl_state* s, const double* test_locs, int64_t np, const do
 /* Kernel timing. While enabled (enable >= 1), every launch of the library's hot kernels is
  * bracketed by a pair of CUDA events on the context's stream, grouped by kernel
  * class and block width: "sptrsv_fwd", "sptrsv_bwd", "spmv_B", "spmv_Bt",
- * "pcg_update", "coldot", "factor", "knn". Costs two event records per launch. */
+ * "pcg_update", "coldot", "factor", "knn", and for LRAC "woodbury" (one
+ * preconditioner apply), "lrac_gram" and "lrac_kxk" (at width k: C = I + L^T W L,
+ * its Cholesky factor and inverse) and "pivoted_cholesky" (at width k). Costs two
+ * event records per launch group. */
 vl_status vl_profile_enable(vl_ctx* ctx, int enable);
 /* With enable >= 2 every triangular solve also records block 0's SM clock at each
  * level boundary; this returns the last such trace of class `cls` ("sptrsv_fwd" /
@@ -263,13 +269,25 @@ vl_status vl_apply(vl_state* s, int op, const double* X, int t, const vl_opts* o
  * overlap on the GPU race. The paper has no counterpart; this is a deployment aid. */
 vl_status vl_apply_A_noalloc(vl_state* s, const double* X, int t, double* Y);
 
-/* Solves (W + Sigma_tilde^{-1}) U = RHS (t columns) by PCG with T extraction (the
- * appendix algorithm, u_0 = 0, per-column stop ||r|| <= cg_tol ||b||), in the
- * precision and preconditioner of opts (LRAC solves the form-2 system, Eq. pcls2).
+/* Solves the preconditioner's system by PCG with T extraction (the appendix
+ * algorithm, u_0 = 0, per-column stop ||r|| <= cg_tol ||b||), in the precision and
+ * preconditioner of opts: (W + Sigma_tilde^{-1}) U = RHS for VADU and LVA (Eq. pcls1),
+ * (Sigma_tilde + W^{-1}) U = RHS for LRAC (Eq. pcls2).
  * T_diag/T_off: t x lmax row-major (may be NULL), iters: t ints (may be NULL),
  * relres: t doubles (may be NULL). */
 vl_status vl_pcg_solve(vl_state* s, const double* RHS, int t, const vl_opts* opts, double* U,
                        int lmax, double* T_diag, double* T_off, int* iters, double* relres);
+
+/* The rank-k pivoted Cholesky factor L_k of Sigma used by the LRAC preconditioner
+ * (Section 3.1.2; Harbrecht, Peters & Schneider 2012): residual diagonal d = diag Sigma
+ * (nugget included), k steps of pivot p = argmax d (ties to the lowest Vecchia index),
+ * L[:, j] = (Sigma[:, p] - L[:, :j] L[p, :j]^T) / sqrt(d_p), d -= L[:, j]^2, d_p = 0, in
+ * float64. Built on first use and kept with the factor until vl_factor_refit.
+ * piv: k int32 Vecchia indices of the pivots (may be NULL); L: n x k float64,
+ * caller order, row-major (may be NULL). Errors: VL_ERR_INVALID_ARG (k outside
+ * [1, min(n, 1024)]), VL_ERR_NOT_SPD (d_p <= 0 before step k: Sigma has numerical
+ * rank < k), VL_ERR_OOM. */
+vl_status vl_lrac_export(vl_factor* f, int k, int32_t* piv, double* L);
 
 #ifdef __cplusplus
 }

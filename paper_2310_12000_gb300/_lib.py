@@ -118,6 +118,7 @@ def library():
         "vl_apply": (st, [vp, i32, vp, i32, vp, vp]),
         "vl_pcg_solve": (st, [vp, vp, i32, vp, vp, i32, vp, vp, vp, vp]),
         "vl_apply_A_noalloc": (st, [vp, vp, i32, vp]),
+        "vl_lrac_export": (st, [vp, i32, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -292,6 +293,13 @@ class Factor:
         self.ctx.check(self.ctx.lib.vl_factor_export(self.h, N.ctypes.data, A.ctypes.data, D.ctypes.data,
                                                      lf.ctypes.data, lb.ctypes.data))
         return {"N": N, "A": A, "D": D, "lev_fwd": lf, "lev_bwd": lb}
+
+    def lrac_export(self, k: int, with_L: bool = True):
+        """(pivots as Vecchia indices, L_k as n x k in caller order or None)."""
+        piv = np.empty(k, np.int32)
+        L = np.empty((self.n, k)) if with_L else None
+        self.ctx.check(self.ctx.lib.vl_lrac_export(self.h, k, piv.ctypes.data, _ptr(L, np.float64)))
+        return piv, L
 
     def find_mode(self, lik: int, y, F=None, opts: Opts | None = None, mode_out=None, allow_unconverged=False):
         y = _host(y, np.float64)

@@ -116,7 +116,8 @@ __global__ void diag_fn_kernel(int n, int mode, const double* __restrict__ W, co
     double v;
     if (mode == 0) v = sqrt(W[s] + 1.0 / D[s]);   // VADU P^{1/2} diagonal
     else if (mode == 1) v = 1.0 / sqrt(D[s]);     // D^{-1/2}
-    else v = sqrt(W[s]);                          // W^{1/2}
+    else if (mode == 2) v = sqrt(W[s]);           // W^{1/2}
+    else v = 1.0 / sqrt(W[s]);                    // W^{-1/2} (LRAC probes)
     out[s] = v;
   }
 }
@@ -159,6 +160,16 @@ __global__ void pred_kernel(int np, int m, const int32_t* __restrict__ nbr, cons
 __global__ void pred_finish_kernel(int np, const double* __restrict__ Dp, double inv_s, double* __restrict__ var) {
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p < np) var[p] = Dp[p] + var[p] * inv_s;
+}
+
+// L_out[s2u[s] * k + j] = L[j * n + s]  (column-major storage rows -> caller rows)
+__global__ void lrac_export_kernel(int n, int k, const int32_t* __restrict__ s2u, const double* __restrict__ L,
+                                   double* __restrict__ out) {
+  const int64_t total = (int64_t)n * k;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(e / n), s = (int)(e % n);
+    out[(int64_t)s2u[s] * k + j] = L[e];
+  }
 }
 
 __global__ void translate_kernel(int64_t total, const int32_t* __restrict__ map, int32_t* __restrict__ idx) {
@@ -248,10 +259,17 @@ static vl_status check_opts(Ctx* c, const vl_opts* o) {
   if (o->precision != VL_FP64 && o->precision != VL_FP32_REFINE)
     return fail(c, VL_ERR_INVALID_ARG, "unknown precision");
   if (o->precond < 0 || o->precond > 2) return fail(c, VL_ERR_INVALID_ARG, "unknown preconditioner");
-  if (o->precond == VL_PREC_LRAC) return fail(c, VL_ERR_INVALID_ARG, "LRAC preconditioner is not available in this build");
+  if (o->precond == VL_PREC_LRAC && (o->k < 1 || o->k > kMaxRank))
+    return fail(c, VL_ERR_INVALID_ARG, "LRAC rank k must be in [1, " + std::to_string(kMaxRank) + "]");
   if (o->t < 1 || o->t > 256 || o->s < 1 || !(o->cg_tol > 0) || o->cg_max_iter < 1 || o->newton_max_iter < 1)
     return fail(c, VL_ERR_INVALID_ARG, "invalid option value");
   return VL_OK;
+}
+
+// The LRAC factor L_k of Sigma (built once per covariance parameters and k).
+static vl_status ensure_precond(Factor* f, const vl_opts* o) {
+  if (o->precond != VL_PREC_LRAC) return VL_OK;
+  return lrac_build(f, o->k);
 }
 
 // ----------------------------------------------------------------------------- log-likelihood pieces
@@ -290,7 +308,7 @@ static vl_status solve1(State* st, const vl_opts* o, Engine<double>& E64, Engine
   const int n = (int)st->f->n;
   int used = 0;
   if (o->precision == VL_FP64) {
-    VL_TRY(E64.pcg(rhs, x, o->cg_tol, o->cg_max_iter, &used));
+    VL_TRY(E64.solve_A1(rhs, x, o->cg_tol, o->cg_max_iter, &used));
     if (stats) {
       stats->cg_calls++;
       stats->cg_iters_total += used;
@@ -319,7 +337,7 @@ static vl_status solve1(State* st, const vl_opts* o, Engine<double>& E64, Engine
     const double inner = std::min(0.1, std::max(1e-6, 0.5 * o->cg_tol * bn / rn));
     convert_kernel<double, float><<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, res, r32);
     VL_CUDA(c, cudaGetLastError());
-    VL_TRY(E32->pcg(r32, d32, inner, o->cg_max_iter, &used));
+    VL_TRY(E32->solve_A1(r32, d32, inner, o->cg_max_iter, &used));
     accumulate_kernel<double, float><<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, x, d32);
     VL_CUDA(c, cudaGetLastError());
     if (stats) {
@@ -343,15 +361,17 @@ __global__ void repack_kernel(int64_t total, const double* __restrict__ in, floa
     out[e] = (float)in[e];
 }
 
-// SLQ (Eq. def_SLQ): probes z = P^{1/2} r, PCG on A u = z with T extraction,
-// gamma_i = (r_0^T z_0)_i e1^T log(T_i) e1. Returns the t gammas on the host.
+// SLQ (Eq. def_SLQ): probes z = P^{1/2} r, PCG on the preconditioner's system with
+// T extraction, gamma_i = (r_0^T z_0)_i e1^T log(T_i) e1. Returns the t gammas on the
+// host and, for LRAC, log det(I + L^T W L) of the same engine in *logdetC.
 template <typename T>
-static vl_status slq_run(State* st, const vl_opts* o, std::vector<double>& gam, vl_stats* stats) {
+static vl_status slq_run(State* st, const vl_opts* o, std::vector<double>& gam, vl_stats* stats, double* logdetC) {
   Ctx* c = st->ctx;
   Factor* f = st->f;
   const int n = (int)f->n, t = o->t;
   Scratch S(c);
   Engine<T> E(c);
+  VL_TRY(ensure_precond(f, o));
   VL_TRY(E.init(f, t, o->precond, st->W, o->cg_max_iter + 1));
   // VADU: z = B^T (W + D^{-1})^{1/2} r;  LVA: z = B^T D^{-1/2} r     (Section 3.1.1)
   T* Rm = S.get<T>((size_t)n * E.ld);
@@ -364,10 +384,20 @@ static vl_status slq_run(State* st, const vl_opts* o, std::vector<double>& gam, 
   int* bad = S.get<int>(1);
   if (!Rm || !Zm || !Um || !sc64 || !sc || !gdev || !work || !bad) return fail(c, VL_ERR_OOM, "workspace exhausted (SLQ)");
   rademacher_kernel<T><<<(n + 127) / 128, 128, 0, VL_STREAM(c)>>>(n, t, E.ld, f->s2u, o->seed, 0, 0, Rm);
-  diag_fn_kernel<<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, o->precond == VL_PREC_VADU ? 0 : 1, st->W, f->D64, sc64);
+  const int dmode = o->precond == VL_PREC_VADU ? 0 : (o->precond == VL_PREC_LVA ? 1 : 3);
+  diag_fn_kernel<<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, dmode, st->W, f->D64, sc64);
   convert_kernel<double, T><<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, sc64, sc);
   VL_CUDA(c, cudaGetLastError());
-  VL_TRY(E.opBt(Rm, sc, nullptr, nullptr, Zm));
+  if (o->precond == VL_PREC_LRAC) {
+    // z = L r1 + W^{-1/2} r2, r1 in {+-1}^k drawn by rank index on stream 3 (Section 3.1.2)
+    double* r1 = S.get<double>((size_t)E.kr * t);
+    if (!r1) return fail(c, VL_ERR_OOM, "workspace exhausted (SLQ probes)");
+    rademacher_kernel<double><<<(E.kr + 127) / 128, 128, 0, VL_STREAM(c)>>>(E.kr, t, t, nullptr, o->seed, 3, 0, r1);
+    VL_CUDA(c, cudaGetLastError());
+    VL_TRY(E.lrac_lowrank_plus(r1, Rm, sc, Zm));
+  } else {
+    VL_TRY(E.opBt(Rm, sc, nullptr, nullptr, Zm));
+  }
   int used = 0;
   VL_TRY(E.pcg(Zm, Um, o->cg_tol, o->cg_max_iter, &used));
   VL_CUDA(c, cudaMemsetAsync(bad, 0, sizeof(int), c->stream));
@@ -393,6 +423,7 @@ static vl_status slq_run(State* st, const vl_opts* o, std::vector<double>& gam, 
   }
   if (relmax > o->cg_tol && itmax >= o->cg_max_iter)
     return fail(c, VL_ERR_NOT_CONVERGED, "SLQ probe solves reached cg_max_iter");
+  if (logdetC) *logdetC = (o->precond == VL_PREC_LRAC) ? E.logdetC : 0.0;
   return VL_OK;
 }
 
@@ -419,7 +450,7 @@ static vl_status sim_block(State* st, const vl_opts* o, Engine<double>& E64, int
   VL_TRY(E64.opBt(z2, sD, z1, sW, z3));
   int used = 0;
   if (o->precision == VL_FP64) {
-    VL_TRY(E64.pcg(z3, U, o->cg_tol, o->cg_max_iter, &used));
+    VL_TRY(E64.solve_A1(z3, U, o->cg_tol, o->cg_max_iter, &used));
     if (stats) {
       stats->cg_calls++;
       stats->cg_iters_total += used;
@@ -450,7 +481,7 @@ static vl_status sim_block(State* st, const vl_opts* o, Engine<double>& E64, int
     if (worst <= o->cg_tol) break;
     repack_kernel<<<grid_for(c, vec), 256, 0, VL_STREAM(c)>>>(vec, res, r32);
     VL_CUDA(c, cudaGetLastError());
-    VL_TRY(E32.pcg(r32, d32, std::max(o->cg_tol, 1e-4), o->cg_max_iter, &used));
+    VL_TRY(E32.solve_A1(r32, d32, std::max(o->cg_tol, 1e-4), o->cg_max_iter, &used));
     accumulate_kernel<double, float><<<grid_for(c, vec), 256, 0, VL_STREAM(c)>>>(vec, U, d32);
     VL_CUDA(c, cudaGetLastError());
     if (stats) {
@@ -471,6 +502,7 @@ static vl_status apply_op(State* st, int op, const double* Xd, int t, const vl_o
   Factor* f = st->f;
   const int n = (int)f->n;
   Engine<T> E(c);
+  VL_TRY(ensure_precond(f, o));
   VL_TRY(E.init(f, t, o->precond, st->W, 0));
   to_storage_kernel<T><<<grid_for(c, (int64_t)n * E.ld), 256, 0, VL_STREAM(c)>>>(n, t, E.ld, f->s2u, Xd, E.u);
   VL_CUDA(c, cudaGetLastError());
@@ -497,6 +529,7 @@ static vl_status pcg_op(State* st, const double* Rd, int t, const vl_opts* o, do
   Factor* f = st->f;
   const int n = (int)f->n;
   Engine<T> E(c);
+  VL_TRY(ensure_precond(f, o));
   VL_TRY(E.init(f, t, o->precond, st->W, o->cg_max_iter + 1));
   Scratch S(c);
   T* Bm = S.get<T>((size_t)n * E.ld);
@@ -726,6 +759,7 @@ vl_status vl_factor_refit(vl_factor* f, double sigma2, double range, const vl_op
   f->sigma2 = sigma2;
   f->rho = range;
   f->nugget = nugget_of(opts, sigma2);
+  lrac_drop(f);   // L_k belongs to the old covariance parameters
   VL_CUDA(c, cudaMemsetAsync(c->dstatus, 0, sizeof(DevStatus), c->stream));
   VL_TRY(factor_rows(c, f->n, f->m, f->locs_s, f->locs_s, f->nbr, f->cov, f->sigma2, f->rho, f->nugget, f->A64, f->D64,
                      f->s2v));
@@ -829,6 +863,7 @@ void vl_factor_destroy(vl_factor* f) {
   if (!f) return;
   Ctx* c = f->ctx;
   cudaStreamSynchronize(c->stream);
+  lrac_drop(f);
   f->mem.free_all();
   delete f;
   ctx_release(c);
@@ -888,22 +923,19 @@ vl_status vl_find_mode(vl_factor* f, int lik, const double* y, const double* F, 
   double psi = 0.0;
   int it = 0;
   bool converged = false;
+  s = ensure_precond(f, opts);
+  if (s != VL_OK) return bail(s);
   s = E64.init(f, 1, opts->precond, st->W, mixed ? 0 : opts->cg_max_iter + 1);
   if (s != VL_OK) return bail(s);
   s = psi_eval(st, E64, S, st->b, &psi, nullptr, nullptr);
   if (s != VL_OK) return bail(s);
   for (it = 1; it <= opts->newton_max_iter; ++it) {
     lik_kernel<<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, lik, st->y, st->F, st->b, st->W, g, rhs, nullptr);
-    diag_prep_kernel<double><<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, opts->precond, st->W, f->D64, E64.W, E64.Dinv,
-                                                                    E64.dsc, E64.Dt, E64.Winv);
+    s = E64.set_W(st->W);
+    if (s != VL_OK) return bail(s);
     if (mixed) {
-      if (!E32.W) {
-        s = E32.init(f, 1, opts->precond, st->W, opts->cg_max_iter + 1);
-        if (s != VL_OK) return bail(s);
-      } else {
-        diag_prep_kernel<float><<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, opts->precond, st->W, f->D64, E32.W,
-                                                                       E32.Dinv, E32.dsc, E32.Dt, E32.Winv);
-      }
+      s = E32.W ? E32.set_W(st->W) : E32.init(f, 1, opts->precond, st->W, opts->cg_max_iter + 1);
+      if (s != VL_OK) return bail(s);
     }
     if (cudaGetLastError() != cudaSuccess) return bail(fail(c, VL_ERR_CUDA, "Newton setup"));
     if (mixed) cudaMemcpyAsync(bn, st->b, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream);  // warm start
@@ -973,10 +1005,11 @@ vl_status vl_log_marglik(vl_state* st, const vl_opts* o, double* lml, double* lo
   VL_CUDA(c, cudaEventRecord(c->ev0, c->stream));
   vl_stats loc{};
   std::vector<double> g;
+  double logdetC = 0.0;
   if (o->precision == VL_FP64)
-    VL_TRY(slq_run<double>(st, o, g, &loc));
+    VL_TRY(slq_run<double>(st, o, g, &loc, &logdetC));
   else
-    VL_TRY(slq_run<float>(st, o, g, &loc));
+    VL_TRY(slq_run<float>(st, o, g, &loc, &logdetC));
   double mean = 0.0;
   for (double v : g) mean += v;
   mean /= t;
@@ -985,16 +1018,21 @@ vl_status vl_log_marglik(vl_state* st, const vl_opts* o, double* lml, double* lo
   const double se = t > 1 ? std::sqrt(var / (t - 1) / t) : 0.0;
   Scratch S(c);
   Engine<double> E1(c);
-  VL_TRY(E1.init(f, 1, o->precond, st->W, 0));
+  VL_TRY(E1.init(f, 1, VL_PREC_VADU, st->W, 0));   // only B products for psi
   double logp = 0.0, quad = 0.0;
   VL_TRY(psi_eval(st, E1, S, st->b, nullptr, &logp, &quad));
-  double sum_log_D = 0.0, sum_log_P = 0.0;
-  VL_TRY(dev_sum(c, S, n, 1, f->D64, nullptr, &sum_log_D));
-  if (o->precond == VL_PREC_VADU)
-    VL_TRY(dev_sum(c, S, n, 2, f->D64, st->W, &sum_log_P));   // log det P = log det(W + D^{-1})
-  else
-    sum_log_P = -sum_log_D;                                   // log det P = log det D^{-1}
-  const double ld = sum_log_D + sum_log_P + mean;             // Eq. logdetsplit
+  double ld = 0.0;
+  if (o->precond == VL_PREC_LRAC) {
+    ld = logdetC + mean;   // Eq. logdetsplit2 with log det P = log det C - log det W
+  } else {
+    double sum_log_D = 0.0, sum_log_P = 0.0;
+    VL_TRY(dev_sum(c, S, n, 1, f->D64, nullptr, &sum_log_D));
+    if (o->precond == VL_PREC_VADU)
+      VL_TRY(dev_sum(c, S, n, 2, f->D64, st->W, &sum_log_P));   // log det P = log det(W + D^{-1})
+    else
+      sum_log_P = -sum_log_D;                                   // log det P = log det D^{-1}
+    ld = sum_log_D + sum_log_P + mean;                          // Eq. logdetsplit
+  }
   *lml = -logp + 0.5 * quad + 0.5 * ld;                       // Eq. VLA_loss
   if (logdet) *logdet = ld;
   st->h_gammas = g;
@@ -1063,6 +1101,7 @@ vl_status vl_pred_var(vl_state* st, const double* test_locs, int64_t np, const d
   pred_kernel<double><<<pg, 256, 0, VL_STREAM(c)>>>((int)np, m, Np, Ap, Dp, dF, st->b, nullptr, 0, 1, dmean, nullptr);
   VL_CUDA(c, cudaGetLastError());
   if (var) {
+    VL_TRY(ensure_precond(f, o));
     for (int col0 = 0; col0 < o->s; col0 += 128) {
       const int sc = std::min(128, o->s - col0);
       Engine<double> E64(c);
@@ -1127,6 +1166,24 @@ vl_status vl_pcg_solve(vl_state* st, const double* RHS, int t, const vl_opts* o,
   else
     VL_TRY(pcg_op<float>(st, dR, t, o, dU, lmax, T_diag, T_off, iters, relres));
   return stage_out(c, dU, U, nt);
+}
+
+vl_status vl_lrac_export(vl_factor* f, int k, int32_t* piv, double* L) {
+  if (!f) return VL_ERR_INVALID_ARG;
+  Ctx* c = f->ctx;
+  VL_TRY(lrac_build(f, k));
+  const int n = (int)f->n;
+  Scratch S(c);
+  if (L) {
+    double* dL = S.get<double>((size_t)n * k);
+    if (!dL) return fail(c, VL_ERR_OOM, "workspace exhausted (LRAC export)");
+    lrac_export_kernel<<<grid_for(c, (int64_t)n * k), 256, 0, VL_STREAM(c)>>>(n, k, f->s2u, f->L64, dL);
+    VL_CUDA(c, cudaGetLastError());
+    VL_TRY(stage_out(c, dL, L, (size_t)n * k));
+  }
+  if (piv) VL_TRY(stage_out(c, f->piv_v, piv, (size_t)k));
+  VL_CUDA(c, cudaStreamSynchronize(c->stream));
+  return VL_OK;
 }
 
 }  // extern "C"

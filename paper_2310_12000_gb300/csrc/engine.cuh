@@ -3,9 +3,10 @@
 // algorithm with per-column freezing and Lanczos T extraction.
 #pragma once
 
+#include <string>
 #include <vector>
 
-#include "kernels.cuh"
+#include "lrac.cuh"
 
 namespace vl {
 
@@ -120,6 +121,17 @@ struct Engine {
   int lmax = 0;
   int* d_count = nullptr;
   int* h_count = nullptr;
+  // LRAC (Section 3.1.2): L (factor-owned), C = I + L^T W L, its Cholesky factor,
+  // R^{-1} and C^{-1} (rebuilt lazily after W changes), the rank-k blocks of one apply
+  int kr = 0;
+  const T* Lk = nullptr;
+  double *Cm = nullptr, *Rinv = nullptr, *Cinv = nullptr, *lpart = nullptr, *Gk = nullptr, *Vk = nullptr;
+  double* dlogdet = nullptr;
+  int* lbad = nullptr;
+  int nch_g = 1, rows_g = 0, nch_a = 1, rows_a = 0;
+  bool lr_dirty = true;
+  double logdetC = 0.0;
+  T* b2 = nullptr;
 
   explicit Engine(Ctx* ctx) : c(ctx), mem(ctx) {}
 
@@ -183,6 +195,125 @@ struct Engine {
       VL_CUDA(c, cudaMemsetAsync(S.Toff, 0, sizeof(double) * t * lmax, c->stream));
     }
     h_count = reinterpret_cast<int*>(c->pinned);
+    if (prec == VL_PREC_LRAC) VL_TRY(lrac_init());
+    return VL_OK;
+  }
+
+  // New W (float64, storage order): the diagonals and, for LRAC, C on next use.
+  vl_status set_W(const double* W64) {
+    diag_prep_kernel<T><<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, prec, W64, f->D64, W, Dinv, dsc, Dt, Winv);
+    VL_CUDA(c, cudaGetLastError());
+    lr_dirty = true;
+    return VL_OK;
+  }
+
+  // ------------------------------------------------------------------ LRAC
+  static int chunks_for(int64_t rows, int64_t tiles, int target) {
+    const int64_t want = std::max<int64_t>(1, (target + tiles - 1) / tiles);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(want, (rows + 255) / 256));
+  }
+
+  vl_status lrac_init() {
+    if (f->lrac_k < 1 || !f->L64) return fail(c, VL_ERR_STATE, "LRAC factor not built");
+    if (!std::is_same<T, double>::value) VL_TRY(lrac_float(f));
+    kr = f->lrac_k;
+    Lk = std::is_same<T, double>::value ? (const T*)f->L64 : (const T*)f->L32;
+    const int64_t kk = (int64_t)kr * kr;
+    const int tq = (kr + 63) / 64;
+    nch_g = chunks_for(n, (int64_t)tq * (tq + 1) / 2, 2 * c->num_sms);
+    rows_g = (int)(((n + nch_g - 1) / nch_g + 31) / 32 * 32);
+    nch_g = (n + rows_g - 1) / rows_g;
+    if (t == 1)
+      nch_a = chunks_for(n, (kr + 7) / 8, 4 * c->num_sms);
+    else
+      nch_a = chunks_for(n, (int64_t)tq * ((t + 63) / 64), 2 * c->num_sms);
+    rows_a = (int)(((n + nch_a - 1) / nch_a + 511) / 512 * 512);
+    nch_a = (n + rows_a - 1) / rows_a;
+    Cm = mem.get<double>(kk);
+    Rinv = mem.get<double>(kk);
+    Cinv = mem.get<double>(kk);
+    lpart = mem.get<double>(std::max<int64_t>((int64_t)nch_g * kk, (int64_t)nch_a * kr * t));
+    Gk = mem.get<double>((size_t)kr * t);
+    Vk = mem.get<double>((size_t)kr * t);
+    dlogdet = mem.get<double>(1);
+    lbad = mem.get<int>(1);
+    b2 = mem.get<T>((size_t)n * ld);
+    if (!Cm || !Rinv || !Cinv || !lpart || !Gk || !Vk || !dlogdet || !lbad || !b2)
+      return fail(c, VL_ERR_OOM, "workspace exhausted (LRAC)");
+    VL_CUDA(c, cudaMemsetAsync(b2, 0, sizeof(T) * (size_t)n * ld, c->stream));
+    lr_dirty = true;
+    return VL_OK;
+  }
+
+  // C = I + L^T W L, its blocked Cholesky factor (log det C), R^{-1} and C^{-1}.
+  vl_status lrac_prepare() {
+    if (!lr_dirty) return VL_OK;
+    const int k = kr;
+    {
+      ProfScope ps(c, "lrac_gram", k);
+      const int tq = (k + 63) / 64;
+      lrac_tn_kernel<T><<<dim3(tq, tq, nch_g), 256, 0, VL_STREAM(c)>>>(n, k, k, rows_g, Lk, Lk, 1, n, W, 1, lpart);
+      lrac_sum_chunks_kernel<<<grid_for(c, (int64_t)k * k), 256, 0, VL_STREAM(c)>>>(nch_g, (int64_t)k * k, lpart, Cm, k);
+    }
+    {
+      ProfScope ps(c, "lrac_kxk", k);
+      VL_CUDA(c, cudaMemsetAsync(dlogdet, 0, sizeof(double), c->stream));
+      VL_CUDA(c, cudaMemsetAsync(lbad, 0, sizeof(int), c->stream));
+      for (int J = 0; J < k; J += kCholNB) {
+        const int b = std::min(kCholNB, k - J), rest = k - J - b;
+        lrac_chol_panel_kernel<<<std::max(1, (rest + 127) / 128), 128, 0, VL_STREAM(c)>>>(k, J, Cm, dlogdet, lbad);
+        if (rest > 0) {
+          const int nt = (rest + 31) / 32;
+          lrac_chol_update_kernel<<<dim3(nt, nt), 256, 0, VL_STREAM(c)>>>(k, J, Cm);
+        }
+      }
+      const size_t smem = sizeof(double) * ((size_t)k * 16 + 256);
+      VL_CUDA(c, cudaFuncSetAttribute(lrac_trinv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      lrac_trinv_kernel<<<(k + 15) / 16, 256, smem, VL_STREAM(c)>>>(k, Cm, Rinv);
+      lrac_cinv_kernel<<<dim3((k + 127) / 128, k), 128, 0, VL_STREAM(c)>>>(k, Rinv, Cinv);
+    }
+    VL_CUDA(c, cudaGetLastError());
+    double* hld = reinterpret_cast<double*>(c->pinned + 64);
+    int* hb = reinterpret_cast<int*>(c->pinned + 128);
+    VL_CUDA(c, cudaMemcpyAsync(hld, dlogdet, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    VL_CUDA(c, cudaMemcpyAsync(hb, lbad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    VL_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (*hb) return fail(c, VL_ERR_NOT_SPD, "LRAC: I + L^T W L is not numerically positive definite");
+    logdetC = *hld;
+    lr_dirty = false;
+    return VL_OK;
+  }
+
+  // Z = (W - W L C^{-1} L^T W) R      (Woodbury form of P_LRAC^{-1})
+  vl_status opPinv_lrac(const T* R, T* Zo) {
+    VL_TRY(lrac_prepare());
+    ProfScope ps(c, "woodbury", t);
+    const int k = kr;
+    if (t == 1) {
+      lrac_tn1_kernel<T><<<dim3((k + 7) / 8, nch_a), 256, 0, VL_STREAM(c)>>>(n, k, rows_a, Lk, R, W, lpart);
+      lrac_sum_chunks_kernel<<<grid_for(c, k), 256, 0, VL_STREAM(c)>>>(nch_a, k, lpart, Gk, 0);
+      lrac_cinv_apply1_kernel<<<(k + 7) / 8, 256, 0, VL_STREAM(c)>>>(k, Cinv, Gk, Vk);
+      lrac_nn1_kernel<T><<<(n + 255) / 256, 256, sizeof(T) * k, VL_STREAM(c)>>>(n, k, Lk, Vk, R, W, W, T(-1), Zo);
+    } else {
+      const int tq = (k + 63) / 64, tt = (t + 63) / 64;
+      lrac_tn_kernel<T><<<dim3(tq, tt, nch_a), 256, 0, VL_STREAM(c)>>>(n, k, t, rows_a, Lk, R, ld, 1, W, 0, lpart);
+      lrac_sum_chunks_kernel<<<grid_for(c, (int64_t)k * t), 256, 0, VL_STREAM(c)>>>(nch_a, (int64_t)k * t, lpart, Gk, 0);
+      lrac_cinv_apply_kernel<<<dim3((t + 63) / 64, k), 64, 0, VL_STREAM(c)>>>(k, t, Cinv, Gk, Vk);
+      lrac_nn_kernel<T><<<dim3((n + 63) / 64, tt), 256, 0, VL_STREAM(c)>>>(n, k, t, ld, Lk, Vk, R, W, W, T(-1), Zo);
+    }
+    VL_CUDA(c, cudaGetLastError());
+    return VL_OK;
+  }
+
+  // Z = a o Y + L V with V (k x t, float64, device): the LRAC probe z = W^{-1/2} r2 + L r1.
+  vl_status lrac_lowrank_plus(const double* V, const T* Y, const T* a, T* Zo) {
+    const int k = kr;
+    if (t == 1)
+      lrac_nn1_kernel<T><<<(n + 255) / 256, 256, sizeof(T) * k, VL_STREAM(c)>>>(n, k, Lk, V, Y, a, nullptr, T(1), Zo);
+    else
+      lrac_nn_kernel<T><<<dim3((n + 63) / 64, (t + 63) / 64), 256, 0, VL_STREAM(c)>>>(n, k, t, ld, Lk, V, Y, a, nullptr,
+                                                                                   T(1), Zo);
+    VL_CUDA(c, cudaGetLastError());
     return VL_OK;
   }
 
@@ -371,8 +502,9 @@ struct Engine {
   vl_status solveB(const T* rhs, const T* q, T* x) { return solve_launch<true>(rhs, q, x); }
   // x = B^{-T} (q o rhs)
   vl_status solveBt(const T* rhs, const T* q, T* x) { return solve_launch<false>(rhs, q, x); }
-  // P^{-1} R for VADU / LVA: B^{-1} dsc B^{-T} R     (Section 3.1.1)
+  // P^{-1} R. VADU / LVA: B^{-1} dsc B^{-T} R (Section 3.1.1); LRAC: Woodbury.
   vl_status opPinv(const T* R, T* Zo) {
+    if (prec == VL_PREC_LRAC) return opPinv_lrac(R, Zo);
     VL_TRY(solveBt(R, nullptr, sv));
     return solveB(sv, dsc, Zo);
   }
@@ -390,8 +522,23 @@ struct Engine {
   }
 
   // ------------------------------------------------------------------ PCG
-  // Solves A U = Bm column by column (u_0 = 0), stopping a column when
-  // ||r|| <= tol ||b||; records T (Lanczos) per column. Operators: form 1.
+  // The system operator of the preconditioner's form: W + B^T D^{-1} B (Eq. pcls1) for
+  // VADU and LVA, Sigma_tilde + W^{-1} (Eq. pcls2) for LRAC.
+  vl_status opSys(const T* X, T* Zo) { return prec == VL_PREC_LRAC ? opA2(X, Zo) : opA(X, Zo); }
+
+  // Solves (W + Sigma_tilde^{-1}) D = Rm. VADU / LVA: PCG on form 1. LRAC: PCG on
+  // form 2, (Sigma_tilde + W^{-1}) X = Sigma_tilde Rm, then D = W^{-1} X.
+  vl_status solve_A1(const T* Rm, T* Dm, double tol, int max_iter, int* iters_used) {
+    if (prec != VL_PREC_LRAC) return pcg(Rm, Dm, tol, max_iter, iters_used);
+    VL_TRY(opSigma(Rm, b2));
+    VL_TRY(pcg(b2, Dm, tol, max_iter, iters_used));
+    scale_rows_kernel<T><<<grid_for(c, (int64_t)n * ld), 256, 0, VL_STREAM(c)>>>(n, t, ld, Winv, Dm);
+    VL_CUDA(c, cudaGetLastError());
+    return VL_OK;
+  }
+
+  // Solves S U = Bm (S = opSys) column by column (u_0 = 0), stopping a column when
+  // ||r|| <= tol ||b||; records T (Lanczos) per column.
   vl_status pcg(const T* Bm, T* U, double tol, int max_iter, int* iters_used) {
     const int64_t vec = (int64_t)n * ld;
     VL_CUDA(c, cudaMemsetAsync(U, 0, sizeof(T) * vec, c->stream));
@@ -405,7 +552,7 @@ struct Engine {
     const double tol2 = tol * tol;
     int it = 0;
     for (; it < max_iter; ++it) {
-      VL_TRY(opA(h, v));
+      VL_TRY(opSys(h, v));
       VL_TRY(coldot(h, v, nullptr, red));
       pcg_alpha_kernel<<<1, 256, 0, VL_STREAM(c)>>>(t, red, S);
       {

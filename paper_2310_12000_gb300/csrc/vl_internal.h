@@ -149,6 +149,14 @@ struct Factor {
   std::vector<int32_t> h_lptr_fwd, h_lptr_bwd;
   std::vector<int64_t> h_lwork_fwd, h_lwork_bwd;   // dependencies per level
   std::vector<int32_t> h_hptr_fwd, h_hptr_bwd;     // host copies of hptr
+  // LRAC (Section 3.1.2): rank-k pivoted Cholesky factor of Sigma, built on first use
+  // and dropped when the covariance parameters change
+  Owned lrac_mem;
+  int lrac_k = 0;
+  double* L64 = nullptr;      // n x k, column-major over the storage rows
+  float* L32 = nullptr;       // float copy, made on first float32 use
+  int32_t* piv_s = nullptr;   // k pivots as storage rows
+  int32_t* piv_v = nullptr;   // k pivots as Vecchia indices
 };
 
 struct State {
@@ -196,6 +204,12 @@ vl_status bbox(Ctx* c, const double* locs, int64_t n, const double* extra, int64
 // the Vecchia-order neighbour table N_v and locations locs_v (both device).
 vl_status build_graph_impl(Factor* f, const int32_t* N_v, const double* locs_v, const int32_t* order_dev);
 vl_status refresh_transpose_values(Factor* f);
+
+// lrac.cu: the rank-k pivoted Cholesky factor of Sigma for the LRAC preconditioner
+// (f->L64, f->piv_*; rebuilt when k changes), and its float32 copy f->L32.
+vl_status lrac_build(Factor* f, int k);
+vl_status lrac_float(Factor* f);
+void lrac_drop(Factor* f);
 
 // factor.cu: A (rows x m) and D (rows) of the Vecchia rows; row_ids (optional)
 // name rows in error messages.
