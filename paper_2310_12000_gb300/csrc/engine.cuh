@@ -97,6 +97,11 @@ vl_status with_shape(int ld, F&& f) {
   return f(I32{}, I4{}, I2{});
 }
 
+// Largest system the t = 1 solve keeps in shared memory (one block).
+constexpr size_t kSmemSolveBytes = 200 * 1024;
+
+inline vl_status cuda_ok(Ctx* c, cudaError_t e) { return e == cudaSuccess ? VL_OK : cuda_fail(c, e, "kernel launch"); }
+
 inline int grid_for(Ctx* c, int64_t work, int block = 256) {
   int64_t g = (work + block - 1) / block;
   return (int)std::max<int64_t>(1, std::min<int64_t>(g, (int64_t)c->num_sms * 16));
@@ -383,11 +388,11 @@ struct Engine {
     *l_tail = tl;
   }
 
-  // Largest cluster (<= 16 blocks of 1024 threads) the device can co-schedule for fn.
-  int cluster_size(const void* fn) {
-    static int cached[2][2] = {{-1, -1}, {-1, -1}};
-    (void)cached;
+  // Largest cluster (<= 16 blocks of 1024 threads, smem bytes of dynamic shared
+  // memory each) the device can co-schedule for fn.
+  int cluster_size(const void* fn, size_t smem = 0) {
     cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
@@ -396,6 +401,7 @@ struct Engine {
     at[0].val.clusterDim.z = 1;
     cfg.gridDim = dim3(16);
     cfg.blockDim = dim3(1024);
+    cfg.dynamicSmemBytes = smem;
     cfg.attrs = at;
     cfg.numAttrs = 0;
     int cs = 0;
@@ -449,6 +455,81 @@ struct Engine {
       }
       return VL_OK;
     };
+    int widest = 0;
+    for (size_t lv = 0; lv + 1 < hl.size(); ++lv) widest = std::max(widest, hl[lv + 1] - hl[lv]);
+    if (t == 1 && (size_t)n * sizeof(T) <= kSmemSolveBytes) {
+      // small system: one block with x in shared memory (see sptrsv_t1_smem_kernel)
+      constexpr int LPV1 = FWD ? 8 : 16;
+      auto fn = sptrsv_t1_smem_kernel<T, FWD, LPV1>;
+      const size_t smem = (size_t)n * sizeof(T);
+      if (smem > 48 * 1024)
+        VL_CUDA(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      L.l_head = 0;
+      L.l_tail = L.nlev;
+      int nn = n;
+      {
+        ProfScope ps(c, cls, t);
+        fn<<<1, 1024, smem, VL_STREAM(c)>>>(L, nn, mm, idx, val, rp, rhs, q, x);
+        VL_CUDA(c, cudaGetLastError());
+      }
+      if (L.trace) {
+        std::vector<long long>& h = c->prof.traces[{cls, t}];
+        h.resize(hl.size());
+        VL_CUDA(c, cudaMemcpyAsync(h.data(), L.trace, sizeof(long long) * h.size(), cudaMemcpyDeviceToHost, c->stream));
+        VL_CUDA(c, cudaStreamSynchronize(c->stream));
+        c->prof.cuts[{cls, t}] = {L.l_head, L.l_tail};
+      }
+      return VL_OK;
+    }
+    if (t > 1) {
+      // narrow level profile: one thread-block cluster (see sptrsv_cluster_kernel)
+      vl_status out = VL_OK;
+      bool done = false;
+      VL_TRY(with_shape<T>(ld, [&](auto Lc, auto N, auto U) {
+        constexpr int LPV = decltype(Lc)::value, NV = decltype(N)::value;
+        if constexpr (NV > 2) {
+          return VL_OK;   // very wide blocks stay on the grid kernel (register budget of 1024-thread blocks)
+        } else {
+        auto fn = sptrsv_cluster_kernel<T, FWD, LPV, NV, decltype(U)::value>;
+        const int tpb = 32 * (32 / LPV);
+        const size_t smem = sizeof(T) * (size_t)tpb * ld;
+        const int cs = cluster_size((const void*)fn, smem);
+        if (cs < 2 || widest > 4 * cs * tpb) return VL_OK;
+        L.l_head = 0;
+        L.l_tail = L.nlev;
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = cs;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(cs);
+        cfg.blockDim = dim3(1024);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = c->stream;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        {
+          ProfScope ps(c, cls, t);
+          ++c->launches;
+          out = cuda_ok(c, cudaLaunchKernelEx(&cfg, fn, L, mm, idx, val, rp, rhs, q, x, l));
+        }
+        done = true;
+        return out;
+        }
+      }));
+      if (done) {
+        if (L.trace) {
+          std::vector<long long>& h = c->prof.traces[{cls, t}];
+          h.resize(hl.size());
+          VL_CUDA(c, cudaMemcpyAsync(h.data(), L.trace, sizeof(long long) * h.size(), cudaMemcpyDeviceToHost,
+                                     c->stream));
+          VL_CUDA(c, cudaStreamSynchronize(c->stream));
+          c->prof.cuts[{cls, t}] = {L.l_head, L.l_tail};
+        }
+        return VL_OK;
+      }
+    }
     if (t == 1) {
       // one thread-block cluster walks all levels (see sptrsv_t1_cluster_kernel)
       constexpr int LPV1 = FWD ? 8 : 16;   // backward rows can list hundreds of dependents
@@ -456,8 +537,6 @@ struct Engine {
       const int cs = cluster_size((const void*)fn);
       // one cluster only pays off while every level fits a few rounds of its teams;
       // the widest levels of large problems need the whole grid
-      int widest = 0;
-      for (size_t l = 0; l + 1 < hl.size(); ++l) widest = std::max(widest, hl[l + 1] - hl[l]);
       const int cluster_teams = cs * (1024 / 32) * (32 / LPV1);
       if (cs >= 2 && widest <= 8 * cluster_teams) {
         L.l_head = 0;

@@ -611,6 +611,105 @@ __global__ void __launch_bounds__(1024) sptrsv_t1_cluster_kernel(LevelPlan L, in
   if (tr) L.trace[L.nlev] = clock64();
 }
 
+// Scalar-row (t = 1) solve of a small system by one block with x resident in
+// shared memory (n * sizeof(T) bytes of dynamic shared memory): a level costs
+// shared-memory gathers and one block barrier, nothing goes through L2 between
+// levels, and the solve occupies a single SM so that independent problems run
+// side by side. Each team prefetches its next row (indices, weights, scaled
+// right-hand side) before the barrier; x is written out once at the end.
+template <typename T, int LPV>
+__device__ __forceinline__ void row_run1_smem(RowPre1<T, LPV>& r, const int32_t* __restrict__ idx,
+                                              const T* __restrict__ val, T* xs) {
+  constexpr int K = RowPre1<T, LPV>::K;
+  const unsigned mask = team_mask<LPV>();
+  const int sl = (threadIdx.x & 31) % LPV;
+  T acc = T(0);
+#pragma unroll
+  for (int u = 0; u < K; ++u) acc += r.j[u] >= 0 ? r.a[u] * xs[r.j[u]] : T(0);
+  for (int e = r.beg + sl + LPV * K; e < r.end; e += LPV) acc += val[e] * xs[idx[e]];
+#pragma unroll
+  for (int off = LPV / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(mask, acc, off, LPV);
+  if (sl == 0) xs[r.s] = r.b + acc;
+}
+
+template <typename T, bool FWD, int LPV>
+__global__ void __launch_bounds__(1024) sptrsv_t1_smem_kernel(LevelPlan L, int n, int m, const int32_t* __restrict__ idx,
+                                                              const T* __restrict__ val,
+                                                              const int32_t* __restrict__ rowptr,
+                                                              const T* __restrict__ rhs, const T* __restrict__ q, T* x) {
+  extern __shared__ unsigned char vl_smem[];
+  T* xs = reinterpret_cast<T*>(vl_smem);
+  constexpr int RPW = 32 / LPV;
+  const int tpb = (blockDim.x >> 5) * RPW;
+  const int tib = (threadIdx.x >> 5) * RPW + (threadIdx.x & 31) / LPV;
+  const bool tr = L.trace && threadIdx.x == 0;
+  RowPre1<T, LPV> r;
+  int p = L.lptr[0] + tib;
+  bool has = L.nlev > 0 && p < L.lptr[1];
+  if (has) row_pre1<T, FWD, LPV>(r, p, m, L, idx, val, rowptr, rhs, q);
+  for (int l = 0; l < L.nlev; ++l) {
+    if (tr) L.trace[l] = clock64();
+    while (has) {
+      row_run1_smem<T, LPV>(r, idx, val, xs);
+      p += tpb;
+      has = p < L.lptr[l + 1];
+      if (has) row_pre1<T, FWD, LPV>(r, p, m, L, idx, val, rowptr, rhs, q);
+    }
+    if (l + 1 < L.nlev) {
+      p = L.lptr[l + 1] + tib;
+      has = p < L.lptr[l + 2];
+      if (has) row_pre1<T, FWD, LPV>(r, p, m, L, idx, val, rowptr, rhs, q);
+    }
+    __syncthreads();
+  }
+  if (tr) L.trace[L.nlev] = clock64();
+  for (int s = threadIdx.x; s < n; s += blockDim.x) x[s] = xs[s];
+}
+
+// Block (t > 1) solve by one thread-block cluster: the level walk of the grid
+// kernel with the hardware cluster barrier in place of the grid barrier. Heavy
+// rows go to whole blocks of the cluster (one row per block at a time), light
+// rows to teams, each prefetched before the barrier.
+template <typename T, bool FWD, int LPV, int NV, int UNR>
+__global__ void __launch_bounds__(1024) sptrsv_cluster_kernel(LevelPlan L, int m, const int32_t* __restrict__ idx,
+                                                              const T* __restrict__ val,
+                                                              const int32_t* __restrict__ rowptr,
+                                                              const T* __restrict__ rhs, const T* __restrict__ q, T* x,
+                                                              int ld) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ unsigned char vl_smem[];
+  T* part = reinterpret_cast<T*>(vl_smem);
+  constexpr int RPW = 32 / LPV;
+  const int tpb = (blockDim.x >> 5) * RPW;
+  const int tib = (threadIdx.x >> 5) * RPW + (threadIdx.x & 31) / LPV;
+  const int nb = (int)cl.num_blocks(), br = (int)cl.block_rank();
+  const int G = nb * tpb, g = br * tpb + tib;
+  const bool tr = L.trace && br == 0 && threadIdx.x == 0;
+  RowPre<T, LPV, NV> r;
+  int p = 0;
+  bool has = L.nlev > 0 && (p = L.hptr[0] + g) < L.lptr[1];
+  if (has) row_pre<T, FWD, LPV, NV>(r, p, m, L, idx, val, rowptr, rhs, q, ld);
+  for (int l = 0; l < L.nlev; ++l) {
+    if (tr) L.trace[l] = clock64();
+    for (int h = L.lptr[l] + br; h < L.hptr[l]; h += nb)
+      heavy_row<T, FWD, LPV, NV, UNR>(h, m, L, idx, val, rowptr, rhs, q, x, ld, part);
+    while (has) {
+      row_run<T, LPV, NV, UNR>(r, idx, val, x, ld);
+      p += G;
+      has = p < L.lptr[l + 1];
+      if (has) row_pre<T, FWD, LPV, NV>(r, p, m, L, idx, val, rowptr, rhs, q, ld);
+    }
+    if (l + 1 < L.nlev) {
+      p = L.hptr[l + 1] + g;
+      has = p < L.lptr[l + 2];
+      if (has) row_pre<T, FWD, LPV, NV>(r, p, m, L, idx, val, rowptr, rhs, q, ld);
+    }
+    cl.sync();
+  }
+  if (tr) L.trace[L.nlev] = clock64();
+}
+
 template <typename T, bool FWD, int LPV, int NV, int UNR>
 __global__ void __launch_bounds__(512) sptrsv_kernel(LevelPlan L, int m, const int32_t* __restrict__ idx,
                                                      const T* __restrict__ val, const int32_t* __restrict__ rowptr,

@@ -1,0 +1,280 @@
+"""Serving form: a request loop over independent latent-GP problems.
+
+Each request is a fresh problem (locations, responses, covariance parameters,
+test points). Serving it runs the whole path on the device: the Vecchia factor
+(Section 2.1), the Laplace mode (Eq. newton), L^VLA with the SLQ log-determinant
+(Eqs. VLA_loss, def_SLQ) and the predictive means and variances (Algorithm simAlgo).
+
+Execution model
+---------------
+* A slot is a library context with its own CUDA stream and a workspace large
+  enough for the biggest admissible request. Slot contexts are made once and reused,
+  so serving allocates no device memory after start-up.
+* Admission is first-come first-served by HBM footprint: the request at the head of
+  the queue is admitted when a slot is free and the estimated device footprint of
+  the requests already running plus its own fits the budget. A request that could
+  never fit is rejected at once.
+* Admitted requests run concurrently, each on its slot's stream from its own host
+  thread (the library releases the interpreter lock), so their kernels overlap on
+  the device as requests arrive and leave.
+* Every kernel of the library is deterministic and requests share no device state,
+  so a request's results are the same whether it runs alone or in the mix.
+
+The scheduler (admission, FIFO order, budget accounting) is plain host logic and
+can be driven with any runner; ``run_request`` is the runner that calls the library.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import threading
+import time
+from typing import Callable
+
+import numpy as np
+
+
+def footprint_bytes(n: int, m: int, t: int = 50, s: int = 100, n_test: int = 1000, k: int = 0) -> int:
+    """Upper estimate of the device workspace one request needs (bytes): the factor
+    (ELL of B and its transpose in float64 and float32, orders, levels), the state,
+    and the largest phase, the simulation solves for predictive variances (float64
+    and float32 Krylov blocks of up to 128 columns plus the refinement vectors), or
+    the SLQ probe block. k > 0 adds the LRAC factor and its float copy."""
+    def lead(c):
+        return 1 if c == 1 else (c + 7) // 8 * 8
+    ls, lt = lead(min(s, 128)), lead(t)
+    factor = n * (200 + 40 * m)
+    sim = n * ls * 132
+    slq = n * lt * 4 * 11
+    test = n_test * (16 * m + 96)
+    lrac = n * k * 12 + n * lt * 4 + 6 * k * k * 8 if k else 0
+    return int(1.15 * (factor + max(sim, slq) + test + lrac)) + (32 << 20)
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    locs: np.ndarray
+    order: np.ndarray
+    y: np.ndarray
+    F: np.ndarray | None
+    cov: int
+    sigma2: float
+    rho: float
+    m: int
+    lik: int
+    test_locs: np.ndarray | None
+    opts: dict
+    arrival: float = 0.0          # server clock, seconds
+    footprint: int = 0
+
+    @property
+    def n(self) -> int:
+        return int(self.locs.shape[0])
+
+    @classmethod
+    def from_problem(cls, rid: int, P, opts: dict, arrival: float = 0.0) -> "Request":
+        r = cls(rid=rid, locs=P.locs, order=P.order, y=P.y, F=P.F, cov=P.cov, sigma2=P.sigma2, rho=P.rho, m=P.m,
+                lik=P.lik, test_locs=P.test_locs, opts=dict(opts), arrival=arrival)
+        r.footprint = footprint_bytes(r.n, r.m, opts.get("t", 50), opts.get("s", 100),
+                                      0 if P.test_locs is None else len(P.test_locs),
+                                      opts.get("k", 0) if opts.get("precond", 0) == 2 else 0)
+        return r
+
+
+@dataclasses.dataclass
+class Result:
+    rid: int
+    n: int
+    slot: int
+    t_arrival: float
+    t_admit: float
+    t_done: float
+    lml: float = float("nan")
+    mode: np.ndarray | None = None
+    mean: np.ndarray | None = None
+    var: np.ndarray | None = None
+    stats: dict = dataclasses.field(default_factory=dict)
+    error: str | None = None
+
+    @property
+    def latency(self) -> float:
+        return self.t_done - self.t_arrival
+
+
+class Scheduler:
+    """FIFO admission by footprint against a device-memory budget."""
+
+    def __init__(self, budget_bytes: int, slot_capacity: int):
+        self.budget = int(budget_bytes)
+        self.capacity = int(slot_capacity)   # bytes one slot can hold
+        self.q: collections.deque[Request] = collections.deque()
+        self.cv = threading.Condition()
+        self.in_use = 0
+        self.running = 0
+        self.peak_in_use = 0
+        self.peak_running = 0
+        self.closed = False
+        self.rejected: list[Request] = []
+
+    def submit(self, req: Request) -> bool:
+        with self.cv:
+            if req.footprint > min(self.budget, self.capacity):
+                self.rejected.append(req)
+                return False
+            self.q.append(req)
+            self.cv.notify_all()
+            return True
+
+    def acquire(self, timeout: float | None = None) -> Request | None:
+        """Block until the head of the queue fits (returning it, admitted) or the
+        scheduler is closed and the queue empty (returning None)."""
+        deadline = None if timeout is None else time.perf_counter() + timeout
+        with self.cv:
+            while True:
+                if self.q and self.in_use + self.q[0].footprint <= self.budget:
+                    req = self.q.popleft()
+                    self.in_use += req.footprint
+                    self.running += 1
+                    self.peak_in_use = max(self.peak_in_use, self.in_use)
+                    self.peak_running = max(self.peak_running, self.running)
+                    self.cv.notify_all()
+                    return req
+                if self.closed and not self.q:
+                    return None
+                left = None if deadline is None else deadline - time.perf_counter()
+                if left is not None and left <= 0:
+                    return None
+                self.cv.wait(left)
+
+    def release(self, req: Request):
+        with self.cv:
+            self.in_use -= req.footprint
+            self.running -= 1
+            self.cv.notify_all()
+
+    def close(self):
+        with self.cv:
+            self.closed = True
+            self.cv.notify_all()
+
+
+def run_request(vl, ctx, req: Request) -> dict:
+    """The whole path for one request on one slot context (device work on its
+    stream): factor, mode, L^VLA, predictive mean and variance."""
+    o = vl.Opts.make(**req.opts)
+    fac = ctx.build_factor(req.locs, req.order, req.cov, req.sigma2, req.rho, req.m, o)
+    st = None
+    try:
+        st = fac.find_mode(req.lik, req.y, req.F, o)
+        lml, stats = st.log_marglik(o, with_stats=True)
+        out = {"lml": lml, "mode": st.mode, "stats": {"mode": st.mode_stats(), "lml": stats}}
+        if req.test_locs is not None and len(req.test_locs):
+            mean, var = st.pred_var(req.test_locs, None, o)
+            out["mean"], out["var"] = mean, var
+        return out
+    finally:
+        if st is not None:
+            st.close()
+        fac.close()
+
+
+class Server:
+    """``slots`` worker threads, each owning one context (made by ``make_ctx(slot)``)
+    and serving admitted requests with ``runner(ctx, req) -> dict``."""
+
+    def __init__(self, slots: int, budget_bytes: int, slot_capacity: int, make_ctx: Callable[[int], object],
+                 runner: Callable[[object, Request], dict], clock: Callable[[], float] = time.perf_counter):
+        self.sched = Scheduler(budget_bytes, slot_capacity)
+        self.make_ctx, self.runner, self.clock = make_ctx, runner, clock
+        self.results: list[Result] = []
+        self._lock = threading.Lock()
+        self._ready = threading.Barrier(slots + 1)
+        self.threads = [threading.Thread(target=self._worker, args=(i,), daemon=True) for i in range(slots)]
+        self.t0 = 0.0
+        self.errors: list[str] = []
+
+    def start(self):
+        for th in self.threads:
+            th.start()
+        self._ready.wait()          # every slot context exists before the clock starts
+        self.t0 = self.clock()
+        return self
+
+    def now(self) -> float:
+        return self.clock() - self.t0
+
+    def submit(self, req: Request, stamp: bool = True) -> bool:
+        if stamp:
+            req.arrival = self.now()
+        ok = self.sched.submit(req)
+        if not ok:
+            with self._lock:
+                self.results.append(Result(req.rid, req.n, -1, req.arrival, req.arrival, req.arrival,
+                                           error="rejected: footprint above the budget"))
+        return ok
+
+    def _worker(self, slot: int):
+        try:
+            ctx = self.make_ctx(slot)
+        except Exception as e:          # noqa: BLE001 - reported to the caller
+            self.errors.append(f"slot {slot}: {e}")
+            self._ready.wait()
+            return
+        self._ready.wait()
+        while True:
+            req = self.sched.acquire()
+            if req is None:
+                break
+            t_admit = self.now()
+            res = Result(req.rid, req.n, slot, req.arrival, t_admit, t_admit)
+            try:
+                out = self.runner(ctx, req)
+                res.lml = out.get("lml", float("nan"))
+                res.mode, res.mean, res.var = out.get("mode"), out.get("mean"), out.get("var")
+                res.stats = out.get("stats", {})
+            except Exception as e:      # noqa: BLE001 - recorded per request
+                res.error = f"{type(e).__name__}: {e}"
+            res.t_done = self.now()
+            self.sched.release(req)
+            with self._lock:
+                self.results.append(res)
+        close = getattr(ctx, "close", None)
+        if close:
+            close()
+
+    def drain(self):
+        """Stop taking requests once the queue is empty and wait for the workers."""
+        self.sched.close()
+        for th in self.threads:
+            th.join()
+        return sorted(self.results, key=lambda r: r.rid)
+
+
+def latency_summary(results: list[Result], wall_s: float) -> dict:
+    ok = [r for r in results if r.error is None]
+    lat = np.array([r.latency for r in ok]) * 1e3
+    svc = np.array([r.t_done - r.t_admit for r in ok]) * 1e3
+    wait = np.array([r.t_admit - r.t_arrival for r in ok]) * 1e3
+    q = (lambda a, p: float(np.percentile(a, p)) if len(a) else None)
+    return {
+        "requests": len(results), "completed": len(ok), "failed": len(results) - len(ok),
+        "p50_latency_ms": q(lat, 50), "p99_latency_ms": q(lat, 99), "max_latency_ms": q(lat, 100),
+        "p50_service_ms": q(svc, 50), "p99_service_ms": q(svc, 99), "p50_queue_ms": q(wait, 50),
+        "p99_queue_ms": q(wait, 99), "throughput_rps": len(ok) / wall_s if wall_s > 0 else None,
+        "points_per_s": float(sum(r.n for r in ok) / wall_s) if wall_s > 0 else None,
+    }
+
+
+def gpu_slots(vl, device: int, ws_bytes: int) -> Callable[[int], object]:
+    """Slot factory: one library context per slot on its own CUDA stream, with a
+    workspace of ws_bytes taken from PyTorch's device memory."""
+    import torch
+
+    def make(slot: int):
+        torch.cuda.set_device(device)
+        stream = torch.cuda.Stream(device)
+        ctx = vl.Context(device, ws_bytes=ws_bytes, stream=stream)
+        ctx._slot_stream = stream      # keep the stream alive with the context
+        return ctx
+    return make

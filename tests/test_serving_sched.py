@@ -1,0 +1,70 @@
+"""Host logic of the serving loop: FIFO admission by device-memory footprint.
+
+A fake runner stands in for the library, so these run without a GPU."""
+import threading
+import time
+
+import numpy as np
+
+from paper_2310_12000_gb300 import serving
+
+
+def _req(rid, footprint):
+    r = serving.Request(rid=rid, locs=np.zeros((10, 2)), order=np.arange(10, dtype=np.int32), y=np.zeros(10),
+                        F=None, cov=1, sigma2=1.0, rho=0.1, m=5, lik=0, test_locs=None, opts={})
+    r.footprint = footprint
+    return r
+
+
+def test_admission_respects_budget_and_fifo():
+    lock = threading.Lock()
+    live = {"bytes": 0, "peak": 0}
+    order = []
+
+    def runner(ctx, req):
+        with lock:
+            live["bytes"] += req.footprint
+            live["peak"] = max(live["peak"], live["bytes"])
+            order.append(req.rid)
+        time.sleep(0.002 * (1 + req.rid % 3))
+        with lock:
+            live["bytes"] -= req.footprint
+        return {"lml": float(req.rid)}
+
+    srv = serving.Server(slots=4, budget_bytes=100, slot_capacity=100, make_ctx=lambda s: None,
+                         runner=runner).start()
+    sizes = [60, 30, 30, 50, 10, 90, 20, 20, 40, 70] * 3
+    for i, fp in enumerate(sizes):
+        srv.submit(_req(i, fp))
+    res = srv.drain()
+    assert [r.rid for r in res] == list(range(len(sizes)))
+    assert all(r.error is None and r.lml == r.rid for r in res)
+    assert live["peak"] <= 100 and srv.sched.peak_in_use <= 100
+    assert order == sorted(order)            # admitted strictly first-come first-served
+    assert srv.sched.peak_running <= 4
+    assert all(r.t_done >= r.t_admit >= r.t_arrival for r in res)
+
+
+def test_oversized_request_rejected_and_failures_recorded():
+    def runner(ctx, req):
+        if req.rid == 2:
+            raise RuntimeError("boom")
+        return {"lml": 0.0}
+
+    srv = serving.Server(slots=2, budget_bytes=100, slot_capacity=80, make_ctx=lambda s: None, runner=runner).start()
+    assert srv.submit(_req(0, 50))
+    assert not srv.submit(_req(1, 90))       # above one slot's capacity
+    assert srv.submit(_req(2, 10))
+    res = {r.rid: r for r in srv.drain()}
+    assert res[1].error.startswith("rejected")
+    assert "boom" in res[2].error and res[0].error is None
+    s = serving.latency_summary(list(res.values()), 1.0)
+    assert s["completed"] == 1 and s["failed"] == 2
+
+
+def test_footprint_grows_with_size():
+    a = serving.footprint_bytes(1000, 20)
+    b = serving.footprint_bytes(200_000, 20)
+    c = serving.footprint_bytes(200_000, 20, k=500)
+    assert a < b < c
+    assert 2e9 < b < 6e9

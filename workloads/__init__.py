@@ -185,3 +185,54 @@ def tiny_problem(n: int, m: int, cov: int = COV_MATERN15, lik: int = LIK_BERNOUL
     return Problem(name=f"tiny_n{n}_m{m}", locs=locs, order=order, y=y, F=F, cov=cov, sigma2=sigma2,
                    rho=rho, m=m, lik=lik, t=8, s=16, test_locs=test, Fp=np.full(n_test, F0),
                    b_true=b, seed=seed)
+
+
+def serving_problem(index: int, seed: int = 7, n: int | None = None) -> Problem:
+    """Request ``index`` of the serving stream: a fresh latent-GP problem with n
+    log-uniform in [1e3, 2e5], uniform locations, Matern-1.5 covariance (sigma^2 = 1)
+    with range uniform in [0.02, 0.2], m = 20, Bernoulli-logit or Poisson-log
+    responses with probability 1/2 each, and 1000 uniform test points (t = 50 probes,
+    s = 100 simulation vectors). The latent field uses 64 random Fourier features so
+    that a stream of thousands of requests can be drawn in seconds."""
+    rng = np.random.default_rng([seed, index])
+    nn = n or int(round(math.exp(rng.uniform(math.log(1e3), math.log(2e5)))))
+    rho = float(rng.uniform(0.02, 0.2))
+    lik = LIK_BERNOULLI_LOGIT if rng.random() < 0.5 else LIK_POISSON_LOG
+    locs = rng.random((nn, 2))
+    b = latent_rff(locs, COV_MATERN15, 1.0, rho, rng, K=64)
+    F = np.zeros(nn)
+    y = responses(F + b, lik, rng)
+    order = rng.permutation(nn).astype(np.int32)
+    test = rng.random((1000, 2))
+    return Problem(name=f"serve_{index}", locs=locs, order=order, y=y, F=F, cov=COV_MATERN15, sigma2=1.0,
+                   rho=rho, m=20, lik=lik, t=50, s=100, test_locs=test, Fp=np.zeros(1000), b_true=b,
+                   seed=seed)
+
+
+def batched_problem(index: int, seed: int = 5, n: int | None = None) -> Problem:
+    """Problem ``index`` of the batched workload: n log-uniform in [5e3, 5e4], m
+    uniform in {10, 20, 30}, uniform locations, exponential covariance (sigma^2 = 1)
+    with range uniform in [0.02, 0.2], Bernoulli-logit responses, t = 50 probes."""
+    rng = np.random.default_rng([seed, index])
+    nn = n or int(round(math.exp(rng.uniform(math.log(5e3), math.log(5e4)))))
+    m = int(rng.choice([10, 20, 30]))
+    rho = float(rng.uniform(0.02, 0.2))
+    locs = rng.random((nn, 2))
+    b = latent_rff(locs, COV_EXPONENTIAL, 1.0, rho, rng, K=64)
+    F = np.zeros(nn)
+    y = responses(F + b, LIK_BERNOULLI_LOGIT, rng)
+    order = rng.permutation(nn).astype(np.int32)
+    return Problem(name=f"batch_{index}", locs=locs, order=order, y=y, F=F, cov=COV_EXPONENTIAL, sigma2=1.0,
+                   rho=rho, m=m, lik=LIK_BERNOULLI_LOGIT, t=50, s=100, test_locs=None, Fp=None, b_true=b,
+                   seed=seed)
+
+
+def poisson_arrivals(rate: float, duration: float, seed: int = 11) -> np.ndarray:
+    """Arrival times (seconds) of a Poisson process of the given rate on [0, duration)."""
+    rng = np.random.default_rng(seed)
+    t, out = 0.0, []
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t >= duration:
+            return np.array(out)
+        out.append(t)
