@@ -6,7 +6,7 @@
 #include <string>
 #include <vector>
 
-#include "lrac.cuh"
+#include "lrac_tc.cuh"
 
 namespace vl {
 
@@ -133,7 +133,9 @@ struct Engine {
   double *Cm = nullptr, *Rinv = nullptr, *Cinv = nullptr, *lpart = nullptr, *Gk = nullptr, *Vk = nullptr;
   double* dlogdet = nullptr;
   int* lbad = nullptr;
-  int nch_g = 1, rows_g = 0, nch_a = 1, rows_a = 0;
+  int nch_g = 1, rows_g = 0, nch_a = 1, rows_a = 0, nch_tc = 1, rows_tc = 0;
+  bool use_tc = false;   // float32 blocks of 2..64 columns with k <= 512: tensor-core products
+  float* Vt = nullptr;   // split image of V for the tensor-core product
   bool lr_dirty = true;
   double logdetC = 0.0;
   T* b2 = nullptr;
@@ -234,10 +236,20 @@ struct Engine {
       nch_a = chunks_for(n, (int64_t)tq * ((t + 63) / 64), 2 * c->num_sms);
     rows_a = (int)(((n + nch_a - 1) / nch_a + 511) / 512 * 512);
     nch_a = (n + rows_a - 1) / rows_a;
+    use_tc = std::is_same<T, float>::value && t > 1 && t <= kTcN && kr <= kTcMaxRank;
+    if (use_tc) {
+      nch_tc = std::max(1, std::min(c->num_sms, (n + 15) / 16));
+      rows_tc = ((n + nch_tc - 1) / nch_tc + 15) / 16 * 16;
+      nch_tc = (n + rows_tc - 1) / rows_tc;
+      Vt = mem.get<float>((size_t)((kr + 31) / 32) * 4096);
+      if (!Vt) return fail(c, VL_ERR_OOM, "workspace exhausted (LRAC tensor-core operands)");
+      VL_CUDA(c, cudaFuncSetAttribute(lrac_tn_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTnSmem));
+      VL_CUDA(c, cudaFuncSetAttribute(lrac_nn_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kNnSmem));
+    }
     Cm = mem.get<double>(kk);
     Rinv = mem.get<double>(kk);
     Cinv = mem.get<double>(kk);
-    lpart = mem.get<double>(std::max<int64_t>((int64_t)nch_g * kk, (int64_t)nch_a * kr * t));
+    lpart = mem.get<double>(std::max<int64_t>((int64_t)nch_g * kk, (int64_t)std::max(nch_a, nch_tc) * kr * t));
     Gk = mem.get<double>((size_t)kr * t);
     Vk = mem.get<double>((size_t)kr * t);
     dlogdet = mem.get<double>(1);
@@ -299,6 +311,14 @@ struct Engine {
       lrac_sum_chunks_kernel<<<grid_for(c, k), 256, 0, VL_STREAM(c)>>>(nch_a, k, lpart, Gk, 0);
       lrac_cinv_apply1_kernel<<<(k + 7) / 8, 256, 0, VL_STREAM(c)>>>(k, Cinv, Gk, Vk);
       lrac_nn1_kernel<T><<<(n + 255) / 256, 256, sizeof(T) * k, VL_STREAM(c)>>>(n, k, Lk, Vk, R, W, W, T(-1), Zo);
+    } else if (use_tc) {
+      if constexpr (std::is_same<T, float>::value) {
+        lrac_tn_tc_kernel<<<nch_tc, 256, kTnSmem, VL_STREAM(c)>>>(n, k, t, ld, rows_tc, Lk, R, W, lpart, c->dstatus);
+        lrac_sum_chunks_kernel<<<grid_for(c, (int64_t)k * t), 256, 0, VL_STREAM(c)>>>(nch_tc, (int64_t)k * t, lpart, Gk,
+                                                                                     0);
+        lrac_cinv_apply_kernel<<<dim3((t + 63) / 64, k), 64, 0, VL_STREAM(c)>>>(k, t, Cinv, Gk, Vk);
+        VL_TRY(nn_tc(Vk, R, W, W, -1.f, Zo));
+      }
     } else {
       const int tq = (k + 63) / 64, tt = (t + 63) / 64;
       lrac_tn_kernel<T><<<dim3(tq, tt, nch_a), 256, 0, VL_STREAM(c)>>>(n, k, t, rows_a, Lk, R, ld, 1, W, 0, lpart);
@@ -310,9 +330,28 @@ struct Engine {
     return VL_OK;
   }
 
+  // Z = a o Y + beta b o (L V) on the tensor cores (float32 blocks; V k x t float64).
+  vl_status nn_tc(const double* V, const T* Y, const T* a, const T* b, float beta, T* Zo) {
+    if constexpr (std::is_same<T, float>::value) {
+      const int k = kr, nkc = (k + 31) / 32;
+      lrac_vprep_kernel<<<grid_for(c, (int64_t)nkc * 32 * kTcN), 256, 0, VL_STREAM(c)>>>(k, t, nkc, V, Vt);
+      const int tiles = (n + 127) / 128;
+      lrac_nn_tc_kernel<<<std::max(1, std::min(tiles, 2 * c->num_sms)), 128, kNnSmem, VL_STREAM(c)>>>(
+          n, k, t, ld, Lk, Vt, Y, a, b, beta, Zo, c->dstatus);
+      VL_CUDA(c, cudaGetLastError());
+      return VL_OK;
+    } else {
+      return fail(c, VL_ERR_STATE, "tensor-core LRAC path is float32 only");
+    }
+  }
+
   // Z = a o Y + L V with V (k x t, float64, device): the LRAC probe z = W^{-1/2} r2 + L r1.
   vl_status lrac_lowrank_plus(const double* V, const T* Y, const T* a, T* Zo) {
     const int k = kr;
+    if (use_tc) {
+      ProfScope ps(c, "woodbury", t);
+      return nn_tc(V, Y, a, nullptr, 1.f, Zo);
+    }
     if (t == 1)
       lrac_nn1_kernel<T><<<(n + 255) / 256, 256, sizeof(T) * k, VL_STREAM(c)>>>(n, k, Lk, V, Y, a, nullptr, T(1), Zo);
     else

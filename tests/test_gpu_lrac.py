@@ -188,3 +188,23 @@ def test_lrac_poisson_grid_consistent_with_exact(ctx, vl):
     f, md = _oracle_all(P)
     L_ex, _ = la.lml_exact(f, md)
     assert abs(lml - L_ex) < 4 * 0.5 * stats["slq_stderr"] + 1e-4 * abs(L_ex)
+
+
+# ----------------------------------------------------------------------------- tensor-core products
+@pytest.mark.parametrize("n,k,t", [(1037, 37, 2), (1037, 130, 7), (2000, 500, 50), (1500, 64, 64), (777, 200, 1)])
+def test_woodbury_apply_float32_tensor_cores(ctx, vl, n, k, t):
+    """Float32 blocks of 2..64 columns take the tcgen05 (tf32, split-operand) products;
+    t = 1 the SIMT ones. Both must agree with the float64 Woodbury identity to
+    float32 accuracy."""
+    P = wl.make_problem("c1_n2000", n=n)
+    o64 = _lrac(vl, k=k, **FP64_TIGHT)
+    o32 = _lrac(vl, k=k, precision=vl.FP32_REFINE, cg_tol=1e-6, newton_tol=1e-7)
+    fac = ctx.build_factor(P.locs, P.order, P.cov, P.sigma2, P.rho, P.m, o64)
+    st = fac.find_mode(P.lik, P.y, P.F, o64)
+    f, md = _oracle_all(P)
+    L_ref, _ = olr.pivoted_cholesky(f.locs, f.cov, f.sigma2, f.rho, f.nugget, k)
+    X = np.random.default_rng(n + t).standard_normal((P.n, t))
+    Y = st.apply(vl.OP_PINV, X, o32)
+    Yv = olr.woodbury_apply(L_ref, md.W, X[f.order])
+    err = np.max(np.abs(Y[f.order] - Yv)) / np.max(np.abs(Yv))
+    assert err < 2e-5, err
