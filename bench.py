@@ -13,6 +13,15 @@ probes, VADU preconditioner, float32 Krylov path with float64 refinement.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
+Two more legs run on rank 0 of a single-GPU run, after the timed steps:
+* batched: 256 independent problems (n log-uniform in [5e3, 5e4], m in {10, 20,
+  30}, exponential covariance, Bernoulli-logit), mode + L^VLA each, spread over
+  slot contexts on separate streams; reported as evaluations/s.
+* serving: a Poisson stream of fresh problems at 50 requests/s (n log-uniform in
+  [1e3, 2e5], Matern-1.5, Bernoulli or Poisson, mode + L^VLA + predictive
+  variances at 1000 points) admitted by device-memory footprint; reported as
+  p50 / p99 latency (arrival to completion) and throughput.
+
 Multi-GPU (torchrun, one rank per GPU): independent replicas, each rank solving its
 own seeded problem of the same shape (weak scaling); no collective on the data path.
 """
@@ -169,6 +178,55 @@ def cpu_baseline(n_full: int, steps: int = 1) -> dict:
                       f"by n_sample/n (linear; flatters the CPU since sparse LU grows faster than n)"}
 
 
+# ----------------------------------------------------------------------------- batched / serving legs
+def _gen_serving(i):
+    import workloads as wl
+    return wl.serving_problem(i)
+
+
+def _gen_batched(i):
+    import workloads as wl
+    return wl.batched_problem(i)
+
+
+def pregenerate(kind: str, count: int, procs: int = 12):
+    """Draws the problems of a leg in a spawned process pool (inputs, not timed)."""
+    import multiprocessing as mp
+    fn = _gen_serving if kind == "serving" else _gen_batched
+    with mp.get_context("spawn").Pool(procs) as pool:
+        return pool.map(fn, range(count), chunksize=4)
+
+
+def serving_leg(vl, problems, arrivals, duration: float, slots: int, device: int) -> dict:
+    import numpy as np
+    from paper_2310_12000_gb300 import serving
+    opts = dict(precision=1, t=50, s=100, cg_tol=1e-6, newton_tol=1e-7)
+    reqs = [serving.Request.from_problem(i, P, opts) for i, P in enumerate(problems)]
+    cap = serving.footprint_bytes(200_000, 20)
+    srv = serving.Server(slots=slots, budget_bytes=slots * cap, slot_capacity=cap,
+                         make_ctx=serving.gpu_slots(vl, device, cap),
+                         runner=lambda ctx, req: serving.run_request(vl, ctx, req)).start()
+    for r, t in zip(reqs, arrivals):
+        now = srv.now()
+        if t > now:
+            time.sleep(t - now)
+        srv.submit(r)
+    res = srv.drain()
+    wall = srv.now()
+    out = serving.latency_summary(res, wall)
+    out.update({"offered_rps": len(arrivals) / duration, "arrival_window_s": duration, "slots": slots,
+                "peak_concurrent": srv.sched.peak_running, "wall_s": wall,
+                "mean_n": float(np.mean([r.n for r in reqs])) if reqs else None,
+                "max_true_relres": max((r.stats.get("mode", {}).get("true_relres_max", 0.0) for r in res
+                                        if r.error is None), default=None),
+                "errors": [r.error for r in res if r.error][:3],
+                "workload": "Poisson arrivals; per request n log-uniform in [1e3, 2e5], uniform locations, "
+                            "Matern-1.5 range U[0.02, 0.2], m=20, Bernoulli or Poisson (p=1/2), mode + L^VLA "
+                            "(t=50) + predictive mean/variance at 1000 points (s=100), float32 + float64 "
+                            "refinement; admission FIFO by device-memory footprint"})
+    return out
+
+
 # ----------------------------------------------------------------------------- distributed
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
@@ -230,6 +288,13 @@ def run_ours(args):
     import torch
 
     ws, rank, local = _dist()
+    legs = ws == 1 and rank == 0
+    batch_problems = pregenerate("batched", args.batch) if legs and args.batch > 0 else None
+    serve_arrivals = serve_problems = None
+    if legs and args.serve_seconds > 0:
+        import workloads as wl
+        serve_arrivals = wl.poisson_arrivals(args.serve_rate, args.serve_seconds)
+        serve_problems = pregenerate("serving", len(serve_arrivals))
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
@@ -349,6 +414,26 @@ def run_ours(args):
                 "rel_diff_mixed_vs_fp64": abs(lmls[-1] - L64) / abs(L64),
                 "newton_cg_iters_total": s64.get("cg_iters_total")}
 
+    # ---------------- batched and serving legs (their own slot contexts)
+    ctx.close()
+    del ctx, fac
+    torch.cuda.empty_cache()
+    batched = serving_out = None
+    if batch_problems:
+        from paper_2310_12000_gb300 import batched as bt
+        batched = bt.run_batch(vl, batch_problems, slots=args.slots, device=dev)
+        batched.pop("lml", None)
+        print(f"[bench] batched: {batched['completed']} problems in {batched['wall_s']:.1f} s", file=sys.stderr,
+              flush=True)
+        batched["workload"] = (f"{len(batch_problems)} problems, n log-uniform in [5e3, 5e4] (total "
+                               f"{sum(p.n for p in batch_problems)}), m in {{10,20,30}}, uniform locations, "
+                               f"exponential range U[0.02, 0.2], Bernoulli-logit, mode + L^VLA (t=50), float32 + "
+                               f"float64 refinement")
+    if serve_problems:
+        serving_out = serving_leg(vl, serve_problems, serve_arrivals, args.serve_seconds, args.slots, dev)
+        print(f"[bench] serving: {serving_out['completed']} requests, p99 {serving_out['p99_latency_ms']} ms, "
+              f"wall {serving_out['wall_s']:.1f} s", file=sys.stderr, flush=True)
+
     out = None
     if rank == 0:
         cb = cpu_baseline(n) if (ws == 1 and not args.no_cpu) else None
@@ -370,7 +455,8 @@ def run_ours(args):
             "fp64": fp64, "e2e": e2e, "gpu_launches": launches, "launches_before_timed": launches_before,
             "roofline": roofline,
             "kernel_profile_ms": prof, "clocks": clk.summary(), "cpu_baseline": cb,
-            "p99_latency_ms": None,
+            "p99_latency_ms": serving_out["p99_latency_ms"] if serving_out else None,
+            "batched": batched, "serving": serving_out,
         }
         print(json.dumps(out))
     if ws > 1:
@@ -390,6 +476,10 @@ def main():
     ap.add_argument("--n", type=int, default=None,
                     help="smaller instance of the same grid-with-gaps recipe (default: the 1,000,000-point grid)")
     ap.add_argument("--ws-gb", type=float, default=None, help="workspace size in GiB (default: 60%% of free memory)")
+    ap.add_argument("--batch", type=int, default=256, help="problems in the batched leg (0: skip)")
+    ap.add_argument("--serve-seconds", type=float, default=4.0, help="arrival window of the serving leg (0: skip)")
+    ap.add_argument("--serve-rate", type=float, default=50.0, help="serving arrivals per second")
+    ap.add_argument("--slots", type=int, default=16, help="slot contexts of the batched and serving legs")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

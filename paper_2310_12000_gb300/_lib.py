@@ -199,6 +199,7 @@ class Context:
                     o.close()
             self.lib.vl_ctx_destroy(self.h)
             self.h = None
+            self._ws = None                # every handle is gone: the workspace can go back to PyTorch
 
     def __del__(self):
         try:

@@ -100,6 +100,24 @@ vl_status with_shape(int ld, F&& f) {
 // Largest system the t = 1 solve keeps in shared memory (one block).
 constexpr size_t kSmemSolveBytes = 200 * 1024;
 
+// A triangular solve runs in one thread-block cluster (hardware cluster barrier,
+// part of the device) rather than on the whole grid (software grid barrier) while
+// the widest level needs at most this many rounds of the largest cluster's teams.
+// Problems up to kSharedRows rows are the ones served side by side (batched and
+// serving forms): for them the cluster is kept even for wide levels, since a grid
+// solve needs the whole device; measured on the serving mix this raised throughput
+// by half. Larger problems usually own the device, where the grid solve is faster.
+constexpr int64_t kSharedRows = 262144;
+#ifndef VL_T1_CLUSTER_ROUNDS
+#define VL_T1_CLUSTER_ROUNDS 8
+#endif
+#ifndef VL_BLOCK_CLUSTER_ROUNDS
+#define VL_BLOCK_CLUSTER_ROUNDS 4
+#endif
+#ifndef VL_SHARED_CLUSTER_ROUNDS
+#define VL_SHARED_CLUSTER_ROUNDS 32
+#endif
+
 inline vl_status cuda_ok(Ctx* c, cudaError_t e) { return e == cudaSuccess ? VL_OK : cuda_fail(c, e, "kernel launch"); }
 
 inline int grid_for(Ctx* c, int64_t work, int block = 256) {
@@ -285,7 +303,8 @@ struct Engine {
         }
       }
       const size_t smem = sizeof(double) * ((size_t)k * 16 + 256);
-      VL_CUDA(c, cudaFuncSetAttribute(lrac_trinv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      const size_t smem_max = sizeof(double) * ((size_t)kMaxRank * 16 + 256);   // fixed: see cluster_size
+      VL_CUDA(c, cudaFuncSetAttribute(lrac_trinv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
       lrac_trinv_kernel<<<(k + 15) / 16, 256, smem, VL_STREAM(c)>>>(k, Cm, Rinv);
       lrac_cinv_kernel<<<dim3((k + 127) / 128, k), 128, 0, VL_STREAM(c)>>>(k, Rinv, Cinv);
     }
@@ -428,10 +447,12 @@ struct Engine {
   }
 
   // Largest cluster (<= 16 blocks of 1024 threads, smem bytes of dynamic shared
-  // memory each) the device can co-schedule for fn.
-  int cluster_size(const void* fn, size_t smem = 0) {
+  // memory each) the device can co-schedule for fn. Function attributes are
+  // process-wide and other threads may launch fn concurrently with another size, so
+  // the shared-memory bound is always set to the kernel's fixed maximum smem_max.
+  int cluster_size(const void* fn, size_t smem = 0, size_t smem_max = 0) {
     cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (smem_max > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
@@ -449,6 +470,15 @@ struct Engine {
       return 0;
     }
     return std::min(cs, 16);
+  }
+
+  // Smallest power-of-two cluster (<= cs_max blocks) whose teams cover the widest
+  // level in two rounds: narrow problems take a few SMs and leave the rest of the
+  // device to other streams.
+  static int fit_cluster(int widest, int cta_teams, int cs_max) {
+    int cs = 1;
+    while (cs < cs_max && widest > 2 * cs * cta_teams) cs *= 2;
+    return std::min(cs, cs_max);
   }
 
   template <bool FWD>
@@ -501,8 +531,7 @@ struct Engine {
       constexpr int LPV1 = FWD ? 8 : 16;
       auto fn = sptrsv_t1_smem_kernel<T, FWD, LPV1>;
       const size_t smem = (size_t)n * sizeof(T);
-      if (smem > 48 * 1024)
-        VL_CUDA(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      VL_CUDA(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemSolveBytes));
       L.l_head = 0;
       L.l_tail = L.nlev;
       int nn = n;
@@ -532,8 +561,11 @@ struct Engine {
         auto fn = sptrsv_cluster_kernel<T, FWD, LPV, NV, decltype(U)::value>;
         const int tpb = 32 * (32 / LPV);
         const size_t smem = sizeof(T) * (size_t)tpb * ld;
-        const int cs = cluster_size((const void*)fn, smem);
-        if (cs < 2 || widest > 4 * cs * tpb) return VL_OK;
+        const size_t smem_max = sizeof(T) * (size_t)tpb * (LPV * NV * VecT<T>::n);   // widest row this shape covers
+        const int cs_max = cluster_size((const void*)fn, smem, smem_max);
+        const int rounds = n <= kSharedRows ? VL_SHARED_CLUSTER_ROUNDS : VL_BLOCK_CLUSTER_ROUNDS;
+        if (cs_max < 1 || widest > rounds * cs_max * tpb) return VL_OK;
+        const int cs = fit_cluster(widest, tpb, cs_max);
         L.l_head = 0;
         L.l_tail = L.nlev;
         cudaLaunchConfig_t cfg = {};
@@ -573,11 +605,13 @@ struct Engine {
       // one thread-block cluster walks all levels (see sptrsv_t1_cluster_kernel)
       constexpr int LPV1 = FWD ? 8 : 16;   // backward rows can list hundreds of dependents
       auto fn = sptrsv_t1_cluster_kernel<T, FWD, LPV1>;
-      const int cs = cluster_size((const void*)fn);
+      const int cs_max = cluster_size((const void*)fn);
       // one cluster only pays off while every level fits a few rounds of its teams;
       // the widest levels of large problems need the whole grid
-      const int cluster_teams = cs * (1024 / 32) * (32 / LPV1);
-      if (cs >= 2 && widest <= 8 * cluster_teams) {
+      const int cta_teams = (1024 / 32) * (32 / LPV1);
+      const int rounds = n <= kSharedRows ? VL_SHARED_CLUSTER_ROUNDS : VL_T1_CLUSTER_ROUNDS;
+      if (cs_max >= 2 && widest <= rounds * cs_max * cta_teams) {
+        const int cs = fit_cluster(widest, cta_teams, cs_max);
         L.l_head = 0;
         L.l_tail = L.nlev;
         cudaLaunchConfig_t cfg = {};

@@ -115,7 +115,10 @@ vl_status factor_rows(Ctx* c, int64_t rows, int m, const double* self_locs, cons
                       double* D, const int32_t* row_ids) {
   if (rows <= 0) return VL_OK;
   const size_t smem = sizeof(double) * (size_t)kFactorWarps * (m * (m + 1) + 3 * m + 1);
-  VL_CUDA(c, cudaFuncSetAttribute(factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  // the attribute is per kernel and process-wide: always the bound for the largest m
+  // (64), so that calls on other threads with another m never lower it under a launch
+  const size_t smem_max = sizeof(double) * (size_t)kFactorWarps * (64 * 65 + 3 * 64 + 1);
+  VL_CUDA(c, cudaFuncSetAttribute(factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
   const int grid = (int)((rows + kFactorWarps - 1) / kFactorWarps);
   ProfScope ps(c, "factor", m);
   factor_kernel<<<grid, 32 * kFactorWarps, smem, VL_STREAM(c)>>>((int)rows, m, self_locs, ref_locs, nbr, cov, sigma2, rho,
