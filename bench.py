@@ -58,10 +58,12 @@ def _nnz(n: int, m: int) -> int:
     return sum(min(k, m) for k in range(min(n, m))) + max(0, n - m) * m
 
 
-def algorithmic_bytes(cls: str, n: int, m: int, t: int, e: int) -> float:
+def algorithmic_bytes(cls: str, n: int, m: int, t: int, e: int, k: int = 0) -> float:
     """Bytes one launch of kernel class `cls` must move (each operand once)."""
     nnz = _nnz(n, m)
     vec = n * t * e
+    if cls == "woodbury":       # L read for L^T(WR) and again for L V; R read twice, W, Z written
+        return 2 * n * k * e + 3 * vec + n * e
     if cls == "sptrsv_fwd":     # ELL (idx + val), task list, rhs, row scale, solution
         return nnz * (4 + e) + 4 * n + vec + n * e + vec
     if cls == "sptrsv_bwd":     # CSR (idx + val + row pointers), task list, rhs, solution
@@ -308,8 +310,9 @@ def run_ours(args):
     ws_bytes = int(args.ws_gb * (1 << 30)) if args.ws_gb else int(min(torch.cuda.mem_get_info(dev)[0] * 0.6, 120 << 30))
     ctx = vl.Context(dev, ws_bytes=ws_bytes)
     stream = torch.cuda.current_stream(dev)
-    o32 = vl.Opts.make(precision=vl.FP32_REFINE, t=50, cg_tol=1e-6, newton_tol=1e-7, cg_max_iter=2000)
-    o64 = vl.Opts.make(precision=vl.FP64, t=50, cg_tol=1e-6, newton_tol=1e-7, cg_max_iter=2000)
+    pre = dict(precond=vl.PREC_LRAC, k=args.k) if args.precond == "lrac" else dict(precond=vl.PREC_VADU)
+    o32 = vl.Opts.make(precision=vl.FP32_REFINE, t=50, cg_tol=1e-6, newton_tol=1e-7, cg_max_iter=3000, **pre)
+    o64 = vl.Opts.make(precision=vl.FP64, t=50, cg_tol=1e-6, newton_tol=1e-7, cg_max_iter=3000, **pre)
 
     # neighbours + levels + factor, once per location set
     t0 = time.perf_counter()
@@ -363,7 +366,7 @@ def run_ours(args):
         barrier()
     elapsed_s, value = replica_throughput(e0.elapsed_time(e1) / 1000.0, args.steps)
     launches = ctx.profile_read("all")[1]
-    classes = ["sptrsv_fwd", "sptrsv_bwd", "spmv_B", "spmv_Bt", "coldot", "pcg_update", "factor"]
+    classes = ["sptrsv_fwd", "sptrsv_bwd", "spmv_B", "spmv_Bt", "coldot", "pcg_update", "factor", "woodbury"]
     prof = {}
     for cls in classes:
         for t in (1, 50):
@@ -376,13 +379,19 @@ def run_ours(args):
                 prof["factor"] = {"ms": ms, "launches": cnt}
     ctx.profile(False)
 
+    for cls in ("pivoted_cholesky", "lrac_gram", "lrac_kxk"):
+        ms, cnt = ctx.profile_read(cls, args.k)
+        if cnt:
+            prof[cls] = {"ms": ms, "launches": cnt}
+
     # roofline for the dominant HBM-bound kernel class
     hbm_peak, peak_kind = _peaks()
-    dom_key = max((k for k in prof if k.split("/")[0] in ("sptrsv_fwd", "sptrsv_bwd", "spmv_B", "spmv_Bt", "coldot")),
+    dom_key = max((k for k in prof if k.split("/")[0] in ("sptrsv_fwd", "sptrsv_bwd", "spmv_B", "spmv_Bt", "coldot",
+                                                          "woodbury")),
                   key=lambda k: prof[k]["ms"])
     dcls, dt = dom_key.split("/")[0], int(dom_key.split("=")[1])
     avg_ms = prof[dom_key]["ms"] / prof[dom_key]["launches"]
-    bytes_launch = algorithmic_bytes(dcls, n, P.m, dt, 4)
+    bytes_launch = algorithmic_bytes(dcls, n, P.m, dt, 4, args.k)
     achieved = bytes_launch / (avg_ms / 1000.0) / 1e9
     total_prof_ms = sum(v["ms"] for v in prof.values())
     roofline = {"bound": "hbm", "kernel": dom_key, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
@@ -445,8 +454,9 @@ def run_ours(args):
             "config": {"workload": f"{WORKLOAD}: " + ("1250x1000 grid" if args.n is None else "square grid")
                                    + f" on [0,1]^2 minus 20% rectangular gaps, "
                                    f"n={n}, Matern-1.5 sigma2=1 rho=0.02, m=20, Poisson-log offset 1.0, "
-                                   f"t=50 Rademacher probes, VADU, float32 Krylov + float64 refinement, "
-                                   f"cg_tol 1e-6",
+                                   f"t=50 Rademacher probes, "
+                                   + (f"LRAC k={args.k}" if args.precond == "lrac" else "VADU")
+                                   + ", float32 Krylov + float64 refinement, cg_tol 1e-6",
                        "step": "factor rows + Newton mode + SLQ log-marglik (neighbours/levels once, excluded)",
                        "l2": "inputs larger than L2 (probe block 1e6 x 56 float32 = 224 MB per vector)",
                        "graph_ms": graph_ms, "levels_fwd": info["nlev_fwd"], "levels_bwd": info["nlev_bwd"]},
@@ -476,6 +486,8 @@ def main():
     ap.add_argument("--n", type=int, default=None,
                     help="smaller instance of the same grid-with-gaps recipe (default: the 1,000,000-point grid)")
     ap.add_argument("--ws-gb", type=float, default=None, help="workspace size in GiB (default: 60%% of free memory)")
+    ap.add_argument("--precond", default="vadu", choices=["vadu", "lrac"], help="preconditioner of the timed step")
+    ap.add_argument("--k", type=int, default=500, help="LRAC rank")
     ap.add_argument("--batch", type=int, default=256, help="problems in the batched leg (0: skip)")
     ap.add_argument("--serve-seconds", type=float, default=4.0, help="arrival window of the serving leg (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=50.0, help="serving arrivals per second")
