@@ -268,10 +268,42 @@ struct LevelPlan {
   long long* trace;            // optional: block 0's clock at each level boundary (nlev + 1)
 };
 
-// Grid barrier with a bounded wait: the last block to arrive bumps the
-// generation. A timeout records VL_ERR_TIMEOUT; after an abort every barrier
-// returns at once so the launch still ends.
-__device__ __forceinline__ void grid_barrier(unsigned* bar, DevStatus* st) {
+// Grid barrier with a bounded wait on a monotonic arrival counter (zero at launch):
+// barrier number e of the launch is passed once the counter reaches e * gridDim.x.
+// Each block adds 1 with release semantics (after a block barrier, so the add
+// publishes the whole block's writes) and polls with acquire loads; nothing has to
+// be written after the last arrival, so waiters leave as soon as it lands in L2.
+// `epoch` counts the barriers this block has passed (kept by thread 0). A timeout
+// records VL_ERR_TIMEOUT; after an abort every barrier returns at once so the
+// launch still ends.
+// Measured at n = 1e6: 10 % faster scalar (t = 1) solves than the generation-word
+// barrier below, but slower block (t = 50) solves, which therefore keep the latter.
+__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void grid_barrier_counter(unsigned* bar, DevStatus* st, unsigned& epoch) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ++epoch;
+    if (!ld_volatile(&st->abort)) {
+      const unsigned target = epoch * gridDim.x;
+      red_release_add(&bar[0], 1u);
+      int spins = 0;
+      // a few tight polls, then back off so the polls do not crowd the arrivals
+      // that land on the same word
+      while (ld_acquire(&bar[0]) < target && ++spins < 4096) {
+        if (spins > 4) __nanosleep(40);
+      }
+      if (spins >= 4096) bounded_wait([&] { return ld_acquire(&bar[0]) >= target; }, st, -1);
+    }
+  }
+  __syncthreads();
+}
+
+// Grid barrier with a bounded wait: the last block to arrive resets the arrival
+// counter and bumps the generation word the others poll (bar[1]; zero at launch).
+__device__ __forceinline__ void grid_barrier_generation(unsigned* bar, DevStatus* st) {
   __syncthreads();
   if (threadIdx.x == 0 && !ld_volatile(&st->abort)) {
     const unsigned gen = ld_acquire(&bar[1]);
@@ -287,6 +319,14 @@ __device__ __forceinline__ void grid_barrier(unsigned* bar, DevStatus* st) {
     }
   }
   __syncthreads();
+}
+
+template <bool COUNTER>
+__device__ __forceinline__ void grid_barrier(unsigned* bar, DevStatus* st, unsigned& epoch) {
+  if constexpr (COUNTER)
+    grid_barrier_counter(bar, st, epoch);
+  else
+    grid_barrier_generation(bar, st);
 }
 
 // Row state loaded ahead of time: everything a team needs before it reads x
@@ -513,7 +553,7 @@ __device__ void heavy_row1(int p, int m, const LevelPlan& L, const int32_t* __re
 // light row (pre) before the barrier that precedes it and finishes it after
 // (run); the heavy rows that lead each level are done first, a block per row
 // (heavy(p), called by every thread of the block).
-template <int LPV, typename Pre, typename Run, typename Heavy>
+template <int LPV, bool COUNTER, typename Pre, typename Run, typename Heavy>
 __device__ __forceinline__ void level_walk(const LevelPlan& L, Pre pre, Run run, Heavy heavy) {
   constexpr int RPW = 32 / LPV;
   const int tpb = (blockDim.x >> 5) * RPW;
@@ -545,8 +585,9 @@ __device__ __forceinline__ void level_walk(const LevelPlan& L, Pre pre, Run run,
       __syncthreads();
     }
   };
+  unsigned epoch = 0;
   if (blockIdx.x == 0) solo(0, L.l_head);
-  if (L.l_head > 0 && L.l_head < L.nlev) grid_barrier(L.bar, L.st);
+  if (L.l_head > 0 && L.l_head < L.nlev) grid_barrier<COUNTER>(L.bar, L.st, epoch);
   {
     int p = 0;
     bool has = L.l_head < L.l_tail && first_light(L.l_head, g, p);
@@ -564,7 +605,7 @@ __device__ __forceinline__ void level_walk(const LevelPlan& L, Pre pre, Run run,
         has = first_light(l + 1, g, p);
         if (has) pre(p);
       }
-      grid_barrier(L.bar, L.st);
+      grid_barrier<COUNTER>(L.bar, L.st, epoch);
     }
   }
   if (blockIdx.x == 0) solo(L.l_tail, L.nlev);
@@ -717,7 +758,7 @@ __global__ void __launch_bounds__(512) sptrsv_kernel(LevelPlan L, int m, const i
   extern __shared__ unsigned char vl_smem[];
   T* part = reinterpret_cast<T*>(vl_smem);
   RowPre<T, LPV, NV> r;
-  level_walk<LPV>(
+  level_walk<LPV, false>(
       L, [&](int p) { row_pre<T, FWD, LPV, NV>(r, p, m, L, idx, val, rowptr, rhs, q, ld); },
       [&]() { row_run<T, LPV, NV, UNR>(r, idx, val, x, ld); },
       [&](int p) { heavy_row<T, FWD, LPV, NV, UNR>(p, m, L, idx, val, rowptr, rhs, q, x, ld, part); });
@@ -730,7 +771,7 @@ __global__ void __launch_bounds__(512) sptrsv_t1_kernel(LevelPlan L, int m, cons
   extern __shared__ unsigned char vl_smem[];
   T* part = reinterpret_cast<T*>(vl_smem);
   RowPre1<T, LPV> r;
-  level_walk<LPV>(
+  level_walk<LPV, true>(
       L, [&](int p) { row_pre1<T, FWD, LPV>(r, p, m, L, idx, val, rowptr, rhs, q); },
       [&]() { row_run1<T, LPV>(r, idx, val, x); },
       [&](int p) { heavy_row1<T, FWD, LPV>(p, m, L, idx, val, rowptr, rhs, q, x, part); });
