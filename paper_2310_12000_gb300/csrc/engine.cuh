@@ -642,7 +642,9 @@ struct Engine {
         return VL_OK;
       }
       void* args[] = {&L, &mm, &idx, &val, &rp, &rhs, &q, &x};
-      return launch((const void*)sptrsv_t1_kernel<T, FWD, 8>, args, 8);
+      // backward rows list up to 48 light dependents: 16 lanes keep them to one round of loads
+      constexpr int LPVG = FWD ? 8 : 16;
+      return launch((const void*)sptrsv_t1_kernel<T, FWD, LPVG>, args, LPVG);
     }
     void* args[] = {&L, &mm, &idx, &val, &rp, &rhs, &q, &x, &l};
     return with_shape<T>(ld, [&](auto Lc, auto N, auto U) {
