@@ -199,14 +199,16 @@ def pregenerate(kind: str, count: int, procs: int = 12):
         return pool.map(fn, range(count), chunksize=4)
 
 
-def serving_leg(vl, problems, arrivals, duration: float, slots: int, device: int) -> dict:
+def serving_leg(vl, problems, arrivals, duration: float, slots: int, device: int, small: int = 0) -> dict:
     import numpy as np
     from paper_2310_12000_gb300 import serving
     opts = dict(precision=1, t=50, s=100, cg_tol=1e-6, newton_tol=1e-7)
     reqs = [serving.Request.from_problem(i, P, opts) for i, P in enumerate(problems)]
-    cap = serving.footprint_bytes(200_000, 20)
-    srv = serving.Server(slots=slots, budget_bytes=slots * cap, slot_capacity=cap,
-                         make_ctx=serving.gpu_slots(vl, device, cap),
+    # slot classes: `small` slots sized for n <= 6e4, the rest for the largest requests (n = 2e5)
+    big = slots - small
+    caps = [serving.footprint_bytes(200_000, 20)] * big + [serving.footprint_bytes(60_000, 20)] * small
+    srv = serving.Server(slots=caps, budget_bytes=sum(caps), slot_capacity=None,
+                         make_ctx=serving.gpu_slots(vl, device),
                          runner=lambda ctx, req: serving.run_request(vl, ctx, req)).start()
     for r, t in zip(reqs, arrivals):
         now = srv.now()
@@ -217,6 +219,7 @@ def serving_leg(vl, problems, arrivals, duration: float, slots: int, device: int
     wall = srv.now()
     out = serving.latency_summary(res, wall)
     out.update({"offered_rps": len(arrivals) / duration, "arrival_window_s": duration, "slots": slots,
+                "slot_classes": {"n<=2e5": big, "n<=6e4": small},
                 "peak_concurrent": srv.sched.peak_running, "wall_s": wall,
                 "mean_n": float(np.mean([r.n for r in reqs])) if reqs else None,
                 "max_true_relres": max((r.stats.get("mode", {}).get("true_relres_max", 0.0) for r in res
@@ -439,7 +442,8 @@ def run_ours(args):
                                f"exponential range U[0.02, 0.2], Bernoulli-logit, mode + L^VLA (t=50), float32 + "
                                f"float64 refinement")
     if serve_problems:
-        serving_out = serving_leg(vl, serve_problems, serve_arrivals, args.serve_seconds, args.slots, dev)
+        serving_out = serving_leg(vl, serve_problems, serve_arrivals, args.serve_seconds, args.slots, dev,
+                                  args.small_slots)
         print(f"[bench] serving: {serving_out['completed']} requests, p99 {serving_out['p99_latency_ms']} ms, "
               f"wall {serving_out['wall_s']:.1f} s", file=sys.stderr, flush=True)
 
@@ -492,6 +496,8 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="arrival window of the serving leg (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=50.0, help="serving arrivals per second")
     ap.add_argument("--slots", type=int, default=16, help="slot contexts of the batched and serving legs")
+    ap.add_argument("--small-slots", type=int, default=0,
+                    help="of the serving slots, how many are sized for n <= 6e4 only (the rest for n = 2e5)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -10,10 +10,12 @@ Execution model
 * A slot is a library context with its own CUDA stream and a workspace large
   enough for the biggest admissible request. Slot contexts are made once and reused,
   so serving allocates no device memory after start-up.
-* Admission is first-come first-served by HBM footprint: the request at the head of
-  the queue is admitted when a slot is free and the estimated device footprint of
-  the requests already running plus its own fits the budget. A request that could
-  never fit is rejected at once.
+* Admission is first-come first-served by HBM footprint: a free slot takes the
+  first queued request that fits its workspace, once the estimated device footprint
+  of the requests already running plus its own fits the budget. Slots may come in
+  size classes (a few sized for the largest requests, many for small ones), so the
+  order is first-come first-served within each class. A request that could never
+  fit is rejected at once.
 * Admitted requests run concurrently, each on its slot's stream from its own host
   thread (the library releases the interpreter lock), so their kernels overlap on
   the device as requests arrive and leave.
@@ -107,7 +109,7 @@ class Scheduler:
 
     def __init__(self, budget_bytes: int, slot_capacity: int):
         self.budget = int(budget_bytes)
-        self.capacity = int(slot_capacity)   # bytes one slot can hold
+        self.capacity = int(slot_capacity)   # bytes the largest slot can hold
         self.q: collections.deque[Request] = collections.deque()
         self.cv = threading.Condition()
         self.in_use = 0
@@ -126,21 +128,31 @@ class Scheduler:
             self.cv.notify_all()
             return True
 
-    def acquire(self, timeout: float | None = None) -> Request | None:
-        """Block until the head of the queue fits (returning it, admitted) or the
-        scheduler is closed and the queue empty (returning None)."""
+    def _first_fitting(self, capacity: int) -> int:
+        for i, r in enumerate(self.q):
+            if r.footprint <= capacity:
+                return i
+        return -1
+
+    def acquire(self, timeout: float | None = None, capacity: int | None = None) -> Request | None:
+        """Block until the first queued request that fits a slot of `capacity` bytes
+        (default: the largest) also fits the budget (returning it, admitted), or the
+        scheduler is closed and no queued request fits this slot (returning None)."""
+        cap = self.capacity if capacity is None else int(capacity)
         deadline = None if timeout is None else time.perf_counter() + timeout
         with self.cv:
             while True:
-                if self.q and self.in_use + self.q[0].footprint <= self.budget:
-                    req = self.q.popleft()
+                i = self._first_fitting(cap)
+                if i >= 0 and self.in_use + self.q[i].footprint <= self.budget:
+                    req = self.q[i]
+                    del self.q[i]
                     self.in_use += req.footprint
                     self.running += 1
                     self.peak_in_use = max(self.peak_in_use, self.in_use)
                     self.peak_running = max(self.peak_running, self.running)
                     self.cv.notify_all()
                     return req
-                if self.closed and not self.q:
+                if self.closed and i < 0:
                     return None
                 left = None if deadline is None else deadline - time.perf_counter()
                 if left is not None and left <= 0:
@@ -180,17 +192,22 @@ def run_request(vl, ctx, req: Request) -> dict:
 
 
 class Server:
-    """``slots`` worker threads, each owning one context (made by ``make_ctx(slot)``)
-    and serving admitted requests with ``runner(ctx, req) -> dict``."""
+    """Worker threads, one per slot, each owning one context (made by
+    ``make_ctx(slot)``, or ``make_ctx(slot, capacity)`` when slots have capacities)
+    and serving admitted requests with ``runner(ctx, req) -> dict``. ``slots`` is a
+    count (every slot holds ``slot_capacity`` bytes) or a list of per-slot capacities."""
 
-    def __init__(self, slots: int, budget_bytes: int, slot_capacity: int, make_ctx: Callable[[int], object],
+    def __init__(self, slots, budget_bytes: int, slot_capacity: int | None, make_ctx: Callable[..., object],
                  runner: Callable[[object, Request], dict], clock: Callable[[], float] = time.perf_counter):
-        self.sched = Scheduler(budget_bytes, slot_capacity)
+        caps = [int(slot_capacity)] * slots if isinstance(slots, int) else [int(c) for c in slots]
+        self.caps = caps
+        self.sched = Scheduler(budget_bytes, max(caps))
         self.make_ctx, self.runner, self.clock = make_ctx, runner, clock
+        self._sized = not isinstance(slots, int)
         self.results: list[Result] = []
         self._lock = threading.Lock()
-        self._ready = threading.Barrier(slots + 1)
-        self.threads = [threading.Thread(target=self._worker, args=(i,), daemon=True) for i in range(slots)]
+        self._ready = threading.Barrier(len(caps) + 1)
+        self.threads = [threading.Thread(target=self._worker, args=(i,), daemon=True) for i in range(len(caps))]
         self.t0 = 0.0
         self.errors: list[str] = []
 
@@ -216,14 +233,14 @@ class Server:
 
     def _worker(self, slot: int):
         try:
-            ctx = self.make_ctx(slot)
+            ctx = self.make_ctx(slot, self.caps[slot]) if self._sized else self.make_ctx(slot)
         except Exception as e:          # noqa: BLE001 - reported to the caller
             self.errors.append(f"slot {slot}: {e}")
             self._ready.wait()
             return
         self._ready.wait()
         while True:
-            req = self.sched.acquire()
+            req = self.sched.acquire(capacity=self.caps[slot])
             if req is None:
                 break
             t_admit = self.now()
@@ -266,15 +283,15 @@ def latency_summary(results: list[Result], wall_s: float) -> dict:
     }
 
 
-def gpu_slots(vl, device: int, ws_bytes: int) -> Callable[[int], object]:
+def gpu_slots(vl, device: int, ws_bytes: int | None = None) -> Callable[..., object]:
     """Slot factory: one library context per slot on its own CUDA stream, with a
-    workspace of ws_bytes taken from PyTorch's device memory."""
+    workspace (ws_bytes, or the slot's capacity) taken from PyTorch's device memory."""
     import torch
 
-    def make(slot: int):
+    def make(slot: int, capacity: int | None = None):
         torch.cuda.set_device(device)
         stream = torch.cuda.Stream(device)
-        ctx = vl.Context(device, ws_bytes=ws_bytes, stream=stream)
+        ctx = vl.Context(device, ws_bytes=int(capacity or ws_bytes), stream=stream)
         ctx._slot_stream = stream      # keep the stream alive with the context
         return ctx
     return make

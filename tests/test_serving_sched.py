@@ -68,3 +68,27 @@ def test_footprint_grows_with_size():
     c = serving.footprint_bytes(200_000, 20, k=500)
     assert a < b < c
     assert 2e9 < b < 6e9
+
+
+def test_slot_classes_take_requests_that_fit():
+    seen = {}
+    lock = threading.Lock()
+
+    def runner(ctx, req):
+        with lock:
+            seen[req.rid] = ctx
+        time.sleep(0.001)
+        return {"lml": 0.0}
+
+    caps = [100, 30, 30, 30]          # one large slot, three small ones
+    srv = serving.Server(slots=caps, budget_bytes=190, slot_capacity=None,
+                         make_ctx=lambda s, cap: cap, runner=runner).start()
+    sizes = [90, 10, 20, 80, 25, 5, 100, 30, 15]
+    for i, fp in enumerate(sizes):
+        assert srv.submit(_req(i, fp))
+    assert not srv.submit(_req(99, 101))     # above every slot
+    res = {r.rid: r for r in srv.drain()}
+    assert all(r.error is None for i, r in res.items() if i != 99)
+    for i, fp in enumerate(sizes):
+        assert fp <= seen[i]                  # ran on a slot large enough for it
+    assert srv.sched.peak_in_use <= 190
