@@ -3,7 +3,11 @@
 // algorithm with per-column freezing and Lanczos T extraction.
 #pragma once
 
+#include <map>
+#include <mutex>
+#include <set>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "lrac_tc.cuh"
@@ -95,6 +99,18 @@ vl_status with_shape(int ld, F&& f) {
   if (nvec <= 32) return f(I32{}, I1{}, I8{});
   if (nvec <= 64) return f(I32{}, I2{}, I4{});
   return f(I32{}, I4{}, I2{});
+}
+
+// Sets a kernel's dynamic shared-memory limit once per device (the value is the
+// kernel's fixed maximum, so repeating it would only cost a driver call per launch).
+inline vl_status smem_limit_once(Ctx* c, const void* fn, size_t bytes) {
+  static std::mutex mu;
+  static std::set<std::pair<int, const void*>> done;
+  std::lock_guard<std::mutex> lk(mu);
+  if (done.count({c->device, fn})) return VL_OK;
+  VL_CUDA(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  done.insert({c->device, fn});
+  return VL_OK;
 }
 
 // Largest system the t = 1 solve keeps in shared memory (one block).
@@ -450,7 +466,24 @@ struct Engine {
   // memory each) the device can co-schedule for fn. Function attributes are
   // process-wide and other threads may launch fn concurrently with another size, so
   // the shared-memory bound is always set to the kernel's fixed maximum smem_max.
+  // The answer depends only on (device, kernel, smem) and is cached: a solve of a small
+  // problem is short enough for a driver query per call to show up in its latency.
   int cluster_size(const void* fn, size_t smem = 0, size_t smem_max = 0) {
+    static std::mutex mu;
+    static std::map<std::tuple<int, const void*, size_t>, int> cache;
+    const auto key = std::make_tuple(c->device, fn, smem);
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      auto it = cache.find(key);
+      if (it != cache.end()) return it->second;
+    }
+    const int cs = cluster_size_query(fn, smem, smem_max);
+    std::lock_guard<std::mutex> lk(mu);
+    cache[key] = cs;
+    return cs;
+  }
+
+  int cluster_size_query(const void* fn, size_t smem, size_t smem_max) {
     cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (smem_max > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
     cudaLaunchConfig_t cfg = {};
@@ -531,7 +564,7 @@ struct Engine {
       constexpr int LPV1 = FWD ? 8 : 16;
       auto fn = sptrsv_t1_smem_kernel<T, FWD, LPV1>;
       const size_t smem = (size_t)n * sizeof(T);
-      VL_CUDA(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemSolveBytes));
+      VL_TRY(smem_limit_once(c, (const void*)fn, kSmemSolveBytes));
       L.l_head = 0;
       L.l_tail = L.nlev;
       int nn = n;

@@ -1,6 +1,9 @@
 // Runtime pieces of libvl: workspace arena, error plumbing, occupancy queries.
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "vl_internal.h"
 
@@ -137,10 +140,25 @@ void prof_release(Ctx* c) {
   c->prof.pool.clear();
 }
 
+// Cached per (device, kernel, block, smem): grid solves ask once per launch.
 int resident_blocks(Ctx* c, const void* kernel, int block, size_t smem) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, const void*, int, size_t>, int> cache;
+  const auto key = std::make_tuple(c->device, kernel, block, smem);
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second * c->num_sms;
+  }
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem) != cudaSuccess) per_sm = 1;
-  return std::max(1, per_sm) * c->num_sms;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem) != cudaSuccess) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  per_sm = std::max(1, per_sm);
+  std::lock_guard<std::mutex> lk(mu);
+  cache[key] = per_sm;
+  return per_sm * c->num_sms;
 }
 
 }  // namespace vl

@@ -340,3 +340,25 @@ def test_lrac_woodbury_and_exact_limit():
     Lf, ldf, g = lrac.lml_lrac_dense(f, md, 70, 5, 3)
     assert np.allclose(g, 0.0, atol=1e-8)
     assert abs(Lf - la.lml_exact(f, md)[0]) < 1e-8
+
+
+def test_lrac_probes_have_covariance_P_and_slq_is_unbiased():
+    """z = L r1 + W^{-1/2} r2 has E z z^T = P (Sec. 3.1.2 with Rademacher r1, r2), and the
+    form-2 estimate log det C + mean gamma matches the exact log det(Sigma_tilde W + I)
+    within four standard errors."""
+    P = wl.tiny_problem(80, 10, rho=0.25)
+    f = la.build_factor(P.locs, P.order, P.cov, P.sigma2, P.rho, P.m, P.nugget)
+    md = la.find_mode(f, P.y, P.F, P.lik)
+    k = 12
+    L, _ = lrac.pivoted_cholesky(f.locs, P.cov, P.sigma2, P.rho, P.nugget, k)
+    N = 4000
+    Z = lrac.lrac_probes(f, L, md.W, N, 5)
+    Pm = L @ L.T + np.diag(1.0 / md.W)
+    # sampling error of the empirical covariance: E||C_N - P||_F^2 <= (tr(P)^2 + ||P||_F^2) / N
+    # (the Gaussian value; Rademacher fourth moments are smaller). A wrong probe covariance
+    # leaves an error that does not shrink with N.
+    bound = np.sqrt((np.trace(Pm) ** 2 + np.linalg.norm(Pm) ** 2) / N)
+    assert np.linalg.norm(Z @ Z.T / N - Pm) < 1.5 * bound
+    _, ld, g = lrac.lml_lrac_dense(f, md, k, 400, 7)
+    _, ld_ex = la.lml_exact(f, md)
+    assert abs(ld - ld_ex) < 4 * g.std(ddof=1) / np.sqrt(len(g)) + 1e-9

@@ -187,6 +187,22 @@ def tiny_problem(n: int, m: int, cov: int = COV_MATERN15, lik: int = LIK_BERNOUL
                    b_true=b, seed=seed)
 
 
+def serving_params(rng) -> tuple[int, float, int]:
+    """(n, range, likelihood) of one serving request, drawn first from its generator."""
+    n = int(round(math.exp(rng.uniform(math.log(1e3), math.log(2e5)))))
+    rho = float(rng.uniform(0.02, 0.2))
+    lik = LIK_BERNOULLI_LOGIT if rng.random() < 0.5 else LIK_POISSON_LOG
+    return n, rho, lik
+
+
+def batched_params(rng) -> tuple[int, int, float]:
+    """(n, m, range) of one problem of the batched workload, drawn first from its generator."""
+    n = int(round(math.exp(rng.uniform(math.log(5e3), math.log(5e4)))))
+    m = int(rng.choice([10, 20, 30]))
+    rho = float(rng.uniform(0.02, 0.2))
+    return n, m, rho
+
+
 def serving_problem(index: int, seed: int = 7, n: int | None = None) -> Problem:
     """Request ``index`` of the serving stream: a fresh latent-GP problem with n
     log-uniform in [1e3, 2e5], uniform locations, Matern-1.5 covariance (sigma^2 = 1)
@@ -195,9 +211,8 @@ def serving_problem(index: int, seed: int = 7, n: int | None = None) -> Problem:
     s = 100 simulation vectors). The latent field uses 64 random Fourier features so
     that a stream of thousands of requests can be drawn in seconds."""
     rng = np.random.default_rng([seed, index])
-    nn = n or int(round(math.exp(rng.uniform(math.log(1e3), math.log(2e5)))))
-    rho = float(rng.uniform(0.02, 0.2))
-    lik = LIK_BERNOULLI_LOGIT if rng.random() < 0.5 else LIK_POISSON_LOG
+    n0, rho, lik = serving_params(rng)
+    nn = n or n0
     locs = rng.random((nn, 2))
     b = latent_rff(locs, COV_MATERN15, 1.0, rho, rng, K=64)
     F = np.zeros(nn)
@@ -214,9 +229,8 @@ def batched_problem(index: int, seed: int = 5, n: int | None = None) -> Problem:
     uniform in {10, 20, 30}, uniform locations, exponential covariance (sigma^2 = 1)
     with range uniform in [0.02, 0.2], Bernoulli-logit responses, t = 50 probes."""
     rng = np.random.default_rng([seed, index])
-    nn = n or int(round(math.exp(rng.uniform(math.log(5e3), math.log(5e4)))))
-    m = int(rng.choice([10, 20, 30]))
-    rho = float(rng.uniform(0.02, 0.2))
+    n0, m, rho = batched_params(rng)
+    nn = n or n0
     locs = rng.random((nn, 2))
     b = latent_rff(locs, COV_EXPONENTIAL, 1.0, rho, rng, K=64)
     F = np.zeros(nn)
