@@ -215,6 +215,11 @@ class Server:
         for th in self.threads:
             th.start()
         self._ready.wait()          # every slot context exists before the clock starts
+        if self.errors:             # a slot without a context would leave its requests unserved
+            self.sched.close()
+            for th in self.threads:
+                th.join()
+            raise RuntimeError("slot context creation failed: " + "; ".join(self.errors))
         self.t0 = self.clock()
         return self
 

@@ -92,3 +92,16 @@ def test_slot_classes_take_requests_that_fit():
     for i, fp in enumerate(sizes):
         assert fp <= seen[i]                  # ran on a slot large enough for it
     assert srv.sched.peak_in_use <= 190
+
+
+def test_start_fails_loudly_when_a_slot_cannot_be_made():
+    import pytest
+
+    def make(slot):
+        if slot == 1:
+            raise RuntimeError("no device memory")
+        return None
+
+    srv = serving.Server(slots=3, budget_bytes=100, slot_capacity=100, make_ctx=make, runner=lambda c, r: {})
+    with pytest.raises(RuntimeError, match="slot 1"):
+        srv.start()
