@@ -656,8 +656,9 @@ __global__ void __launch_bounds__(1024) sptrsv_t1_cluster_kernel(LevelPlan L, in
 // shared memory (n * sizeof(T) bytes of dynamic shared memory): a level costs
 // shared-memory gathers and one block barrier, nothing goes through L2 between
 // levels, and the solve occupies a single SM so that independent problems run
-// side by side. Each team prefetches its next row (indices, weights, scaled
-// right-hand side) before the barrier; x is written out once at the end.
+// side by side. Each team keeps its rows (indices, weights, scaled right-hand side)
+// for the next few levels in registers, so their loads are issued levels before
+// they are used; x is written out once at the end.
 template <typename T, int LPV>
 __device__ __forceinline__ void row_run1_smem(RowPre1<T, LPV>& r, const int32_t* __restrict__ idx,
                                               const T* __restrict__ val, T* xs) {
@@ -681,27 +682,46 @@ __global__ void __launch_bounds__(1024) sptrsv_t1_smem_kernel(LevelPlan L, int n
   extern __shared__ unsigned char vl_smem[];
   T* xs = reinterpret_cast<T*>(vl_smem);
   constexpr int RPW = 32 / LPV;
+  // levels of look-ahead (a level is too short to hide one L2 round trip); two for float64
+  // rows, which need twice the registers of the 64-register budget of 1024-thread blocks
+  constexpr int D = sizeof(T) == 4 ? 3 : 2;
   const int tpb = (blockDim.x >> 5) * RPW;
   const int tib = (threadIdx.x >> 5) * RPW + (threadIdx.x & 31) / LPV;
   const bool tr = L.trace && threadIdx.x == 0;
-  RowPre1<T, LPV> r;
-  int p = L.lptr[0] + tib;
-  bool has = L.nlev > 0 && p < L.lptr[1];
-  if (has) row_pre1<T, FWD, LPV>(r, p, m, L, idx, val, rowptr, rhs, q);
-  for (int l = 0; l < L.nlev; ++l) {
-    if (tr) L.trace[l] = clock64();
-    while (has) {
-      row_run1_smem<T, LPV>(r, idx, val, xs);
-      p += tpb;
-      has = p < L.lptr[l + 1];
-      if (has) row_pre1<T, FWD, LPV>(r, p, m, L, idx, val, rowptr, rhs, q);
+  // r[d]: this team's first row of level l + d, loaded D levels before it is needed
+  RowPre1<T, LPV> r[D];
+  bool h[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    const int p = d < L.nlev ? L.lptr[d] + tib : 0;
+    h[d] = d < L.nlev && p < L.lptr[d + 1];
+    if (h[d]) row_pre1<T, FWD, LPV>(r[d], p, m, L, idx, val, rowptr, rhs, q);
+  }
+  // the level loop is unrolled by D so that every ring slot has a fixed index: a
+  // register move from slot to slot would wait for the slot's loads and undo the
+  // look-ahead
+  for (int l0 = 0; l0 < L.nlev; l0 += D) {
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      const int l = l0 + d;
+      if (l < L.nlev) {   // uniform across the block
+        if (tr) L.trace[l] = clock64();
+        if (h[d]) {
+          row_run1_smem<T, LPV>(r[d], idx, val, xs);
+          // levels wider than the block's teams: the further rows are loaded on the spot
+          for (int p = L.lptr[l] + tib + tpb; p < L.lptr[l + 1]; p += tpb) {
+            RowPre1<T, LPV> e;
+            row_pre1<T, FWD, LPV>(e, p, m, L, idx, val, rowptr, rhs, q);
+            row_run1_smem<T, LPV>(e, idx, val, xs);
+          }
+        }
+        const int ln = l + D;
+        const int p = ln < L.nlev ? L.lptr[ln] + tib : 0;
+        h[d] = ln < L.nlev && p < L.lptr[ln + 1];
+        if (h[d]) row_pre1<T, FWD, LPV>(r[d], p, m, L, idx, val, rowptr, rhs, q);
+        __syncthreads();
+      }
     }
-    if (l + 1 < L.nlev) {
-      p = L.lptr[l + 1] + tib;
-      has = p < L.lptr[l + 2];
-      if (has) row_pre1<T, FWD, LPV>(r, p, m, L, idx, val, rowptr, rhs, q);
-    }
-    __syncthreads();
   }
   if (tr) L.trace[L.nlev] = clock64();
   for (int s = threadIdx.x; s < n; s += blockDim.x) x[s] = xs[s];
