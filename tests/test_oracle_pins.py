@@ -362,3 +362,47 @@ def test_lrac_probes_have_covariance_P_and_slq_is_unbiased():
     _, ld, g = lrac.lml_lrac_dense(f, md, k, 400, 7)
     _, ld_ex = la.lml_exact(f, md)
     assert abs(ld - ld_ex) < 4 * g.std(ddof=1) / np.sqrt(len(g)) + 1e-9
+
+
+# --------------------------------------------------------------------------- likelihood pieces
+@pytest.mark.parametrize("lik", [la.LIK_BERNOULLI_LOGIT, la.LIK_POISSON_LOG])
+def test_likelihood_derivatives_and_normalisation(lik):
+    """grad and W are the first and negated second derivatives of log p (by central
+    differences), and p(. | mu) sums to one over y, which pins the constant terms
+    (-log y! for Poisson) that L^VLA includes."""
+    mu = np.linspace(-3.0, 2.5, 23)
+    y = (np.arange(23) % 2).astype(float) if lik == la.LIK_BERNOULLI_LOGIT else (np.arange(23) % 5).astype(float)
+    h = 1e-5
+    d1 = (la.log_lik(y, mu + h, lik) - la.log_lik(y, mu - h, lik)) / (2 * h)
+    assert np.allclose(la.grad_lik(y, mu, lik), d1, rtol=1e-7, atol=1e-8)
+    d2 = (la.grad_lik(y, mu + h, lik) - la.grad_lik(y, mu - h, lik)) / (2 * h)
+    assert np.allclose(la.W_lik(y, mu, lik), -d2, rtol=1e-6, atol=1e-8)
+    ys = np.arange(2.0) if lik == la.LIK_BERNOULLI_LOGIT else np.arange(400.0)
+    for m0 in (-2.0, 0.3, 2.5):
+        total = np.exp(la.log_lik(ys, np.full(len(ys), m0), lik)).sum()
+        assert abs(total - 1.0) < 1e-12
+
+
+@pytest.mark.parametrize("lik", [la.LIK_BERNOULLI_LOGIT, la.LIK_POISSON_LOG])
+def test_textbook_laplace_one_point_closed_form(lik):
+    """n = 1: the mode solves d/db [log p(y | F + b) - b^2 / (2 s2)] = 0 (a scalar root),
+    and the Laplace value is -log p(y | F + b*) + b*^2 / (2 s2) + log(1 + s2 W(b*)) / 2."""
+    from scipy.optimize import brentq
+    s2, F = 1.7, 0.4
+    for yv in ((0.0, 1.0) if lik == la.LIK_BERNOULLI_LOGIT else (0.0, 3.0, 11.0)):
+        y = np.array([yv])
+        g = lambda b: float(la.grad_lik(y, np.array([F + b]), lik)[0]) - b / s2
+        b = brentq(g, -30.0, 30.0, xtol=1e-15, rtol=1e-15)
+        W = float(la.W_lik(y, np.array([F + b]), lik)[0])
+        ref = -float(la.log_lik(y, np.array([F + b]), lik)[0]) + b * b / (2 * s2) + 0.5 * np.log1p(s2 * W)
+        f, nlml, _, _ = textbook.gp_laplace(np.array([[s2]]), y, np.array([F]), lik)
+        assert abs(f[0] - b) < 1e-10 and abs(nlml - ref) < 1e-12 * (1 + abs(ref))
+
+
+def test_refit_equals_a_fresh_factor():
+    P = wl.tiny_problem(120, 8)
+    f = la.build_factor(P.locs, P.order, P.cov, P.sigma2, P.rho, P.m, P.nugget)
+    g = la.refit(f, 2.5, 0.07, 3e-9)
+    h = la.build_factor(P.locs, P.order, P.cov, 2.5, 0.07, P.m, 3e-9)
+    assert np.array_equal(g.N, h.N) and np.allclose(g.A, h.A, rtol=0, atol=0) and np.allclose(g.D, h.D, rtol=0, atol=0)
+    assert (g.sigma2, g.rho, g.nugget) == (2.5, 0.07, 3e-9)
