@@ -30,6 +30,9 @@ laplace    likelihoods, Newton mode (Eq. newton), L^VLA (Eq. VLA_loss) with the
            simAlgo)
 lrac       pivoted Cholesky of Sigma and the LRAC preconditioner (Section
            3.1.2, Eqs. pcls2, logdetsplit2)
+gradients  derivatives of L^VLA in (sigma2, rho): factor derivatives, the exact
+           gradient with the implicit mode term, and the same-probe stochastic
+           trace estimate with the control variate (Section 3, appendix)
 textbook   the dense GP Laplace approximation in the covariance
            parametrisation (Rasmussen & Williams 2006, Algorithms 3.1 and 3.2),
            used only to pin the Vecchia-Laplace oracle at m = n - 1

@@ -34,7 +34,6 @@ var_p = D_p + (1/s) sum_k z4[p, k]^2.
 from __future__ import annotations
 
 import dataclasses
-import math
 
 import numpy as np
 import scipy.sparse as sp

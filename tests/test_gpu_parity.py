@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 
 import workloads as wl
-from oracle import geometry, krylov, laplace as la, rng as orng, vecchia
+from oracle import geometry, krylov, laplace as la
 
 pytestmark = pytest.mark.gpu
 
@@ -129,7 +129,6 @@ def test_operator_parity(ctx, vl, t):
     X = np.random.default_rng(t).standard_normal((P.n, t))
     Xv = X[f.order]
     B, D, W = f.B, f.D, md.W
-    import scipy.sparse.linalg as spla
     Bd = B.toarray()
     ref = {
         vl.OP_B: B @ Xv,
