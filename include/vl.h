@@ -278,6 +278,16 @@ vl_status vl_apply_A_noalloc(vl_state* s, const double* X, int t, double* Y);
 vl_status vl_pcg_solve(vl_state* s, const double* RHS, int t, const vl_opts* opts, double* U,
                        int lmax, double* T_diag, double* T_off, int* iters, double* relres);
 
+/* Gradient of L^VLA with respect to (sigma2, range) at the state's mode (appendix
+ * "Gradients of Vecchia-Laplace approximations"): grad[0] = dL/dsigma2, grad[1] = dL/drange
+ * (host doubles), with every log-determinant derivative by stochastic trace estimation
+ * (Eq. grad_STE) on the opts->t probes of vl_log_marglik (same seed, same z = P^{1/2} r) and
+ * the control variate r(z) = z^T P^{-1} dP P^{-1} z with weight c = Cov(h, r) / Var(r)
+ * (Section 3; c = 0 when r does not vary over the probes), and the implicit dependence through
+ * the mode by one more solve with W + Sigma_tilde^{-1}. The nugget is taken to scale with sigma2.
+ * This build: VL_FP64 with VL_PREC_VADU only (VL_ERR_INVALID_ARG otherwise). */
+vl_status vl_lml_grad(vl_state* s, const vl_opts* opts, double* grad, vl_stats* stats);
+
 /* The rank-k pivoted Cholesky factor L_k of Sigma used by the LRAC preconditioner
  * (Section 3.1.2; Harbrecht, Peters & Schneider 2012): residual diagonal d = diag Sigma
  * (nugget included), k steps of pivot p = argmax d (ties to the lowest Vecchia index),
