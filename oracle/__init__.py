@@ -33,6 +33,8 @@ lrac       pivoted Cholesky of Sigma and the LRAC preconditioner (Section
 gradients  derivatives of L^VLA in (sigma2, rho): factor derivatives, the exact
            gradient with the implicit mode term, and the same-probe stochastic
            trace estimate with the control variate (Section 3, appendix)
+lanczos_pred  predictive variances by preconditioned partial Lanczos with full
+           reorthogonalisation (Section 4, preconditioners P_L1 and P_L2)
 textbook   the dense GP Laplace approximation in the covariance
            parametrisation (Rasmussen & Williams 2006, Algorithms 3.1 and 3.2),
            used only to pin the Vecchia-Laplace oracle at m = n - 1

@@ -406,3 +406,19 @@ def test_refit_equals_a_fresh_factor():
     h = la.build_factor(P.locs, P.order, P.cov, 2.5, 0.07, P.m, 3e-9)
     assert np.array_equal(g.N, h.N) and np.allclose(g.A, h.A, rtol=0, atol=0) and np.allclose(g.D, h.D, rtol=0, atol=0)
     assert (g.sigma2, g.rho, g.nugget) == (2.5, 0.07, 3e-9)
+
+
+@pytest.mark.parametrize("precond", [1, 2])
+def test_lanczos_variances_are_exact_at_full_rank_and_converge(precond):
+    """At k = n the preconditioned Lanczos factorisation is exact, so the variances equal
+    the direct ones; with growing k the error falls."""
+    from oracle import lanczos_pred as lp
+    P = wl.tiny_problem(90, 10, rho=0.2, n_test=12)
+    f = la.build_factor(P.locs, P.order, P.cov, P.sigma2, P.rho, P.m, P.nugget)
+    md = la.find_mode(f, P.y, P.F, P.lik)
+    pf = la.pred_factor(f, P.test_locs, P.m)
+    exact = la.pred_var_exact(f, md, pf)
+    full = lp.pred_var_lanczos(f, md, pf, 90, precond)
+    assert np.allclose(full, exact, rtol=1e-8, atol=1e-10)
+    errs = [np.max(np.abs(lp.pred_var_lanczos(f, md, pf, k, precond) - exact)) for k in (5, 20, 60)]
+    assert errs[2] <= errs[1] <= errs[0] + 1e-12
