@@ -285,8 +285,10 @@ vl_status vl_pcg_solve(vl_state* s, const double* RHS, int t, const vl_opts* opt
  * the control variate r(z) = z^T P^{-1} dP P^{-1} z with weight c = Cov(h, r) / Var(r)
  * (Section 3; c = 0 when r does not vary over the probes), and the implicit dependence through
  * the mode by one more solve with W + Sigma_tilde^{-1}. The nugget is taken to scale with sigma2.
- * This build: VL_FP64 with VL_PREC_VADU only (VL_ERR_INVALID_ARG otherwise). */
-vl_status vl_lml_grad(vl_state* s, const vl_opts* opts, double* grad, vl_stats* stats);
+ * dF (n doubles, caller order, host or device; may be NULL) receives dL/dF =
+ * -grad log p(y | mu*) + g - W (W + Sigma_tilde^{-1})^{-1} g with g = 1/2 dlogdet/dmu* by the
+ * same estimator. This build: VL_FP64 with VL_PREC_VADU only (VL_ERR_INVALID_ARG otherwise). */
+vl_status vl_lml_grad(vl_state* s, const vl_opts* opts, double* grad, double* dF, vl_stats* stats);
 
 /* The rank-k pivoted Cholesky factor L_k of Sigma used by the LRAC preconditioner
  * (Section 3.1.2; Harbrecht, Peters & Schneider 2012): residual diagonal d = diag Sigma

@@ -17,6 +17,8 @@ Vecchia factor (row i, N = N(i), A_i = Sigma_{i,N} Sigma_N^{-1}):
     dD_i = dSigma_ii - dA_i Sigma_{N,i} - A_i dSigma_{N,i}
     dB_{i,N} = -dA_i
     d Sigma_tilde^{-1} = dB^T D^{-1} B + B^T D^{-1} dB - B^T D^{-1} dD D^{-1} B
+Gradient in the offset F (same appendix; db*/dF_i = -A^{-1} W e_i):
+    dL/dF = -grad log p(y | mu*) + g - W o (A^{-1} g).
 Exact gradient (A = W + Sigma_tilde^{-1}, b* the mode, W'_i = dW_ii / d mu_i):
     dL/dtheta = 1/2 b*^T dSinv b* + 1/2 [sum_i dD_i / D_i + tr(A^{-1} dSinv)]
                 - (A^{-1} g)^T dSinv b*,    g_i = dL / db*_i = 1/2 (A^{-1})_ii W'_i,
@@ -128,6 +130,16 @@ def lml_grad_exact(f: laplace.Factor, md: laplace.Mode) -> dict:
     return out
 
 
+def lml_grad_F_exact(f: laplace.Factor, md: laplace.Mode) -> np.ndarray:
+    """dL^VLA / dF in caller order (dense A^{-1}, small n only)."""
+    Ainv = np.linalg.inv(np.diag(md.W) + f.Sinv.toarray())
+    g = 0.5 * np.diag(Ainv) * W_prime(md.y, md.mu, md.lik)
+    dF = -laplace.grad_lik(md.y, md.mu, md.lik) + g - md.W * (Ainv @ g)
+    out = np.empty(f.n)
+    out[f.order] = dF
+    return out
+
+
 def _solvers(f: laplace.Factor, W):
     lo, up = laplace._tri_solvers(f.B)          # B^{-1} and B^{-T}
     A_lu = laplace._lu(sp.diags(W) + f.Sinv)
@@ -160,7 +172,9 @@ def lml_grad_ste(f: laplace.Factor, md: laplace.Mode, t: int, seed: int, control
     dld_dmu = cj * Wp / (W + 1.0 / f.D) + (hj - cj[:, None] * rj).mean(1)
     g = 0.5 * dld_dmu
     Ag = A_lu.solve(g)
-    out, samples = {}, {}
+    dF = np.empty(f.n)
+    dF[f.order] = -laplace.grad_lik(md.y, md.mu, md.lik) + g - W * Ag
+    out, samples = {"F": dF}, {}
     for par in PARAMS:
         dA, dD = factor_derivatives(f, par)
         dB = dB_matrix(f, dA)

@@ -119,7 +119,7 @@ def library():
         "vl_pcg_solve": (st, [vp, vp, i32, vp, vp, i32, vp, vp, vp, vp]),
         "vl_apply_A_noalloc": (st, [vp, vp, i32, vp]),
         "vl_lrac_export": (st, [vp, i32, vp, vp]),
-        "vl_lml_grad": (st, [vp, vp, vp, vp]),
+        "vl_lml_grad": (st, [vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -346,13 +346,17 @@ class State:
         self.ctx.check(self.ctx.lib.vl_log_marglik(self.h, C.byref(opts), C.byref(lml), C.byref(ld), C.byref(st)))
         return (lml.value, st.as_dict()) if with_stats else lml.value
 
-    def lml_grad(self, opts: Opts | None = None, with_stats: bool = False):
-        """(dL/dsigma2, dL/drange) by stochastic trace estimation on the SLQ probes."""
+    def lml_grad(self, opts: Opts | None = None, with_stats: bool = False, offset: bool = False):
+        """(dL/dsigma2, dL/drange) by stochastic trace estimation on the SLQ probes; with
+        offset=True also dL/dF (caller order) as a second result."""
         opts = opts or Opts.make()
         g = np.zeros(2)
+        dF = np.zeros(self.fac.n) if offset else None
         st = Stats()
-        self.ctx.check(self.ctx.lib.vl_lml_grad(self.h, C.byref(opts), g.ctypes.data, C.byref(st)))
-        return (g, st.as_dict()) if with_stats else g
+        self.ctx.check(self.ctx.lib.vl_lml_grad(self.h, C.byref(opts), g.ctypes.data, _ptr(dF, np.float64),
+                                                C.byref(st)))
+        out = (g, dF) if offset else g
+        return (out, st.as_dict()) if with_stats else out
 
     def slq_gammas(self, t: int):
         g = np.empty(t)

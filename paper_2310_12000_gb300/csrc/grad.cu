@@ -7,6 +7,7 @@
 //   h(z) = (A^{-1} z)^T dSinv P^{-1} z,  r(z) = (P^{-1} z)^T (dSinv + dB^T W B + B^T W dB) P^{-1} z
 //   g_j = 1/2 [c_j W'_j / (W_j + 1/D_j) + mean_k (h_j - c_j r_j)],
 //   h_j = (A^{-1} z)_j W'_j (P^{-1} z)_j,  r_j = (B P^{-1} z)_j^2 W'_j
+//   dL/dF = -grad log p(y | mu*) + g - W o (A^{-1} g)        (db*/dF_i = -A^{-1} W e_i)
 // with A = W + Sigma_tilde^{-1}, W' = dW/dmu, c = Cov(h, r) / Var(r) (0 when r does not
 // vary over the probes: then any c gives the same estimate, and the ratio would only
 // amplify rounding). The factor derivatives (appendix "Derivatives of the
@@ -267,6 +268,18 @@ __global__ void dlog_sums_kernel(int n, const double* __restrict__ D, const doub
   }
 }
 
+// dF[s2u[s]] = -d log p / d mu_s + g_s - W_s (A^{-1} g)_s     (caller order)
+__global__ void offset_grad_kernel(int n, int lik, const int32_t* __restrict__ s2u, const double* __restrict__ y,
+                                   const double* __restrict__ F, const double* __restrict__ b,
+                                   const double* __restrict__ W, const double* __restrict__ g,
+                                   const double* __restrict__ Ag, double* __restrict__ dF) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+    const double mu = (F ? F[s] : 0.0) + b[s];
+    const double gl = lik == VL_LIK_BERNOULLI_LOGIT ? y[s] - 1.0 / (1.0 + exp(-mu)) : y[s] - exp(mu);
+    dF[s2u[s]] = -gl + g[s] - W[s] * Ag[s];
+  }
+}
+
 __global__ void probe_scale_kernel(int n, const double* __restrict__ W, const double* __restrict__ D,
                                    double* __restrict__ sc) {
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x)
@@ -296,7 +309,7 @@ vl_status apply_dsinv(Engine<double>& E, Factor* f, const double* dA, const doub
 }  // namespace
 }  // namespace vl
 
-extern "C" vl_status vl_lml_grad(vl_state* st, const vl_opts* o, double* grad, vl_stats* stats) {
+extern "C" vl_status vl_lml_grad(vl_state* st, const vl_opts* o, double* grad, double* dF, vl_stats* stats) {
   using namespace vl;
   if (!st) return VL_ERR_INVALID_ARG;
   State* S = static_cast<State*>(st);
@@ -401,6 +414,15 @@ extern "C" vl_status vl_lml_grad(vl_state* st, const vl_opts* o, double* grad, v
     }
     const double dlogdet = sm[0] + cw * sm[1] + (mh - cw * mr);
     grad[par] = 0.5 * s2[0] + 0.5 * dlogdet - s2[1];
+  }
+  if (dF) {
+    double* dFd = M.get<double>(n);
+    if (!dFd) return fail(c, VL_ERR_OOM, "workspace exhausted (vl_lml_grad)");
+    offset_grad_kernel<<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, S->lik, f->s2u, S->y, S->F, S->b, S->W, g, Ag,
+                                                               dFd);
+    VL_CUDA(c, cudaGetLastError());
+    VL_CUDA(c, cudaMemcpyAsync(dF, dFd, sizeof(double) * n, cudaMemcpyDefault, c->stream));
+    VL_CUDA(c, cudaStreamSynchronize(c->stream));
   }
   if (stats) {
     *stats = vl_stats{};

@@ -20,12 +20,13 @@ def test_lml_grad_matches_oracle_same_probes(name, n, t):
     opts = vl.Opts.make(t=t, **FP64_TIGHT)
     fac = ctx.build_factor(P.locs, P.order, P.cov, P.sigma2, P.rho, P.m, opts)
     st = fac.find_mode(P.lik, P.y, P.F, opts)
-    g = st.lml_grad(opts)
+    g, dF = st.lml_grad(opts, offset=True)
     f = la.build_factor(P.locs, P.order, P.cov, P.sigma2, P.rho, P.m, P.nugget)
     md = la.find_mode(f, P.y, P.F, P.lik, newton_tol=1e-12)
     ref = gr.lml_grad_ste(f, md, t, 1)["grad"]
     for k, par in enumerate(gr.PARAMS):
         assert abs(g[k] - ref[par]) < 1e-7 * (1.0 + abs(ref[par])), (par, g[k], ref[par])
+    assert np.max(np.abs(dF - ref["F"])) < 1e-7 * (1.0 + np.max(np.abs(ref["F"])))
     ctx.close()
 
 

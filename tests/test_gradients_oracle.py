@@ -81,3 +81,25 @@ def test_ste_log_det_derivative_is_unbiased_and_the_control_variate_reduces_vari
         assert abs(out["grad"][par] - grad_ex[par]) < 4 * np.std(pp, ddof=1) / np.sqrt(t) + 1e-12
     # sigma2's control variate is constant under Rademacher probes: its weight must be 0
     assert out["samples"]["sigma2"]["c"] == 0.0
+
+
+def test_offset_gradient_matches_central_differences():
+    """dL^VLA/dF_i (implicit mode term included) for a few coordinates."""
+    P = wl.tiny_problem(110, 9, lik=la.LIK_POISSON_LOG, rho=0.2, F0=0.3)
+    f = _factor(P, P.sigma2, P.rho)
+
+    def L(F):
+        md_ = la.find_mode(f, P.y, F, P.lik, newton_tol=1e-14)
+        return la.lml_exact(f, md_)[0]
+
+    md = la.find_mode(f, P.y, P.F, P.lik, newton_tol=1e-14)
+    dF = gr.lml_grad_F_exact(f, md)
+    h = 1e-5
+    for i in (0, 17, 56, 109):
+        e = np.zeros(P.n)
+        e[i] = h
+        fd = (L(P.F + e) - L(P.F - e)) / (2 * h)
+        assert abs(dF[i] - fd) < 1e-6 * (1 + abs(fd)), (i, dF[i], fd)
+    # the STE form with many probes tracks the exact one
+    ste = gr.lml_grad_ste(f, md, 2000, 5)["grad"]["F"]
+    assert np.max(np.abs(ste - dF)) < 0.05 * np.max(np.abs(dF))
