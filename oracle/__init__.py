@@ -23,14 +23,16 @@ vecchia    covariance functions (Section 4.1) and the Vecchia factor B, D
 krylov     preconditioned CG with the Lanczos tridiagonal (Appendix, "PCG
            algorithm"), explicit Lanczos with full reorthogonalisation,
            e1^T log(T) e1
-laplace    likelihoods, Newton mode (Eq. newton), L^VLA (Eq. VLA_loss) with the
+laplace    likelihoods (Bernoulli-logit, Poisson-log; gamma-log with shape xi,
+           Section 5), Newton mode (Eq. newton), L^VLA (Eq. VLA_loss) with the
            exact sparse-LU log-determinant, same-probe SLQ (Eqs. logdetsplit,
            def_SLQ) for the VADU and LVA preconditioners (Section 3.1.1),
            predictive means/variances (Eq. latentpostpredictive, Algorithm
            simAlgo)
 lrac       pivoted Cholesky of Sigma and the LRAC preconditioner (Section
            3.1.2, Eqs. pcls2, logdetsplit2)
-gradients  derivatives of L^VLA in (sigma2, rho): factor derivatives, the exact
+gradients  derivatives of L^VLA in (sigma2, rho), the offset F, the coefficients
+           beta of F = X beta and the gamma shape xi: factor derivatives, the exact
            gradient with the implicit mode term, and the same-probe stochastic
            trace estimate with the control variate (Section 3, appendix)
 lanczos_pred  predictive variances by preconditioned partial Lanczos with full

@@ -31,7 +31,13 @@ STE (probes z with E z z^T = P, P = B^T (W + D^{-1}) B):
     r(z) = (P^{-1} z)^T (dSinv + dB^T W B + B^T W dB) P^{-1} z    (= z^T P^{-1} dP P^{-1} z)
     d logdet/d mu_j ~ c_j (W + D^{-1})^{-1}_jj W'_j + mean_i [h_j(z_i) - c_j r_j(z_i)],
     h_j(z) = (A^{-1} z)_j W'_j (P^{-1} z)_j,  r_j(z) = (B P^{-1} z)_j^2 W'_j,
-with c = Cov(h, r) / Var(r) over the probes (c = 0: plain STE). When the control
+with c = Cov(h, r) / Var(r) over the probes (c = 0: plain STE).
+Auxiliary likelihood parameter xi (gamma shape alpha; same appendix), with
+dW/dxi = -d^3 log p / dxi dmu^2 and db*/dxi = A^{-1} d^2 log p / dxi dmu:
+    dL/dxi = -sum_i d log p_i / dxi + 1/2 tr(A^{-1} dW/dxi) + (A^{-1} g)^T d^2 log p / dxi dmu,
+    STE: d logdet / dxi ~ c tr((W + D^{-1})^{-1} dW/dxi) + mean_i [h(z_i) - c r(z_i)],
+         h(z) = (A^{-1} z)^T dW/dxi P^{-1} z,   r(z) = (B P^{-1} z)^T dW/dxi (B P^{-1} z).
+Linear fixed effects F = X beta (Section 2): dL/dbeta = X^T dL/dF. When the control
 variate is constant over the probes its variance is rounding noise and c is set to 0:
 with Rademacher probes and VADU this happens for sigma2 (B does not depend on sigma2
 and r(z) = -sum_i (W_i + 1/D_i)^{-1} / (sigma2 D_i) for every z), where Cov / Var would
@@ -43,18 +49,43 @@ import math
 
 import numpy as np
 import scipy.sparse as sp
+from scipy.special import digamma
 
 from . import laplace, vecchia
 
 PARAMS = ("sigma2", "rho")
 
 
-def W_prime(y, mu, lik):
+def W_prime(y, mu, lik, xi: float = 1.0):
     """dW/dmu = -d^3 log p / d mu^3 (W = -d^2 log p / d mu^2)."""
     if lik == laplace.LIK_BERNOULLI_LOGIT:
         p = 1.0 / (1.0 + np.exp(-mu))
         return p * (1.0 - p) * (1.0 - 2.0 * p)
+    if lik == laplace.LIK_GAMMA_LOG:
+        return -float(xi) * y * np.exp(-mu)
     return np.exp(mu)
+
+
+# gamma, u = y e^{-mu}:  d log p / d alpha = log alpha + 1 - digamma(alpha) + log y - mu - u,
+# d^2 log p / d alpha d mu = u - 1,   dW / d alpha = u.
+def dloglik_dxi(y, mu, lik, xi):
+    _gamma_only(lik)
+    return np.log(xi) + 1.0 - digamma(xi) + np.log(y) - mu - y * np.exp(-mu)
+
+
+def d2loglik_dxi_dmu(y, mu, lik, xi):
+    _gamma_only(lik)
+    return y * np.exp(-mu) - 1.0
+
+
+def dW_dxi(y, mu, lik, xi):
+    _gamma_only(lik)
+    return y * np.exp(-mu)
+
+
+def _gamma_only(lik):
+    if lik != laplace.LIK_GAMMA_LOG:
+        raise ValueError("only the gamma likelihood has an auxiliary parameter")
 
 
 def dcov(h, cov, sigma2, rho, param, nugget_ratio, same_point):
@@ -118,7 +149,7 @@ def lml_grad_exact(f: laplace.Factor, md: laplace.Mode) -> dict:
     """dL^VLA / d theta by the formulas above with dense A^{-1} (small n only)."""
     A = np.diag(md.W) + f.Sinv.toarray()
     Ainv = np.linalg.inv(A)
-    g = 0.5 * np.diag(Ainv) * W_prime(md.y, md.mu, md.lik)
+    g = 0.5 * np.diag(Ainv) * W_prime(md.y, md.mu, md.lik, md.xi)
     Ag = Ainv @ g
     out = {}
     for par in PARAMS:
@@ -133,11 +164,26 @@ def lml_grad_exact(f: laplace.Factor, md: laplace.Mode) -> dict:
 def lml_grad_F_exact(f: laplace.Factor, md: laplace.Mode) -> np.ndarray:
     """dL^VLA / dF in caller order (dense A^{-1}, small n only)."""
     Ainv = np.linalg.inv(np.diag(md.W) + f.Sinv.toarray())
-    g = 0.5 * np.diag(Ainv) * W_prime(md.y, md.mu, md.lik)
-    dF = -laplace.grad_lik(md.y, md.mu, md.lik) + g - md.W * (Ainv @ g)
+    g = 0.5 * np.diag(Ainv) * W_prime(md.y, md.mu, md.lik, md.xi)
+    dF = -laplace.grad_lik(md.y, md.mu, md.lik, md.xi) + g - md.W * (Ainv @ g)
     out = np.empty(f.n)
     out[f.order] = dF
     return out
+
+
+def lml_grad_xi_exact(f: laplace.Factor, md: laplace.Mode) -> float:
+    """dL^VLA / dxi (gamma shape) with dense A^{-1} (small n only)."""
+    Ainv = np.linalg.inv(np.diag(md.W) + f.Sinv.toarray())
+    g = 0.5 * np.diag(Ainv) * W_prime(md.y, md.mu, md.lik, md.xi)
+    explicit = -float(np.sum(dloglik_dxi(md.y, md.mu, md.lik, md.xi)))
+    logdet = float(np.sum(np.diag(Ainv) * dW_dxi(md.y, md.mu, md.lik, md.xi)))
+    implicit = float((Ainv @ g) @ d2loglik_dxi_dmu(md.y, md.mu, md.lik, md.xi))
+    return explicit + 0.5 * logdet + implicit
+
+
+def lml_grad_beta(X, dF) -> np.ndarray:
+    """dL^VLA / dbeta = X^T dL/dF for F = X beta (X n x p and dF in caller order)."""
+    return np.asarray(X, float).T @ np.asarray(dF, float)
 
 
 def _solvers(f: laplace.Factor, W):
@@ -152,7 +198,7 @@ def lml_grad_ste(f: laplace.Factor, md: laplace.Mode, t: int, seed: int, control
     """dL^VLA / d theta with every log-determinant derivative by STE on the same t
     Rademacher probes z = P^{1/2} r (VADU); the implicit term solves A once for
     A^{-1} g. Returns the gradient and, per parameter, the samples h and r."""
-    W, Wp = md.W, W_prime(md.y, md.mu, md.lik)
+    W, Wp = md.W, W_prime(md.y, md.mu, md.lik, md.xi)
     R = laplace.probes(f, t, seed)
     Z = f.B.T @ (np.sqrt(W + 1.0 / f.D)[:, None] * R)          # z = P^{1/2} r
     A_lu, P_inv = _solvers(f, W)
@@ -173,8 +219,22 @@ def lml_grad_ste(f: laplace.Factor, md: laplace.Mode, t: int, seed: int, control
     g = 0.5 * dld_dmu
     Ag = A_lu.solve(g)
     dF = np.empty(f.n)
-    dF[f.order] = -laplace.grad_lik(md.y, md.mu, md.lik) + g - W * Ag
+    dF[f.order] = -laplace.grad_lik(md.y, md.mu, md.lik, md.xi) + g - W * Ag
     out, samples = {"F": dF}, {}
+    if md.lik == laplace.LIK_GAMMA_LOG:
+        dW = dW_dxi(md.y, md.mu, md.lik, md.xi)
+        h = np.einsum("ij,ij->j", AZ, dW[:, None] * PZ)
+        r = np.einsum("ij,ij->j", BPZ, dW[:, None] * BPZ)
+        c = 0.0
+        if control_variate and t > 1 and r.var(ddof=1) > 1e-20 * r.mean() ** 2:
+            c = float(np.cov(h, r, ddof=1)[0, 1] / r.var(ddof=1))
+        dlogdet = c * float(np.sum(dW / (W + 1.0 / f.D))) + float(np.mean(h - c * r))
+        d2 = d2loglik_dxi_dmu(md.y, md.mu, md.lik, md.xi)
+        out["xi"] = (-float(np.sum(dloglik_dxi(md.y, md.mu, md.lik, md.xi))) + 0.5 * dlogdet
+                     + float(Ag @ d2))
+        w = A_lu.solve(d2)
+        per_probe = 0.5 * (h - c * r) + 0.5 * (w[:, None] * (hj - cj[:, None] * rj)).sum(0)
+        samples["xi"] = {"h": h, "r": r, "c": c, "dlogdet": dlogdet, "per_probe": per_probe}
     for par in PARAMS:
         dA, dD = factor_derivatives(f, par)
         dB = dB_matrix(f, dA)

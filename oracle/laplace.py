@@ -44,28 +44,41 @@ from . import geometry, krylov, rng as orng, vecchia
 
 LIK_BERNOULLI_LOGIT = 0
 LIK_POISSON_LOG = 1
+LIK_GAMMA_LOG = 2
 PREC_VADU = 0
 PREC_LVA = 1
 
 
 # ----------------------------------------------------------------------------- likelihoods
-def log_lik(y: np.ndarray, mu: np.ndarray, lik: int) -> np.ndarray:
+# Gamma (Section 5, the MODIS application): y | mu ~ Gamma(shape alpha, rate alpha e^{-mu}),
+# so E[y | mu] = e^mu; alpha is the auxiliary parameter xi of Section 2. With u = y e^{-mu}:
+#   log p = alpha log alpha - log Gamma(alpha) + (alpha - 1) log y - alpha mu - alpha u,
+#   d log p / d mu = alpha (u - 1),   W = alpha u  (> 0 for y > 0: log-concave in mu).
+# Bernoulli and Poisson have no auxiliary parameter and ignore xi.
+def log_lik(y: np.ndarray, mu: np.ndarray, lik: int, xi: float = 1.0) -> np.ndarray:
     if lik == LIK_BERNOULLI_LOGIT:
         # y mu - log(1 + e^mu)
         return y * mu - np.logaddexp(0.0, mu)
+    if lik == LIK_GAMMA_LOG:
+        a = float(xi)
+        return a * np.log(a) - gammaln(a) + (a - 1.0) * np.log(y) - a * mu - a * y * np.exp(-mu)
     return y * mu - np.exp(mu) - gammaln(y + 1.0)
 
 
-def grad_lik(y, mu, lik):
+def grad_lik(y, mu, lik, xi: float = 1.0):
     if lik == LIK_BERNOULLI_LOGIT:
         return y - 1.0 / (1.0 + np.exp(-mu))
+    if lik == LIK_GAMMA_LOG:
+        return float(xi) * (y * np.exp(-mu) - 1.0)
     return y - np.exp(mu)
 
 
-def W_lik(y, mu, lik):
+def W_lik(y, mu, lik, xi: float = 1.0):
     if lik == LIK_BERNOULLI_LOGIT:
         p = 1.0 / (1.0 + np.exp(-mu))
         return p * (1.0 - p)
+    if lik == LIK_GAMMA_LOG:
+        return float(xi) * y * np.exp(-mu)
     return np.exp(mu)
 
 
@@ -164,35 +177,36 @@ class Mode:
     lik: int
     iters: int
     psi: float
+    xi: float = 1.0        # auxiliary likelihood parameter (gamma shape)
 
 
-def psi(f: Factor, y, F, b, lik) -> float:
-    return float(np.sum(log_lik(y, F + b, lik)) - 0.5 * b @ (f.Sinv @ b))
+def psi(f: Factor, y, F, b, lik, xi: float = 1.0) -> float:
+    return float(np.sum(log_lik(y, F + b, lik, xi)) - 0.5 * b @ (f.Sinv @ b))
 
 
-def find_mode(f: Factor, y_user, F_user, lik, newton_tol=1e-9, max_iter=100) -> Mode:
+def find_mode(f: Factor, y_user, F_user, lik, newton_tol=1e-9, max_iter=100, xi: float = 1.0) -> Mode:
     y = np.asarray(y_user, float)[f.order]
     F = np.zeros(f.n) if F_user is None else np.asarray(F_user, float)[f.order]
     b = np.zeros(f.n)
-    ps = psi(f, y, F, b, lik)
+    ps = psi(f, y, F, b, lik, xi)
     it = 0
     for it in range(1, max_iter + 1):
         mu = F + b
-        W = W_lik(y, mu, lik)
-        rhs = W * b + grad_lik(y, mu, lik)
+        W = W_lik(y, mu, lik, xi)
+        rhs = W * b + grad_lik(y, mu, lik, xi)
         b_new = _lu(sp.diags(W) + f.Sinv).solve(rhs)
-        ps_new = psi(f, y, F, b_new, lik)
+        ps_new = psi(f, y, F, b_new, lik, xi)
         halvings = 0
         while ps_new < ps - 1e-12 * (1.0 + abs(ps)) and halvings < 30:
             b_new = b + 0.5 * (b_new - b)
-            ps_new = psi(f, y, F, b_new, lik)
+            ps_new = psi(f, y, F, b_new, lik, xi)
             halvings += 1
         step = np.max(np.abs(b_new - b)) if f.n else 0.0
         b, ps = b_new, ps_new
         if step <= newton_tol * (1.0 + (np.max(np.abs(b)) if f.n else 0.0)):
             break
     mu = F + b
-    return Mode(b=b, W=W_lik(y, mu, lik), mu=mu, y=y, F=F, lik=lik, iters=it, psi=ps)
+    return Mode(b=b, W=W_lik(y, mu, lik, xi), mu=mu, y=y, F=F, lik=lik, iters=it, psi=ps, xi=float(xi))
 
 
 def mode_user(f: Factor, md: Mode) -> np.ndarray:
@@ -203,7 +217,7 @@ def mode_user(f: Factor, md: Mode) -> np.ndarray:
 
 # ----------------------------------------------------------------------------- L^VLA
 def lml_parts(f: Factor, md: Mode) -> dict:
-    nll = -float(np.sum(log_lik(md.y, md.mu, md.lik)))
+    nll = -float(np.sum(log_lik(md.y, md.mu, md.lik, md.xi)))
     quad = 0.5 * float(md.b @ (f.Sinv @ md.b))
     return {"neg_loglik": nll, "quad": quad, "sum_log_D": float(np.sum(np.log(f.D)))}
 

@@ -21,15 +21,15 @@ import scipy.linalg as sla
 from . import laplace
 
 
-def gp_laplace(K: np.ndarray, y: np.ndarray, F: np.ndarray, lik: int, tol=1e-13, max_iter=200):
+def gp_laplace(K: np.ndarray, y: np.ndarray, F: np.ndarray, lik: int, tol=1e-13, max_iter=200, xi: float = 1.0):
     n = len(y)
     f = np.zeros(n)
     for _ in range(max_iter):
         mu = F + f
-        W = laplace.W_lik(y, mu, lik)
+        W = laplace.W_lik(y, mu, lik, xi)
         sW = np.sqrt(W)
         L = np.linalg.cholesky(np.eye(n) + sW[:, None] * K * sW[None, :])
-        bb = W * f + laplace.grad_lik(y, mu, lik)
+        bb = W * f + laplace.grad_lik(y, mu, lik, xi)
         rhs = sW * (K @ bb)
         a = bb - sW * sla.solve_triangular(L.T, sla.solve_triangular(L, rhs, lower=True), lower=False)
         f_new = K @ a
@@ -38,17 +38,17 @@ def gp_laplace(K: np.ndarray, y: np.ndarray, F: np.ndarray, lik: int, tol=1e-13,
         if done:
             break
     mu = F + f
-    W = laplace.W_lik(y, mu, lik)
+    W = laplace.W_lik(y, mu, lik, xi)
     sW = np.sqrt(W)
     L = np.linalg.cholesky(np.eye(n) + sW[:, None] * K * sW[None, :])
     a = np.linalg.solve(K, f)
-    nlml = 0.5 * a @ f - np.sum(laplace.log_lik(y, mu, lik)) + np.sum(np.log(np.diag(L)))
+    nlml = 0.5 * a @ f - np.sum(laplace.log_lik(y, mu, lik, xi)) + np.sum(np.log(np.diag(L)))
     return f, float(nlml), L, W
 
 
-def gp_predict(K: np.ndarray, Ks: np.ndarray, kss: np.ndarray, y, F, Fp, f, L, W, lik):
+def gp_predict(K: np.ndarray, Ks: np.ndarray, kss: np.ndarray, y, F, Fp, f, L, W, lik, xi: float = 1.0):
     """Ks: (n, n_p) cross covariances, kss: (n_p,) prior variances at test points."""
-    g = laplace.grad_lik(y, F + f, lik)
+    g = laplace.grad_lik(y, F + f, lik, xi)
     mean = np.asarray(Fp, float) + Ks.T @ g
     v = sla.solve_triangular(L, np.sqrt(W)[:, None] * Ks, lower=True)
     return mean, kss - np.sum(v * v, axis=0)

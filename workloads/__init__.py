@@ -33,6 +33,7 @@ COV_EXPONENTIAL = 0
 COV_MATERN15 = 1
 LIK_BERNOULLI_LOGIT = 0
 LIK_POISSON_LOG = 1
+LIK_GAMMA_LOG = 2
 
 
 @dataclasses.dataclass
@@ -48,13 +49,16 @@ class Problem:
     sigma2: float
     rho: float
     m: int
-    lik: int                  # LIK_BERNOULLI_LOGIT | LIK_POISSON_LOG
+    lik: int                  # LIK_BERNOULLI_LOGIT | LIK_POISSON_LOG | LIK_GAMMA_LOG
     t: int = 50               # SLQ probes
     s: int = 100              # simulation vectors for predictive variances
     test_locs: np.ndarray | None = None   # (n_p, 2)
     Fp: np.ndarray | None = None          # (n_p,)
     b_true: np.ndarray | None = None      # latent draw (user order), for reference only
     seed: int = 1
+    xi: float = 1.0                       # gamma shape (auxiliary likelihood parameter)
+    X: np.ndarray | None = None           # (n, p) predictors of F = X beta, user order
+    beta: np.ndarray | None = None        # (p,) coefficients that made F
 
     @property
     def n(self) -> int:
@@ -95,11 +99,20 @@ def latent_rff(locs: np.ndarray, cov: int, sigma2: float, rho: float, rng, K: in
     return math.sqrt(sigma2) * math.sqrt(2.0 / K) * b
 
 
-def responses(mu: np.ndarray, lik: int, rng) -> np.ndarray:
+def responses(mu: np.ndarray, lik: int, rng, xi: float = 1.0) -> np.ndarray:
     if lik == LIK_BERNOULLI_LOGIT:
         p = 1.0 / (1.0 + np.exp(-mu))
         return (rng.random(len(mu)) < p).astype(np.float64)
+    if lik == LIK_GAMMA_LOG:
+        # shape xi, rate xi e^{-mu} (numpy takes the scale = 1 / rate): mean e^mu
+        return rng.gamma(xi, np.exp(mu) / xi).astype(np.float64)
     return rng.poisson(np.exp(mu)).astype(np.float64)
+
+
+def intercept_and_coords(locs: np.ndarray) -> np.ndarray:
+    """Predictors of the linear term F = X beta used in Section 5: an intercept and the
+    two coordinates, centred."""
+    return np.column_stack([np.ones(len(locs)), locs - locs.mean(0) if len(locs) else locs])
 
 
 def grid_with_gaps(nx: int, ny: int, remove: int, rng) -> np.ndarray:
@@ -173,18 +186,27 @@ def make_problem(name: str, seed: int = 1, n: int | None = None) -> Problem:
 
 def tiny_problem(n: int, m: int, cov: int = COV_MATERN15, lik: int = LIK_BERNOULLI_LOGIT,
                  rho: float = 0.2, sigma2: float = 1.0, seed: int = 3, n_test: int = 7,
-                 F0: float = 0.0) -> Problem:
-    """Small uniform problem with an exact latent draw, for pins and edge cases."""
+                 F0: float = 0.0, xi: float = 1.0, beta=None) -> Problem:
+    """Small uniform problem with an exact latent draw, for pins and edge cases. With
+    ``beta`` the offset is F = X beta, X = intercept_and_coords(locs) (F0 is then unused)."""
     rng = np.random.default_rng(seed)
     locs = rng.random((n, 2))
     b = latent_exact(locs, cov, sigma2, rho, rng) if n > 0 else np.zeros(0)
-    F = np.full(n, F0)
-    y = responses(F + b, lik, rng)
+    X = None
+    if beta is None:
+        F, Fp = np.full(n, F0), np.full(n_test, F0)
+    else:
+        beta = np.asarray(beta, float)
+        X = intercept_and_coords(locs)
+        F = X @ beta
+    y = responses(F + b, lik, rng, xi)
     order = rng.permutation(n).astype(np.int32)
     test = rng.random((n_test, 2))
+    if beta is not None:
+        Fp = np.column_stack([np.ones(n_test), test - locs.mean(0)]) @ beta
     return Problem(name=f"tiny_n{n}_m{m}", locs=locs, order=order, y=y, F=F, cov=cov, sigma2=sigma2,
-                   rho=rho, m=m, lik=lik, t=8, s=16, test_locs=test, Fp=np.full(n_test, F0),
-                   b_true=b, seed=seed)
+                   rho=rho, m=m, lik=lik, t=8, s=16, test_locs=test, Fp=Fp,
+                   b_true=b, seed=seed, xi=xi, X=X, beta=beta)
 
 
 def serving_params(rng) -> tuple[int, float, int]:
