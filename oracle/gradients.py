@@ -37,7 +37,19 @@ dW/dxi = -d^3 log p / dxi dmu^2 and db*/dxi = A^{-1} d^2 log p / dxi dmu:
     dL/dxi = -sum_i d log p_i / dxi + 1/2 tr(A^{-1} dW/dxi) + (A^{-1} g)^T d^2 log p / dxi dmu,
     STE: d logdet / dxi ~ c tr((W + D^{-1})^{-1} dW/dxi) + mean_i [h(z_i) - c r(z_i)],
          h(z) = (A^{-1} z)^T dW/dxi P^{-1} z,   r(z) = (B P^{-1} z)^T dW/dxi (B P^{-1} z).
-Linear fixed effects F = X beta (Section 2): dL/dbeta = X^T dL/dF. When the control
+Linear fixed effects F = X beta (Section 2): dL/dbeta = X^T dL/dF.
+LRAC form (appendix, "Preconditioner LRAC"; P = L_k L_k^T + W^{-1}, probes z = L_k r1 +
+W^{-1/2} r2, form-2 matrix Sigma_tilde + W^{-1}). With the pivot set I fixed, the rank-k
+pivoted Cholesky factor satisfies L_k L_k^T = Sigma_{:,I} Sigma_{I,I}^{-1} Sigma_{I,:}, so
+    d(L_k L_k^T) = dS_{:,I} G + G^T dS_{I,:} - G^T dS_{I,I} G,   G = Sigma_{I,I}^{-1} Sigma_{I,:},
+and the control variate's mean is tr(P^{-1} d(L_k L_k^T)) = d log det P:
+    d logdet / d theta ~ c tr(P^{-1} d(LL^T)) + mean_i [h(z_i) - c r(z_i)],
+        h(z) = -((Sigma_tilde + W^{-1})^{-1} z)^T Sigma_tilde dSinv Sigma_tilde P^{-1} z,
+        r(z) = (P^{-1} z)^T d(LL^T) P^{-1} z;
+    d logdet / d mu_j ~ W'_j / W_j + c_j (W'_j (L C^{-1} L^T)_jj - W'_j / W_j) - mean_i [h_j - c_j r_j],
+        h_j(z) = ((Sigma_tilde + W^{-1})^{-1} z)_j W'_j / W_j^2 (P^{-1} z)_j,
+        r_j(z) = (P^{-1} z)_j^2 W'_j / W_j^2,       C = I_k + L^T W L,
+using (Sigma_tilde + W^{-1})^{-1} = W A^{-1} Sigma_tilde^{-1}. When the control
 variate is constant over the probes its variance is rounding noise and c is set to 0:
 with Rademacher probes and VADU this happens for sigma2 (B does not depend on sigma2
 and r(z) = -sum_i (W_i + 1/D_i)^{-1} / (sigma2 D_i) for every z), where Cov / Var would
@@ -51,7 +63,7 @@ import numpy as np
 import scipy.sparse as sp
 from scipy.special import digamma
 
-from . import laplace, vecchia
+from . import laplace, lrac, vecchia
 
 PARAMS = ("sigma2", "rho")
 
@@ -266,3 +278,75 @@ def dlogdet_exact(f: laplace.Factor, md: laplace.Mode) -> dict:
         dS = dSinv_matrix(f, dB_matrix(f, dA), dD)
         out[par] = float(np.sum(dD / f.D) + np.sum(Ainv * dS.toarray()))
     return out
+
+
+# ----------------------------------------------------------------------------- LRAC form
+def lowrank_derivative(f: laplace.Factor, piv, param: str) -> np.ndarray:
+    """d(L_k L_k^T)/dtheta (dense n x n, Vecchia order) at the fixed pivot set piv."""
+    piv = np.asarray(piv, np.int64)
+    n = f.n
+    ratio = f.nugget / f.sigma2
+    h = vecchia.dist(f.locs[:, None, :], f.locs[piv][None, :, :])               # n x k
+    same = np.arange(n)[:, None] == piv[None, :]
+    S = vecchia.cov_fn(h, f.cov, f.sigma2, f.rho) + np.where(same, f.nugget, 0.0)
+    dS = dcov(h, f.cov, f.sigma2, f.rho, param, ratio, same)
+    G = np.linalg.solve(S[piv], S.T)                                            # Sigma_II^{-1} Sigma_I:
+    return dS @ G + G.T @ dS.T - G.T @ dS[piv] @ G
+
+
+def _cv_weight(h, r, t, control_variate):
+    if control_variate and t > 1 and r.var(ddof=1) > 1e-20 * r.mean() ** 2:
+        return float(np.cov(h, r, ddof=1)[0, 1] / r.var(ddof=1))
+    return 0.0
+
+
+def lml_grad_ste_lrac(f: laplace.Factor, md: laplace.Mode, k: int, t: int, seed: int,
+                      control_variate: bool = True) -> dict:
+    """dL^VLA / d theta and dL/dF with the log-determinant derivatives by STE on the LRAC
+    probes (dense pieces: small n only). Same return layout as lml_grad_ste."""
+    W, Wp = md.W, W_prime(md.y, md.mu, md.lik, md.xi)
+    L, piv = lrac.pivoted_cholesky(f.locs, f.cov, f.sigma2, f.rho, f.nugget, k)
+    Z = lrac.lrac_probes(f, L, W, t, seed)
+    PZ = lrac.woodbury_apply(L, W, Z)                                   # P^{-1} z
+    A_lu = laplace._lu(sp.diags(W) + f.Sinv)
+    UZ = W[:, None] * A_lu.solve(f.Sinv @ Z)                            # (Sigma_tilde + W^{-1})^{-1} z
+    C = np.eye(L.shape[1]) + L.T @ (W[:, None] * L)
+    lo, up = laplace._tri_solvers(f.B)
+    St = lambda V: np.column_stack([lo(f.D * up(V[:, j])) for j in range(V.shape[1])])   # Sigma_tilde V
+    # d logdet / d mu_j (implicit term)
+    q = Wp / (W * W)
+    hj = UZ * q[:, None] * PZ
+    rj = PZ * PZ * q[:, None]
+    if control_variate and t > 1:
+        vr = rj.var(axis=1, ddof=1)
+        live = vr > 1e-20 * rj.mean(1) ** 2
+        cj = np.where(live, ((hj - hj.mean(1, keepdims=True)) * (rj - rj.mean(1, keepdims=True))).sum(1)
+                      / (t - 1) / np.where(live, vr, 1.0), 0.0)
+    else:
+        cj = np.zeros(f.n)
+    diag_LCL = np.einsum("ij,ij->i", L, np.linalg.solve(C, L.T).T)
+    trW = Wp / W
+    dld_dmu = trW + cj * (Wp * diag_LCL - trW) - (hj - cj[:, None] * rj).mean(1)
+    g = 0.5 * dld_dmu
+    Ag = A_lu.solve(g)
+    dF = np.empty(f.n)
+    dF[f.order] = -laplace.grad_lik(md.y, md.mu, md.lik, md.xi) + g - W * Ag
+    out, samples = {"F": dF}, {}
+    StU, StP = St(UZ), St(PZ)
+    for par in PARAMS:
+        dA, dD = factor_derivatives(f, par)
+        dS = dSinv_matrix(f, dB_matrix(f, dA), dD)
+        h = -np.einsum("ij,ij->j", StU, dS @ StP)
+        dLL = lowrank_derivative(f, piv, par)
+        r = np.einsum("ij,ij->j", PZ, dLL @ PZ)
+        c = _cv_weight(h, r, t, control_variate)
+        tr_dlogP = float(np.trace(lrac.woodbury_apply(L, W, dLL)))      # tr(P^{-1} d(LL^T))
+        dlogdet = c * tr_dlogP + float(np.mean(h - c * r))
+        dSb = dS @ md.b
+        out[par] = 0.5 * float(md.b @ dSb) + 0.5 * dlogdet - float(Ag @ dSb)
+        w = A_lu.solve(dSb)
+        per_probe = 0.5 * (h - c * r) + 0.5 * (w[:, None] * (hj - cj[:, None] * rj)).sum(0)
+        samples[par] = {"h": h, "r": r, "c": c, "dlogdet": dlogdet, "per_probe": per_probe,
+                        "tr_dlogP": tr_dlogP}
+    samples["mu"] = {"h": hj, "r": rj, "c": cj, "dlogdet": dld_dmu}
+    return {"grad": out, "samples": samples, "pivots": piv}

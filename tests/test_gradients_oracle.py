@@ -103,3 +103,63 @@ def test_offset_gradient_matches_central_differences():
     # the STE form with many probes tracks the exact one
     ste = gr.lml_grad_ste(f, md, 2000, 5)["grad"]["F"]
     assert np.max(np.abs(ste - dF)) < 0.05 * np.max(np.abs(dF))
+
+
+# --------------------------------------------------------------------------- LRAC form
+def test_lowrank_product_is_nystrom_and_its_derivative_matches_central_differences():
+    """L_k L_k^T of the pivoted Cholesky equals Sigma_{:,I} Sigma_{I,I}^{-1} Sigma_{I,:} on its
+    pivots, and d(L_k L_k^T)/dtheta at fixed pivots matches central differences of the
+    pivoted Cholesky itself (whose pivots do not move under the perturbation)."""
+    from oracle import lrac
+    P = wl.tiny_problem(70, 8, rho=0.2)
+    f = _factor(P, 1.2, 0.2)
+    k = 12
+    L, piv = lrac.pivoted_cholesky(f.locs, f.cov, f.sigma2, f.rho, f.nugget, k)
+    S = vecchia.dense_cov(f.locs, f.cov, f.sigma2, f.rho, f.nugget)
+    ny = S[:, piv] @ np.linalg.solve(S[np.ix_(piv, piv)], S[piv])
+    assert np.max(np.abs(L @ L.T - ny)) < 1e-10 * np.max(np.abs(ny))
+    h = 1e-5
+    for par in gr.PARAMS:
+        s2p, s2m = (1.2 + h, 1.2 - h) if par == "sigma2" else (1.2, 1.2)
+        rp, rm = (0.2, 0.2) if par == "sigma2" else (0.2 + h, 0.2 - h)
+        Lp, pp = lrac.pivoted_cholesky(f.locs, f.cov, s2p, rp, 1e-10 * s2p, k)
+        Lm, pm = lrac.pivoted_cholesky(f.locs, f.cov, s2m, rm, 1e-10 * s2m, k)
+        assert np.array_equal(pp, piv) and np.array_equal(pm, piv)
+        fd = (Lp @ Lp.T - Lm @ Lm.T) / (2 * h)
+        dLL = gr.lowrank_derivative(f, piv, par)
+        assert np.max(np.abs(dLL - fd)) < 1e-6 * max(1.0, np.max(np.abs(fd))), par
+    # sigma2 scales Sigma (the nugget follows it), so d(LL^T)/dsigma2 = LL^T / sigma2
+    assert np.max(np.abs(gr.lowrank_derivative(f, piv, "sigma2") - L @ L.T / 1.2)) < 1e-12
+
+
+def test_lrac_ste_gradient_is_unbiased_with_the_control_variate():
+    P = wl.tiny_problem(90, 8, lik=la.LIK_POISSON_LOG, rho=0.2, F0=0.3)
+    f = _factor(P, P.sigma2, P.rho)
+    md = la.find_mode(f, P.y, P.F, P.lik, newton_tol=1e-13)
+    t, k = 1500, 10
+    out = gr.lml_grad_ste_lrac(f, md, k, t, 4)
+    plain = gr.lml_grad_ste_lrac(f, md, k, t, 4, control_variate=False)
+    exact = gr.dlogdet_exact(f, md)
+    grad_ex = gr.lml_grad_exact(f, md)
+    for par in gr.PARAMS:
+        s = out["samples"][par]
+        h, r, c = s["h"], s["r"], s["c"]
+        # the control variate has the stated mean tr(P^{-1} d(LL^T))
+        assert abs(r.mean() - s["tr_dlogP"]) < 4 * r.std(ddof=1) / np.sqrt(t) + 1e-12
+        se = np.std(h - c * r, ddof=1) / np.sqrt(t)
+        assert abs(s["dlogdet"] - exact[par]) < 4 * se + 1e-12, par
+        assert np.var(h - c * r) <= np.var(h) + 1e-15
+        s0 = plain["samples"][par]
+        assert abs(s0["dlogdet"] - exact[par]) < 4 * np.std(s0["h"], ddof=1) / np.sqrt(t) + 1e-12
+        pp = s["per_probe"]
+        assert abs(out["grad"][par] - grad_ex[par]) < 4 * np.std(pp, ddof=1) / np.sqrt(t) + 1e-12, par
+    # d logdet / d mu_j against (A^{-1})_jj W'_j, row by row within four standard errors
+    Ainv = np.linalg.inv(np.diag(md.W) + f.Sinv.toarray())
+    ex_mu = np.diag(Ainv) * gr.W_prime(md.y, md.mu, md.lik)
+    sm = out["samples"]["mu"]
+    dev = sm["h"] - sm["c"][:, None] * sm["r"]
+    se_mu = dev.std(axis=1, ddof=1) / np.sqrt(t)
+    assert np.all(np.abs(sm["dlogdet"] - ex_mu) < 4 * se_mu + 1e-12)
+    # the offset gradient tracks the exact one
+    dF = gr.lml_grad_F_exact(f, md)
+    assert np.max(np.abs(out["grad"]["F"] - dF)) < 0.05 * np.max(np.abs(dF))
