@@ -54,3 +54,40 @@ def test_invalid_arguments_are_rejected_before_any_device_work(lib):
     assert L.vl_ctx_create(0, None, None, 10, None) == 1     # out == NULL / ws too small
     assert L.vl_build_factor(None, None, 10, None, 0, 1.0, 1.0, 5, None, None) == 1
     assert L.vl_find_mode(None, 0, None, None, None, None, None) == 1
+
+
+def test_binding_structs_and_constants_match_the_c_header(tmp_path):
+    """The ctypes mirrors of vl_opts and vl_stats have the size and field offsets that a C
+    compiler gives the declarations in include/vl.h (a mismatch would corrupt every call), and
+    the binding's enum constants have the header's values."""
+    import shutil
+    import subprocess
+
+    import paper_2310_12000_gb300 as vl
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"vl_opts": vl.Opts, "vl_stats": vl.Stats}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "vl.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    consts = ["COV_EXPONENTIAL", "COV_MATERN15", "LIK_BERNOULLI_LOGIT", "LIK_POISSON_LOG", "PREC_VADU",
+              "PREC_LVA", "PREC_LRAC", "FP64", "FP32_REFINE", "OP_A", "OP_PINV", "OP_B", "OP_BT", "OP_BINV",
+              "OP_BTINV", "OP_SIGMA", "OP_A2"]
+    for name in consts:
+        lines.append(f'  printf("const {name} %d\\n", (int)VL_{name});')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for name in consts:
+        assert got[("const", name)] == getattr(vl, name), name
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
