@@ -2,7 +2,8 @@
 
 Neighbour sets and level schedules must be bit-exact. The float64 path must
 match the oracle within 1e-9 relative on the mode, L^VLA and predictive
-variances; the factor within 1e-12. The mixed-precision path must reach
+variances; the factor within 1e-10 (D_i cancels digits and the oracle solves by LU, the kernel
+by Cholesky). The mixed-precision path must reach
 relative residual <= 1e-6 on every refined solve and 1e-4 relative on L^VLA.
 """
 import json
