@@ -287,7 +287,7 @@ vl_status vl_pcg_solve(vl_state* s, const double* RHS, int t, const vl_opts* opt
  * the mode by one more solve with W + Sigma_tilde^{-1}. The nugget is taken to scale with sigma2.
  * dF (n doubles, caller order, host or device; may be NULL) receives dL/dF =
  * -grad log p(y | mu*) + g - W (W + Sigma_tilde^{-1})^{-1} g with g = 1/2 dlogdet/dmu* by the
- * same estimator. This build: VL_FP64 with VL_PREC_VADU only (VL_ERR_INVALID_ARG otherwise). */
+ * same estimator. Supported: VL_FP64 with VL_PREC_VADU (VL_ERR_INVALID_ARG otherwise). */
 vl_status vl_lml_grad(vl_state* s, const vl_opts* opts, double* grad, double* dF, vl_stats* stats);
 
 /* The rank-k pivoted Cholesky factor L_k of Sigma used by the LRAC preconditioner

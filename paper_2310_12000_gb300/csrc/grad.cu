@@ -317,7 +317,7 @@ extern "C" vl_status vl_lml_grad(vl_state* st, const vl_opts* o, double* grad, d
   Factor* f = S->f;
   if (!o || !grad) return fail(c, VL_ERR_INVALID_ARG, "vl_lml_grad: opts and grad must be non-null");
   if (o->precision != VL_FP64 || o->precond != VL_PREC_VADU)
-    return fail(c, VL_ERR_INVALID_ARG, "vl_lml_grad: float64 with the VADU preconditioner only in this build");
+    return fail(c, VL_ERR_INVALID_ARG, "vl_lml_grad: supported for float64 with the VADU preconditioner only");
   if (o->t < 1 || o->t > 256 || !(o->cg_tol > 0) || o->cg_max_iter < 1)
     return fail(c, VL_ERR_INVALID_ARG, "vl_lml_grad: invalid option value");
   const int n = (int)f->n, m = f->m, t = o->t;
