@@ -2,9 +2,10 @@
 
 Argument marshalling only: every computation runs in the CUDA kernels behind the
 C ABI declared in ``include/vl.h``. Arrays may be numpy arrays (host) or torch
-tensors (host or CUDA); they are passed by pointer. Importing this package loads
-``_build/libvl.so`` and fails loudly if it has not been built (there is no CPU
-fallback); ``paper_2310_12000_gb300.build.build()`` compiles it with nvcc.
+tensors (host or CUDA); they are passed by pointer. The first call that needs the
+library (``library()``, ``Context()``) loads ``_build/libvl.so`` and raises ImportError
+if it has not been built (there is no CPU fallback);
+``paper_2310_12000_gb300.build.build()`` compiles it with nvcc.
 
 The calls mirror the ABI and the paper's problem statement:
 

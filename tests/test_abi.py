@@ -91,3 +91,14 @@ def test_binding_structs_and_constants_match_the_c_header(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(py), cname
         for fname, _ in py._fields_:
             assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without libvl.so there is no fallback: loading the library and making a context raise."""
+    from paper_2310_12000_gb300 import _lib
+    monkeypatch.setattr(_lib, "_lib", None)
+    monkeypatch.setattr(_lib, "lib_path", lambda: str(tmp_path / "libvl.so"))
+    with pytest.raises(ImportError, match="no CPU fallback"):
+        _lib.library()
+    with pytest.raises(ImportError):
+        _lib.Context(0, ws_bytes=1 << 24)
