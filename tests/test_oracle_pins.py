@@ -422,3 +422,26 @@ def test_lanczos_variances_are_exact_at_full_rank_and_converge(precond):
     assert np.allclose(full, exact, rtol=1e-8, atol=1e-10)
     errs = [np.max(np.abs(lp.pred_var_lanczos(f, md, pf, k, precond) - exact)) for k in (5, 20, 60)]
     assert errs[2] <= errs[1] <= errs[0] + 1e-12
+
+
+@pytest.mark.parametrize("k", [3, 8, 15])
+def test_lanczos_basis_invariants_and_cg_equivalence(k):
+    """At any k the Lanczos basis is orthonormal, Q^T M Q = T, and ||v0|| Q T^{-1} e1 is the
+    k-th CG iterate for M x = v0 from x = 0 (computed by the separate CG routine)."""
+    from oracle import lanczos_pred as lp
+    P = wl.tiny_problem(80, 8, lik=la.LIK_POISSON_LOG, rho=0.2)
+    f = la.build_factor(P.locs, P.order, P.cov, P.sigma2, P.rho, P.m, P.nugget)
+    md = la.find_mode(f, P.y, P.F, P.lik)
+    lo, up = la._tri_solvers(f.B)
+    s = la.precond_scale(f, md.W, la.PREC_VADU)
+    Aap = la.A_apply_fn(f, md.W)
+    M = lambda v: s * up(Aap(lo(s * v)))
+    v0 = np.random.default_rng(2).standard_normal(P.n)
+    Q, T = lp.lanczos_basis(M, v0, k)
+    assert Q.shape == (P.n, k)
+    assert np.max(np.abs(Q.T @ Q - np.eye(k))) < 1e-12
+    MQ = np.column_stack([M(Q[:, j]) for j in range(k)])
+    assert np.max(np.abs(Q.T @ MQ - T)) < 1e-10 * np.max(np.abs(T))
+    x_l = np.linalg.norm(v0) * Q @ np.linalg.solve(T, np.eye(k)[:, 0])
+    x_cg = krylov.pcg_with_T(M, lambda r: r, v0, 0.0, k)[0]
+    assert np.linalg.norm(x_l - x_cg) < 1e-8 * np.linalg.norm(x_cg)
