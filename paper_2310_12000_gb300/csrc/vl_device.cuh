@@ -78,8 +78,16 @@ __device__ __forceinline__ double cov_eval(double h, int cov, double sigma2, dou
 struct Philox4 {
   uint64_t v[4];
 };
-__device__ __forceinline__ Philox4 philox4x64_10(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3,
-                                                 uint64_t k0, uint64_t k1) {
+// High word of the 64 x 64 -> 128-bit product (host form for checks on the CPU).
+__host__ __device__ __forceinline__ uint64_t mulhi64(uint64_t a, uint64_t b) {
+#ifdef __CUDA_ARCH__
+  return __umul64hi(a, b);
+#else
+  return (uint64_t)(((unsigned __int128)a * b) >> 64);
+#endif
+}
+__host__ __device__ __forceinline__ Philox4 philox4x64_10(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3,
+                                                          uint64_t k0, uint64_t k1) {
   const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
   const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
 #pragma unroll
@@ -88,8 +96,8 @@ __device__ __forceinline__ Philox4 philox4x64_10(uint64_t c0, uint64_t c1, uint6
       k0 += W0;
       k1 += W1;
     }
-    uint64_t lo0 = M0 * c0, hi0 = __umul64hi(M0, c0);
-    uint64_t lo1 = M1 * c2, hi1 = __umul64hi(M1, c2);
+    uint64_t lo0 = M0 * c0, hi0 = mulhi64(M0, c0);
+    uint64_t lo1 = M1 * c2, hi1 = mulhi64(M1, c2);
     uint64_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
     c0 = n0;
     c1 = lo1;
