@@ -983,20 +983,13 @@ __global__ void pcg_update2_kernel(int64_t total, int t, int ld, const double* _
 // symmetric tridiagonal T_c (size iters[c]), by implicit symmetric QR steps with
 // Wilkinson shifts (Golub & Van Loan, Sec. 8.3) while rotating only the first
 // row of the eigenvector matrix. One thread per column, float64.
-static __global__ void slq_quad_kernel(int t, int lmax, const double* __restrict__ Tdiag, const double* __restrict__ Toff,
-                                const int* __restrict__ iters, const double* __restrict__ w,
-                                double* __restrict__ work, double* __restrict__ gamma, int* __restrict__ bad) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= t) return;
-  const int l = iters[c];
-  double* d = work + (int64_t)c * 3 * lmax;
-  double* e = d + lmax;
-  double* z = e + lmax;
-  for (int i = 0; i < l; ++i) {
-    d[i] = Tdiag[(int64_t)c * lmax + i];
-    e[i] = (i + 1 < l) ? Toff[(int64_t)c * lmax + i] : 0.0;
-    z[i] = (i == 0) ? 1.0 : 0.0;
-  }
+// e1^T log(T) e1 of the l x l symmetric tridiagonal T (diagonal d, off-diagonal e, both
+// overwritten; z is scratch of length l) by implicit-shift QR with Wilkinson shifts, carrying
+// the first row of the eigenvector matrix in z: sum_i z_i^2 log(theta_i). *bad is set when the
+// iteration did not converge or an eigenvalue is not positive. Host-callable for checks on the
+// CPU.
+__host__ __device__ inline double tridiag_log_quad(int l, double* d, double* e, double* z, bool* bad) {
+  for (int i = 0; i < l; ++i) z[i] = (i == 0) ? 1.0 : 0.0;
   const double eps = 2.220446049250313e-16;
   int hi = l - 1;
   int guard = 0;
@@ -1043,7 +1036,26 @@ static __global__ void slq_quad_kernel(int t, int lmax, const double* __restrict
     if (!(d[i] > 0.0)) ++nb;
     g += z[i] * z[i] * log(d[i]);
   }
-  if (hi > 0 || nb) atomicAdd(bad, 1);
+  *bad = (hi > 0 || nb);
+  return g;
+}
+
+static __global__ void slq_quad_kernel(int t, int lmax, const double* __restrict__ Tdiag, const double* __restrict__ Toff,
+                                const int* __restrict__ iters, const double* __restrict__ w,
+                                double* __restrict__ work, double* __restrict__ gamma, int* __restrict__ bad) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= t) return;
+  const int l = iters[c];
+  double* d = work + (int64_t)c * 3 * lmax;
+  double* e = d + lmax;
+  double* z = e + lmax;
+  for (int i = 0; i < l; ++i) {
+    d[i] = Tdiag[(int64_t)c * lmax + i];
+    e[i] = (i + 1 < l) ? Toff[(int64_t)c * lmax + i] : 0.0;
+  }
+  bool bad_c = false;
+  const double g = tridiag_log_quad(l, d, e, z, &bad_c);
+  if (bad_c) atomicAdd(bad, 1);
   gamma[c] = (l > 0) ? w[c] * g : 0.0;
 }
 
