@@ -1061,7 +1061,8 @@ static __global__ void slq_quad_kernel(int t, int lmax, const double* __restrict
 
 // ----------------------------------------------------------------------------- likelihood
 // mu = F + b; g = d log p / d mu; W = -d^2 log p / d mu^2; logp; rhs = W b + g.
-__device__ __forceinline__ void lik_terms(int lik, double y, double mu, double& lp, double& g, double& W) {
+// lik_terms is host-callable for checks on the CPU.
+__host__ __device__ __forceinline__ void lik_terms(int lik, double y, double mu, double& lp, double& g, double& W) {
   if (lik == VL_LIK_BERNOULLI_LOGIT) {
     const double p = 1.0 / (1.0 + exp(-mu));
     g = y - p;

@@ -65,10 +65,15 @@ __device__ __forceinline__ double dist2_exact(double ax, double ay, double bx, d
   return __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
 }
 
-// c(h) for the supported covariance families (float64).
-__device__ __forceinline__ double cov_eval(double h, int cov, double sigma2, double rho) {
+// c(h) for the supported covariance families (float64). Host-callable for checks on the CPU
+// (there the product sqrt(3) h is an ordinary, separately rounded multiply).
+__host__ __device__ __forceinline__ double cov_eval(double h, int cov, double sigma2, double rho) {
   if (cov == VL_COV_EXPONENTIAL) return sigma2 * exp(-h / rho);
+#ifdef __CUDA_ARCH__
   double a = __dmul_rn(kSqrt3, h) / rho;
+#else
+  double a = (kSqrt3 * h) / rho;
+#endif
   return sigma2 * (1.0 + a) * exp(-a);
 }
 
