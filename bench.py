@@ -98,6 +98,8 @@ def algorithmic_bytes(cls: str, n: int, m: int, t: int, e: int, k: int = 0) -> f
         return nnz * (4 + e) + 4 * (n + 1) + 3 * vec + n * e
     if cls == "coldot":
         return 2 * vec
+    if cls == "pcg_update":     # two kernels per step, alternating: u, h, r, v -> u, r (6 vectors); z, h -> h (3)
+        return 4.5 * vec
     return float("nan")
 
 

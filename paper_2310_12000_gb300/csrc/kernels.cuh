@@ -979,15 +979,11 @@ __global__ void pcg_update2_kernel(int64_t total, int t, int ld, const double* _
 }
 
 // ----------------------------------------------------------------------------- SLQ quadrature
-// gamma_c = w_c * e1^T log(T_c) e1 = w_c * sum_j q_{1j}^2 log(theta_j) for the
-// symmetric tridiagonal T_c (size iters[c]), by implicit symmetric QR steps with
-// Wilkinson shifts (Golub & Van Loan, Sec. 8.3) while rotating only the first
-// row of the eigenvector matrix. One thread per column, float64.
-// e1^T log(T) e1 of the l x l symmetric tridiagonal T (diagonal d, off-diagonal e, both
-// overwritten; z is scratch of length l) by implicit-shift QR with Wilkinson shifts, carrying
-// the first row of the eigenvector matrix in z: sum_i z_i^2 log(theta_i). *bad is set when the
-// iteration did not converge or an eigenvalue is not positive. Host-callable for checks on the
-// CPU.
+// e1^T log(T) e1 = sum_j q_{1j}^2 log(theta_j) of the l x l symmetric tridiagonal T (diagonal d,
+// off-diagonal e, both overwritten; z is scratch of length l) by implicit symmetric QR steps with
+// Wilkinson shifts (Golub & Van Loan, Sec. 8.3), rotating only the first row of the eigenvector
+// matrix (kept in z). *bad is set when the iteration did not converge or an eigenvalue is not
+// positive. Host-callable for checks on the CPU.
 __host__ __device__ inline double tridiag_log_quad(int l, double* d, double* e, double* z, bool* bad) {
   for (int i = 0; i < l; ++i) z[i] = (i == 0) ? 1.0 : 0.0;
   const double eps = 2.220446049250313e-16;
@@ -1040,6 +1036,8 @@ __host__ __device__ inline double tridiag_log_quad(int l, double* d, double* e, 
   return g;
 }
 
+// gamma_c = w_c * e1^T log(T_c) e1 for the Lanczos tridiagonal T_c of column c (size iters[c]).
+// One thread per column, float64.
 static __global__ void slq_quad_kernel(int t, int lmax, const double* __restrict__ Tdiag, const double* __restrict__ Toff,
                                 const int* __restrict__ iters, const double* __restrict__ w,
                                 double* __restrict__ work, double* __restrict__ gamma, int* __restrict__ bad) {
