@@ -21,3 +21,13 @@ def test_nnz_counts_the_short_leading_rows():
     assert bench._nnz(1, 5) == 0
     assert bench._nnz(4, 5) == 0 + 1 + 2 + 3
     assert bench._nnz(10, 3) == 0 + 1 + 2 + 7 * 3
+
+
+def test_algorithmic_bytes_of_the_streaming_classes():
+    n, m, t, e = 1000, 5, 8, 4
+    vec = n * t * e
+    nnz = bench._nnz(n, m)
+    assert bench.algorithmic_bytes("coldot", n, m, t, e) == 2 * vec
+    assert bench.algorithmic_bytes("pcg_update", n, m, t, e) == 4.5 * vec
+    assert bench.algorithmic_bytes("spmv_B", n, m, t, e) == nnz * (4 + e) + 2 * vec + n * e
+    assert bench.algorithmic_bytes("woodbury", n, m, t, e, k=16) == 2 * n * 16 * e + 3 * vec + n * e
