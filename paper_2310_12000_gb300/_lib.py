@@ -155,6 +155,29 @@ def _host(a, dtype):
     return np.ascontiguousarray(a, dtype=dtype)
 
 
+def _numel(a):
+    if isinstance(a, np.ndarray):
+        return a.size
+    numel = getattr(a, "numel", None)         # torch tensors
+    return int(numel()) if callable(numel) else None
+
+
+def _need(a, count: int, name: str):
+    """The C ABI takes bare pointers: refuse an array that does not hold exactly `count`
+    elements before the library reads or writes past its end."""
+    k = None if a is None else _numel(a)
+    if k is not None and k != count:
+        raise ValueError(f"{name}: expected {count} elements, got {k}")
+
+
+def _points(a, name: str) -> int:
+    """Number of rows of an (n, 2) location array (numpy or torch)."""
+    shape = tuple(getattr(a, "shape", ()))
+    if len(shape) != 2 or shape[1] != 2:
+        raise ValueError(f"{name}: expected an (n, 2) array of locations, got shape {shape}")
+    return int(shape[0])
+
+
 class Context:
     """A libvl context on one CUDA device: a stream and a workspace.
 
@@ -238,7 +261,8 @@ class Context:
                      opts: Opts | None = None) -> "Factor":
         locs = _host(locs, np.float64)
         order = _host(order, np.int32)
-        n = locs.shape[0]
+        n = _points(locs, "locs")
+        _need(order, n, "order")
         opts = opts or Opts.make()
         h = C.c_void_p()
         self.check(self.lib.vl_build_factor(self.h, _ptr(locs, np.float64), n, _ptr(order, np.int32), cov,
@@ -247,14 +271,18 @@ class Context:
 
     def knn_prev(self, locs, m: int, out=None):
         locs = _host(locs, np.float64)
-        n = locs.shape[0]
+        n = _points(locs, "locs")
         out = np.empty((n, m), np.int32) if out is None else out
+        _need(out, n * m, "out")
         self.check(self.lib.vl_knn_prev(self.h, _ptr(locs, np.float64), n, m, _ptr(out, np.int32)))
         return out
 
     def knn_cross(self, train, test, m: int, out=None):
         train, test = _host(train, np.float64), _host(test, np.float64)
-        out = np.empty((test.shape[0], m), np.int32) if out is None else out
+        _points(train, "train")
+        n_p = _points(test, "test")
+        out = np.empty((n_p, m), np.int32) if out is None else out
+        _need(out, n_p * m, "out")
         self.check(self.lib.vl_knn_cross(self.h, _ptr(train, np.float64), train.shape[0], _ptr(test, np.float64),
                                          test.shape[0], m, _ptr(out, np.int32)))
         return out
@@ -306,6 +334,9 @@ class Factor:
     def find_mode(self, lik: int, y, F=None, opts: Opts | None = None, mode_out=None, allow_unconverged=False):
         y = _host(y, np.float64)
         F = _host(F, np.float64)
+        _need(y, self.n, "y")
+        _need(F, self.n, "F")
+        _need(mode_out, self.n, "mode_out")
         opts = opts or Opts.make()
         mode = np.empty(self.n) if mode_out is None else mode_out
         h = C.c_void_p()
@@ -368,7 +399,10 @@ class State:
         test_locs = _host(test_locs, np.float64)
         Fp = _host(Fp, np.float64)
         opts = opts or Opts.make()
-        n_p = test_locs.shape[0]
+        n_p = _points(test_locs, "test_locs")
+        _need(Fp, n_p, "Fp")
+        _need(mean_out, n_p, "mean_out")
+        _need(var_out, n_p, "var_out")
         mean = np.empty(n_p) if mean_out is None else mean_out
         var = np.empty(n_p) if var_out is None else var_out
         st = Stats()
@@ -381,6 +415,8 @@ class State:
         X = np.ascontiguousarray(X, dtype=np.float64)
         if X.ndim == 1:
             X = X[:, None]
+        if X.ndim != 2 or X.shape[0] != self.fac.n:
+            raise ValueError(f"X: expected {self.fac.n} rows, got shape {X.shape}")
         opts = opts or Opts.make()
         Y = np.empty_like(X)
         self.ctx.check(self.ctx.lib.vl_apply(self.h, op, X.ctypes.data, X.shape[1], C.byref(opts), Y.ctypes.data))
@@ -390,6 +426,8 @@ class State:
         """(W + B^T D^{-1} B) X for device tensors X, Y (n x t float64) without
         allocating; see vl_apply_A_noalloc in include/vl.h."""
         t = 1 if len(X_dev.shape) == 1 else X_dev.shape[1]
+        _need(X_dev, self.fac.n * t, "X")
+        _need(Y_dev, self.fac.n * t, "Y")
         self.ctx.check(self.ctx.lib.vl_apply_A_noalloc(self.h, _ptr(X_dev, np.float64), t, _ptr(Y_dev, np.float64)))
         return Y_dev
 
@@ -397,6 +435,8 @@ class State:
         R = np.ascontiguousarray(RHS, dtype=np.float64)
         if R.ndim == 1:
             R = R[:, None]
+        if R.ndim != 2 or R.shape[0] != self.fac.n:
+            raise ValueError(f"RHS: expected {self.fac.n} rows, got shape {R.shape}")
         t = R.shape[1]
         opts = opts or Opts.make()
         U = np.empty_like(R)
