@@ -144,7 +144,8 @@ vl_status vl_ctx_synchronize(vl_ctx* ctx);
 vl_status vl_ctx_mem(const vl_ctx* ctx, size_t* in_use, size_t* peak);
 
 /* Vecchia factor (Section 2.1): for locations `locs` (n x 2, caller order) and the
- * ordering `order` (n entries, a permutation of 0..n-1; NULL = identity), finds
+ * ordering `order` (n entries, a permutation of 0..n-1; NULL = identity; not checked here:
+ * an entry outside 0..n-1 is an out-of-bounds access, the Python binding checks host arrays), finds
  * N(i) = the min(i, m) nearest earlier points under the key (d2, index) with d2 in
  * float64 and no fused multiply-add (bit-exact, ties to the lower index), the
  * forward/backward level schedules of B, and for every row the m x m covariance

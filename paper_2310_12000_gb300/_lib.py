@@ -170,6 +170,20 @@ def _need(a, count: int, name: str):
         raise ValueError(f"{name}: expected {count} elements, got {k}")
 
 
+def _check_permutation(order, n: int):
+    """order must be a permutation of 0..n-1 (the library gathers through it unchecked).
+    Host arrays are checked here; a device tensor is the caller's responsibility."""
+    if order is None:
+        return
+    if not isinstance(order, np.ndarray):
+        if getattr(order, "is_cuda", False):
+            return
+        order = np.asarray(order)
+    o = order.astype(np.int64, copy=False).ravel()
+    if o.size and (o.min() < 0 or o.max() >= n or np.bincount(o, minlength=n).max() != 1):
+        raise ValueError("order: expected a permutation of 0..n-1")
+
+
 def _points(a, name: str) -> int:
     """Number of rows of an (n, 2) location array (numpy or torch)."""
     shape = tuple(getattr(a, "shape", ()))
@@ -263,6 +277,7 @@ class Context:
         order = _host(order, np.int32)
         n = _points(locs, "locs")
         _need(order, n, "order")
+        _check_permutation(order, n)
         opts = opts or Opts.make()
         h = C.c_void_p()
         self.check(self.lib.vl_build_factor(self.h, _ptr(locs, np.float64), n, _ptr(order, np.int32), cov,

@@ -90,6 +90,13 @@ def test_context_calls_check_locations():
         ctx.build_factor(np.zeros(10), None, 0, 1.0, 0.1, 3)
     with pytest.raises(ValueError, match="order"):
         ctx.build_factor(np.zeros((10, 2)), np.arange(9, dtype=np.int32), 0, 1.0, 0.1, 3)
+    bad = np.arange(10, dtype=np.int32)
+    bad[3] = 4                                       # a duplicate
+    with pytest.raises(ValueError, match="permutation"):
+        ctx.build_factor(np.zeros((10, 2)), bad, 0, 1.0, 0.1, 3)
+    bad[3] = 10                                      # out of range
+    with pytest.raises(ValueError, match="permutation"):
+        ctx.build_factor(np.zeros((10, 2)), bad, 0, 1.0, 0.1, 3)
     with pytest.raises(ValueError, match="out"):
         ctx.knn_prev(np.zeros((10, 2)), 3, out=np.zeros((10, 2), np.int32))
     with pytest.raises(ValueError, match="test"):
@@ -97,5 +104,6 @@ def test_context_calls_check_locations():
     assert ctx.lib.calls == []
     assert ctx.knn_prev(np.zeros((10, 2)), 3).shape == (10, 3)
     assert ctx.knn_cross(np.zeros((10, 2)), np.zeros((4, 2)), 3).shape == (4, 3)
-    f = ctx.build_factor(np.zeros((10, 2)), np.arange(10, dtype=np.int32), 0, 1.0, 0.1, 3)
+    f = ctx.build_factor(np.zeros((10, 2)), np.random.default_rng(0).permutation(10).astype(np.int32),
+                         0, 1.0, 0.1, 3)
     f.h = None
