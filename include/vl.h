@@ -66,7 +66,9 @@ typedef enum vl_cov {
 /* Likelihood p(y_i | mu_i) (Section 2; log-concave in mu). */
 typedef enum vl_lik {
   VL_LIK_BERNOULLI_LOGIT = 0, /* y in {0,1}, p = 1 / (1 + exp(-mu))             */
-  VL_LIK_POISSON_LOG = 1      /* y in {0,1,2,...}, mean exp(mu)                  */
+  VL_LIK_POISSON_LOG = 1,     /* y in {0,1,2,...}, mean exp(mu)                  */
+  VL_LIK_GAMMA_LOG = 2        /* y > 0, Gamma(shape a, rate a exp(-mu)), mean exp(mu),
+                               * a = opts->lik_shape (Section 5)                  */
 } vl_lik;
 
 /* Preconditioner (Section 3.1). VADU and LVA use Eqs. pcls1/logdetsplit; LRAC uses
@@ -97,6 +99,7 @@ typedef struct vl_opts {
   int newton_max_iter;  /*                                               default 100 */
   double nugget;        /* added to diag(Sigma); < 0 means 1e-10 sigma2  default -1 */
   uint64_t seed;        /* Philox4x64-10 key for probes and simulation   default 1 */
+  double lik_shape;     /* gamma shape a > 0 (VL_LIK_GAMMA_LOG only)     default 1 */
 } vl_opts;
 
 /* Per-call diagnostics (any pointer argument of this type may be NULL). */
@@ -174,7 +177,8 @@ void vl_factor_destroy(vl_factor* f);
  * b^0 = 0, a step halved (at most 30 times) while it lowers
  * psi(b) = log p(y|F+b) - b^T Sigma_tilde^{-1} b / 2 by more than 1e-12 (1 + |psi|),
  * stopping when max|b^{t+1} - b^t| <= newton_tol (1 + max|b^{t+1}|). y, F (F may be NULL
- * = 0) and mode_out (may be NULL) have n entries in caller order. The state keeps b*,
+ * = 0) and mode_out (may be NULL) have n entries in caller order. With VL_LIK_GAMMA_LOG the
+ * shape is opts->lik_shape (> 0, else VL_ERR_INVALID_ARG) and every y must be > 0. The state keeps b*,
  * W and the factor resident for vl_log_marglik / vl_pred_var; it references f,
  * which must outlive it. Errors: VL_ERR_NOT_CONVERGED, VL_ERR_TIMEOUT, ... */
 vl_status vl_find_mode(vl_factor* f, int lik, const double* y, const double* F,
@@ -288,7 +292,8 @@ vl_status vl_pcg_solve(vl_state* s, const double* RHS, int t, const vl_opts* opt
  * the mode by one more solve with W + Sigma_tilde^{-1}. The nugget is taken to scale with sigma2.
  * dF (n doubles, caller order, host or device; may be NULL) receives dL/dF =
  * -grad log p(y | mu*) + g - W (W + Sigma_tilde^{-1})^{-1} g with g = 1/2 dlogdet/dmu* by the
- * same estimator. Supported: VL_FP64 with VL_PREC_VADU (VL_ERR_INVALID_ARG otherwise). */
+ * same estimator. Supported: VL_FP64 with VL_PREC_VADU, Bernoulli or Poisson likelihood
+ * (VL_ERR_INVALID_ARG otherwise). */
 vl_status vl_lml_grad(vl_state* s, const vl_opts* opts, double* grad, double* dF, vl_stats* stats);
 
 /* The rank-k pivoted Cholesky factor L_k of Sigma used by the LRAC preconditioner

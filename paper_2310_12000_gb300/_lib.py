@@ -9,7 +9,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 
 COV_EXPONENTIAL, COV_MATERN15 = 0, 1
-LIK_BERNOULLI_LOGIT, LIK_POISSON_LOG = 0, 1
+LIK_BERNOULLI_LOGIT, LIK_POISSON_LOG, LIK_GAMMA_LOG = 0, 1, 2
 PREC_VADU, PREC_LVA, PREC_LRAC = 0, 1, 2
 FP64, FP32_REFINE = 0, 1
 OP_A, OP_PINV, OP_B, OP_BT, OP_BINV, OP_BTINV, OP_SIGMA, OP_A2 = range(8)
@@ -28,7 +28,7 @@ class Opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("precond", C.c_int), ("t", C.c_int), ("k", C.c_int),
                 ("s", C.c_int), ("cg_tol", C.c_double), ("cg_max_iter", C.c_int),
                 ("newton_tol", C.c_double), ("newton_max_iter", C.c_int), ("nugget", C.c_double),
-                ("seed", C.c_uint64)]
+                ("seed", C.c_uint64), ("lik_shape", C.c_double)]
 
     @classmethod
     def make(cls, **kw) -> "Opts":

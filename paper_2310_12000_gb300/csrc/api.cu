@@ -280,7 +280,8 @@ static vl_status psi_eval(State* st, Engine<double>& E1, Scratch& S, const doubl
   const int n = (int)st->f->n;
   double* lp = S.get<double>(n);
   if (!lp) return fail(c, VL_ERR_OOM, "workspace exhausted (psi)");
-  lik_kernel<<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, st->lik, st->y, st->F, b, nullptr, nullptr, nullptr, lp);
+  lik_kernel<<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, st->lik, st->shape, st->y, st->F, b, nullptr, nullptr, nullptr,
+                                                       lp);
   VL_CUDA(c, cudaGetLastError());
   double logp = 0.0, quad = 0.0;
   VL_TRY(dev_sum(c, S, n, 0, lp, nullptr, &logp));
@@ -588,6 +589,7 @@ void vl_opts_default(vl_opts* o) {
   o->newton_max_iter = 100;
   o->nugget = -1.0;
   o->seed = 1;
+  o->lik_shape = 1.0;
 }
 
 vl_status vl_ctx_create(int device, void* cuda_stream, void* workspace, size_t ws_bytes, vl_ctx** out) {
@@ -874,9 +876,11 @@ vl_status vl_find_mode(vl_factor* f, int lik, const double* y, const double* F, 
                        double* mode_out, vl_state** out) {
   if (!f) return VL_ERR_INVALID_ARG;
   Ctx* c = f->ctx;
-  if (!out || !y || (lik != VL_LIK_BERNOULLI_LOGIT && lik != VL_LIK_POISSON_LOG))
+  if (!out || !y || (lik != VL_LIK_BERNOULLI_LOGIT && lik != VL_LIK_POISSON_LOG && lik != VL_LIK_GAMMA_LOG))
     return fail(c, VL_ERR_INVALID_ARG, "vl_find_mode: invalid argument");
   VL_TRY(check_opts(c, opts));
+  if (lik == VL_LIK_GAMMA_LOG && !(opts->lik_shape > 0.0 && std::isfinite(opts->lik_shape)))
+    return fail(c, VL_ERR_INVALID_ARG, "vl_find_mode: the gamma shape must be > 0");
   *out = nullptr;
   const int n = (int)f->n;
   cudaEventRecord(c->ev0, c->stream);
@@ -885,6 +889,7 @@ vl_status vl_find_mode(vl_factor* f, int lik, const double* y, const double* F, 
   st->ctx = c;
   st->mem.ctx = c;
   st->lik = lik;
+  st->shape = lik == VL_LIK_GAMMA_LOG ? opts->lik_shape : 1.0;
   auto bail = [&](vl_status s) {
     st->mem.free_all();
     delete st;
@@ -930,7 +935,7 @@ vl_status vl_find_mode(vl_factor* f, int lik, const double* y, const double* F, 
   s = psi_eval(st, E64, S, st->b, &psi, nullptr, nullptr);
   if (s != VL_OK) return bail(s);
   for (it = 1; it <= opts->newton_max_iter; ++it) {
-    lik_kernel<<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, lik, st->y, st->F, st->b, st->W, g, rhs, nullptr);
+    lik_kernel<<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, lik, st->shape, st->y, st->F, st->b, st->W, g, rhs, nullptr);
     s = E64.set_W(st->W);
     if (s != VL_OK) return bail(s);
     if (mixed) {
@@ -961,7 +966,8 @@ vl_status vl_find_mode(vl_factor* f, int lik, const double* y, const double* F, 
     }
   }
   // W at the mode
-  lik_kernel<<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, lik, st->y, st->F, st->b, st->W, nullptr, nullptr, nullptr);
+  lik_kernel<<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, lik, st->shape, st->y, st->F, st->b, st->W, nullptr, nullptr,
+                                                       nullptr);
   if (cudaGetLastError() != cudaSuccess) return bail(fail(c, VL_ERR_CUDA, "lik"));
   if (mode_out) {
     double* mu = S.get<double>(n);

@@ -318,6 +318,8 @@ extern "C" vl_status vl_lml_grad(vl_state* st, const vl_opts* o, double* grad, d
   if (!o || !grad) return fail(c, VL_ERR_INVALID_ARG, "vl_lml_grad: opts and grad must be non-null");
   if (o->precision != VL_FP64 || o->precond != VL_PREC_VADU)
     return fail(c, VL_ERR_INVALID_ARG, "vl_lml_grad: supported for float64 with the VADU preconditioner only");
+  if (S->lik != VL_LIK_BERNOULLI_LOGIT && S->lik != VL_LIK_POISSON_LOG)
+    return fail(c, VL_ERR_INVALID_ARG, "vl_lml_grad: supported for the Bernoulli and Poisson likelihoods only");
   if (o->t < 1 || o->t > 256 || !(o->cg_tol > 0) || o->cg_max_iter < 1)
     return fail(c, VL_ERR_INVALID_ARG, "vl_lml_grad: invalid option value");
   const int n = (int)f->n, m = f->m, t = o->t;

@@ -1060,8 +1060,16 @@ static __global__ void slq_quad_kernel(int t, int lmax, const double* __restrict
 // ----------------------------------------------------------------------------- likelihood
 // mu = F + b; g = d log p / d mu; W = -d^2 log p / d mu^2; logp; rhs = W b + g.
 // lik_terms is host-callable for checks on the CPU.
-__host__ __device__ __forceinline__ void lik_terms(int lik, double y, double mu, double& lp, double& g, double& W) {
-  if (lik == VL_LIK_BERNOULLI_LOGIT) {
+// Gamma (shape a, rate a e^{-mu}), u = y e^{-mu}: log p = a log a - lgamma(a) + (a - 1) log y
+// - a mu - a u, d log p / d mu = a (u - 1), W = a u.
+__host__ __device__ __forceinline__ void lik_terms(int lik, double shape, double y, double mu, double& lp, double& g,
+                                                   double& W) {
+  if (lik == VL_LIK_GAMMA_LOG) {
+    const double u = y * exp(-mu);
+    g = shape * (u - 1.0);
+    W = shape * u;
+    lp = shape * log(shape) - lgamma(shape) + (shape - 1.0) * log(y) - shape * mu - shape * u;
+  } else if (lik == VL_LIK_BERNOULLI_LOGIT) {
     const double p = 1.0 / (1.0 + exp(-mu));
     g = y - p;
     W = p * (1.0 - p);
@@ -1075,12 +1083,12 @@ __host__ __device__ __forceinline__ void lik_terms(int lik, double y, double mu,
   }
 }
 
-static __global__ void lik_kernel(int n, int lik, const double* __restrict__ y, const double* __restrict__ F,
+static __global__ void lik_kernel(int n, int lik, double shape, const double* __restrict__ y, const double* __restrict__ F,
                            const double* __restrict__ b, double* __restrict__ W, double* __restrict__ g,
                            double* __restrict__ rhs, double* __restrict__ logp) {
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
     double lp, gg, ww;
-    lik_terms(lik, y[s], F[s] + b[s], lp, gg, ww);
+    lik_terms(lik, shape, y[s], F[s] + b[s], lp, gg, ww);
     if (W) W[s] = ww;
     if (g) g[s] = gg;
     if (rhs) rhs[s] = ww * b[s] + gg;

@@ -164,6 +164,7 @@ struct State {
   Ctx* ctx = nullptr;
   Owned mem;
   int lik = 0;
+  double shape = 1.0;   // gamma shape (VL_LIK_GAMMA_LOG)
   double* y = nullptr;     // storage order
   double* F = nullptr;
   double* b = nullptr;     // mode

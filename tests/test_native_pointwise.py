@@ -30,19 +30,24 @@ def run(tmp_path_factory):
     return go
 
 
-@pytest.mark.parametrize("lik", [la.LIK_BERNOULLI_LOGIT, la.LIK_POISSON_LOG])
-def test_likelihood_terms_match_the_oracle(run, lik):
+@pytest.mark.parametrize("lik,shape", [(la.LIK_BERNOULLI_LOGIT, 1.0), (la.LIK_POISSON_LOG, 1.0),
+                                       (la.LIK_GAMMA_LOG, 0.7), (la.LIK_GAMMA_LOG, 6.0), (la.LIK_GAMMA_LOG, 28.0)])
+def test_likelihood_terms_match_the_oracle(run, lik, shape):
     if lik == la.LIK_BERNOULLI_LOGIT:
         mu = np.concatenate([np.linspace(-40.0, 40.0, 161), [-1e-12, 0.0, 1e-12]])
         ys = (0.0, 1.0)
-    else:
+    elif lik == la.LIK_POISSON_LOG:
         mu = np.linspace(-10.0, 5.0, 121)
         ys = (0.0, 1.0, 3.0, 17.0, 50.0)
+    else:
+        mu = np.linspace(-6.0, 6.0, 121)
+        ys = (1e-3, 0.4, 1.0, 2.7, 55.0)
     y = np.repeat(np.array(ys), len(mu))
     m = np.tile(mu, len(ys))
-    got = run([f"L {lik} {float(yy)!r} {float(mm)!r}" for yy, mm in zip(y, m)])
-    for k, ref in enumerate((la.log_lik(y, m, lik), la.grad_lik(y, m, lik), la.W_lik(y, m, lik))):
-        assert np.allclose(got[:, k], ref, rtol=1e-14, atol=1e-15 * max(1.0, np.max(np.abs(ref)))), k
+    got = run([f"L {lik} {shape!r} {float(yy)!r} {float(mm)!r}" for yy, mm in zip(y, m)])
+    refs = (la.log_lik(y, m, lik, shape), la.grad_lik(y, m, lik, shape), la.W_lik(y, m, lik, shape))
+    for k, ref in enumerate(refs):
+        assert np.allclose(got[:, k], ref, rtol=1e-13, atol=1e-14 * max(1.0, np.max(np.abs(ref)))), k
 
 
 @pytest.mark.parametrize("cov", [vecchia.COV_EXPONENTIAL, vecchia.COV_MATERN15])
