@@ -107,3 +107,32 @@ def test_fit_rejects_mismatched_bounds():
     import pytest
     with pytest.raises(ValueError):
         estimate.fit(lambda th: (0.0, np.zeros(3)), [1.0, 0.1, 0.0], bounds=[(1e-3, 1e3)], n_positive=2)
+
+
+def test_joint_fit_with_the_gamma_shape():
+    """Section 5's parameter set: covariance (sigma2, range), the gamma shape alpha (all
+    positive, searched in log space) and the coefficients beta, on the oracle's exact L^VLA
+    and gradient. The fit reaches a stationary point and a local minimum."""
+    P = wl.tiny_problem(120, 8, lik=wl.LIK_GAMMA_LOG, rho=0.2, sigma2=0.5, seed=6, xi=5.0, beta=[0.3, 0.4, -0.2])
+    base = la.build_factor(P.locs, P.order, P.cov, P.sigma2, P.rho, P.m, P.nugget)
+
+    def obj(theta):
+        s2, rho, a = (float(v) for v in theta[:3])
+        f = la.refit(base, s2, rho, 1e-10 * s2)
+        F = P.X @ theta[3:]
+        md = la.find_mode(f, P.y, F, la.LIK_GAMMA_LOG, newton_tol=1e-12, xi=a)
+        L, _ = la.lml_exact(f, md)
+        g = gr.lml_grad_exact(f, md)
+        dF = gr.lml_grad_F_exact(f, md)
+        return L, np.concatenate([[g["sigma2"], g["rho"], gr.lml_grad_xi_exact(f, md)], gr.lml_grad_beta(P.X, dF)])
+
+    bounds = [(1e-3, 1e3), (1e-3, 10.0), (1e-2, 1e4), (None, None), (None, None), (None, None)]
+    r = estimate.fit(obj, [1.0, 0.1, 2.0, 0.0, 0.0, 0.0], max_iter=200, n_positive=3, bounds=bounds)
+    assert r.converged, r.message
+    scale = np.concatenate([r.theta[:3], np.ones(3)])
+    assert np.max(np.abs(r.grad * scale)) < 1e-3
+    for k in range(6):
+        for s in (-1, 1):
+            th = r.theta.copy()
+            th[k] = th[k] * (1 + 0.03 * s) if k < 3 else th[k] + 0.03 * s
+            assert obj(th)[0] >= r.value - 1e-9
