@@ -83,12 +83,16 @@ __host__ __device__ __forceinline__ double cov_eval(double h, int cov, double si
 struct Philox4 {
   uint64_t v[4];
 };
-// High word of the 64 x 64 -> 128-bit product (host form for checks on the CPU).
+// High word of the 64 x 64 -> 128-bit product. The host form (for checks on the CPU) sums the
+// four 32 x 32-bit partial products, so it needs no 128-bit integer type.
 __host__ __device__ __forceinline__ uint64_t mulhi64(uint64_t a, uint64_t b) {
 #ifdef __CUDA_ARCH__
   return __umul64hi(a, b);
 #else
-  return (uint64_t)(((unsigned __int128)a * b) >> 64);
+  const uint64_t al = a & 0xFFFFFFFFull, ah = a >> 32, bl = b & 0xFFFFFFFFull, bh = b >> 32;
+  const uint64_t ll = al * bl, lh = al * bh, hl = ah * bl, hh = ah * bh;
+  const uint64_t mid = (ll >> 32) + (lh & 0xFFFFFFFFull) + (hl & 0xFFFFFFFFull);
+  return hh + (lh >> 32) + (hl >> 32) + (mid >> 32);
 #endif
 }
 __host__ __device__ __forceinline__ Philox4 philox4x64_10(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3,
