@@ -78,6 +78,16 @@ def derived_metrics(prof: dict, n: int, m: int, ms_per_step: float, graph_ms: fl
     return out
 
 
+def newton_summary(ms: dict) -> dict:
+    """Newton steps, PCG iterations (all refinement passes) and iterations per step of one
+    mode computation, from the state's statistics."""
+    steps = int(ms.get("newton_iters") or 0)
+    its = int(ms.get("cg_iters_total") or 0)
+    return {"steps": steps, "cg_iters_total": its, "cg_iters_per_step": its / steps if steps else None,
+            "pcg_solves": ms.get("cg_calls"), "refine_passes": ms.get("refine_steps"),
+            "true_relres": ms.get("true_relres_max")}
+
+
 def _nnz(n: int, m: int) -> int:
     return sum(min(k, m) for k in range(min(n, m))) + max(0, n - m) * m
 
@@ -188,22 +198,50 @@ def _oracle_eval_seconds(n_sub: int, seed: int) -> tuple[float, float]:
     return time.perf_counter() - t0, L
 
 
-def cpu_baseline(n_full: int, steps: int = 1) -> dict:
-    """The oracle timed on this host in a single-threaded child process."""
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+def cpu_model() -> str:
+    try:
+        for line in open("/proc/cpuinfo"):
+            key = line.split(":")[0].strip().lower()
+            if key in ("model name", "cpu part", "hardware"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def _oracle_seconds(threads: int, steps: int) -> list:
+    """Seconds per oracle evaluation in a child process with `threads` BLAS/OpenMP threads."""
+    t = str(threads)
+    env = dict(os.environ, OMP_NUM_THREADS=t, OPENBLAS_NUM_THREADS=t, MKL_NUM_THREADS=t)
     code = (f"import sys; sys.path.insert(0, {ROOT!r}); import bench, json; "
             f"r = [bench._oracle_eval_seconds({CPU_SAMPLE_N}, 1) for _ in range({steps})]; "
             f"print(json.dumps([x[0] for x in r]))")
     out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=1800)
     if out.returncode != 0:
-        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": out.stderr[-400:]}
-    secs = json.loads(out.stdout.strip().splitlines()[-1])
-    s = statistics.median(secs)
-    return {"value": (1.0 / s) * (CPU_SAMPLE_N / n_full), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "seconds_per_eval_at_sample": s,
+        raise RuntimeError(out.stderr[-400:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline(n_full: int, steps: int = 1) -> dict:
+    """The oracle timed on this host in child processes, single-threaded and with every core
+    available to its BLAS (SuperLU itself is single-threaded)."""
+    cores = os.cpu_count() or 1
+    try:
+        one = statistics.median(_oracle_seconds(1, steps))
+        allc = statistics.median(_oracle_seconds(cores, steps))
+    except RuntimeError as exc:
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": str(exc)}
+    best, used = (one, 1) if one <= allc else (allc, cores)
+    scale = CPU_SAMPLE_N / n_full
+    return {"value": (1.0 / best) * scale, "unit": UNIT, "cores": used, "kind": "oracle",
+            "single_thread": {"value": scale / one, "seconds_per_eval_at_sample": one, "cores": 1},
+            "all_cores": {"value": scale / allc, "seconds_per_eval_at_sample": allc, "cores": cores},
+            "host": {"nproc": cores, "cpu_model": cpu_model()},
             "sample": f"one LML evaluation (factor rows + Newton with sparse-LU solves + exact log-det) of the "
-                      f"same grid-with-gaps recipe at n={CPU_SAMPLE_N}, single thread, scaled to n={n_full} "
-                      f"by n_sample/n (linear; flatters the CPU since sparse LU grows faster than n)"}
+                      f"same grid-with-gaps recipe at n={CPU_SAMPLE_N}, scaled to n={n_full} by n_sample/n "
+                      f"(linear; flatters the CPU since sparse LU grows faster than n); value = the faster of "
+                      f"1 thread and {cores} BLAS threads"}
 
 
 # ----------------------------------------------------------------------------- batched / serving legs
@@ -340,6 +378,7 @@ def run_ours(args):
     ctx = vl.Context(dev, ws_bytes=ws_bytes)
     stream = torch.cuda.current_stream(dev)
     pre = dict(precond=vl.PREC_LRAC, k=args.k) if args.precond == "lrac" else dict(precond=vl.PREC_VADU)
+    pre["newton_eta_max"] = args.newton_eta_max
     o32 = vl.Opts.make(precision=vl.FP32_REFINE, t=50, cg_tol=1e-6, newton_tol=1e-7, cg_max_iter=3000, **pre)
     o64 = vl.Opts.make(precision=vl.FP64, t=50, cg_tol=1e-6, newton_tol=1e-7, cg_max_iter=3000, **pre)
 
@@ -363,9 +402,10 @@ def run_ours(args):
             st = fac.find_mode(P.lik, y_h.numpy(), F_h.numpy(), opts, mode_out=mode_h.numpy())
         else:
             st = fac.find_mode(P.lik, y_d, F_d, opts, mode_out=mode_d)
-        val = st.log_marglik(opts, with_stats=True)
+        L, ls = st.log_marglik(opts, with_stats=True)
+        ls = dict(ls, mode=st.mode_stats())
         st.close()
-        return val
+        return L, ls
 
     def barrier():
         if ws > 1:
@@ -433,7 +473,7 @@ def run_ours(args):
     # ---------------- e2e: host buffers, copies inside the timed region
     barrier()
     t0 = time.perf_counter()
-    e2e_steps = 1
+    e2e_steps = max(2, min(args.steps, 3))
     for _ in range(e2e_steps):
         step(o32, host=True)
     barrier()
@@ -450,7 +490,7 @@ def run_ours(args):
         barrier()
         fp64 = {"evals_per_s": ws / max_over_ranks(time.perf_counter() - t0), "lml": L64,
                 "rel_diff_mixed_vs_fp64": abs(lmls[-1] - L64) / abs(L64),
-                "newton_cg_iters_total": s64.get("cg_iters_total")}
+                "newton": newton_summary(s64["mode"]), "slq_cg_iters_max": s64.get("cg_iters_max")}
 
     # ---------------- batched and serving legs (their own slot contexts)
     ctx.close()
@@ -490,8 +530,10 @@ def run_ours(args):
                        "step": "factor rows + Newton mode + SLQ log-marglik (neighbours/levels once, excluded)",
                        "l2": "inputs larger than L2 (probe block 1e6 x 56 float32 = 224 MB per vector)",
                        "graph_ms": graph_ms, "levels_fwd": info["nlev_fwd"], "levels_bwd": info["nlev_bwd"]},
-            "lml": lmls[-1], "newton_cg_iters_total": s_last.get("cg_iters_total"),
-            "slq_cg_iters_max": s_last.get("cg_iters_max"), "slq_stderr": s_last.get("slq_stderr"),
+            "lml": lmls[-1], "newton": newton_summary(s_last["mode"]),
+            "slq_cg_iters_max": s_last.get("cg_iters_max"), "slq_cg_iters_total": s_last.get("cg_iters_total"),
+            "slq_stderr": s_last.get("slq_stderr"), "probe_relres_max": s_last.get("probe_relres_max"),
+            "probe_refine_steps": s_last.get("probe_refine_steps"),
             "fp64": fp64, "e2e": e2e, "gpu_launches": launches, "launches_before_timed": launches_before,
             "roofline": roofline,
             "kernel_profile_ms": prof, "clocks": clk.summary(), "cpu_baseline": cb,
@@ -522,6 +564,8 @@ def main():
     ap.add_argument("--ws-gb", type=float, default=None, help="workspace size in GiB (default: 60%% of free memory)")
     ap.add_argument("--precond", default="vadu", choices=["vadu", "lrac"], help="preconditioner of the timed step")
     ap.add_argument("--k", type=int, default=500, help="LRAC rank")
+    ap.add_argument("--newton-eta-max", type=float, default=0.1,
+                    help="largest inexact-Newton forcing term (0: every Newton solve to cg_tol)")
     ap.add_argument("--batch", type=int, default=256, help="problems in the batched leg (0: skip)")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="arrival window of the serving leg (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=50.0, help="serving arrivals per second")

@@ -100,6 +100,11 @@ typedef struct vl_opts {
   double nugget;        /* added to diag(Sigma); < 0 means 1e-10 sigma2  default -1 */
   uint64_t seed;        /* Philox4x64-10 key for probes and simulation   default 1 */
   double lik_shape;     /* gamma shape a > 0 (VL_LIK_GAMMA_LOG only)     default 1 */
+  double newton_eta_max; /* inexact Newton: each Newton solve stops once ||rhs - A x|| <=
+                            max(cg_tol ||rhs||, eta_k ||grad psi||) with the Eisenstat-Walker
+                            forcing term eta_k <= newton_eta_max (capped at 0.9); the
+                            iteration ends only after a solve to cg_tol. 0: every solve to
+                            cg_tol                                      default 0.1 */
 } vl_opts;
 
 /* Per-call diagnostics (any pointer argument of this type may be NULL). */
@@ -115,6 +120,11 @@ typedef struct vl_stats {
   double slq_stderr;       /* standard error of that mean over the probes          */
   double logdet;           /* log det(Sigma_tilde W + I) used in L^VLA             */
   double ms_total;         /* device time of the call (CUDA events)                */
+  double probe_relres_max; /* vl_log_marglik: largest float64 relative residual
+                              ||z - S u|| / ||z|| of the SLQ probe solves (S the
+                              preconditioner's system operator); float32 solves are
+                              refined until it meets cg_tol, which leaves T alone */
+  int probe_refine_steps;  /* vl_log_marglik: float64 refinement passes of the probe block */
 } vl_stats;
 
 typedef struct vl_ctx vl_ctx;
@@ -145,6 +155,37 @@ const char* vl_last_error(const vl_ctx* ctx);
 vl_status vl_ctx_synchronize(vl_ctx* ctx);
 /* Bytes of workspace currently in use / peak use. */
 vl_status vl_ctx_mem(const vl_ctx* ctx, size_t* in_use, size_t* peak);
+
+/* Upper bound, in SM clock cycles, on each bounded device-side wait of the library's
+ * kernels on this context (grid and cluster-free level barriers, the level-schedule walk);
+ * 0 restores the default of 4e9 cycles (about 2 s). A wait that runs out records
+ * VL_ERR_TIMEOUT and the row, makes every other wait of that launch give up at once, and
+ * the call returns VL_ERR_TIMEOUT with a message; the context stays usable. Synchronises
+ * the stream. VL_ERR_INVALID_ARG for cycles < 0. For tests of that path and for callers
+ * that want a shorter watchdog. */
+vl_status vl_ctx_set_wait_limit(vl_ctx* ctx, long long cycles);
+/* Runs one bounded device-side wait on a flag that nothing sets, under the context's wait
+ * limit, and returns what a library call returns when one of its waits runs out:
+ * VL_ERR_TIMEOUT with its message. A check of the timeout path that every bounded wait
+ * shares; the paper has no counterpart. */
+vl_status vl_ctx_wait_probe(vl_ctx* ctx);
+
+/* Form of the level-scheduled triangular solves with B and B^T (the two solves of the
+ * VADU / LVA preconditioners, Section 3.1.1, and of Sigma_tilde = B^{-1} D B^{-T}).
+ * By default each solve picks its form from n, t and the widest level; forcing one
+ * serves tests (every form against the oracle) and tuning. */
+typedef enum vl_solve_form {
+  VL_SOLVE_AUTO = 0,    /* chosen per solve                                          */
+  VL_SOLVE_SHARED = 1,  /* t = 1: one block, x in shared memory (n * sizeof <= 200 KiB);
+                           block solves (t > 1) keep the automatic choice              */
+  VL_SOLVE_CLUSTER = 2, /* one thread-block cluster, hardware cluster barrier per level */
+  VL_SOLVE_GRID = 3     /* cooperative grid, bounded software grid barrier per level   */
+} vl_solve_form;
+/* Sets the form for every later solve on this context (VL_ERR_INVALID_ARG for an
+ * unknown form). A solve the forced form cannot run (VL_SOLVE_SHARED with too many
+ * rows; VL_SOLVE_CLUSTER when no cluster fits the kernel, or float64 blocks wider
+ * than 128 columns) fails with VL_ERR_INVALID_ARG. */
+vl_status vl_ctx_set_solve_form(vl_ctx* ctx, int form);
 
 /* Vecchia factor (Section 2.1): for locations `locs` (n x 2, caller order) and the
  * ordering `order` (n entries, a permutation of 0..n-1; NULL = identity; not checked here:
@@ -177,8 +218,11 @@ void vl_factor_destroy(vl_factor* f);
  * b^0 = 0, a step halved (at most 30 times) while it lowers
  * psi(b) = log p(y|F+b) - b^T Sigma_tilde^{-1} b / 2 by more than 1e-12 (1 + |psi|),
  * stopping when max|b^{t+1} - b^t| <= newton_tol (1 + max|b^{t+1}|). y, F (F may be NULL
- * = 0) and mode_out (may be NULL) have n entries in caller order. With VL_LIK_GAMMA_LOG the
- * shape is opts->lik_shape (> 0, else VL_ERR_INVALID_ARG) and every y must be > 0. The state keeps b*,
+ * = 0) and mode_out (may be NULL) have n entries in caller order. Every y must lie in the
+ * likelihood's support (Bernoulli: 0 or 1; Poisson: a non-negative integer; gamma: > 0) and
+ * y and F must be finite, else VL_ERR_INVALID_ARG naming the first offending caller index.
+ * With VL_LIK_GAMMA_LOG the shape is opts->lik_shape (> 0, else VL_ERR_INVALID_ARG). A float64
+ * PCG solve that stops at cg_max_iter above cg_tol is VL_ERR_NOT_CONVERGED. The state keeps b*,
  * W and the factor resident for vl_log_marglik / vl_pred_var; it references f,
  * which must outlive it. Errors: VL_ERR_NOT_CONVERGED, VL_ERR_TIMEOUT, ... */
 vl_status vl_find_mode(vl_factor* f, int lik, const double* y, const double* F,

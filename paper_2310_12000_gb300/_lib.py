@@ -13,6 +13,7 @@ LIK_BERNOULLI_LOGIT, LIK_POISSON_LOG, LIK_GAMMA_LOG = 0, 1, 2
 PREC_VADU, PREC_LVA, PREC_LRAC = 0, 1, 2
 FP64, FP32_REFINE = 0, 1
 OP_A, OP_PINV, OP_B, OP_BT, OP_BINV, OP_BTINV, OP_SIGMA, OP_A2 = range(8)
+SOLVE_AUTO, SOLVE_SHARED, SOLVE_CLUSTER, SOLVE_GRID = range(4)
 
 _STATUS = {0: "VL_OK", 1: "VL_ERR_INVALID_ARG", 2: "VL_ERR_OOM", 3: "VL_ERR_NOT_SPD",
            4: "VL_ERR_NOT_CONVERGED", 5: "VL_ERR_TIMEOUT", 6: "VL_ERR_CUDA", 7: "VL_ERR_STATE"}
@@ -28,7 +29,7 @@ class Opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("precond", C.c_int), ("t", C.c_int), ("k", C.c_int),
                 ("s", C.c_int), ("cg_tol", C.c_double), ("cg_max_iter", C.c_int),
                 ("newton_tol", C.c_double), ("newton_max_iter", C.c_int), ("nugget", C.c_double),
-                ("seed", C.c_uint64), ("lik_shape", C.c_double)]
+                ("seed", C.c_uint64), ("lik_shape", C.c_double), ("newton_eta_max", C.c_double)]
 
     @classmethod
     def make(cls, **kw) -> "Opts":
@@ -45,7 +46,8 @@ class Stats(C.Structure):
     _fields_ = [("newton_iters", C.c_int), ("cg_calls", C.c_int), ("cg_iters_max", C.c_int),
                 ("cg_iters_total", C.c_int), ("cg_relres_max", C.c_double), ("refine_steps", C.c_int),
                 ("true_relres_max", C.c_double), ("slq_mean", C.c_double), ("slq_stderr", C.c_double),
-                ("logdet", C.c_double), ("ms_total", C.c_double)]
+                ("logdet", C.c_double), ("ms_total", C.c_double), ("probe_relres_max", C.c_double),
+                ("probe_refine_steps", C.c_int)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -99,6 +101,9 @@ def library():
         "vl_last_error": (C.c_char_p, [vp]),
         "vl_ctx_synchronize": (st, [vp]),
         "vl_ctx_mem": (st, [vp, vp, vp]),
+        "vl_ctx_set_solve_form": (st, [vp, i32]),
+        "vl_ctx_set_wait_limit": (st, [vp, C.c_longlong]),
+        "vl_ctx_wait_probe": (st, [vp]),
         "vl_profile_enable": (st, [vp, i32]),
         "vl_profile_read": (st, [vp, C.c_char_p, i32, vp, vp, i32]),
         "vl_profile_trace": (st, [vp, C.c_char_p, i32, vp, i32, vp, vp, vp]),
@@ -252,6 +257,21 @@ class Context:
         a, b = C.c_size_t(), C.c_size_t()
         self.check(self.lib.vl_ctx_mem(self.h, C.byref(a), C.byref(b)))
         return a.value, b.value
+
+    def set_solve_form(self, form: int):
+        """Force the triangular-solve form (SOLVE_AUTO, SOLVE_SHARED, SOLVE_CLUSTER,
+        SOLVE_GRID) of every later solve on this context; SOLVE_AUTO restores the
+        per-solve choice."""
+        self.check(self.lib.vl_ctx_set_solve_form(self.h, int(form)))
+
+    def set_wait_limit(self, cycles: int):
+        """Cycle limit of every bounded device-side wait on this context (0: the default,
+        about 2 s); a wait that runs out makes the call fail with VL_ERR_TIMEOUT."""
+        self.check(self.lib.vl_ctx_set_wait_limit(self.h, int(cycles)))
+
+    def wait_probe(self):
+        """One bounded wait on a flag nothing sets: raises VLError(VL_ERR_TIMEOUT)."""
+        self.check(self.lib.vl_ctx_wait_probe(self.h))
 
     def profile(self, enable=True):
         """enable: False/0 off, True/1 kernel timing, 2 also per-level solve traces."""

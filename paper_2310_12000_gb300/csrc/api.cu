@@ -4,6 +4,7 @@
 // reads back scalars and makes the stopping decisions.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <numeric>
 #include <string>
@@ -104,6 +105,30 @@ __global__ void absmax_kernel(int n, const double* __restrict__ a, const double*
   }
 }
 
+// Smallest storage row whose response lies outside the likelihood's support (Bernoulli:
+// {0, 1}; Poisson: non-negative integers; gamma: y > 0) or whose y or offset is not finite.
+__global__ void check_inputs_kernel(int n, int lik, const double* __restrict__ y, const double* __restrict__ F,
+                                    int* __restrict__ first_bad) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+    const double v = y[s];
+    bool ok = isfinite(v) && isfinite(F[s]);
+    if (lik == VL_LIK_BERNOULLI_LOGIT)
+      ok = ok && (v == 0.0 || v == 1.0);
+    else if (lik == VL_LIK_POISSON_LOG)
+      ok = ok && v >= 0.0 && v == floor(v);
+    else
+      ok = ok && v > 0.0;
+    if (!ok) atomicMin(first_bad, s);
+  }
+}
+
+__global__ void set_wait_limit_kernel(DevStatus* st, long long cycles) { st->limit = cycles; }
+
+// One bounded wait on a flag that nothing sets (the library's timeout path).
+__global__ void wait_probe_kernel(const int* flag, DevStatus* st) {
+  if (threadIdx.x == 0) bounded_wait([&] { return ld_acquire(flag) != 0; }, st, -1);
+}
+
 // b_new <- b + 0.5 (b_new - b)
 __global__ void halve_kernel(int n, const double* __restrict__ b, double* __restrict__ bn) {
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) bn[s] = b[s] + 0.5 * (bn[s] - b[s]);
@@ -188,12 +213,24 @@ static bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Device memory that kernels on the context's device may not use (another GPU's memory).
+static bool foreign_device_ptr(Ctx* c, const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice && !device_memory_usable(a.type, a.device, c->device);
+}
+
 template <typename T>
 static vl_status stage_in(Ctx* c, Scratch& S, const T* p, size_t count, const T** out) {
   if (!p || count == 0) {
     *out = p;
     return VL_OK;
   }
+  if (foreign_device_ptr(c, p)) return fail(c, VL_ERR_INVALID_ARG, "a device pointer is not on the context's device");
   if (is_device_ptr(p)) {
     *out = p;
     return VL_OK;
@@ -208,6 +245,7 @@ static vl_status stage_in(Ctx* c, Scratch& S, const T* p, size_t count, const T*
 template <typename T>
 static vl_status stage_out(Ctx* c, const T* dev, T* p, size_t count) {
   if (!p || count == 0) return VL_OK;
+  if (foreign_device_ptr(c, p)) return fail(c, VL_ERR_INVALID_ARG, "a device pointer is not on the context's device");
   const bool d = is_device_ptr(p);
   VL_CUDA(c, cudaMemcpyAsync(p, dev, sizeof(T) * count, d ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                              c->stream));
@@ -298,58 +336,101 @@ static vl_status psi_eval(State* st, Engine<double>& E1, Scratch& S, const doubl
   return VL_OK;
 }
 
-// Solve (W + Sigma_tilde^{-1}) x = rhs (one column, float64 in/out).
-// FP64: one PCG from x = 0 (the appendix algorithm). Mixed: x enters holding a
-// starting guess (the current Newton iterate); float32 PCG solves for corrections
-// d of the float64 residual, each to the relative accuracy still missing
-// (0.5 tol ||rhs|| / ||res||, at least 1e-6), until ||rhs - A x|| <= tol ||rhs||.
+// VL_ERR_NOT_CONVERGED when a column of the engine's last PCG run stopped at cg_max_iter
+// above cg_tol.
+template <typename T>
+static vl_status cg_converged(Engine<T>& E, const vl_opts* o, const char* what) {
+  std::vector<int> iters;
+  std::vector<double> rel;
+  VL_TRY(E.column_stats(iters, rel));
+  for (int k = 0; k < E.t; ++k)
+    if (rel[k] > o->cg_tol && iters[k] >= o->cg_max_iter)
+      return fail(E.c, VL_ERR_NOT_CONVERGED, std::string(what) + ": PCG reached cg_max_iter above cg_tol");
+  return VL_OK;
+}
+
+// Newton system (W + Sigma_tilde^{-1}) x = rhs for one column (Eq. newton), float64 in and
+// out; x enters holding the current Newton iterate b, whose residual rhs - A b is grad psi(b).
+// The correction of x is solved by PCG from zero (the appendix algorithm) until
+//   ||rhs - A x|| <= target = max(cg_tol ||rhs||, eta ||rhs - A b||):
+// eta = 0 asks for the full tolerance, eta > 0 makes an inexact Newton step (Eisenstat &
+// Walker, SIAM J. Sci. Comput. 17, 1996). FP64: float64 PCG on the correction. Mixed: float32
+// PCG on corrections of the float64 residual, each to the relative accuracy still missing
+// (at least 1e-6), until the float64 residual meets the target (iterative refinement).
+// The forcing term comes from `fc` once ||grad psi(b)|| is known; fc is updated for the next
+// step. *full: the solve met cg_tol ||rhs||.
+struct Forcing {
+  double eta_max = 0.0;    // 0: every solve to the full tolerance
+  double g_prev = -1.0;    // ||grad psi|| at the previous Newton iterate (< 0: none yet)
+  double eta_prev = -1.0;
+  bool force_full = false;
+  // Eisenstat & Walker (1996), choice 2: eta_k = 0.9 (||g_k|| / ||g_{k-1}||)^2, kept at least
+  // 0.9 eta_{k-1}^2 while that exceeds 0.1, at most eta_max; eta_max while no history exists.
+  double next(double g) {
+    double eta = eta_max;
+    if (force_full || eta_max <= 0.0) {
+      eta = 0.0;
+    } else if (g_prev > 0.0) {
+      eta = 0.9 * (g / g_prev) * (g / g_prev);
+      if (eta_prev > 0.0 && 0.9 * eta_prev * eta_prev > 0.1) eta = std::max(eta, 0.9 * eta_prev * eta_prev);
+      eta = std::min(eta, eta_max);
+    }
+    g_prev = g;
+    eta_prev = eta;
+    return eta;
+  }
+};
+
 static vl_status solve1(State* st, const vl_opts* o, Engine<double>& E64, Engine<float>* E32, const double* rhs,
-                        double* x, vl_stats* stats) {
+                        double* x, Forcing* fc, vl_stats* stats, bool* full) {
   Ctx* c = st->ctx;
   const int n = (int)st->f->n;
-  int used = 0;
-  if (o->precision == VL_FP64) {
-    VL_TRY(E64.solve_A1(rhs, x, o->cg_tol, o->cg_max_iter, &used));
-    if (stats) {
-      stats->cg_calls++;
-      stats->cg_iters_total += used;
-      stats->cg_iters_max = used;
-    }
-    return VL_OK;
-  }
+  const bool fp64 = o->precision == VL_FP64;
   Scratch S(c);
   double* res = S.get<double>(n);
-  float* r32 = S.get<float>(n);
-  float* d32 = S.get<float>(n);
-  if (!res || !r32 || !d32) return fail(c, VL_ERR_OOM, "workspace exhausted (refinement)");
+  double* d64 = fp64 ? S.get<double>(n) : nullptr;
+  float* r32 = fp64 ? nullptr : S.get<float>(n);
+  float* d32 = fp64 ? nullptr : S.get<float>(n);
+  if (!res || (fp64 ? !d64 : (!r32 || !d32))) return fail(c, VL_ERR_OOM, "workspace exhausted (Newton solve)");
   VL_TRY(E64.coldot(rhs, rhs, nullptr, E64.red));
   vl_status s = VL_OK;
   const double bn = std::sqrt(read_scalar(c, E64.red, &s));
   VL_TRY(s);
-  double rel = 1.0;
+  double rn = 0.0, target = 0.0;
+  int used = 0;
   for (int pass = 0; pass < 12; ++pass) {
     VL_TRY(E64.opA(x, res));
     residual_kernel<<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, rhs, res);
     VL_TRY(E64.coldot(res, res, nullptr, E64.red));
-    const double rn = std::sqrt(read_scalar(c, E64.red, &s));
+    rn = std::sqrt(read_scalar(c, E64.red, &s));
     VL_TRY(s);
-    rel = bn > 0 ? rn / bn : 0.0;
-    if (rel <= o->cg_tol) break;
-    const double inner = std::min(0.1, std::max(1e-6, 0.5 * o->cg_tol * bn / rn));
-    convert_kernel<double, float><<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, res, r32);
-    VL_CUDA(c, cudaGetLastError());
-    VL_TRY(E32->solve_A1(r32, d32, inner, o->cg_max_iter, &used));
-    accumulate_kernel<double, float><<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, x, d32);
+    if (pass == 0) target = std::max(o->cg_tol * bn, (fc ? fc->next(rn) : 0.0) * rn);
+    if (rn <= target) break;
+    const double inner = std::min(0.1, std::max(fp64 ? 1e-15 : 1e-6, 0.5 * target / rn));
+    if (fp64) {
+      VL_TRY(E64.solve_A1(res, d64, inner, o->cg_max_iter, &used));
+      VL_TRY(cg_converged(E64, o, "Newton solve"));
+      accumulate_kernel<double, double><<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, x, d64);
+    } else {
+      convert_kernel<double, float><<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, res, r32);
+      VL_CUDA(c, cudaGetLastError());
+      VL_TRY(E32->solve_A1(r32, d32, inner, o->cg_max_iter, &used));
+      accumulate_kernel<double, float><<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, x, d32);
+    }
     VL_CUDA(c, cudaGetLastError());
     if (stats) {
       stats->cg_calls++;
       stats->cg_iters_total += used;
       stats->cg_iters_max = used;
-      stats->refine_steps++;
+      if (!fp64) stats->refine_steps++;
     }
   }
-  if (stats) stats->true_relres_max = std::max(stats->true_relres_max, rel);
-  if (rel > o->cg_tol) return fail(c, VL_ERR_NOT_CONVERGED, "mixed-precision refinement did not reach cg_tol");
+  const double rel = bn > 0 ? rn / bn : 0.0;
+  if (full) *full = rel <= o->cg_tol;
+  if (stats && rel <= o->cg_tol) stats->true_relres_max = std::max(stats->true_relres_max, rel);
+  if (rn > target)
+    return fail(c, VL_ERR_NOT_CONVERGED, fp64 ? "Newton solve did not reach its tolerance"
+                                              : "mixed-precision refinement did not reach cg_tol");
   return VL_OK;
 }
 
@@ -360,6 +441,104 @@ namespace vl {
 __global__ void repack_kernel(int64_t total, const double* __restrict__ in, float* __restrict__ out) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
     out[e] = (float)in[e];
+}
+
+// Zeroes the columns whose flag is 0 (columns that already meet the tolerance get no
+// correction: a zero right-hand side leaves its PCG column inactive).
+template <typename T>
+__global__ void mask_columns_kernel(int64_t total, int ld, const int* __restrict__ keep, T* __restrict__ X) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
+    if (!keep[e % ld]) X[e] = T(0);
+}
+
+// Float64 relative residuals ||z_i - S u_i|| / ||z_i|| of the SLQ probe solves (S the system
+// operator of the preconditioner's form, z_i = P^{1/2} r_i built again in float64 from the same
+// probes). Float32 solves are refined by float32 correction solves of the float64 residual until
+// every column meets cg_tol; this leaves T (already turned into gamma_i) alone.
+template <typename T>
+static vl_status probe_residuals(State* st, const vl_opts* o, Engine<T>& E, T* Rm, T* Zm, T* Um, const double* r1,
+                                 vl_stats* stats) {
+  Ctx* c = st->ctx;
+  Factor* f = st->f;
+  const int n = (int)f->n, t = o->t, ld = E.ld;
+  const int64_t vec = (int64_t)n * ld;
+  std::vector<double> bn(t), rn(t);
+  auto norms = [&](Engine<double>& E64, const double* X, std::vector<double>& out) -> vl_status {
+    VL_TRY(E64.coldot(X, X, nullptr, E64.red));
+    VL_CUDA(c, cudaMemcpyAsync(out.data(), E64.red, sizeof(double) * t, cudaMemcpyDeviceToHost, c->stream));
+    VL_CUDA(c, cudaStreamSynchronize(c->stream));
+    return VL_OK;
+  };
+  auto worst = [&]() {
+    double w = 0.0;
+    for (int k = 0; k < t; ++k) w = std::max(w, bn[k] > 0 ? std::sqrt(rn[k] / bn[k]) : 0.0);
+    return w;
+  };
+  if constexpr (std::is_same<T, double>::value) {
+    VL_TRY(E.opSys(Um, E.v));
+    residual_kernel<<<grid_for(c, vec), 256, 0, VL_STREAM(c)>>>(vec, Zm, E.v);
+    VL_CUDA(c, cudaGetLastError());
+    VL_TRY(norms(E, Zm, bn));
+    VL_TRY(norms(E, E.v, rn));
+    if (stats) stats->probe_relres_max = worst();
+    return VL_OK;
+  } else {
+    Scratch S(c);
+    Engine<double> E64(c);
+    VL_TRY(E64.init(f, t, o->precond, st->W, 0, /*ops_only=*/true));
+    double* Zd = S.get<double>(vec);
+    double* Ud = S.get<double>(vec);
+    double* Res = S.get<double>(vec);
+    double* sc64 = S.get<double>(n);
+    int* keep = S.get<int>(ld);
+    if (!Zd || !Ud || !Res || !sc64 || !keep) return fail(c, VL_ERR_OOM, "workspace exhausted (probe residuals)");
+    // the probes of slq_run again, in float64
+    rademacher_kernel<double><<<(n + 127) / 128, 128, 0, VL_STREAM(c)>>>(n, t, ld, f->s2u, o->seed, 0, 0, Res);
+    const int dmode = o->precond == VL_PREC_VADU ? 0 : (o->precond == VL_PREC_LVA ? 1 : 3);
+    diag_fn_kernel<<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, dmode, st->W, f->D64, sc64);
+    VL_CUDA(c, cudaGetLastError());
+    if (o->precond == VL_PREC_LRAC)
+      VL_TRY(E64.lrac_lowrank_plus(r1, Res, sc64, Zd));
+    else
+      VL_TRY(E64.opBt(Res, sc64, nullptr, nullptr, Zd));
+    VL_TRY(norms(E64, Zd, bn));
+    std::vector<int> hkeep(ld, 0);
+    double rel = 1.0;
+    int pass = 0;
+    for (;; ++pass) {
+      convert_kernel<float, double><<<grid_for(c, vec), 256, 0, VL_STREAM(c)>>>(vec, Um, Ud);
+      VL_TRY(E64.opSys(Ud, Res));
+      residual_kernel<<<grid_for(c, vec), 256, 0, VL_STREAM(c)>>>(vec, Zd, Res);
+      VL_CUDA(c, cudaGetLastError());
+      VL_TRY(norms(E64, Res, rn));
+      rel = worst();
+      if (rel <= o->cg_tol || pass == 12) break;
+      // correction solves for the columns still above cg_tol, each to the accuracy it lacks
+      double inner = 0.5;
+      for (int k = 0; k < t; ++k) {
+        const double rk = bn[k] > 0 ? std::sqrt(rn[k] / bn[k]) : 0.0;
+        hkeep[k] = rk > o->cg_tol ? 1 : 0;
+        if (hkeep[k]) inner = std::min(inner, 0.5 * o->cg_tol / rk);
+      }
+      inner = std::max(inner, 1e-6);
+      VL_CUDA(c, cudaMemcpyAsync(keep, hkeep.data(), sizeof(int) * ld, cudaMemcpyHostToDevice, c->stream));
+      convert_kernel<double, float><<<grid_for(c, vec), 256, 0, VL_STREAM(c)>>>(vec, Res, Zm);
+      mask_columns_kernel<float><<<grid_for(c, vec), 256, 0, VL_STREAM(c)>>>(vec, ld, keep, Zm);
+      VL_CUDA(c, cudaGetLastError());
+      int used = 0;
+      VL_TRY(E.pcg(Zm, Rm, inner, o->cg_max_iter, &used));
+      accumulate_kernel<float, float><<<grid_for(c, vec), 256, 0, VL_STREAM(c)>>>(vec, Um, Rm);
+      VL_CUDA(c, cudaGetLastError());
+      if (stats) stats->cg_iters_total += used;
+    }
+    if (stats) {
+      stats->probe_relres_max = rel;
+      stats->probe_refine_steps = pass;
+      stats->true_relres_max = std::max(stats->true_relres_max, rel);
+    }
+    if (rel > o->cg_tol) return fail(c, VL_ERR_NOT_CONVERGED, "SLQ probe solves: refinement did not reach cg_tol");
+    return VL_OK;
+  }
 }
 
 // SLQ (Eq. def_SLQ): probes z = P^{1/2} r, PCG on the preconditioner's system with
@@ -389,9 +568,10 @@ static vl_status slq_run(State* st, const vl_opts* o, std::vector<double>& gam, 
   diag_fn_kernel<<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, dmode, st->W, f->D64, sc64);
   convert_kernel<double, T><<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, sc64, sc);
   VL_CUDA(c, cudaGetLastError());
+  double* r1 = nullptr;
   if (o->precond == VL_PREC_LRAC) {
     // z = L r1 + W^{-1/2} r2, r1 in {+-1}^k drawn by rank index on stream 3 (Section 3.1.2)
-    double* r1 = S.get<double>((size_t)E.kr * t);
+    r1 = S.get<double>((size_t)E.kr * t);
     if (!r1) return fail(c, VL_ERR_OOM, "workspace exhausted (SLQ probes)");
     rademacher_kernel<double><<<(E.kr + 127) / 128, 128, 0, VL_STREAM(c)>>>(E.kr, t, t, nullptr, o->seed, 3, 0, r1);
     VL_CUDA(c, cudaGetLastError());
@@ -425,7 +605,7 @@ static vl_status slq_run(State* st, const vl_opts* o, std::vector<double>& gam, 
   if (relmax > o->cg_tol && itmax >= o->cg_max_iter)
     return fail(c, VL_ERR_NOT_CONVERGED, "SLQ probe solves reached cg_max_iter");
   if (logdetC) *logdetC = (o->precond == VL_PREC_LRAC) ? E.logdetC : 0.0;
-  return VL_OK;
+  return probe_residuals<T>(st, o, E, Rm, Zm, Um, r1, stats);
 }
 
 // U = (W + Sigma_tilde^{-1})^{-1} z3 for simulation columns [col0, col0 + sc),
@@ -457,7 +637,7 @@ static vl_status sim_block(State* st, const vl_opts* o, Engine<double>& E64, int
       stats->cg_iters_total += used;
       stats->cg_iters_max = used;
     }
-    return VL_OK;
+    return cg_converged(E64, o, "simulation solves");
   }
   Engine<float> E32(c);
   VL_TRY(E32.init(f, sc, o->precond, st->W, o->cg_max_iter + 1));
@@ -590,6 +770,7 @@ void vl_opts_default(vl_opts* o) {
   o->nugget = -1.0;
   o->seed = 1;
   o->lik_shape = 1.0;
+  o->newton_eta_max = 0.1;
 }
 
 vl_status vl_ctx_create(int device, void* cuda_stream, void* workspace, size_t ws_bytes, vl_ctx** out) {
@@ -711,6 +892,34 @@ vl_status vl_profile_read(vl_ctx* c, const char* cls, int t, double* ms, int64_t
   return VL_OK;
 }
 
+vl_status vl_ctx_set_wait_limit(vl_ctx* c, long long cycles) {
+  if (!c) return VL_ERR_INVALID_ARG;
+  if (cycles < 0) return fail(c, VL_ERR_INVALID_ARG, "wait limit must be >= 0 cycles");
+  set_wait_limit_kernel<<<1, 1, 0, VL_STREAM(c)>>>(c->dstatus, cycles);
+  VL_CUDA(c, cudaGetLastError());
+  VL_CUDA(c, cudaStreamSynchronize(c->stream));
+  return VL_OK;
+}
+
+vl_status vl_ctx_wait_probe(vl_ctx* c) {
+  if (!c) return VL_ERR_INVALID_ARG;
+  Scratch S(c);
+  int* flag = S.get<int>(1);
+  if (!flag) return fail(c, VL_ERR_OOM, "workspace exhausted (wait probe)");
+  VL_CUDA(c, cudaMemsetAsync(flag, 0, sizeof(int), c->stream));
+  VL_CUDA(c, status_clear(c));
+  wait_probe_kernel<<<1, 32, 0, VL_STREAM(c)>>>(flag, c->dstatus);
+  VL_CUDA(c, cudaGetLastError());
+  return check_dev_status(c, "wait probe");
+}
+
+vl_status vl_ctx_set_solve_form(vl_ctx* c, int form) {
+  if (!c) return VL_ERR_INVALID_ARG;
+  if (form < VL_SOLVE_AUTO || form > VL_SOLVE_GRID) return fail(c, VL_ERR_INVALID_ARG, "unknown solve form");
+  c->solve_form = form;
+  return VL_OK;
+}
+
 vl_status vl_ctx_mem(const vl_ctx* c, size_t* in_use, size_t* peak) {
   if (!c) return VL_ERR_INVALID_ARG;
   if (in_use) *in_use = c->arena.in_use();
@@ -762,7 +971,7 @@ vl_status vl_factor_refit(vl_factor* f, double sigma2, double range, const vl_op
   f->rho = range;
   f->nugget = nugget_of(opts, sigma2);
   lrac_drop(f);   // L_k belongs to the old covariance parameters
-  VL_CUDA(c, cudaMemsetAsync(c->dstatus, 0, sizeof(DevStatus), c->stream));
+  VL_CUDA(c, status_clear(c));
   VL_TRY(factor_rows(c, f->n, f->m, f->locs_s, f->locs_s, f->nbr, f->cov, f->sigma2, f->rho, f->nugget, f->A64, f->D64,
                      f->s2v));
   VL_TRY(refresh_transpose_values(f));
@@ -914,6 +1123,27 @@ vl_status vl_find_mode(vl_factor* f, int lik, const double* y, const double* F, 
       cudaMemsetAsync(st->F, 0, sizeof(double) * n, c->stream);
     cudaMemsetAsync(st->b, 0, sizeof(double) * n, c->stream);
     if (cudaGetLastError() != cudaSuccess) return bail(fail(c, VL_ERR_CUDA, "staging y/F"));
+    // responses in the likelihood's support, finite offsets
+    int* bad = S.get<int>(2);
+    if (!bad) return bail(fail(c, VL_ERR_OOM, "workspace exhausted (input check)"));
+    cudaMemsetAsync(bad, 0x7f, sizeof(int), c->stream);
+    check_inputs_kernel<<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, lik, st->y, st->F, bad);
+    int hb[2] = {0, 0};
+    double hv[2] = {0.0, 0.0};
+    if (cudaMemcpyAsync(hb, bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+      return bail(fail(c, VL_ERR_CUDA, "input check"));
+    if (hb[0] >= 0 && hb[0] < n) {
+      cudaMemcpyAsync(&hb[1], f->s2u + hb[0], sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+      cudaMemcpyAsync(&hv[0], st->y + hb[0], sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+      cudaMemcpyAsync(&hv[1], st->F + hb[0], sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+      cudaStreamSynchronize(c->stream);
+      char buf[256];
+      snprintf(buf, sizeof buf,
+               "vl_find_mode: y[%d] = %g (offset %g) is not a finite value in the support of the likelihood", hb[1],
+               hv[0], hv[1]);
+      return bail(fail(c, VL_ERR_INVALID_ARG, buf));
+    }
   }
   // Newton iterations (Eq. newton)
   Scratch S(c);
@@ -934,6 +1164,11 @@ vl_status vl_find_mode(vl_factor* f, int lik, const double* y, const double* F, 
   if (s != VL_OK) return bail(s);
   s = psi_eval(st, E64, S, st->b, &psi, nullptr, nullptr);
   if (s != VL_OK) return bail(s);
+  // inexact Newton: forcing terms eta_k = 0.9 (||grad psi_k|| / ||grad psi_{k-1}||)^2 with the
+  // safeguard max(eta_k, 0.9 eta_{k-1}^2) while that exceeds 0.1, capped at opts->newton_eta_max
+  // (Eisenstat & Walker 1996, choice 2); the iteration ends only after a full-tolerance solve
+  Forcing fc;
+  fc.eta_max = opts->newton_eta_max > 0.0 ? std::min(opts->newton_eta_max, 0.9) : 0.0;
   for (it = 1; it <= opts->newton_max_iter; ++it) {
     lik_kernel<<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, lik, st->shape, st->y, st->F, st->b, st->W, g, rhs, nullptr);
     s = E64.set_W(st->W);
@@ -943,8 +1178,9 @@ vl_status vl_find_mode(vl_factor* f, int lik, const double* y, const double* F, 
       if (s != VL_OK) return bail(s);
     }
     if (cudaGetLastError() != cudaSuccess) return bail(fail(c, VL_ERR_CUDA, "Newton setup"));
-    if (mixed) cudaMemcpyAsync(bn, st->b, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream);  // warm start
-    s = solve1(st, opts, E64, mixed ? &E32 : nullptr, rhs, bn, &stats);
+    cudaMemcpyAsync(bn, st->b, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream);  // the correction form
+    bool full = false;
+    s = solve1(st, opts, E64, mixed ? &E32 : nullptr, rhs, bn, &fc, &stats, &full);
     if (s != VL_OK) return bail(s);
     double psi_new = 0.0;
     s = psi_eval(st, E64, S, bn, &psi_new, nullptr, nullptr);
@@ -961,8 +1197,11 @@ vl_status vl_find_mode(vl_factor* f, int lik, const double* y, const double* F, 
     psi = psi_new;
     if (!std::isfinite(psi)) return bail(fail(c, VL_ERR_NOT_CONVERGED, "Newton: non-finite objective"));
     if (step <= opts->newton_tol * (1.0 + bmax)) {
-      converged = true;
-      break;
+      if (full) {
+        converged = true;
+        break;
+      }
+      fc.force_full = true;   // a small step from an inexact solve: confirm with a full one
     }
   }
   // W at the mode
@@ -1099,7 +1338,7 @@ vl_status vl_pred_var(vl_state* st, const double* test_locs, int64_t np, const d
     translate_kernel<<<grid_for(c, npm), 256, 0, VL_STREAM(c)>>>(npm, f->v2s, Np);
     VL_CUDA(c, cudaGetLastError());
   }
-  VL_CUDA(c, cudaMemsetAsync(c->dstatus, 0, sizeof(DevStatus), c->stream));
+  VL_CUDA(c, status_clear(c));
   VL_TRY(factor_rows(c, np, m, dq, f->locs_s, Np, f->cov, f->sigma2, f->rho, f->nugget, Ap, Dp, nullptr));
   VL_TRY(check_dev_status(c, "prediction rows"));
   VL_CUDA(c, cudaMemsetAsync(dvar, 0, sizeof(double) * np, c->stream));

@@ -180,7 +180,9 @@ struct Engine {
   // float32 and float64 blocks, so mixed-precision refinement converts in place).
   static int lead(int t_) { return t_ == 1 ? 1 : (t_ + 7) / 8 * 8; }
 
-  vl_status init(Factor* fac, int t_, int prec_, const double* W64, int lmax_) {
+  // ops_only: only the operators (opA, opA2, opSigma, opB, opBt, coldot) are used, so only
+  // their intermediate blocks are made; no Krylov vectors, no PCG state, no LRAC inverse.
+  vl_status init(Factor* fac, int t_, int prec_, const double* W64, int lmax_, bool ops_only = false) {
     f = fac;
     n = (int)f->n;
     m = f->m;
@@ -201,6 +203,7 @@ struct Engine {
     const size_t vec = (size_t)n * ld;
     T** vs[] = {&u, &r, &z, &h, &v, &y, &sv};
     for (T** p : vs) {
+      if (ops_only && p != &y && !(p == &sv && prec == VL_PREC_LRAC)) continue;
       *p = mem.get<T>(vec);
       if (!*p) return fail(c, VL_ERR_OOM, "workspace exhausted (Krylov vectors)");
       VL_CUDA(c, cudaMemsetAsync(*p, 0, sizeof(T) * vec, c->stream));
@@ -236,7 +239,13 @@ struct Engine {
       VL_CUDA(c, cudaMemsetAsync(S.Toff, 0, sizeof(double) * t * lmax, c->stream));
     }
     h_count = reinterpret_cast<int*>(c->pinned);
-    if (prec == VL_PREC_LRAC) VL_TRY(lrac_init());
+    if (prec == VL_PREC_LRAC) {
+      if (!ops_only) VL_TRY(lrac_init());
+      else if (f->lrac_k >= 1 && std::is_same<T, double>::value) {   // probes L r1 need L only
+        kr = f->lrac_k;
+        Lk = (const T*)f->L64;
+      }
+    }
     return VL_OK;
   }
 
@@ -522,6 +531,9 @@ struct Engine {
     LevelPlan L{FWD ? f->task_fwd : f->task_bwd, FWD ? f->lptr_fwd : f->lptr_bwd, FWD ? f->hptr_fwd : f->hptr_bwd, 0, 0,
                 (int)hl.size() - 1, c->gbar, c->dstatus, nullptr};
     const char* cls = FWD ? "sptrsv_fwd" : "sptrsv_bwd";
+    // form: chosen from n, t and the widest level, or forced by vl_ctx_set_solve_form
+    // (VL_SOLVE_SHARED concerns single-column solves; block solves keep the automatic choice)
+    const int form = (c->solve_form == VL_SOLVE_SHARED && t > 1) ? VL_SOLVE_AUTO : c->solve_form;
     if (c->prof.trace) {
       if (c->prof.dtrace_len < hl.size()) {
         if (c->prof.dtrace) c->arena.release(c->prof.dtrace);
@@ -539,6 +551,10 @@ struct Engine {
       const int tpb = 16 * (32 / lpv);   // row teams per 512-thread block
       const size_t smem = sizeof(T) * (size_t)tpb * (t == 1 ? 1 : ld);   // heavy-row partials
       level_cut(hl, hh, hw, t == 1 ? 1 : ld / VecT<T>::n, &L.l_head, &L.l_tail);
+      if (form == VL_SOLVE_GRID) {   // forced: every level on the whole grid (no single-block head / tail)
+        L.l_head = 0;
+        L.l_tail = L.nlev;
+      }
       const int body_rows = hl[L.l_tail] - hl[L.l_head];
       // at most two blocks per SM: fewer arrivals per grid barrier
       const int maxb = std::min(resident_blocks(c, fn, 512, smem), 2 * c->num_sms);
@@ -559,7 +575,10 @@ struct Engine {
     };
     int widest = 0;
     for (size_t lv = 0; lv + 1 < hl.size(); ++lv) widest = std::max(widest, hl[lv + 1] - hl[lv]);
-    if (t == 1 && (size_t)n * sizeof(T) <= kSmemSolveBytes) {
+    const bool smem_fits = t == 1 && (size_t)n * sizeof(T) <= kSmemSolveBytes;
+    if (form == VL_SOLVE_SHARED && !smem_fits)
+      return fail(c, VL_ERR_INVALID_ARG, "solve form VL_SOLVE_SHARED needs n * sizeof(value) <= 200 KiB");
+    if (smem_fits && (form == VL_SOLVE_AUTO || form == VL_SOLVE_SHARED)) {
       // small system: one block with x in shared memory (see sptrsv_t1_smem_kernel)
       constexpr int LPV1 = FWD ? 8 : 16;
       auto fn = sptrsv_t1_smem_kernel<T, FWD, LPV1>;
@@ -582,14 +601,17 @@ struct Engine {
       }
       return VL_OK;
     }
-    if (t > 1) {
+    if (t > 1 && form != VL_SOLVE_GRID) {
       // narrow level profile: one thread-block cluster (see sptrsv_cluster_kernel)
       vl_status out = VL_OK;
       bool done = false;
       VL_TRY(with_shape<T>(ld, [&](auto Lc, auto N, auto U) {
         constexpr int LPV = decltype(Lc)::value, NV = decltype(N)::value;
         if constexpr (NV > 2) {
-          return VL_OK;   // very wide blocks stay on the grid kernel (register budget of 1024-thread blocks)
+          // very wide blocks stay on the grid kernel (register budget of 1024-thread blocks)
+          return form == VL_SOLVE_CLUSTER ? fail(c, VL_ERR_INVALID_ARG, "solve form VL_SOLVE_CLUSTER covers float64 "
+                                                                         "blocks of at most 128 columns")
+                                          : VL_OK;
         } else {
         auto fn = sptrsv_cluster_kernel<T, FWD, LPV, NV, decltype(U)::value>;
         const int tpb = 32 * (32 / LPV);
@@ -597,7 +619,10 @@ struct Engine {
         const size_t smem_max = sizeof(T) * (size_t)tpb * (LPV * NV * VecT<T>::n);   // widest row this shape covers
         const int cs_max = cluster_size((const void*)fn, smem, smem_max);
         const int rounds = n <= kSharedRows ? VL_SHARED_CLUSTER_ROUNDS : VL_BLOCK_CLUSTER_ROUNDS;
-        if (cs_max < 1 || widest > rounds * cs_max * tpb) return VL_OK;
+        if (cs_max < 1)
+          return form == VL_SOLVE_CLUSTER ? fail(c, VL_ERR_INVALID_ARG, "no thread-block cluster fits this solve")
+                                          : VL_OK;
+        if (form == VL_SOLVE_AUTO && widest > rounds * cs_max * tpb) return VL_OK;
         const int cs = fit_cluster(widest, tpb, cs_max);
         L.l_head = 0;
         L.l_tail = L.nlev;
@@ -634,7 +659,7 @@ struct Engine {
         return VL_OK;
       }
     }
-    if (t == 1) {
+    if (t == 1 && form != VL_SOLVE_GRID) {
       // one thread-block cluster walks all levels (see sptrsv_t1_cluster_kernel)
       constexpr int LPV1 = FWD ? 8 : 16;   // backward rows can list hundreds of dependents
       auto fn = sptrsv_t1_cluster_kernel<T, FWD, LPV1>;
@@ -643,7 +668,10 @@ struct Engine {
       // the widest levels of large problems need the whole grid
       const int cta_teams = (1024 / 32) * (32 / LPV1);
       const int rounds = n <= kSharedRows ? VL_SHARED_CLUSTER_ROUNDS : VL_T1_CLUSTER_ROUNDS;
-      if (cs_max >= 2 && widest <= rounds * cs_max * cta_teams) {
+      if (form == VL_SOLVE_CLUSTER && cs_max < 1)
+        return fail(c, VL_ERR_INVALID_ARG, "no thread-block cluster fits this solve");
+      if ((form == VL_SOLVE_CLUSTER && cs_max >= 1) ||
+          (form == VL_SOLVE_AUTO && cs_max >= 2 && widest <= rounds * cs_max * cta_teams)) {
         const int cs = fit_cluster(widest, cta_teams, cs_max);
         L.l_head = 0;
         L.l_tail = L.nlev;

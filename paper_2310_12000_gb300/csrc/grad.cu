@@ -374,7 +374,7 @@ extern "C" vl_status vl_lml_grad(vl_state* st, const vl_opts* o, double* grad, d
   const size_t smem_max = sizeof(double) * (size_t)kDerivWarps * (64 * 65 + 4 * 64);
   VL_CUDA(c, cudaFuncSetAttribute(factor_deriv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
   for (int par = 0; par < 2; ++par) {
-    VL_CUDA(c, cudaMemsetAsync(c->dstatus, 0, sizeof(DevStatus), c->stream));
+    VL_CUDA(c, status_clear(c));
     factor_deriv_kernel<<<(n + kDerivWarps - 1) / kDerivWarps, threads, smem, VL_STREAM(c)>>>(
         n, m, f->locs_s, f->nbr, f->A64, f->cov, f->sigma2, f->rho, f->nugget, par, dA, dD, c->dstatus);
     if (f->nnz > 0) gather_kernel<<<grid_for(c, f->nnz), 256, 0, VL_STREAM(c)>>>(f->nnz, f->permT, dA, dAT);

@@ -282,7 +282,7 @@ vl_status build_graph_impl(Factor* f, const int32_t* N_v, const double* locs_v, 
   // levels
   VL_CUDA(c, cudaMemsetAsync(f->lev_fwd, 0xff, sizeof(int) * n, c->stream));
   VL_CUDA(c, cudaMemsetAsync(f->lev_bwd, 0xff, sizeof(int) * n, c->stream));
-  VL_CUDA(c, cudaMemsetAsync(c->dstatus, 0, sizeof(DevStatus), c->stream));
+  VL_CUDA(c, status_clear(c));
   {
     int nn = n, mm = m;
     const int32_t* a1 = f->nbr;

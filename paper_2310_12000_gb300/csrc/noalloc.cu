@@ -76,13 +76,15 @@ vl_status noalloc_scratch(Ctx* c, char** out) {
   return VL_OK;
 }
 
-bool on_device(const void* p) {
+// Device (or managed) memory of the given device: the kernels of this call run on the
+// context's device and must not touch another GPU's memory.
+bool on_device(const void* p, int device) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  return device_memory_usable(a.type, a.device, device);
 }
 
 }  // namespace
@@ -96,8 +98,8 @@ extern "C" vl_status vl_apply_A_noalloc(vl_state* st, const double* X, int t, do
   Factor* f = S->f;
   if (!X || !Y || t < 1 || t > 256)
     return fail(c, VL_ERR_INVALID_ARG, "vl_apply_A_noalloc: X and Y must be non-null and 1 <= t <= 256");
-  if (!on_device(X) || !on_device(Y))
-    return fail(c, VL_ERR_INVALID_ARG, "vl_apply_A_noalloc: X and Y must be device pointers");
+  if (!on_device(X, c->device) || !on_device(Y, c->device))
+    return fail(c, VL_ERR_INVALID_ARG, "vl_apply_A_noalloc: X and Y must be device pointers on the context's device");
   const int n = (int)f->n, m = f->m;
   const int ld = Engine<double>::lead(t);
   const size_t vec = (size_t)n * ld * sizeof(double);

@@ -80,7 +80,7 @@ vl_status check_dev_status(Ctx* c, const char* what) {
   if (c->prof.on && c->prof.pending.size() > 256) prof_drain(c);
   if (c->hstatus->code != 0) {
     const int code = c->hstatus->code, row = c->hstatus->row;
-    VL_CUDA(c, cudaMemsetAsync(c->dstatus, 0, sizeof(DevStatus), c->stream));
+    VL_CUDA(c, status_clear(c));
     VL_CUDA(c, cudaStreamSynchronize(c->stream));
     char buf[256];
     if (code == VL_ERR_NOT_SPD)

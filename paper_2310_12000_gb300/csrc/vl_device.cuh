@@ -38,16 +38,19 @@ __device__ __forceinline__ void raise_error(DevStatus* st, int code, int row) {
 }
 
 // Bounded wait until pred() holds. Returns false (after recording VL_ERR_TIMEOUT)
-// when the wait runs past kSpinLimitCycles, or at once when another wait aborted.
+// when the wait runs past the status block's limit (kSpinLimitCycles unless a
+// positive limit was set on the context), or at once when another wait aborted.
 template <typename Pred>
 __device__ __forceinline__ bool bounded_wait(Pred pred, DevStatus* st, int row) {
   if (pred()) return true;
   long long t0 = clock64();
+  const long long set = *(volatile const long long*)&st->limit;
+  const long long limit = set > 0 ? set : kSpinLimitCycles;
   for (int it = 1;; ++it) {
     if (pred()) return true;
     if ((it & 31) == 0) {
       if (ld_volatile(&st->abort)) return false;
-      if (clock64() - t0 > kSpinLimitCycles) {
+      if (clock64() - t0 > limit) {
         raise_error(st, VL_ERR_TIMEOUT, row);
         return false;
       }

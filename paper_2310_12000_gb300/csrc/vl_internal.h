@@ -22,7 +22,9 @@ struct DevStatus {
   int row;
   int abort;
   int pad;
+  long long limit;   // cycles a bounded wait may take (0: the default); kept by status_clear
 };
+constexpr size_t kStatusClearBytes = 4 * sizeof(int);   // code, row, abort, pad
 
 // ----------------------------------------------------------------------------- arena
 // First-fit sub-allocator over one device buffer (the caller's workspace).
@@ -80,6 +82,7 @@ struct Ctx {
   Profiler prof;
   int64_t launches = 0;           // kernels launched on this context
   unsigned* gbar = nullptr;       // grid-barrier state {count, generation} (device)
+  int solve_form = 0;             // vl_solve_form: 0 = chosen per solve, else forced
   int refs = 1;                   // the context itself + every live factor and state
   bool closed = false;            // vl_ctx_destroy was called
 };
@@ -175,9 +178,18 @@ struct State {
 };
 
 // ----------------------------------------------------------------------------- helpers
+// Whether memory that the CUDA driver describes as (type, device) may be handed straight to
+// kernels running on device ctx_device: managed memory, or device memory of that device.
+// Host-callable pure logic (tested on the CPU).
+inline bool device_memory_usable(int type, int device, int ctx_device) {
+  return type == cudaMemoryTypeManaged || (type == cudaMemoryTypeDevice && device == ctx_device);
+}
+
 vl_status cuda_fail(Ctx* c, cudaError_t e, const char* what);
 vl_status fail(Ctx* c, vl_status s, const std::string& msg);
 vl_status check_dev_status(Ctx* c, const char* what);   // syncs the stream
+// Clears the device status (error code, row, abort flag), keeping the wait limit.
+inline cudaError_t status_clear(Ctx* c) { return cudaMemsetAsync(c->dstatus, 0, kStatusClearBytes, c->stream); }
 int resident_blocks(Ctx* c, const void* kernel, int block, size_t smem);
 
 #define VL_CUDA(ctx, call)                                                 \

@@ -21,6 +21,7 @@ from __future__ import annotations
 import types
 
 import numpy as np
+import scipy.sparse as sp
 
 from oracle import geometry, laplace as la, vecchia
 
@@ -90,3 +91,25 @@ def gamma_lower_bound(D, W) -> float:
     """Theorem 3.1 (VADU): every eigenvalue of P^{-1/2} A P^{-T/2} is at least
     min_i (D_i W_ii + 1)^{-1}, so gamma_i / n is at least the log of it."""
     return -float(np.log(np.max(D * W + 1.0)))
+
+
+def solve_backward_error(N, A, X, Y, transpose: bool = False) -> float:
+    """Componentwise backward error of a unit-triangular solve Y = B^{-1} X (or B^{-T} X):
+    max over entries of |X - M Y| / (|X| + |M_off| |Y|), M = B or B^T. A substitution in a
+    precision with unit roundoff u keeps it below gamma_k (rows of at most k terms; Higham,
+    Accuracy and Stability of Numerical Algorithms, Thm 8.5), whatever the size."""
+    B = vecchia.B_matrix(N, A)
+    M = (B.T if transpose else B).tocsr()
+    off = abs(M - sp.identity(M.shape[0], format="csr"))
+    res = np.abs(X - M @ Y)
+    scale = np.abs(X) + off @ np.abs(Y)
+    return float(np.max(res / np.maximum(scale, np.finfo(float).tiny)))
+
+
+def max_row_terms(N, transpose: bool = False) -> int:
+    """Terms of the longest row of B (m + 1) or of B^T (1 + most dependents of one point)."""
+    valid = N >= 0
+    if not transpose:
+        return int(valid.sum(1).max(initial=0)) + 1
+    cnt = np.bincount(N[valid].ravel(), minlength=N.shape[0])
+    return int(cnt.max(initial=0)) + 1

@@ -36,6 +36,7 @@ def test_version_and_defaults(lib):
     o = vl.Opts.make()
     assert (o.t, o.s, o.precond, o.precision, o.cg_max_iter) == (50, 100, vl.PREC_VADU, vl.FP64, 1000)
     assert o.cg_tol == 1e-6 and o.newton_tol == 1e-9 and o.nugget == -1.0 and o.lik_shape == 1.0
+    assert o.newton_eta_max == 0.1
 
 
 def test_context_creation_fails_cleanly_without_gpu(lib):
@@ -75,7 +76,7 @@ def test_binding_structs_and_constants_match_the_c_header(tmp_path):
             lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
     consts = ["COV_EXPONENTIAL", "COV_MATERN15", "LIK_BERNOULLI_LOGIT", "LIK_POISSON_LOG", "LIK_GAMMA_LOG", "PREC_VADU",
               "PREC_LVA", "PREC_LRAC", "FP64", "FP32_REFINE", "OP_A", "OP_PINV", "OP_B", "OP_BT", "OP_BINV",
-              "OP_BTINV", "OP_SIGMA", "OP_A2"]
+              "OP_BTINV", "OP_SIGMA", "OP_A2", "SOLVE_AUTO", "SOLVE_SHARED", "SOLVE_CLUSTER", "SOLVE_GRID"]
     for name in consts:
         lines.append(f'  printf("const {name} %d\\n", (int)VL_{name});')
     lines += ["  return 0;", "}"]

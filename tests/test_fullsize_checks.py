@@ -52,3 +52,25 @@ def test_checks_accept_the_oracle_and_reject_planted_mistakes():
 
     lb_g = fs.gamma_lower_bound(f.D, md.W)
     assert np.all(gam / P.n >= lb_g)
+
+
+def test_solve_backward_error_accepts_exact_solves_and_rejects_planted_mistakes():
+    import scipy.sparse.linalg as spla
+    P = wl.make_problem("c3_grid1m", n=3000)
+    f = la.build_factor(P.locs, P.order, P.cov, P.sigma2, P.rho, P.m, P.nugget)
+    X = np.random.default_rng(2).standard_normal((P.n, 4))
+    kf, kb = fs.max_row_terms(f.N), fs.max_row_terms(f.N, transpose=True)
+    assert kf == P.m + 1 and kb > kf
+    u = 2.0 ** -53
+    Y = spla.spsolve_triangular(f.B.tocsr(), X, lower=True)
+    assert fs.solve_backward_error(f.N, f.A, X, Y) <= kf * u * 4
+    Yt = spla.spsolve_triangular(f.B.T.tocsr(), X, lower=False)
+    assert fs.solve_backward_error(f.N, f.A, X, Yt, transpose=True) <= kb * u * 4
+    # one wrong entry, a transposed solve and a solve with another row's weights are caught
+    bad = Y.copy()
+    bad[1234, 2] *= 1 + 1e-9
+    assert fs.solve_backward_error(f.N, f.A, X, bad) > 1e3 * kf * u
+    assert fs.solve_backward_error(f.N, f.A, X, Yt) > 1e3 * kf * u
+    A2 = f.A.copy()
+    A2[[10, 11]] = A2[[11, 10]]
+    assert fs.solve_backward_error(f.N, A2, X, Y) > 1e3 * kf * u

@@ -1,0 +1,191 @@
+"""Every form of the level-scheduled triangular solves against the oracle, through the C ABI.
+
+The preconditioners of Section 3.1.1 and Sigma_tilde = B^{-1} D B^{-T} are applied by solves
+with B and B^T. A solve runs in one of three forms: one block with x in shared memory
+(single-column solves of small systems), one thread-block cluster, or the cooperative grid
+with a bounded software barrier per level (large problems). The automatic choice depends
+on n, t and the widest level, so the small parity cases elsewhere reach only the first two;
+here each form is forced (vl_ctx_set_solve_form) and checked:
+
+* every operator of vl_apply at t = 1, 5, 40 and 50, in float64 and float32, element by
+  element against the oracle's dense float64 result under the rounding-error bound of the
+  operator (tests/errbounds.py: gamma_k of the rows' dot products, propagated through |B^{-1}|
+  for the solves); float64 results also within 1e-9 relative;
+* the Laplace mode, L^VLA, every SLQ term (float64, 1e-9) and the mixed-precision L^VLA
+  (1e-4) with the whole path in that form;
+* at n = 300,000 of the grid workload, where the automatic choice takes the grid (or cluster)
+  form with the single-block head and tail: neighbour sets and factor rows of sampled rows
+  against the oracle, and the componentwise backward error of B^{-1} X and B^{-T} X on every
+  element (Higham, Thm 8.5: below gamma_k, rows of at most k terms).
+"""
+import numpy as np
+import pytest
+
+import errbounds as eb
+import fullsize as fs
+import workloads as wl
+from oracle import laplace as la
+
+pytestmark = pytest.mark.gpu
+
+FORMS = ["shared", "cluster", "grid"]
+FP64_TIGHT = dict(cg_tol=1e-12, newton_tol=1e-10, cg_max_iter=2000)
+
+
+@pytest.fixture(scope="module")
+def vl():
+    import paper_2310_12000_gb300 as vl
+    vl.library()
+    return vl
+
+
+@pytest.fixture(scope="module")
+def ctx(vl):
+    c = vl.Context(0, ws_bytes=8 << 30)
+    yield c
+    c.set_solve_form(vl.SOLVE_AUTO)
+
+
+def _form(vl, name):
+    return {"auto": vl.SOLVE_AUTO, "shared": vl.SOLVE_SHARED, "cluster": vl.SOLVE_CLUSTER,
+            "grid": vl.SOLVE_GRID}[name]
+
+
+_CACHE = {}
+
+
+def _oracle(P, key):
+    if key not in _CACHE:
+        f = la.build_factor(P.locs, P.order, P.cov, P.sigma2, P.rho, P.m, P.nugget)
+        md = la.find_mode(f, P.y, P.F, P.lik, newton_tol=1e-10)
+        _CACHE[key] = (f, md)
+    return _CACHE[key]
+
+
+@pytest.fixture(scope="module")
+def op_case(ctx, vl):
+    """A factor and a mode (float64, automatic forms) of the c1 recipe at n = 700; the
+    operators are then applied with each forced form."""
+    P = wl.make_problem("c1_n2000", n=700)
+    f, md = _oracle(P, "c1_700")
+    fac = ctx.build_factor(P.locs, P.order, P.cov, P.sigma2, P.rho, P.m)
+    ctx.set_solve_form(vl.SOLVE_AUTO)
+    st = fac.find_mode(P.lik, P.y, P.F, vl.Opts.make(**FP64_TIGHT))
+    return P, f, md, st
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("t", [1, 5, 40, 50])
+@pytest.mark.parametrize("form", FORMS)
+def test_operators_by_form(ctx, vl, op_case, form, t, prec):
+    P, f, md, st = op_case
+    ops = {"A": vl.OP_A, "PINV": vl.OP_PINV, "B": vl.OP_B, "BT": vl.OP_BT, "BINV": vl.OP_BINV,
+           "BTINV": vl.OP_BTINV, "SIGMA": vl.OP_SIGMA, "A2": vl.OP_A2}
+    opts = vl.Opts.make(precision=vl.FP64 if prec == "fp64" else vl.FP32_REFINE)
+    X = np.random.default_rng(100 + t).standard_normal((P.n, t))
+    Xv = X[f.order]
+    ctx.set_solve_form(_form(vl, form))
+    try:
+        Y = {op: st.apply(op, X, opts)[f.order] for op in ops.values()}
+    finally:
+        ctx.set_solve_form(vl.SOLVE_AUTO)
+    B, D, W = f.B, f.D, md.W
+    Bd = B.toarray()
+    dsc = 1.0 / (W + 1.0 / D)
+    ref = {
+        vl.OP_B: Bd @ Xv, vl.OP_BT: Bd.T @ Xv,
+        vl.OP_A: W[:, None] * Xv + Bd.T @ ((Bd @ Xv) / D[:, None]),
+        vl.OP_BINV: np.linalg.solve(Bd, Xv), vl.OP_BTINV: np.linalg.solve(Bd.T, Xv),
+    }
+    ref[vl.OP_SIGMA] = np.linalg.solve(Bd, D[:, None] * ref[vl.OP_BTINV])
+    ref[vl.OP_PINV] = np.linalg.solve(Bd, dsc[:, None] * ref[vl.OP_BTINV])
+    ref[vl.OP_A2] = ref[vl.OP_SIGMA] + Xv / W[:, None]
+    u = eb.U64 if prec == "fp64" else eb.U32
+    bound = eb.operator_bounds(B, D, W, dsc, Xv, Y, ops, u)
+    for name, op in ops.items():
+        err = np.abs(Y[op] - ref[op])
+        ok = err <= eb.BOUND_SLACK * bound[op]
+        assert ok.all(), (form, t, prec, name, float((err / bound[op]).max()))
+        if prec == "fp64":
+            assert err.max() <= 1e-9 * np.abs(ref[op]).max(), (form, t, name)
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("name,n", [("c1_n2000", None), ("c3_grid1m", 3000)])
+def test_mode_and_lml_by_form(ctx, vl, form, name, n):
+    P = wl.make_problem(name, n=n)
+    t = 50
+    opts = vl.Opts.make(t=t, **FP64_TIGHT)
+    f, md = _oracle(P, (name, n))
+    ctx.set_solve_form(_form(vl, form))
+    try:
+        fac = ctx.build_factor(P.locs, P.order, P.cov, P.sigma2, P.rho, P.m, opts)
+        st = fac.find_mode(P.lik, P.y, P.F, opts)
+        lml = st.log_marglik(opts)
+        g = st.slq_gammas(t)
+        o32 = vl.Opts.make(t=t, precision=vl.FP32_REFINE, cg_tol=1e-6, newton_tol=1e-7)
+        st32 = fac.find_mode(P.lik, P.y, P.F, o32)
+        lml32, s32 = st32.log_marglik(o32, with_stats=True)
+    finally:
+        ctx.set_solve_form(vl.SOLVE_AUTO)
+    b_ref = la.mode_user(f, md)
+    assert np.max(np.abs(st.mode - b_ref)) / np.max(np.abs(b_ref)) < 1e-9
+    L_ref, _, g_ref = la.lml_slq(f, md, t, 1)
+    assert np.max(np.abs(g - g_ref) / np.maximum(np.abs(g_ref), 1.0)) < 1e-9
+    assert abs(lml - L_ref) / abs(L_ref) < 1e-9
+    assert abs(lml32 - L_ref) / abs(L_ref) < 1e-4
+    assert st32.mode_stats()["true_relres_max"] <= 1e-6
+
+
+def test_forced_form_that_cannot_run_is_refused(ctx, vl, op_case):
+    """A forced shared-memory solve of a system too large for one block's shared memory
+    fails cleanly, and the context keeps working."""
+    P = wl.make_problem("c1_n2000", n=30000)
+    fac = ctx.build_factor(P.locs, P.order, P.cov, P.sigma2, P.rho, P.m)
+    st = fac.find_mode(P.lik, P.y, P.F, vl.Opts.make(cg_tol=1e-8))
+    ctx.set_solve_form(vl.SOLVE_SHARED)
+    try:
+        with pytest.raises(vl.VLError) as e:
+            st.apply(vl.OP_BINV, np.ones((P.n, 1)), vl.Opts.make())
+        assert e.value.status == 1 and "SHARED" in str(e.value)
+    finally:
+        ctx.set_solve_form(vl.SOLVE_AUTO)
+    with pytest.raises(vl.VLError):
+        ctx.set_solve_form(7)
+    Y = st.apply(vl.OP_B, np.ones((P.n, 1)), vl.Opts.make())
+    assert np.all(np.isfinite(Y))
+
+
+@pytest.mark.parametrize("form", ["auto", "grid", "cluster"])
+def test_large_solves_by_form(ctx, vl, form):
+    """n = 300,000 of the grid-with-gaps workload (m = 20, hundreds of levels)."""
+    P = wl.make_problem("c3_grid1m", n=300_000)
+    n, m = P.n, P.m
+    fac = ctx.build_factor(P.locs, P.order, P.cov, P.sigma2, P.rho, m)
+    ex = fac.export()
+    locs_v = P.locs[P.order]
+    rows = fs.sample_rows(n, m, 120, 1)
+    N_ref, A_ref, D_ref = fs.factor_rows(locs_v, rows, m, P.cov, P.sigma2, P.rho, P.nugget)
+    assert np.array_equal(ex["N"][rows], N_ref)
+    assert np.max(np.abs(ex["A"][rows] - A_ref)) < 1e-9 * max(1.0, np.max(np.abs(A_ref)))
+    assert np.max(np.abs(ex["D"][rows] - D_ref) / D_ref) < 1e-9
+    st = fac.find_mode(P.lik, P.y, P.F, vl.Opts.make(precision=vl.FP32_REFINE, cg_tol=1e-6, newton_tol=1e-6,
+                                                      cg_max_iter=3000))
+    kf, kb = fs.max_row_terms(ex["N"]), fs.max_row_terms(ex["N"], transpose=True)
+    ctx.set_solve_form(_form(vl, form))
+    try:
+        for prec, u in (("fp64", eb.U64), ("fp32", eb.U32)):
+            opts = vl.Opts.make(precision=vl.FP64 if prec == "fp64" else vl.FP32_REFINE)
+            for t in (1, 50):
+                X = np.random.default_rng(t).standard_normal((n, t))
+                Xv = X[P.order]
+                Y = st.apply(vl.OP_BINV, X, opts)[P.order]
+                Yt = st.apply(vl.OP_BTINV, X, opts)[P.order]
+                assert np.all(np.isfinite(Y)) and np.all(np.isfinite(Yt))
+                # X and the weights are rounded to the working precision first: 2u more
+                w = fs.solve_backward_error(ex["N"], ex["A"], Xv, Y)
+                wt = fs.solve_backward_error(ex["N"], ex["A"], Xv, Yt, transpose=True)
+                assert w <= eb.BOUND_SLACK * (eb.gamma(kf, u) + 2 * u), (prec, t, w)
+                assert wt <= eb.BOUND_SLACK * (eb.gamma(kb, u) + 2 * u), (prec, t, wt)
+    finally:
+        ctx.set_solve_form(vl.SOLVE_AUTO)

@@ -222,6 +222,45 @@ def test_vadu_identity_factor_gives_exact_one_step():
     assert it == 1
 
 
+def test_lva_identity_factor_closed_form():
+    """m = 0: B = I and D = diag(Sigma), so P_LVA = D^{-1} and the preconditioned matrix is
+    D^{1/2} (W + D^{-1}) D^{1/2} = I + D W (Section 3.1.1). Every Rademacher probe then gives
+    gamma_i = sum_j r_j^2 log(1 + D_j W_j) = sum_j log(1 + D_j W_j) exactly, and the LVA split
+    sum log D + log det P_LVA + gamma = sum log(1 + D W) is the exact log det(Sigma_tilde W + I).
+    A sign error in log det P_LVA = -sum log D would move the total by 2 sum log D."""
+    P = wl.tiny_problem(60, 0, lik=la.LIK_POISSON_LOG, rho=0.2, F0=0.4)
+    f = la.build_factor(P.locs, P.order, P.cov, P.sigma2, P.rho, 0, P.nugget)
+    md = la.find_mode(f, P.y, P.F, P.lik, newton_tol=1e-12)
+    closed = float(np.sum(np.log1p(f.D * md.W)))
+    L, ld, g = la.lml_slq(f, md, 7, 3, prec=la.PREC_LVA)
+    assert np.allclose(g, closed, rtol=1e-12, atol=1e-12)
+    assert abs(ld - closed) < 1e-12 * abs(closed)
+    assert abs(la.logdet_P(f, md.W, la.PREC_LVA) + np.sum(np.log(f.D))) < 1e-12
+    L_ex, ld_ex = la.lml_exact(f, md)
+    assert abs(ld - ld_ex) < 1e-11 * abs(ld_ex) and abs(L - L_ex) < 1e-11 * abs(L_ex)
+
+
+def test_lva_estimate_brackets_the_exact_logdet():
+    """With neighbours (m = 6), the LVA split with a dense-eigendecomposition SLQ over 4000
+    Rademacher probes lies within 4 standard errors of the exact log det(Sigma_tilde W + I), and
+    the oracle's Lanczos gammas equal the dense quadratic forms r^T log(M_LVA) r."""
+    P = wl.tiny_problem(120, 6, rho=0.25, seed=5)
+    f = la.build_factor(P.locs, P.order, P.cov, P.sigma2, P.rho, P.m, P.nugget)
+    md = la.find_mode(f, P.y, P.F, P.lik, newton_tol=1e-12)
+    M = _dense_M(f, md.W, la.PREC_LVA)
+    th, V = np.linalg.eigh(M)
+    logM = (V * np.log(th)) @ V.T
+    R = la.probes(f, 4000, seed=9)
+    g_dense = np.einsum("ij,ij->j", R, logM @ R)
+    base = float(np.sum(np.log(f.D))) + la.logdet_P(f, md.W, la.PREC_LVA)
+    _, ld_ex = la.lml_exact(f, md)
+    se = g_dense.std(ddof=1) / math.sqrt(len(g_dense))
+    assert abs(base + g_dense.mean() - ld_ex) < 4 * se
+    _, ld_slq, g = la.lml_slq(f, md, 6, 9, prec=la.PREC_LVA)
+    assert np.allclose(g, g_dense[:6], rtol=1e-10, atol=1e-10)
+    assert abs(ld_slq - (base + g.mean())) < 1e-10 * abs(ld_slq)
+
+
 @pytest.mark.parametrize("prec", [la.PREC_VADU, la.PREC_LVA])
 def test_theorem_3_1_eigenvalue_bounds(prec):
     P = wl.tiny_problem(200, 10, rho=0.2)

@@ -26,16 +26,22 @@ def test_apply_A_noalloc_matches_workspace_product():
         ref = st.apply(vl.OP_A, X, opts)
         Xd = torch.from_numpy(X).cuda()
         Yd = torch.full_like(Xd, float("nan"))
+        torch.cuda.synchronize()
+        mem_before = ctx.mem()
         st.apply_A_noalloc(Xd, Yd)
         torch.cuda.synchronize()
+        # the context workspace is not touched: neither its use nor its peak moves
+        assert ctx.mem() == mem_before, (call, t)
         Y = Yd.cpu().numpy()
         assert np.max(np.abs(Y - ref)) <= 1e-12 * np.max(np.abs(ref)), (call, t)
     # beyond the fixed array: a clear error, nothing written
-    Xd = torch.zeros((P.n, 256), dtype=torch.float64, device="cuda")
+    Xd = torch.ones((P.n, 256), dtype=torch.float64, device="cuda")
     Yd = torch.zeros_like(Xd)
     with pytest.raises(vl.VLError) as e:
         st.apply_A_noalloc(Xd, Yd)
     assert "64 MiB" in str(e.value) and e.value.status == 1
+    torch.cuda.synchronize()
+    assert int(torch.count_nonzero(Yd)) == 0
     # host buffers are refused by the entry point (it has nowhere to stage them)
     with pytest.raises(vl.VLError) as e:
         st.apply_A_noalloc(np.zeros((P.n, 2)), Yd[:, :2].contiguous())
