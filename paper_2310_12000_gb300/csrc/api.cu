@@ -505,8 +505,10 @@ static vl_status probe_residuals(State* st, const vl_opts* o, Engine<T>& E, T* R
     std::vector<int> hkeep(ld, 0);
     double rel = 1.0;
     int pass = 0;
+    // the solution is carried in float64 from here on: a float32 copy of it could not hold
+    // a residual below about cond * 2^-24
+    convert_kernel<float, double><<<grid_for(c, vec), 256, 0, VL_STREAM(c)>>>(vec, Um, Ud);
     for (;; ++pass) {
-      convert_kernel<float, double><<<grid_for(c, vec), 256, 0, VL_STREAM(c)>>>(vec, Um, Ud);
       VL_TRY(E64.opSys(Ud, Res));
       residual_kernel<<<grid_for(c, vec), 256, 0, VL_STREAM(c)>>>(vec, Zd, Res);
       VL_CUDA(c, cudaGetLastError());
@@ -527,7 +529,7 @@ static vl_status probe_residuals(State* st, const vl_opts* o, Engine<T>& E, T* R
       VL_CUDA(c, cudaGetLastError());
       int used = 0;
       VL_TRY(E.pcg(Zm, Rm, inner, o->cg_max_iter, &used));
-      accumulate_kernel<float, float><<<grid_for(c, vec), 256, 0, VL_STREAM(c)>>>(vec, Um, Rm);
+      accumulate_kernel<double, float><<<grid_for(c, vec), 256, 0, VL_STREAM(c)>>>(vec, Ud, Rm);
       VL_CUDA(c, cudaGetLastError());
       if (stats) stats->cg_iters_total += used;
     }

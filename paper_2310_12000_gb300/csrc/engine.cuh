@@ -659,7 +659,7 @@ struct Engine {
         return VL_OK;
       }
     }
-    if (t == 1 && form != VL_SOLVE_GRID) {
+    if (t == 1) {
       // one thread-block cluster walks all levels (see sptrsv_t1_cluster_kernel)
       constexpr int LPV1 = FWD ? 8 : 16;   // backward rows can list hundreds of dependents
       auto fn = sptrsv_t1_cluster_kernel<T, FWD, LPV1>;
@@ -670,8 +670,8 @@ struct Engine {
       const int rounds = n <= kSharedRows ? VL_SHARED_CLUSTER_ROUNDS : VL_T1_CLUSTER_ROUNDS;
       if (form == VL_SOLVE_CLUSTER && cs_max < 1)
         return fail(c, VL_ERR_INVALID_ARG, "no thread-block cluster fits this solve");
-      if ((form == VL_SOLVE_CLUSTER && cs_max >= 1) ||
-          (form == VL_SOLVE_AUTO && cs_max >= 2 && widest <= rounds * cs_max * cta_teams)) {
+      if (form != VL_SOLVE_GRID && ((form == VL_SOLVE_CLUSTER && cs_max >= 1) ||
+                                    (form == VL_SOLVE_AUTO && cs_max >= 2 && widest <= rounds * cs_max * cta_teams))) {
         const int cs = fit_cluster(widest, cta_teams, cs_max);
         L.l_head = 0;
         L.l_tail = L.nlev;
@@ -707,6 +707,8 @@ struct Engine {
       constexpr int LPVG = FWD ? 8 : 16;
       return launch((const void*)sptrsv_t1_kernel<T, FWD, LPVG>, args, LPVG);
     }
+    // block kernels read rows as float4 / double2 words: ld must be a multiple of 8
+    if (ld % 8 != 0) return fail(c, VL_ERR_STATE, "block solve with a row width that is not a multiple of 8");
     void* args[] = {&L, &mm, &idx, &val, &rp, &rhs, &q, &x, &l};
     return with_shape<T>(ld, [&](auto Lc, auto N, auto U) {
       constexpr int LPV = decltype(Lc)::value;

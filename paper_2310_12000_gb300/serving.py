@@ -41,13 +41,14 @@ def footprint_bytes(n: int, m: int, t: int = 50, s: int = 100, n_test: int = 100
     (ELL of B and its transpose in float64 and float32, orders, levels), the state,
     and the largest phase, the simulation solves for predictive variances (float64
     and float32 Krylov blocks of up to 128 columns plus the refinement vectors), or
-    the SLQ probe block. k > 0 adds the LRAC factor and its float copy."""
+    the SLQ probe block with its float64 residual check. k > 0 adds the LRAC factor and its
+    float copy."""
     def lead(c):
         return 1 if c == 1 else (c + 7) // 8 * 8
     ls, lt = lead(min(s, 128)), lead(t)
     factor = n * (200 + 40 * m)
     sim = n * ls * 132
-    slq = n * lt * 4 * 11
+    slq = n * lt * (4 * 10 + 8 * 4)   # float32 engine + probe blocks, float64 probe residual blocks
     test = n_test * (16 * m + 96)
     lrac = n * k * 12 + n * lt * 4 + 6 * k * k * 8 if k else 0
     return int(1.15 * (factor + max(sim, slq) + test + lrac)) + (32 << 20)
