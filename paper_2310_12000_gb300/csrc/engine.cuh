@@ -141,6 +141,64 @@ inline int grid_for(Ctx* c, int64_t work, int block = 256) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(g, (int64_t)c->num_sms * 16));
 }
 
+// Heavy rows of every level (task[lptr[l] .. hptr[l])) cut into chunks of at most ch
+// dependencies, with level-local partial slots and row counters (see HeavyChunk). Built once
+// per factor, direction and chunk size from host copies of the task list and row lengths.
+inline vl_status chunk_plan(Ctx* c, Factor* f, bool fwd, int ch, const Factor::ChunkPlan** out) {
+  auto key = std::make_pair(fwd ? 1 : 0, ch);
+  auto it = f->chunk_plans.find(key);
+  if (it != f->chunk_plans.end()) {
+    *out = &it->second;
+    return VL_OK;
+  }
+  const int n = (int)f->n, m = f->m;
+  const std::vector<int32_t>& lp = fwd ? f->h_lptr_fwd : f->h_lptr_bwd;
+  const std::vector<int32_t>& hp = fwd ? f->h_hptr_fwd : f->h_hptr_bwd;
+  const int nlev = (int)lp.size() - 1;
+  int64_t nheavy = 0;
+  for (int l = 0; l < nlev; ++l) nheavy += hp[l] - lp[l];
+  std::vector<HeavyChunk> items;
+  std::vector<int32_t> cptr(nlev + 1, 0);
+  Factor::ChunkPlan plan;
+  if (nheavy > 0) {
+    // heavy rows are at most a few percent of the rows: copy only what is needed
+    std::vector<int32_t> task(n), rp;
+    VL_CUDA(c, cudaMemcpyAsync(task.data(), fwd ? f->task_fwd : f->task_bwd, sizeof(int32_t) * n,
+                               cudaMemcpyDeviceToHost, c->stream));
+    if (!fwd) {
+      rp.resize(n + 1);
+      VL_CUDA(c, cudaMemcpyAsync(rp.data(), f->rowptrT, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost,
+                                 c->stream));
+    }
+    VL_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (int l = 0; l < nlev; ++l) {
+      cptr[l] = (int32_t)items.size();
+      int slot = 0, row = 0;
+      for (int p = lp[l]; p < hp[l]; ++p, ++row) {
+        const int s = task[p];
+        const int beg = fwd ? s * m : rp[s], end = fwd ? s * m + m : rp[s + 1];
+        const int nch = std::max(1, (end - beg + ch - 1) / ch);
+        for (int k = 0; k < nch; ++k)
+          items.push_back(HeavyChunk{p, beg + k * ch, std::min(end, beg + (k + 1) * ch), slot + k, slot, nch, row, 0});
+        slot += nch;
+      }
+      plan.max_slots = std::max(plan.max_slots, slot);
+      plan.max_rows = std::max(plan.max_rows, row);
+    }
+  }
+  cptr[nlev] = (int32_t)items.size();
+  plan.cptr = f->mem.get<int32_t>(nlev + 1);
+  plan.chunk = f->mem.get<HeavyChunk>(std::max<size_t>(items.size(), 1));
+  if (!plan.cptr || !plan.chunk) return fail(c, VL_ERR_OOM, "workspace exhausted (heavy-row chunks)");
+  VL_CUDA(c, cudaMemcpyAsync(plan.cptr, cptr.data(), sizeof(int32_t) * (nlev + 1), cudaMemcpyHostToDevice, c->stream));
+  if (!items.empty())
+    VL_CUDA(c, cudaMemcpyAsync(plan.chunk, items.data(), sizeof(HeavyChunk) * items.size(), cudaMemcpyHostToDevice,
+                               c->stream));
+  VL_CUDA(c, cudaStreamSynchronize(c->stream));
+  *out = &(f->chunk_plans[key] = plan);
+  return VL_OK;
+}
+
 // ----------------------------------------------------------------------------- engine
 template <typename T>
 struct Engine {
@@ -173,8 +231,35 @@ struct Engine {
   bool lr_dirty = true;
   double logdetC = 0.0;
   T* b2 = nullptr;
+  // partial rows and row counters of the heavy-row chunks (grid solves), grown on demand
+  T* chunk_part = nullptr;
+  int* chunk_cnt = nullptr;
+  int part_slots = 0, cnt_len = 0;
 
   explicit Engine(Ctx* ctx) : c(ctx), mem(ctx) {}
+
+  // Heavy-row chunk plan of a grid solve, with partial slots and zeroed counters.
+  vl_status chunk_setup(bool fwd, int ch, LevelPlan& L) {
+    const Factor::ChunkPlan* pl = nullptr;
+    VL_TRY(chunk_plan(c, f, fwd, ch, &pl));
+    const int w = t == 1 ? 1 : ld;
+    if (pl->max_slots > part_slots) {
+      chunk_part = mem.get<T>((size_t)pl->max_slots * w);
+      if (!chunk_part) return fail(c, VL_ERR_OOM, "workspace exhausted (heavy-row partials)");
+      part_slots = pl->max_slots;
+    }
+    if (pl->max_rows > cnt_len) {
+      chunk_cnt = mem.get<int>(pl->max_rows);
+      if (!chunk_cnt) return fail(c, VL_ERR_OOM, "workspace exhausted (heavy-row counters)");
+      cnt_len = pl->max_rows;
+    }
+    if (cnt_len > 0) VL_CUDA(c, cudaMemsetAsync(chunk_cnt, 0, sizeof(int) * cnt_len, c->stream));
+    L.chunk = static_cast<const HeavyChunk*>(pl->chunk);
+    L.cptr = pl->cptr;
+    L.part = chunk_part;
+    L.cnt = chunk_cnt;
+    return VL_OK;
+  }
 
   // Leading dimension: 1 for a single column, else a multiple of 8 (the same for
   // float32 and float64 blocks, so mixed-precision refinement converts in place).
@@ -529,7 +614,7 @@ struct Engine {
     const std::vector<int64_t>& hw = FWD ? f->h_lwork_fwd : f->h_lwork_bwd;
     const std::vector<int32_t>& hh = FWD ? f->h_hptr_fwd : f->h_hptr_bwd;
     LevelPlan L{FWD ? f->task_fwd : f->task_bwd, FWD ? f->lptr_fwd : f->lptr_bwd, FWD ? f->hptr_fwd : f->hptr_bwd, 0, 0,
-                (int)hl.size() - 1, c->gbar, c->dstatus, nullptr};
+                (int)hl.size() - 1, c->gbar, c->dstatus, nullptr, nullptr, nullptr, nullptr, nullptr};
     const char* cls = FWD ? "sptrsv_fwd" : "sptrsv_bwd";
     // form: chosen from n, t and the widest level, or forced by vl_ctx_set_solve_form
     // (VL_SOLVE_SHARED concerns single-column solves; block solves keep the automatic choice)
@@ -549,6 +634,9 @@ struct Engine {
     VL_CUDA(c, cudaMemsetAsync(c->gbar, 0, 2 * sizeof(unsigned), c->stream));
     auto launch = [&](const void* fn, void** args, int lpv) -> vl_status {
       const int tpb = 16 * (32 / lpv);   // row teams per 512-thread block
+      // heavy rows of the grid body in chunks: one round of loads of a team
+      // (t = 1: lpv lanes x 4 loads; blocks: lpv dependency rows)
+      VL_TRY(chunk_setup(FWD, t == 1 ? lpv * 4 : lpv, L));
       const size_t smem = sizeof(T) * (size_t)tpb * (t == 1 ? 1 : ld);   // heavy-row partials
       level_cut(hl, hh, hw, t == 1 ? 1 : ld / VecT<T>::n, &L.l_head, &L.l_tail);
       if (form == VL_SOLVE_GRID) {   // forced: every level on the whole grid (no single-block head / tail)

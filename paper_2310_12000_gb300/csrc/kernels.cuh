@@ -258,6 +258,21 @@ __global__ void __launch_bounds__(256) spmv_Bt_t1_kernel(int n, const int32_t* _
 // Values of x produced in this launch are read through L2 (ld.global.cg).
 //   FWD (B^{-1}):   x_s = q_s r_s + sum_{c} A[s,c] x_{nbr[s,c]}
 //   BWD (B^{-T}):   x_s = q_s r_s + sum_{e in row s of B^T} valT[e] x_{colT[e]}
+// A piece of a heavy row's dependency list: the grid walk splits every heavy row of a level
+// into chunks of at most CH dependencies that separate teams gather at the same time; each
+// writes its partial row to a level-local slot and the team that completes the row's last
+// chunk (an arrival counter per row) adds q_s rhs_s and the partials in slot order, so the
+// result does not depend on which team finishes last.
+struct HeavyChunk {
+  int32_t p;       // task index of the row (its storage row is task[p])
+  int32_t beg, end;   // dependency range in idx / val
+  int32_t slot;    // level-local slot of this chunk's partial row
+  int32_t base;    // slot of the row's first chunk; the row has nch consecutive slots
+  int32_t nch;
+  int32_t hrow;    // level-local index of the row (its arrival counter)
+  int32_t pad;
+};
+
 struct LevelPlan {
   const int32_t* task;
   const int32_t* lptr;
@@ -266,6 +281,13 @@ struct LevelPlan {
   unsigned* bar;               // {count, generation}, count == 0 at launch
   DevStatus* st;
   long long* trace;            // optional: block 0's clock at each level boundary (nlev + 1)
+  // grid body only (null: heavy rows by whole blocks): the heavy rows of level l as the
+  // chunks chunk[cptr[l] .. cptr[l+1]), partial rows in `part`, per-row arrival counters
+  // in `cnt` (zero at launch; each row's finishing team sets its counter back to zero)
+  const HeavyChunk* chunk;
+  const int32_t* cptr;
+  void* part;
+  int* cnt;
 };
 
 // Grid barrier with a bounded wait on a monotonic arrival counter (zero at launch):
@@ -549,12 +571,99 @@ __device__ void heavy_row1(int p, int m, const LevelPlan& L, const int32_t* __re
   __syncthreads();
 }
 
+// One chunk of a heavy row (block rows, t > 1): the team gathers its dependencies, stores the
+// partial row, and the team that completes the row's last chunk finishes the row.
+template <typename T, int LPV, int NV, int UNR>
+__device__ __forceinline__ void chunk_run(const HeavyChunk& hc, const LevelPlan& L, const int32_t* __restrict__ idx,
+                                          const T* __restrict__ val, const T* __restrict__ rhs,
+                                          const T* __restrict__ q, T* x, int ld) {
+  constexpr int VEC = VecT<T>::n;
+  using V = typename VecT<T>::type;
+  const unsigned mask = team_mask<LPV>();
+  const int sl = (threadIdx.x & 31) % LPV;
+  T* part = static_cast<T*>(L.part);
+  T acc[NV * VEC];
+#pragma unroll
+  for (int i = 0; i < NV * VEC; ++i) acc[i] = T(0);
+  for (int e0 = hc.beg; e0 < hc.end; e0 += LPV) {
+    const int cnt = min(LPV, hc.end - e0);
+    const int jl = sl < cnt ? idx[e0 + sl] : -1;
+    const T al = jl >= 0 ? val[e0 + sl] : T(0);
+    chunk_gather<T, LPV, NV, UNR>(acc, jl, al, cnt, x, ld);
+  }
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const int col = (sl + LPV * v) * VEC;
+    if (col < ld) store_vec(part + (int64_t)hc.slot * ld + col, acc + v * VEC);
+  }
+  __threadfence();
+  __syncwarp(mask);
+  int last = 0;
+  if (sl == 0) last = atomicAdd(&L.cnt[hc.hrow], 1) == hc.nch - 1;
+  last = __shfl_sync(mask, last, 0, LPV);
+  if (!last) return;
+  __threadfence();
+  const int s = L.task[hc.p];
+  team_init<T, LPV, NV>(acc, s, ld, q ? q[s] : T(1), rhs, T(0), nullptr);
+  for (int k = 0; k < hc.nch; ++k)
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const int col = (sl + LPV * v) * VEC;
+      if (col < ld) fma_vec(acc + v * VEC, T(1), ldcg_vec(part + (int64_t)(hc.base + k) * ld + col));
+    }
+  team_store<T, LPV, NV>(x, s, ld, T(1), acc);
+  if (sl == 0) L.cnt[hc.hrow] = 0;
+}
+
+// One chunk of a heavy scalar row (t = 1): the team's lanes split the chunk's dependencies
+// (K loads each in flight), lane 0 stores the partial; the last chunk's team finishes the row.
+template <typename T, int LPV>
+__device__ __forceinline__ void chunk_run1(const HeavyChunk& hc, const LevelPlan& L, const int32_t* __restrict__ idx,
+                                           const T* __restrict__ val, const T* __restrict__ rhs,
+                                           const T* __restrict__ q, T* x) {
+  constexpr int K = 4;
+  const unsigned mask = team_mask<LPV>();
+  const int sl = (threadIdx.x & 31) % LPV;
+  T* part = static_cast<T*>(L.part);
+  T acc = T(0);
+  for (int e0 = hc.beg + sl; e0 < hc.end; e0 += LPV * K) {
+    int j[K];
+    T a[K], xv[K];
+#pragma unroll
+    for (int u = 0; u < K; ++u) {
+      const int e = e0 + u * LPV;
+      j[u] = e < hc.end ? idx[e] : -1;
+      a[u] = j[u] >= 0 ? val[e] : T(0);
+      xv[u] = j[u] >= 0 ? __ldcg(&x[j[u]]) : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < K; ++u) acc += a[u] * xv[u];
+  }
+#pragma unroll
+  for (int off = LPV / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(mask, acc, off, LPV);
+  int last = 0;
+  if (sl == 0) {
+    part[hc.slot] = acc;
+    __threadfence();
+    last = atomicAdd(&L.cnt[hc.hrow], 1) == hc.nch - 1;
+    if (last) {
+      __threadfence();
+      const int s = L.task[hc.p];
+      T sum = (q ? q[s] : T(1)) * rhs[s];
+      for (int k = 0; k < hc.nch; ++k) sum += __ldcg(&part[hc.base + k]);
+      x[s] = sum;
+      L.cnt[hc.hrow] = 0;
+    }
+  }
+  __syncwarp(mask);
+}
+
 // Walks the levels with the head/body/tail split; each team prefetches its next
 // light row (pre) before the barrier that precedes it and finishes it after
 // (run); the heavy rows that lead each level are done first, a block per row
 // (heavy(p), called by every thread of the block).
-template <int LPV, bool COUNTER, typename Pre, typename Run, typename Heavy>
-__device__ __forceinline__ void level_walk(const LevelPlan& L, Pre pre, Run run, Heavy heavy) {
+template <int LPV, bool COUNTER, typename Pre, typename Run, typename Heavy, typename Chunk>
+__device__ __forceinline__ void level_walk(const LevelPlan& L, Pre pre, Run run, Heavy heavy, Chunk chunk) {
   constexpr int RPW = 32 / LPV;
   const int tpb = (blockDim.x >> 5) * RPW;
   const int tib = (threadIdx.x >> 5) * RPW + (threadIdx.x & 31) / LPV;
@@ -594,7 +703,12 @@ __device__ __forceinline__ void level_walk(const LevelPlan& L, Pre pre, Run run,
     if (has) pre(p);
     for (int l = L.l_head; l < L.l_tail; ++l) {
       if (tr) L.trace[l] = clock64();
-      for (int h = L.lptr[l] + blockIdx.x; h < L.hptr[l]; h += gridDim.x) heavy(h);
+      if (L.chunk) {
+        // chunks from the last team down, light rows from the first team up
+        for (int c = L.cptr[l] + (G - 1 - g); c < L.cptr[l + 1]; c += G) chunk(L.chunk[c]);
+      } else {
+        for (int h = L.lptr[l] + blockIdx.x; h < L.hptr[l]; h += gridDim.x) heavy(h);
+      }
       while (has) {
         run();
         p += G;
@@ -781,7 +895,8 @@ __global__ void __launch_bounds__(512) sptrsv_kernel(LevelPlan L, int m, const i
   level_walk<LPV, false>(
       L, [&](int p) { row_pre<T, FWD, LPV, NV>(r, p, m, L, idx, val, rowptr, rhs, q, ld); },
       [&]() { row_run<T, LPV, NV, UNR>(r, idx, val, x, ld); },
-      [&](int p) { heavy_row<T, FWD, LPV, NV, UNR>(p, m, L, idx, val, rowptr, rhs, q, x, ld, part); });
+      [&](int p) { heavy_row<T, FWD, LPV, NV, UNR>(p, m, L, idx, val, rowptr, rhs, q, x, ld, part); },
+      [&](const HeavyChunk& hc) { chunk_run<T, LPV, NV, UNR>(hc, L, idx, val, rhs, q, x, ld); });
 }
 
 template <typename T, bool FWD, int LPV>
@@ -794,7 +909,8 @@ __global__ void __launch_bounds__(512) sptrsv_t1_kernel(LevelPlan L, int m, cons
   level_walk<LPV, true>(
       L, [&](int p) { row_pre1<T, FWD, LPV>(r, p, m, L, idx, val, rowptr, rhs, q); },
       [&]() { row_run1<T, LPV>(r, idx, val, x); },
-      [&](int p) { heavy_row1<T, FWD, LPV>(p, m, L, idx, val, rowptr, rhs, q, x, part); });
+      [&](int p) { heavy_row1<T, FWD, LPV>(p, m, L, idx, val, rowptr, rhs, q, x, part); },
+      [&](const HeavyChunk& hc) { chunk_run1<T, LPV>(hc, L, idx, val, rhs, q, x); });
 }
 
 // ----------------------------------------------------------------------------- column reductions

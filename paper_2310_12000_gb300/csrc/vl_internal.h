@@ -152,6 +152,14 @@ struct Factor {
   std::vector<int32_t> h_lptr_fwd, h_lptr_bwd;
   std::vector<int64_t> h_lwork_fwd, h_lwork_bwd;   // dependencies per level
   std::vector<int32_t> h_hptr_fwd, h_hptr_bwd;     // host copies of hptr
+  // heavy rows split into dependency chunks for the grid solves, per direction and chunk size
+  // (built on first use; device arrays owned by `mem`)
+  struct ChunkPlan {
+    void* chunk = nullptr;     // HeavyChunk array
+    int32_t* cptr = nullptr;   // nlev + 1
+    int max_slots = 0, max_rows = 0;
+  };
+  std::map<std::pair<int, int>, ChunkPlan> chunk_plans;   // (fwd, chunk size) -> plan
   // LRAC (Section 3.1.2): rank-k pivoted Cholesky factor of Sigma, built on first use
   // and dropped when the covariance parameters change
   Owned lrac_mem;
