@@ -809,6 +809,8 @@ vl_status vl_ctx_create(int device, void* cuda_stream, void* workspace, size_t w
   if (!c->dstatus || !c->gbar) return bail(VL_ERR_OOM);
   if (cudaMemsetAsync(c->dstatus, 0, sizeof(DevStatus), c->stream) != cudaSuccess) return bail(VL_ERR_CUDA);
   if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) return bail(VL_ERR_CUDA);
+  for (cudaEvent_t& e : c->ev_ring)
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return bail(VL_ERR_CUDA);
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return bail(VL_ERR_CUDA);
   *out = c;
   return VL_OK;
@@ -823,6 +825,8 @@ static void ctx_release(Ctx* cc) {
   prof_release(c);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
+  for (cudaEvent_t e : c->ev_ring)
+    if (e) cudaEventDestroy(e);
   if (c->owns_ws && c->ws) cudaFree(c->ws);
   if (c->pinned) cudaFreeHost(c->pinned);
   delete c;

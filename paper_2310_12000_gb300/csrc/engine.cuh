@@ -3,6 +3,7 @@
 // algorithm with per-column freezing and Lanczos T extraction.
 #pragma once
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <set>
@@ -141,8 +142,9 @@ inline int grid_for(Ctx* c, int64_t work, int block = 256) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(g, (int64_t)c->num_sms * 16));
 }
 
-// Heavy rows of every level (task[lptr[l] .. hptr[l])) cut into chunks of at most ch
-// dependencies, with level-local partial slots and row counters (see HeavyChunk). Built once
+// Heavy rows (task[lptr[l] .. hptr[l])) of the levels that have more of them than
+// min_rows, cut into chunks of at most ch dependencies, with level-local partial slots and
+// row counters (see HeavyChunk); other levels keep a whole block per heavy row. Built once
 // per factor, direction and chunk size from host copies of the task list and row lengths.
 inline vl_status chunk_plan(Ctx* c, Factor* f, bool fwd, int ch, const Factor::ChunkPlan** out) {
   auto key = std::make_pair(fwd ? 1 : 0, ch);
@@ -152,6 +154,7 @@ inline vl_status chunk_plan(Ctx* c, Factor* f, bool fwd, int ch, const Factor::C
     return VL_OK;
   }
   const int n = (int)f->n, m = f->m;
+  const int min_rows = 4 * c->num_sms;   // about two rounds of the grid's blocks
   const std::vector<int32_t>& lp = fwd ? f->h_lptr_fwd : f->h_lptr_bwd;
   const std::vector<int32_t>& hp = fwd ? f->h_hptr_fwd : f->h_hptr_bwd;
   const int nlev = (int)lp.size() - 1;
@@ -174,6 +177,7 @@ inline vl_status chunk_plan(Ctx* c, Factor* f, bool fwd, int ch, const Factor::C
     for (int l = 0; l < nlev; ++l) {
       cptr[l] = (int32_t)items.size();
       int slot = 0, row = 0;
+      if (hp[l] - lp[l] <= min_rows) continue;
       for (int p = lp[l]; p < hp[l]; ++p, ++row) {
         const int s = task[p];
         const int beg = fwd ? s * m : rp[s], end = fwd ? s * m + m : rp[s + 1];
@@ -212,6 +216,9 @@ struct Engine {
   T *u = nullptr, *r = nullptr, *z = nullptr, *h = nullptr, *v = nullptr, *y = nullptr, *sv = nullptr;
   double *partial = nullptr, *red = nullptr, *red2 = nullptr;
   int nblk = 1, rpb = 1;
+  int nseg = 1, ncol = 1;          // segments (problems of a batch) and nseg * t scalar columns
+  BlockRows br{};                  // reduction blocks (segment-aligned)
+  unsigned* done = nullptr;        // arrival counter of the fused reductions
   dim3 cb;
   size_t csh = 0;
   PcgScalars S{};
@@ -296,32 +303,39 @@ struct Engine {
     const int cx = (t == 1) ? 1 : (t + 31) / 32 * 32;
     cb = dim3(cx, 256 / cx);
     csh = sizeof(double) * 256;
+    nseg = std::max(1, f->nseg);
+    ncol = nseg * t;
     const int64_t want = (n + (int64_t)cb.y * 8 - 1) / ((int64_t)cb.y * 8);
     nblk = (int)std::max<int64_t>(1, std::min<int64_t>(want, 4LL * c->num_sms));
     rpb = (n + nblk - 1) / nblk;
+    br = BlockRows{n, rpb, nblk, 1, nullptr, nullptr, nullptr, nullptr};
+    if (nseg > 1) VL_TRY(segment_blocks());
     partial = mem.get<double>((size_t)nblk * t);
-    red = mem.get<double>(t);
-    red2 = mem.get<double>(t);
-    if (!partial || !red || !red2) return fail(c, VL_ERR_OOM, "workspace exhausted (reductions)");
+    red = mem.get<double>(ncol);
+    red2 = mem.get<double>(ncol);
+    done = mem.get<unsigned>(1);
+    if (!partial || !red || !red2 || !done) return fail(c, VL_ERR_OOM, "workspace exhausted (reductions)");
+    VL_CUDA(c, cudaMemsetAsync(done, 0, sizeof(unsigned), c->stream));
     lmax = lmax_;
     if (lmax > 0) {
       double** ds[] = {&S.rz, &S.rz0, &S.alpha, &S.beta, &S.alpha_prev, &S.beta_prev, &S.bnorm2, &S.rnorm2, &S.relres};
       for (double** p : ds) {
-        *p = mem.get<double>(t);
+        *p = mem.get<double>(ncol);
         if (!*p) return fail(c, VL_ERR_OOM, "workspace exhausted (PCG scalars)");
       }
-      S.active = mem.get<int>(t);
-      S.stop = mem.get<int>(t);
-      S.iters = mem.get<int>(t);
-      S.Tdiag = mem.get<double>((size_t)t * lmax);
-      S.Toff = mem.get<double>((size_t)t * lmax);
+      S.tol2 = nullptr;
+      S.active = mem.get<int>(ncol);
+      S.stop = mem.get<int>(ncol);
+      S.iters = mem.get<int>(ncol);
+      S.Tdiag = mem.get<double>((size_t)ncol * lmax);
+      S.Toff = mem.get<double>((size_t)ncol * lmax);
       d_count = mem.get<int>(1);
       S.count = d_count;
       S.lmax = lmax;
       if (!S.active || !S.stop || !S.iters || !S.Tdiag || !S.Toff || !d_count)
         return fail(c, VL_ERR_OOM, "workspace exhausted (PCG state)");
-      VL_CUDA(c, cudaMemsetAsync(S.Tdiag, 0, sizeof(double) * t * lmax, c->stream));
-      VL_CUDA(c, cudaMemsetAsync(S.Toff, 0, sizeof(double) * t * lmax, c->stream));
+      VL_CUDA(c, cudaMemsetAsync(S.Tdiag, 0, sizeof(double) * ncol * lmax, c->stream));
+      VL_CUDA(c, cudaMemsetAsync(S.Toff, 0, sizeof(double) * ncol * lmax, c->stream));
     }
     h_count = reinterpret_cast<int*>(c->pinned);
     if (prec == VL_PREC_LRAC) {
@@ -490,11 +504,44 @@ struct Engine {
     return VL_OK;
   }
 
+  // Segment-aligned reduction blocks of about rpb rows: each problem of a batch gets
+  // ceil(rows / rpb) blocks of its own.
+  vl_status segment_blocks() {
+    const std::vector<int64_t>& r0 = f->seg_row0;
+    if ((int)r0.size() != nseg + 1) return fail(c, VL_ERR_STATE, "batch segments missing");
+    std::vector<int32_t> b0, b1, bs, sb(nseg + 1, 0);
+    for (int k = 0; k < nseg; ++k) {
+      sb[k] = (int32_t)b0.size();
+      for (int64_t a = r0[k]; a < r0[k + 1]; a += rpb) {
+        b0.push_back((int32_t)a);
+        b1.push_back((int32_t)std::min<int64_t>(r0[k + 1], a + rpb));
+        bs.push_back(k);
+      }
+    }
+    sb[nseg] = (int32_t)b0.size();
+    nblk = std::max(1, (int)b0.size());
+    int32_t* d = mem.get<int32_t>((size_t)3 * nblk + nseg + 1);
+    if (!d) return fail(c, VL_ERR_OOM, "workspace exhausted (reduction blocks)");
+    std::vector<int32_t> all;
+    all.insert(all.end(), b0.begin(), b0.end());
+    all.insert(all.end(), b1.begin(), b1.end());
+    all.insert(all.end(), bs.begin(), bs.end());
+    all.insert(all.end(), sb.begin(), sb.end());
+    VL_CUDA(c, cudaMemcpyAsync(d, all.data(), sizeof(int32_t) * all.size(), cudaMemcpyHostToDevice, c->stream));
+    VL_CUDA(c, cudaStreamSynchronize(c->stream));
+    br = BlockRows{n, rpb, nblk, nseg, d, d + nblk, d + 2 * nblk, d + 3 * nblk};
+    return VL_OK;
+  }
+
+  ReduceTail tail(int epi, double* out = nullptr, double tol2 = 0.0, int max_iter = 0) const {
+    return ReduceTail{epi, out, S, tol2, max_iter, done};
+  }
+
   // ------------------------------------------------------------------ primitives
+  // out[k * t + c] = sum over segment k's rows of w_s X[s,c] Y[s,c]
   vl_status coldot(const T* X, const T* Y, const T* w, double* out) {
     ProfScope ps(c, "coldot", t);
-    coldot_kernel<T><<<nblk, cb, csh, VL_STREAM(c)>>>(n, t, ld, rpb, X, Y, w, partial);
-    reduce_partials_kernel<<<1, 256, 0, VL_STREAM(c)>>>(nblk, t, partial, out);
+    coldot_kernel<T><<<nblk, cb, csh, VL_STREAM(c)>>>(br, t, ld, X, Y, w, partial, tail(EPI_NONE, out));
     VL_CUDA(c, cudaGetLastError());
     return VL_OK;
   }
@@ -844,7 +891,40 @@ struct Engine {
 
   // Solves S U = Bm (S = opSys) column by column (u_0 = 0), stopping a column when
   // ||r|| <= tol ||b||; records T (Lanczos) per column.
-  vl_status pcg(const T* Bm, T* U, double tol, int max_iter, int* iters_used) {
+  // One PCG iteration (Appendix, PCG algorithm) on every active column: v = S h; alpha
+  // (fused into the h^T v reduction); u += alpha h, r -= alpha v with the stopping test
+  // (fused into the ||r||^2 reduction); z = P^{-1} r; beta, T entries and freezing (fused into
+  // the r^T z reduction); h = z + beta h.
+  vl_status pcg_step(T* U, double tol2, int max_iter) {
+    VL_TRY(opSys(h, v));
+    {
+      ProfScope ps(c, "coldot", t);
+      coldot_kernel<T><<<nblk, cb, csh, VL_STREAM(c)>>>(br, t, ld, h, v, nullptr, partial, tail(EPI_ALPHA));
+    }
+    {
+      ProfScope ps(c, "pcg_update", t);
+      pcg_update1_kernel<T><<<nblk, cb, csh, VL_STREAM(c)>>>(br, t, ld, U, r, h, v, partial,
+                                                              tail(EPI_STOP, nullptr, tol2));
+    }
+    VL_CUDA(c, cudaGetLastError());
+    VL_TRY(opPinv(r, z));
+    {
+      ProfScope ps(c, "coldot", t);
+      coldot_kernel<T><<<nblk, cb, csh, VL_STREAM(c)>>>(br, t, ld, r, z, nullptr, partial,
+                                                         tail(EPI_BETA, nullptr, 0.0, max_iter));
+    }
+    {
+      ProfScope ps(c, "pcg_update", t);
+      pcg_update2_kernel<T><<<nblk, cb, 0, VL_STREAM(c)>>>(br, t, ld, S.beta, S.active, z, h);
+    }
+    VL_CUDA(c, cudaGetLastError());
+    return VL_OK;
+  }
+
+  // Solves S U = Bm (S = opSys) column by column (u_0 = 0), stopping a column when
+  // ||r|| <= tol ||b|| (or per column sqrt(tol2[q]) when tol2 is given, device, ncol entries);
+  // records T (Lanczos) per column. Finished columns are frozen on the device.
+  vl_status pcg(const T* Bm, T* U, double tol, int max_iter, int* iters_used, const double* tol2v = nullptr) {
     const int64_t vec = (int64_t)n * ld;
     VL_CUDA(c, cudaMemsetAsync(U, 0, sizeof(T) * vec, c->stream));
     VL_CUDA(c, cudaMemcpyAsync(r, Bm, sizeof(T) * vec, cudaMemcpyDeviceToDevice, c->stream));
@@ -852,46 +932,48 @@ struct Engine {
     VL_CUDA(c, cudaMemcpyAsync(h, z, sizeof(T) * vec, cudaMemcpyDeviceToDevice, c->stream));
     VL_TRY(coldot(r, z, nullptr, S.rz));
     VL_TRY(coldot(Bm, Bm, nullptr, S.bnorm2));
-    pcg_init_kernel<<<1, 256, 0, VL_STREAM(c)>>>(t, S);
+    S.tol2 = tol2v;
+    pcg_init_kernel<<<1, 256, 0, VL_STREAM(c)>>>(ncol, S);
     VL_CUDA(c, cudaGetLastError());
     const double tol2 = tol * tol;
-    int it = 0;
-    for (; it < max_iter; ++it) {
-      VL_TRY(opSys(h, v));
-      VL_TRY(coldot(h, v, nullptr, red));
-      pcg_alpha_kernel<<<1, 256, 0, VL_STREAM(c)>>>(t, red, S);
-      {
-        ProfScope ps(c, "pcg_update", t);
-        pcg_update1_kernel<T><<<nblk, cb, csh, VL_STREAM(c)>>>(n, t, ld, rpb, S.alpha, U, r, h, v, partial);
-      }
-      reduce_partials_kernel<<<1, 256, 0, VL_STREAM(c)>>>(nblk, t, partial, S.rnorm2);
-      pcg_stop_kernel<<<1, 256, 0, VL_STREAM(c)>>>(t, tol2, S);
-      VL_CUDA(c, cudaGetLastError());
-      VL_TRY(opPinv(r, z));
-      VL_TRY(coldot(r, z, nullptr, red2));
-      pcg_beta_kernel<<<1, 256, 0, VL_STREAM(c)>>>(t, red2, max_iter, S);
-      {
-        ProfScope ps(c, "pcg_update", t);
-        pcg_update2_kernel<T><<<grid_for(c, vec), 256, 0, VL_STREAM(c)>>>(vec, t, ld, S.beta, S.active, z, h);
-      }
-      VL_CUDA(c, cudaGetLastError());
-      VL_CUDA(c, cudaMemcpyAsync(h_count, d_count, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-      VL_TRY(check_dev_status(c, "PCG"));
-      if (*h_count == 0) {
-        ++it;
-        break;
+    // The host stays one iteration ahead: it issues iteration i + 1, then waits for the
+    // active count (and device status) of iteration i, so the GPU never waits for the host;
+    // at most one iteration runs after the last column finished, and it changes nothing.
+    int* ring = reinterpret_cast<int*>(c->pinned + 256);   // {count, status} x 2
+    cudaEvent_t ev[2] = {c->ev_ring[0], c->ev_ring[1]};
+    bool stop = false;
+    for (int it = 0; it < max_iter && !stop; ++it) {
+      VL_TRY(pcg_step(U, tol2, max_iter));
+      const int k = it & 1;
+      VL_CUDA(c, cudaMemcpyAsync(ring + 2 * k, d_count, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+      VL_CUDA(c, cudaMemcpyAsync(ring + 2 * k + 1, &c->dstatus->code, sizeof(int), cudaMemcpyDeviceToHost,
+                                 c->stream));
+      VL_CUDA(c, cudaEventRecord(ev[k], c->stream));
+      if (it > 0) {
+        VL_CUDA(c, cudaEventSynchronize(ev[k ^ 1]));
+        stop = ring[2 * (k ^ 1)] == 0 || ring[2 * (k ^ 1) + 1] != 0;
       }
     }
-    if (iters_used) *iters_used = it;
+    VL_TRY(check_dev_status(c, "PCG"));
+    S.tol2 = nullptr;
+    // iterations actually taken: the most any column took
+    if (iters_used) {
+      std::vector<int> its(ncol);
+      VL_CUDA(c, cudaMemcpyAsync(its.data(), S.iters, sizeof(int) * ncol, cudaMemcpyDeviceToHost, c->stream));
+      VL_CUDA(c, cudaStreamSynchronize(c->stream));
+      *iters_used = its.empty() ? 0 : *std::max_element(its.begin(), its.end());
+    }
     return VL_OK;
   }
 
+
+
   // Host copies of per-column results.
   vl_status column_stats(std::vector<int>& iters, std::vector<double>& relres) {
-    iters.resize(t);
-    relres.resize(t);
-    VL_CUDA(c, cudaMemcpyAsync(iters.data(), S.iters, sizeof(int) * t, cudaMemcpyDeviceToHost, c->stream));
-    VL_CUDA(c, cudaMemcpyAsync(relres.data(), S.relres, sizeof(double) * t, cudaMemcpyDeviceToHost, c->stream));
+    iters.resize(ncol);
+    relres.resize(ncol);
+    VL_CUDA(c, cudaMemcpyAsync(iters.data(), S.iters, sizeof(int) * ncol, cudaMemcpyDeviceToHost, c->stream));
+    VL_CUDA(c, cudaMemcpyAsync(relres.data(), S.relres, sizeof(double) * ncol, cudaMemcpyDeviceToHost, c->stream));
     VL_CUDA(c, cudaStreamSynchronize(c->stream));
     return VL_OK;
   }

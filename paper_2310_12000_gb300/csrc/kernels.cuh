@@ -283,7 +283,9 @@ struct LevelPlan {
   long long* trace;            // optional: block 0's clock at each level boundary (nlev + 1)
   // grid body only (null: heavy rows by whole blocks): the heavy rows of level l as the
   // chunks chunk[cptr[l] .. cptr[l+1]), partial rows in `part`, per-row arrival counters
-  // in `cnt` (zero at launch; each row's finishing team sets its counter back to zero)
+  // in `cnt` (zero at launch; each row's finishing team sets its counter back to zero).
+  // A level without chunks keeps a whole block per heavy row (one round of loads, no
+  // partials): chunks only pay off when a level has more heavy rows than blocks.
   const HeavyChunk* chunk;
   const int32_t* cptr;
   void* part;
@@ -703,7 +705,7 @@ __device__ __forceinline__ void level_walk(const LevelPlan& L, Pre pre, Run run,
     if (has) pre(p);
     for (int l = L.l_head; l < L.l_tail; ++l) {
       if (tr) L.trace[l] = clock64();
-      if (L.chunk) {
+      if (L.chunk && L.cptr[l + 1] > L.cptr[l]) {
         // chunks from the last team down, light rows from the first team up
         for (int c = L.cptr[l] + (G - 1 - g); c < L.cptr[l + 1]; c += G) chunk(L.chunk[c]);
       } else {
@@ -914,16 +916,151 @@ __global__ void __launch_bounds__(512) sptrsv_t1_kernel(LevelPlan L, int m, cons
 }
 
 // ----------------------------------------------------------------------------- column reductions
-// Block layout for column sweeps: blockDim = (cx, 256 / cx) with cx = 1 for t == 1
-// and a multiple of 32 covering t otherwise. Block b owns rows [b*rpb, (b+1)*rpb).
-// partial[b * t + c] = sum over its rows of w_s X[s,c] Y[s,c] (w == nullptr: 1),
-// accumulated in Acc (float64 for float64 data; float32 per thread then float64).
+// Rows are swept by reduction blocks of blockDim = (cx, 256 / cx), cx = 1 for t == 1, else a
+// multiple of 32 covering t. Block b covers rows [row0(b), row1(b)) of segment seg(b): the
+// problems of a batch are segments of the storage rows, a single problem is one segment with
+// blocks of rpb rows. A block never straddles segments, so a per-(segment, column) sum is a
+// sum of whole blocks taken in block order, and results do not depend on scheduling.
+struct BlockRows {
+  int n, rpb, nblk, nseg;
+  const int32_t* r0;    // per block first row (null: b * rpb)
+  const int32_t* r1;    // per block end row (null: min(n, (b + 1) * rpb))
+  const int32_t* seg;   // per block segment (null: 0)
+  const int32_t* sb0;   // per segment first block, nseg + 1 entries (null: 0, nblk)
+  __device__ __forceinline__ int row0(int b) const { return r0 ? r0[b] : b * rpb; }
+  __device__ __forceinline__ int row1(int b) const { return r1 ? r1[b] : min(n, (b + 1) * rpb); }
+  __device__ __forceinline__ int segment(int b) const { return seg ? seg[b] : 0; }
+  __device__ __forceinline__ int blk0(int k) const { return sb0 ? sb0[k] : 0; }
+  __device__ __forceinline__ int blk1(int k) const { return sb0 ? sb0[k + 1] : nblk; }
+};
+
+// ----------------------------------------------------------------------------- PCG scalars
+// Per (segment, column) q = k * t + c, ncol = nseg * t entries each.
+struct PcgScalars {
+  double* rz;          // r_l^T z_l
+  double* rz0;         // r_0^T z_0 = ||P^{-1/2} b||^2
+  double* alpha;       // alpha_{l+1}
+  double* beta;        // beta_{l+1}
+  double* alpha_prev;  // alpha_l   (alpha_0 = 1)
+  double* beta_prev;   // beta_l    (beta_0 = 0)
+  double* bnorm2;
+  double* rnorm2;
+  double* relres;
+  const double* tol2;  // per column squared relative tolerance (null: the scalar of the call)
+  int* active;
+  int* stop;
+  int* iters;
+  double* Tdiag;       // ncol x lmax
+  double* Toff;        // ncol x lmax
+  int lmax;
+  int* count;          // number of active columns after the update
+};
+
+// r_0 = b, z_0 = P^{-1} r_0: set rz, rz0, bnorm2 (already reduced into rz/bnorm2) and flags.
+static __global__ void pcg_init_kernel(int ncol, PcgScalars S) {
+  for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
+    S.rz0[c] = S.rz[c];
+    S.alpha_prev[c] = 1.0;
+    S.beta_prev[c] = 0.0;
+    S.iters[c] = 0;
+    S.stop[c] = 0;
+    S.alpha[c] = 0.0;
+    S.beta[c] = 0.0;
+    const bool act = S.bnorm2[c] > 0.0 && S.rz[c] > 0.0;
+    S.active[c] = act ? 1 : 0;
+    S.relres[c] = act ? 1.0 : 0.0;
+  }
+  if (threadIdx.x == 0) *S.count = 1;
+}
+
+// What the last block of a column reduction does with the sums (Appendix, PCG algorithm):
+enum ReduceEpilogue {
+  EPI_NONE = 0,   // out = the sums
+  EPI_ALPHA = 1,  // alpha_{l+1} = r_l^T z_l / h_l^T v_l (active columns; 0 otherwise)
+  EPI_STOP = 2,   // ||r_{l+1}||^2 and the stopping test (before the T update, as in the algorithm)
+  EPI_BETA = 3    // beta_{l+1}, the T entries, the freeze of finished columns, the active count
+};
+
+struct ReduceTail {
+  int epi;
+  double* out;          // EPI_NONE: ncol sums
+  PcgScalars S;
+  double tol2;          // EPI_STOP: squared relative tolerance (when S.tol2 is null)
+  int max_iter;         // EPI_BETA
+  unsigned* done;       // arrival counter of the launch's blocks (zero at launch, reset by the last)
+};
+
+// Runs in the last block to finish: per (segment, column) sums of the block partials in block
+// order, then the epilogue. Every thread of the block calls it.
+__device__ __forceinline__ void reduce_tail(const BlockRows& br, int t, const double* __restrict__ partial,
+                                            const ReduceTail& rt) {
+  __shared__ int last;
+  __shared__ int cnt;
+  __syncthreads();
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
+  if (tid == 0) {
+    __threadfence();
+    last = atomicAdd(rt.done, 1u) == gridDim.x - 1;
+    cnt = 0;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const PcgScalars& S = rt.S;
+  int local = 0;
+  const int ncol = br.nseg * t;
+  for (int q = tid; q < ncol; q += nth) {
+    const int k = q / t, c = q - k * t;
+    double sum = 0.0;
+    for (int b = br.blk0(k); b < br.blk1(k); ++b) sum += __ldcg(&partial[(int64_t)b * t + c]);
+    if (rt.epi == EPI_NONE) {
+      rt.out[q] = sum;
+    } else if (rt.epi == EPI_ALPHA) {
+      const double a = S.active[q] ? S.rz[q] / sum : 0.0;
+      S.alpha[q] = (S.active[q] && isfinite(a)) ? a : 0.0;
+    } else if (rt.epi == EPI_STOP) {
+      if (!S.active[q]) continue;
+      S.rnorm2[q] = sum;
+      S.relres[q] = sqrt(sum / S.bnorm2[q]);
+      const double tl = S.tol2 ? S.tol2[q] : rt.tol2;
+      S.stop[q] = (sum <= tl * S.bnorm2[q]) ? 1 : 0;
+    } else {   // EPI_BETA
+      if (!S.active[q]) continue;
+      const int l = S.iters[q];
+      const double a = S.alpha[q], ap = S.alpha_prev[q], bp = S.beta_prev[q];
+      const double bt = sum / S.rz[q];
+      if (l < S.lmax) {
+        S.Tdiag[(int64_t)q * S.lmax + l] = 1.0 / a + bp / ap;
+        if (l > 0) S.Toff[(int64_t)q * S.lmax + l - 1] = sqrt(bp) / ap;
+      }
+      S.beta[q] = bt;
+      S.alpha_prev[q] = a;
+      S.beta_prev[q] = bt;
+      S.rz[q] = sum;
+      S.iters[q] = l + 1;
+      if (S.stop[q] || l + 1 >= rt.max_iter || l + 1 >= S.lmax || !(a > 0.0) || !isfinite(bt))
+        S.active[q] = 0;
+      else
+        ++local;
+    }
+  }
+  if (rt.epi == EPI_BETA) {
+    atomicAdd(&cnt, local);
+    __syncthreads();
+    if (tid == 0) *S.count = cnt;
+  }
+  if (tid == 0) *rt.done = 0u;
+}
+
+// partial[b * t + c] = sum over block b's rows of w_s X[s,c] Y[s,c] (w == nullptr: 1), then
+// the last block's reduce_tail. Accumulation: float64 for float64 data; float32 partials of
+// 16 rows each, flushed to float64.
 template <typename T>
-__global__ void coldot_kernel(int n, int t, int ld, int rpb, const T* __restrict__ X, const T* __restrict__ Y,
-                              const T* __restrict__ w, double* __restrict__ partial) {
+__global__ void coldot_kernel(BlockRows br, int t, int ld, const T* __restrict__ X, const T* __restrict__ Y,
+                              const T* __restrict__ w, double* __restrict__ partial, ReduceTail rt) {
   const int cx = blockDim.x, ry = blockDim.y;
   const int c = threadIdx.x;
-  const int r0 = blockIdx.x * rpb, r1 = min(n, r0 + rpb);
+  const int r0 = br.row0(blockIdx.x), r1 = br.row1(blockIdx.x);
   double acc = 0.0;
   if (c < t) {
     T a = T(0);
@@ -948,114 +1085,24 @@ __global__ void coldot_kernel(int n, int t, int ld, int rpb, const T* __restrict
     double sum = 0.0;
     for (int y = 0; y < ry; ++y) sum += sh[y * cx + c];
     partial[(int64_t)blockIdx.x * t + c] = sum;
+    __threadfence();
   }
+  reduce_tail(br, t, partial, rt);
 }
 
-// out[c] = sum_b partial[b * t + c] (fixed order)
-static __global__ void reduce_partials_kernel(int nblk, int t, const double* __restrict__ partial, double* __restrict__ out) {
-  for (int c = threadIdx.x; c < t; c += blockDim.x) {
-    double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += partial[(int64_t)b * t + c];
-    out[c] = s;
-  }
-}
-
-// ----------------------------------------------------------------------------- PCG scalars
-struct PcgScalars {
-  double* rz;          // r_l^T z_l
-  double* rz0;         // r_0^T z_0 = ||P^{-1/2} b||^2
-  double* alpha;       // alpha_{l+1}
-  double* beta;        // beta_{l+1}
-  double* alpha_prev;  // alpha_l   (alpha_0 = 1)
-  double* beta_prev;   // beta_l    (beta_0 = 0)
-  double* bnorm2;
-  double* rnorm2;
-  double* relres;
-  int* active;
-  int* stop;
-  int* iters;
-  double* Tdiag;       // t x lmax
-  double* Toff;        // t x lmax
-  int lmax;
-  int* count;          // number of active columns after the update
-};
-
-// r_0 = b, z_0 = P^{-1} r_0: set rz, rz0, bnorm2 (already reduced into rz/bnorm2) and flags.
-static __global__ void pcg_init_kernel(int t, PcgScalars S) {
-  for (int c = threadIdx.x; c < t; c += blockDim.x) {
-    S.rz0[c] = S.rz[c];
-    S.alpha_prev[c] = 1.0;
-    S.beta_prev[c] = 0.0;
-    S.iters[c] = 0;
-    S.stop[c] = 0;
-    S.alpha[c] = 0.0;
-    S.beta[c] = 0.0;
-    const bool act = S.bnorm2[c] > 0.0 && S.rz[c] > 0.0;
-    S.active[c] = act ? 1 : 0;
-    S.relres[c] = act ? 1.0 : 0.0;
-  }
-}
-
-// alpha_{l+1} = r_l^T z_l / h_l^T v_l for active columns (0 otherwise).
-static __global__ void pcg_alpha_kernel(int t, const double* __restrict__ hv, PcgScalars S) {
-  for (int c = threadIdx.x; c < t; c += blockDim.x) {
-    const double a = S.active[c] ? S.rz[c] / hv[c] : 0.0;
-    S.alpha[c] = (S.active[c] && isfinite(a)) ? a : 0.0;
-  }
-}
-
-// early-stopping test on ||r_{l+1}|| (before the T update, as in the algorithm).
-static __global__ void pcg_stop_kernel(int t, double tol2, PcgScalars S) {
-  for (int c = threadIdx.x; c < t; c += blockDim.x) {
-    if (!S.active[c]) continue;
-    const double rn = S.rnorm2[c];
-    S.relres[c] = sqrt(rn / S.bnorm2[c]);
-    S.stop[c] = (rn <= tol2 * S.bnorm2[c]) ? 1 : 0;
-  }
-}
-
-// beta_{l+1}, the T update, and the freeze of converged columns.
-static __global__ void pcg_beta_kernel(int t, const double* __restrict__ rz_new, int max_iter, PcgScalars S) {
-  __shared__ int cnt;
-  if (threadIdx.x == 0) cnt = 0;
-  __syncthreads();
-  int local = 0;
-  for (int c = threadIdx.x; c < t; c += blockDim.x) {
-    if (!S.active[c]) continue;
-    const int l = S.iters[c];
-    const double a = S.alpha[c], ap = S.alpha_prev[c], bp = S.beta_prev[c];
-    const double b = rz_new[c] / S.rz[c];
-    if (l < S.lmax) {
-      S.Tdiag[(int64_t)c * S.lmax + l] = 1.0 / a + bp / ap;
-      if (l > 0) S.Toff[(int64_t)c * S.lmax + l - 1] = sqrt(bp) / ap;
-    }
-    S.beta[c] = b;
-    S.alpha_prev[c] = a;
-    S.beta_prev[c] = b;
-    S.rz[c] = rz_new[c];
-    S.iters[c] = l + 1;
-    if (S.stop[c] || l + 1 >= max_iter || l + 1 >= S.lmax || !(a > 0.0) || !isfinite(b)) {
-      S.active[c] = 0;
-    } else {
-      ++local;
-    }
-  }
-  atomicAdd(&cnt, local);
-  __syncthreads();
-  if (threadIdx.x == 0) *S.count = cnt;
-}
-
-// u += alpha h, r -= alpha v  (alpha = 0 for frozen columns); fused ||r||^2 partials.
+// u += alpha h, r -= alpha v (alpha = 0 for frozen columns) with ||r||^2 partials, then the
+// stopping test in the last block.
 template <typename T>
-__global__ void pcg_update1_kernel(int n, int t, int ld, int rpb, const double* __restrict__ alpha, T* __restrict__ u,
-                                   T* __restrict__ r, const T* __restrict__ h, const T* __restrict__ v,
-                                   double* __restrict__ partial) {
+__global__ void pcg_update1_kernel(BlockRows br, int t, int ld, T* __restrict__ u, T* __restrict__ r,
+                                   const T* __restrict__ h, const T* __restrict__ v, double* __restrict__ partial,
+                                   ReduceTail rt) {
   const int cx = blockDim.x, ry = blockDim.y;
   const int c = threadIdx.x;
-  const int r0 = blockIdx.x * rpb, r1 = min(n, r0 + rpb);
+  const int r0 = br.row0(blockIdx.x), r1 = br.row1(blockIdx.x);
+  const int k = br.segment(blockIdx.x);
   double acc = 0.0;
   if (c < t) {
-    const T a = (T)alpha[c];
+    const T a = (T)rt.S.alpha[k * t + c];
     T part = T(0);
     int cntf = 0;
     for (int s = r0 + threadIdx.y; s < r1; s += ry) {
@@ -1081,16 +1128,34 @@ __global__ void pcg_update1_kernel(int n, int t, int ld, int rpb, const double* 
     double sum = 0.0;
     for (int y = 0; y < ry; ++y) sum += sh[y * cx + c];
     partial[(int64_t)blockIdx.x * t + c] = sum;
+    __threadfence();
   }
+  reduce_tail(br, t, partial, rt);
 }
 
 // h = z + beta h for active columns.
 template <typename T>
-__global__ void pcg_update2_kernel(int64_t total, int t, int ld, const double* __restrict__ beta,
+__global__ void pcg_update2_kernel(BlockRows br, int t, int ld, const double* __restrict__ beta,
                                    const int* __restrict__ active, const T* __restrict__ z, T* __restrict__ h) {
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int c = (int)(e % ld);
-    if (c < t && active[c]) h[e] = z[e] + (T)beta[c] * h[e];
+  const int c = threadIdx.x;
+  if (c >= t) return;
+  const int q = br.segment(blockIdx.x) * t + c;
+  if (!active[q]) return;
+  const T bt = (T)beta[q];
+  const int r1 = br.row1(blockIdx.x);
+  for (int s = br.row0(blockIdx.x) + threadIdx.y; s < r1; s += blockDim.y) {
+    const int64_t o = (int64_t)s * ld + c;
+    h[o] = z[o] + bt * h[o];
+  }
+}
+
+// out[c] = sum_b partial[b * t + c] (fixed order)
+static __global__ void reduce_partials_kernel(int nblk, int t, const double* __restrict__ partial,
+                                              double* __restrict__ out) {
+  for (int c = threadIdx.x; c < t; c += blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += partial[(int64_t)b * t + c];
+    out[c] = s;
   }
 }
 

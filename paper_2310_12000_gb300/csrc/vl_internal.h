@@ -79,6 +79,7 @@ struct Ctx {
   size_t pinned_bytes = 0;
   int num_sms = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaEvent_t ev_ring[2] = {nullptr, nullptr};   // PCG read-backs one iteration behind
   Profiler prof;
   int64_t launches = 0;           // kernels launched on this context
   unsigned* gbar = nullptr;       // grid-barrier state {count, generation} (device)
@@ -121,6 +122,10 @@ struct Factor {
   Owned mem;
   int64_t n = 0;
   int m = 0;
+  // a batch of independent problems merged into one block-diagonal system: problem k owns the
+  // storage rows [seg_row0[k], seg_row0[k + 1]); a single problem is one segment
+  int nseg = 1;
+  std::vector<int64_t> seg_row0;
   int cov = 0;
   double sigma2 = 1.0, rho = 1.0, nugget = 0.0;
   int64_t nnz = 0;            // off-diagonal entries of B
