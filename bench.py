@@ -499,14 +499,18 @@ def run_ours(args):
     batched = serving_out = None
     if batch_problems:
         from paper_2310_12000_gb300 import batched as bt
-        batched = bt.run_batch(vl, batch_problems, slots=args.slots, device=dev)
+        batched = bt.run_merged(vl, batch_problems, device=dev, steps=2, warmup=1)
         batched.pop("lml", None)
-        print(f"[bench] batched: {batched['completed']} problems in {batched['wall_s']:.1f} s", file=sys.stderr,
-              flush=True)
+        print(f"[bench] batched (merged): {batched['problems']} problems, {batched['seconds_per_batch']:.2f} s per "
+              f"batch", file=sys.stderr, flush=True)
+        if args.batch_streams:
+            streams = bt.run_batch(vl, batch_problems, slots=args.slots, device=dev)
+            streams.pop("lml", None)
+            batched["streams"] = streams
         batched["workload"] = (f"{len(batch_problems)} problems, n log-uniform in [5e3, 5e4] (total "
                                f"{sum(p.n for p in batch_problems)}), m in {{10,20,30}}, uniform locations, "
-                               f"exponential range U[0.02, 0.2], Bernoulli-logit, mode + L^VLA (t=50), float32 + "
-                               f"float64 refinement")
+                               f"exponential range U[0.02, 0.2], Bernoulli-logit, factor rows + mode + L^VLA (t=50), "
+                               f"float32 + float64 refinement, merged into one block-diagonal system")
     if serve_problems:
         serving_out = serving_leg(vl, serve_problems, serve_arrivals, args.serve_seconds, args.slots, dev,
                                   args.small_slots)
@@ -570,6 +574,8 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="arrival window of the serving leg (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=50.0, help="serving arrivals per second")
     ap.add_argument("--slots", type=int, default=16, help="slot contexts of the batched and serving legs")
+    ap.add_argument("--batch-streams", action="store_true",
+                    help="also run the batched problems on slot contexts (one stream each)")
     ap.add_argument("--small-slots", type=int, default=0,
                     help="of the serving slots, how many are sized for n <= 6e4 only (the rest for n = 2e5)")
     args = ap.parse_args()

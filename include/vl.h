@@ -340,6 +340,41 @@ vl_status vl_pcg_solve(vl_state* s, const double* RHS, int t, const vl_opts* opt
  * (VL_ERR_INVALID_ARG otherwise). */
 vl_status vl_lml_grad(vl_state* s, const vl_opts* opts, double* grad, double* dF, vl_stats* stats);
 
+/* ------------------------------------------------------------------------------
+ * Batches: independent problems (the same method, Sections 2-3, applied to each) merged into
+ * one block-diagonal system. The rows of the problems are concatenated and the level sets of
+ * their triangular factors merged level by level, so one launch of every kernel serves all
+ * problems and a triangular solve takes as many levels as the deepest problem. Reductions
+ * are per problem and the Newton and PCG scalars per (problem, column): each problem follows
+ * its own Newton iteration and its own PCG stopping rule, with the probes and tolerances it
+ * would have alone (results equal the problems solved one by one, up to rounding).
+ * Vectors of a batch are the problems' vectors concatenated in problem order, each in its
+ * problem's caller order.
+ * ---------------------------------------------------------------------------- */
+typedef struct vl_batch vl_batch;
+/* Merges nprob factors made by vl_build_factor on ctx (they must outlive the batch; any m,
+ * covariance and size). Copies their neighbour tables, weights and level schedules.
+ * Errors: VL_ERR_INVALID_ARG, VL_ERR_OOM. */
+vl_status vl_batch_create(vl_ctx* ctx, int nprob, vl_factor* const* factors, vl_batch** out);
+/* Copies the members' factor values again after vl_factor_refit of any of them. */
+vl_status vl_batch_refresh(vl_batch* b);
+/* Total rows and the levels of the merged forward / backward solves (pointers may be NULL). */
+vl_status vl_batch_info(const vl_batch* b, int64_t* n_total, int* nlev_fwd, int* nlev_bwd);
+/* Laplace modes of every problem (Eq. newton, as vl_find_mode): lik[k] is problem k's
+ * likelihood (a gamma problem takes opts->lik_shape); y, F (F may be NULL = 0) and mode_out
+ * (may be NULL) hold sum n_k values; stats (NULL or nprob entries) receives each problem's
+ * Newton statistics. VADU or LVA preconditioner. The batch keeps the modes for
+ * vl_batch_log_marglik. VL_ERR_NOT_CONVERGED if any problem stops at newton_max_iter. */
+vl_status vl_batch_find_mode(vl_batch* b, const int* lik, const double* y, const double* F,
+                             const vl_opts* opts, double* mode_out, vl_stats* stats);
+/* L^VLA of every problem at its mode (as vl_log_marglik, each problem with its own opts->t
+ * probes): lml[k] (host, nprob), logdet (NULL or nprob), stats (NULL or nprob). */
+vl_status vl_batch_log_marglik(vl_batch* b, const vl_opts* opts, double* lml, double* logdet,
+                               vl_stats* stats);
+/* SLQ values of the last vl_batch_log_marglik: nprob x t host doubles, problem-major. */
+vl_status vl_batch_gammas(const vl_batch* b, double* gammas, int t);
+void vl_batch_destroy(vl_batch* b);
+
 /* The rank-k pivoted Cholesky factor L_k of Sigma used by the LRAC preconditioner
  * (Section 3.1.2; Harbrecht, Peters & Schneider 2012): residual diagonal d = diag Sigma
  * (nugget included), k steps of pivot p = argmax d (ties to the lowest Vecchia index),

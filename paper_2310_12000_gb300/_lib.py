@@ -63,7 +63,7 @@ def _track(obj):
 
 
 def _close_all():
-    for kind in (State, Factor, Context):
+    for kind in (State, Batch, Factor, Context):
         for r in list(_live):
             o = r()
             if isinstance(o, kind):
@@ -125,6 +125,13 @@ def library():
         "vl_apply_A_noalloc": (st, [vp, vp, i32, vp]),
         "vl_lrac_export": (st, [vp, i32, vp, vp]),
         "vl_lml_grad": (st, [vp, vp, vp, vp, vp]),
+        "vl_batch_create": (st, [vp, i32, vp, vp]),
+        "vl_batch_refresh": (st, [vp]),
+        "vl_batch_info": (st, [vp, vp, vp, vp]),
+        "vl_batch_find_mode": (st, [vp, vp, vp, vp, vp, vp, vp]),
+        "vl_batch_log_marglik": (st, [vp, vp, vp, vp, vp]),
+        "vl_batch_gammas": (st, [vp, vp, i32]),
+        "vl_batch_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -483,3 +490,79 @@ class State:
                                                  Td.ctypes.data if lmax else None, To.ctypes.data if lmax else None,
                                                  it.ctypes.data, rel.ctypes.data))
         return U, Td, To, it, rel
+
+
+class Batch:
+    """Independent problems merged into one block-diagonal system (vl_batch_* in include/vl.h):
+    one launch of every kernel serves all problems, each following its own Newton iteration
+    and PCG stopping rule. Vectors are lists, one array per problem in its caller order."""
+
+    def __init__(self, ctx: Context, factors):
+        self.ctx, self.factors = ctx, list(factors)
+        arr = (C.c_void_p * len(self.factors))(*[f.h.value for f in self.factors])
+        h = C.c_void_p()
+        ctx.check(ctx.lib.vl_batch_create(ctx.h, len(self.factors), arr, C.byref(h)))
+        self.h = h
+        self.sizes = [f.n for f in self.factors]
+        self.offsets = np.concatenate([[0], np.cumsum(self.sizes)]).astype(np.int64)
+        _track(self)
+
+    def close(self):
+        if self.h:
+            self.ctx.lib.vl_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def refresh(self):
+        """Copy the members' factor values again (after Factor.refit of any of them)."""
+        self.ctx.check(self.ctx.lib.vl_batch_refresh(self.h))
+
+    def info(self):
+        n, a, b = C.c_int64(), C.c_int(), C.c_int()
+        self.ctx.check(self.ctx.lib.vl_batch_info(self.h, C.byref(n), C.byref(a), C.byref(b)))
+        return {"n": n.value, "nlev_fwd": a.value, "nlev_bwd": b.value}
+
+    def _split(self, flat):
+        return [flat[self.offsets[k]:self.offsets[k + 1]] for k in range(len(self.sizes))]
+
+    def find_mode(self, liks, ys, Fs=None, opts: Opts | None = None, with_stats: bool = False):
+        """Modes of every problem (a list of arrays); raises if any problem does not converge."""
+        P = len(self.sizes)
+        if len(ys) != P or len(liks) != P or (Fs is not None and len(Fs) != P):
+            raise ValueError(f"expected {P} problems")
+        for k, y in enumerate(ys):
+            _need(y, self.sizes[k], f"y[{k}]")
+        y = np.ascontiguousarray(np.concatenate([np.asarray(v, np.float64) for v in ys]))
+        F = None
+        if Fs is not None:
+            for k, v in enumerate(Fs):
+                _need(v, self.sizes[k], f"F[{k}]")
+            F = np.ascontiguousarray(np.concatenate([np.asarray(v, np.float64) for v in Fs]))
+        lik = np.ascontiguousarray(np.asarray(liks, np.int32))
+        opts = opts or Opts.make()
+        mode = np.empty(int(self.offsets[-1]))
+        st = (Stats * P)()
+        self.ctx.check(self.ctx.lib.vl_batch_find_mode(self.h, lik.ctypes.data, y.ctypes.data, _ptr(F, np.float64),
+                                                       C.byref(opts), mode.ctypes.data, st))
+        modes = self._split(mode)
+        return (modes, [x.as_dict() for x in st]) if with_stats else modes
+
+    def log_marglik(self, opts: Opts | None = None, with_stats: bool = False):
+        """L^VLA of every problem at its mode (an array of nprob values)."""
+        P = len(self.sizes)
+        opts = opts or Opts.make()
+        lml = np.empty(P)
+        ld = np.empty(P)
+        st = (Stats * P)()
+        self.ctx.check(self.ctx.lib.vl_batch_log_marglik(self.h, C.byref(opts), lml.ctypes.data, ld.ctypes.data, st))
+        return (lml, [x.as_dict() for x in st]) if with_stats else lml
+
+    def gammas(self, t: int):
+        g = np.empty(len(self.sizes) * t)
+        self.ctx.check(self.ctx.lib.vl_batch_gammas(self.h, g.ctypes.data, t))
+        return g.reshape(len(self.sizes), t)

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libvl.so")
-SOURCES = ["runtime.cu", "knn.cu", "graph.cu", "factor.cu", "lrac.cu", "api.cu", "grad.cu", "noalloc.cu"]
+SOURCES = ["runtime.cu", "knn.cu", "graph.cu", "factor.cu", "lrac.cu", "api.cu", "grad.cu", "batch.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

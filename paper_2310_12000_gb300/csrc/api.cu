@@ -10,7 +10,7 @@
 #include <string>
 #include <vector>
 
-#include "engine.cuh"
+#include "laplace.cuh"
 
 namespace vl {
 
@@ -105,46 +105,11 @@ __global__ void absmax_kernel(int n, const double* __restrict__ a, const double*
   }
 }
 
-// Smallest storage row whose response lies outside the likelihood's support (Bernoulli:
-// {0, 1}; Poisson: non-negative integers; gamma: y > 0) or whose y or offset is not finite.
-__global__ void check_inputs_kernel(int n, int lik, const double* __restrict__ y, const double* __restrict__ F,
-                                    int* __restrict__ first_bad) {
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
-    const double v = y[s];
-    bool ok = isfinite(v) && isfinite(F[s]);
-    if (lik == VL_LIK_BERNOULLI_LOGIT)
-      ok = ok && (v == 0.0 || v == 1.0);
-    else if (lik == VL_LIK_POISSON_LOG)
-      ok = ok && v >= 0.0 && v == floor(v);
-    else
-      ok = ok && v > 0.0;
-    if (!ok) atomicMin(first_bad, s);
-  }
-}
-
 __global__ void set_wait_limit_kernel(DevStatus* st, long long cycles) { st->limit = cycles; }
 
 // One bounded wait on a flag that nothing sets (the library's timeout path).
 __global__ void wait_probe_kernel(const int* flag, DevStatus* st) {
   if (threadIdx.x == 0) bounded_wait([&] { return ld_acquire(flag) != 0; }, st, -1);
-}
-
-// b_new <- b + 0.5 (b_new - b)
-__global__ void halve_kernel(int n, const double* __restrict__ b, double* __restrict__ bn) {
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) bn[s] = b[s] + 0.5 * (bn[s] - b[s]);
-}
-
-// elementwise helpers for diagonal scalings used by probes / simulation
-__global__ void diag_fn_kernel(int n, int mode, const double* __restrict__ W, const double* __restrict__ D,
-                               double* __restrict__ out) {
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
-    double v;
-    if (mode == 0) v = sqrt(W[s] + 1.0 / D[s]);   // VADU P^{1/2} diagonal
-    else if (mode == 1) v = 1.0 / sqrt(D[s]);     // D^{-1/2}
-    else if (mode == 2) v = sqrt(W[s]);           // W^{1/2}
-    else v = 1.0 / sqrt(W[s]);                    // W^{-1/2} (LRAC probes)
-    out[s] = v;
-  }
 }
 
 // Prediction: mean_p = Fp + sum_c Ap[p,c] b[nbr_p,c];  var_p = Dp + mean_k z4[p,k]^2 with
@@ -261,37 +226,6 @@ static double read_scalar(Ctx* c, const double* dev, vl_status* st) {
   return v;
 }
 
-// sum over n of mode-selected terms (see sum_kernel); float64, fixed order.
-static vl_status dev_sum(Ctx* c, Scratch& S, int n, int mode, const double* a, const double* b, double* host_out) {
-  const int nb = std::max(1, std::min(c->num_sms * 2, (n + 255) / 256));
-  double* part = S.get<double>(nb + 1);
-  if (!part) return fail(c, VL_ERR_OOM, "workspace exhausted (sum)");
-  sum_kernel<<<nb, 256, 0, VL_STREAM(c)>>>(n, mode, a, b, part);
-  reduce_partials_kernel<<<1, 32, 0, VL_STREAM(c)>>>(nb, 1, part, part + nb);
-  VL_CUDA(c, cudaGetLastError());
-  vl_status st = VL_OK;
-  *host_out = read_scalar(c, part + nb, &st);
-  return st;
-}
-
-static vl_status dev_absmax(Ctx* c, Scratch& S, int n, const double* a, const double* b, double* diff, double* amax) {
-  const int nb = std::max(1, std::min(c->num_sms * 2, (n + 255) / 256));
-  double* part = S.get<double>(2 * nb);
-  if (!part) return fail(c, VL_ERR_OOM, "workspace exhausted (absmax)");
-  absmax_kernel<<<nb, 256, 0, VL_STREAM(c)>>>(n, a, b, part);
-  VL_CUDA(c, cudaGetLastError());
-  std::vector<double> h(2 * nb);
-  VL_CUDA(c, cudaMemcpyAsync(h.data(), part, sizeof(double) * 2 * nb, cudaMemcpyDeviceToHost, c->stream));
-  VL_CUDA(c, cudaStreamSynchronize(c->stream));
-  *diff = 0.0;
-  *amax = 0.0;
-  for (int i = 0; i < nb; ++i) {
-    *diff = std::max(*diff, h[2 * i]);
-    *amax = std::max(*amax, h[2 * i + 1]);
-  }
-  return VL_OK;
-}
-
 static vl_status check_opts(Ctx* c, const vl_opts* o) {
   if (!o) return fail(c, VL_ERR_INVALID_ARG, "opts is NULL");
   if (o->precision != VL_FP64 && o->precision != VL_FP32_REFINE)
@@ -310,32 +244,6 @@ static vl_status ensure_precond(Factor* f, const vl_opts* o) {
   return lrac_build(f, o->k);
 }
 
-// ----------------------------------------------------------------------------- log-likelihood pieces
-// psi(b) = sum log p(y | F + b) - b^T Sigma_tilde^{-1} b / 2     (float64)
-static vl_status psi_eval(State* st, Engine<double>& E1, Scratch& S, const double* b, double* psi_out,
-                          double* logp_out, double* quad_out) {
-  Ctx* c = st->ctx;
-  const int n = (int)st->f->n;
-  double* lp = S.get<double>(n);
-  if (!lp) return fail(c, VL_ERR_OOM, "workspace exhausted (psi)");
-  lik_kernel<<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, st->lik, st->shape, st->y, st->F, b, nullptr, nullptr, nullptr,
-                                                       lp);
-  VL_CUDA(c, cudaGetLastError());
-  double logp = 0.0, quad = 0.0;
-  VL_TRY(dev_sum(c, S, n, 0, lp, nullptr, &logp));
-  VL_TRY(E1.opB(b, nullptr, E1.y));
-  VL_TRY(E1.coldot(E1.y, E1.y, E1.Dinv, E1.red));
-  vl_status s = VL_OK;
-  quad = read_scalar(c, E1.red, &s);
-  VL_TRY(s);
-  c->arena.release(lp);
-  S.blocks.erase(std::find(S.blocks.begin(), S.blocks.end(), (void*)lp));
-  if (psi_out) *psi_out = logp - 0.5 * quad;
-  if (logp_out) *logp_out = logp;
-  if (quad_out) *quad_out = quad;
-  return VL_OK;
-}
-
 // VL_ERR_NOT_CONVERGED when a column of the engine's last PCG run stopped at cg_max_iter
 // above cg_tol.
 template <typename T>
@@ -349,91 +257,6 @@ static vl_status cg_converged(Engine<T>& E, const vl_opts* o, const char* what) 
   return VL_OK;
 }
 
-// Newton system (W + Sigma_tilde^{-1}) x = rhs for one column (Eq. newton), float64 in and
-// out; x enters holding the current Newton iterate b, whose residual rhs - A b is grad psi(b).
-// The correction of x is solved by PCG from zero (the appendix algorithm) until
-//   ||rhs - A x|| <= target = max(cg_tol ||rhs||, eta ||rhs - A b||):
-// eta = 0 asks for the full tolerance, eta > 0 makes an inexact Newton step (Eisenstat &
-// Walker, SIAM J. Sci. Comput. 17, 1996). FP64: float64 PCG on the correction. Mixed: float32
-// PCG on corrections of the float64 residual, each to the relative accuracy still missing
-// (at least 1e-6), until the float64 residual meets the target (iterative refinement).
-// The forcing term comes from `fc` once ||grad psi(b)|| is known; fc is updated for the next
-// step. *full: the solve met cg_tol ||rhs||.
-struct Forcing {
-  double eta_max = 0.0;    // 0: every solve to the full tolerance
-  double g_prev = -1.0;    // ||grad psi|| at the previous Newton iterate (< 0: none yet)
-  double eta_prev = -1.0;
-  bool force_full = false;
-  // Eisenstat & Walker (1996), choice 2: eta_k = 0.9 (||g_k|| / ||g_{k-1}||)^2, kept at least
-  // 0.9 eta_{k-1}^2 while that exceeds 0.1, at most eta_max; eta_max while no history exists.
-  double next(double g) {
-    double eta = eta_max;
-    if (force_full || eta_max <= 0.0) {
-      eta = 0.0;
-    } else if (g_prev > 0.0) {
-      eta = 0.9 * (g / g_prev) * (g / g_prev);
-      if (eta_prev > 0.0 && 0.9 * eta_prev * eta_prev > 0.1) eta = std::max(eta, 0.9 * eta_prev * eta_prev);
-      eta = std::min(eta, eta_max);
-    }
-    g_prev = g;
-    eta_prev = eta;
-    return eta;
-  }
-};
-
-static vl_status solve1(State* st, const vl_opts* o, Engine<double>& E64, Engine<float>* E32, const double* rhs,
-                        double* x, Forcing* fc, vl_stats* stats, bool* full) {
-  Ctx* c = st->ctx;
-  const int n = (int)st->f->n;
-  const bool fp64 = o->precision == VL_FP64;
-  Scratch S(c);
-  double* res = S.get<double>(n);
-  double* d64 = fp64 ? S.get<double>(n) : nullptr;
-  float* r32 = fp64 ? nullptr : S.get<float>(n);
-  float* d32 = fp64 ? nullptr : S.get<float>(n);
-  if (!res || (fp64 ? !d64 : (!r32 || !d32))) return fail(c, VL_ERR_OOM, "workspace exhausted (Newton solve)");
-  VL_TRY(E64.coldot(rhs, rhs, nullptr, E64.red));
-  vl_status s = VL_OK;
-  const double bn = std::sqrt(read_scalar(c, E64.red, &s));
-  VL_TRY(s);
-  double rn = 0.0, target = 0.0;
-  int used = 0;
-  for (int pass = 0; pass < 12; ++pass) {
-    VL_TRY(E64.opA(x, res));
-    residual_kernel<<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, rhs, res);
-    VL_TRY(E64.coldot(res, res, nullptr, E64.red));
-    rn = std::sqrt(read_scalar(c, E64.red, &s));
-    VL_TRY(s);
-    if (pass == 0) target = std::max(o->cg_tol * bn, (fc ? fc->next(rn) : 0.0) * rn);
-    if (rn <= target) break;
-    const double inner = std::min(0.1, std::max(fp64 ? 1e-15 : 1e-6, 0.5 * target / rn));
-    if (fp64) {
-      VL_TRY(E64.solve_A1(res, d64, inner, o->cg_max_iter, &used));
-      VL_TRY(cg_converged(E64, o, "Newton solve"));
-      accumulate_kernel<double, double><<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, x, d64);
-    } else {
-      convert_kernel<double, float><<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, res, r32);
-      VL_CUDA(c, cudaGetLastError());
-      VL_TRY(E32->solve_A1(r32, d32, inner, o->cg_max_iter, &used));
-      accumulate_kernel<double, float><<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, x, d32);
-    }
-    VL_CUDA(c, cudaGetLastError());
-    if (stats) {
-      stats->cg_calls++;
-      stats->cg_iters_total += used;
-      stats->cg_iters_max = used;
-      if (!fp64) stats->refine_steps++;
-    }
-  }
-  const double rel = bn > 0 ? rn / bn : 0.0;
-  if (full) *full = rel <= o->cg_tol;
-  if (stats && rel <= o->cg_tol) stats->true_relres_max = std::max(stats->true_relres_max, rel);
-  if (rn > target)
-    return fail(c, VL_ERR_NOT_CONVERGED, fp64 ? "Newton solve did not reach its tolerance"
-                                              : "mixed-precision refinement did not reach cg_tol");
-  return VL_OK;
-}
-
 }  // namespace vl
 
 namespace vl {
@@ -441,173 +264,6 @@ namespace vl {
 __global__ void repack_kernel(int64_t total, const double* __restrict__ in, float* __restrict__ out) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
     out[e] = (float)in[e];
-}
-
-// Zeroes the columns whose flag is 0 (columns that already meet the tolerance get no
-// correction: a zero right-hand side leaves its PCG column inactive).
-template <typename T>
-__global__ void mask_columns_kernel(int64_t total, int ld, const int* __restrict__ keep, T* __restrict__ X) {
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
-    if (!keep[e % ld]) X[e] = T(0);
-}
-
-// Float64 relative residuals ||z_i - S u_i|| / ||z_i|| of the SLQ probe solves (S the system
-// operator of the preconditioner's form, z_i = P^{1/2} r_i built again in float64 from the same
-// probes). Float32 solves are refined by float32 correction solves of the float64 residual until
-// every column meets cg_tol; this leaves T (already turned into gamma_i) alone.
-template <typename T>
-static vl_status probe_residuals(State* st, const vl_opts* o, Engine<T>& E, T* Rm, T* Zm, T* Um, const double* r1,
-                                 vl_stats* stats) {
-  Ctx* c = st->ctx;
-  Factor* f = st->f;
-  const int n = (int)f->n, t = o->t, ld = E.ld;
-  const int64_t vec = (int64_t)n * ld;
-  std::vector<double> bn(t), rn(t);
-  auto norms = [&](Engine<double>& E64, const double* X, std::vector<double>& out) -> vl_status {
-    VL_TRY(E64.coldot(X, X, nullptr, E64.red));
-    VL_CUDA(c, cudaMemcpyAsync(out.data(), E64.red, sizeof(double) * t, cudaMemcpyDeviceToHost, c->stream));
-    VL_CUDA(c, cudaStreamSynchronize(c->stream));
-    return VL_OK;
-  };
-  auto worst = [&]() {
-    double w = 0.0;
-    for (int k = 0; k < t; ++k) w = std::max(w, bn[k] > 0 ? std::sqrt(rn[k] / bn[k]) : 0.0);
-    return w;
-  };
-  if constexpr (std::is_same<T, double>::value) {
-    VL_TRY(E.opSys(Um, E.v));
-    residual_kernel<<<grid_for(c, vec), 256, 0, VL_STREAM(c)>>>(vec, Zm, E.v);
-    VL_CUDA(c, cudaGetLastError());
-    VL_TRY(norms(E, Zm, bn));
-    VL_TRY(norms(E, E.v, rn));
-    if (stats) stats->probe_relres_max = worst();
-    return VL_OK;
-  } else {
-    Scratch S(c);
-    Engine<double> E64(c);
-    VL_TRY(E64.init(f, t, o->precond, st->W, 0, /*ops_only=*/true));
-    double* Zd = S.get<double>(vec);
-    double* Ud = S.get<double>(vec);
-    double* Res = S.get<double>(vec);
-    double* sc64 = S.get<double>(n);
-    int* keep = S.get<int>(ld);
-    if (!Zd || !Ud || !Res || !sc64 || !keep) return fail(c, VL_ERR_OOM, "workspace exhausted (probe residuals)");
-    // the probes of slq_run again, in float64
-    rademacher_kernel<double><<<(n + 127) / 128, 128, 0, VL_STREAM(c)>>>(n, t, ld, f->s2u, o->seed, 0, 0, Res);
-    const int dmode = o->precond == VL_PREC_VADU ? 0 : (o->precond == VL_PREC_LVA ? 1 : 3);
-    diag_fn_kernel<<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, dmode, st->W, f->D64, sc64);
-    VL_CUDA(c, cudaGetLastError());
-    if (o->precond == VL_PREC_LRAC)
-      VL_TRY(E64.lrac_lowrank_plus(r1, Res, sc64, Zd));
-    else
-      VL_TRY(E64.opBt(Res, sc64, nullptr, nullptr, Zd));
-    VL_TRY(norms(E64, Zd, bn));
-    std::vector<int> hkeep(ld, 0);
-    double rel = 1.0;
-    int pass = 0;
-    // the solution is carried in float64 from here on: a float32 copy of it could not hold
-    // a residual below about cond * 2^-24
-    convert_kernel<float, double><<<grid_for(c, vec), 256, 0, VL_STREAM(c)>>>(vec, Um, Ud);
-    for (;; ++pass) {
-      VL_TRY(E64.opSys(Ud, Res));
-      residual_kernel<<<grid_for(c, vec), 256, 0, VL_STREAM(c)>>>(vec, Zd, Res);
-      VL_CUDA(c, cudaGetLastError());
-      VL_TRY(norms(E64, Res, rn));
-      rel = worst();
-      if (rel <= o->cg_tol || pass == 12) break;
-      // correction solves for the columns still above cg_tol, each to the accuracy it lacks
-      double inner = 0.5;
-      for (int k = 0; k < t; ++k) {
-        const double rk = bn[k] > 0 ? std::sqrt(rn[k] / bn[k]) : 0.0;
-        hkeep[k] = rk > o->cg_tol ? 1 : 0;
-        if (hkeep[k]) inner = std::min(inner, 0.5 * o->cg_tol / rk);
-      }
-      inner = std::max(inner, 1e-6);
-      VL_CUDA(c, cudaMemcpyAsync(keep, hkeep.data(), sizeof(int) * ld, cudaMemcpyHostToDevice, c->stream));
-      convert_kernel<double, float><<<grid_for(c, vec), 256, 0, VL_STREAM(c)>>>(vec, Res, Zm);
-      mask_columns_kernel<float><<<grid_for(c, vec), 256, 0, VL_STREAM(c)>>>(vec, ld, keep, Zm);
-      VL_CUDA(c, cudaGetLastError());
-      int used = 0;
-      VL_TRY(E.pcg(Zm, Rm, inner, o->cg_max_iter, &used));
-      accumulate_kernel<double, float><<<grid_for(c, vec), 256, 0, VL_STREAM(c)>>>(vec, Ud, Rm);
-      VL_CUDA(c, cudaGetLastError());
-      if (stats) stats->cg_iters_total += used;
-    }
-    if (stats) {
-      stats->probe_relres_max = rel;
-      stats->probe_refine_steps = pass;
-      stats->true_relres_max = std::max(stats->true_relres_max, rel);
-    }
-    if (rel > o->cg_tol) return fail(c, VL_ERR_NOT_CONVERGED, "SLQ probe solves: refinement did not reach cg_tol");
-    return VL_OK;
-  }
-}
-
-// SLQ (Eq. def_SLQ): probes z = P^{1/2} r, PCG on the preconditioner's system with
-// T extraction, gamma_i = (r_0^T z_0)_i e1^T log(T_i) e1. Returns the t gammas on the
-// host and, for LRAC, log det(I + L^T W L) of the same engine in *logdetC.
-template <typename T>
-static vl_status slq_run(State* st, const vl_opts* o, std::vector<double>& gam, vl_stats* stats, double* logdetC) {
-  Ctx* c = st->ctx;
-  Factor* f = st->f;
-  const int n = (int)f->n, t = o->t;
-  Scratch S(c);
-  Engine<T> E(c);
-  VL_TRY(ensure_precond(f, o));
-  VL_TRY(E.init(f, t, o->precond, st->W, o->cg_max_iter + 1));
-  // VADU: z = B^T (W + D^{-1})^{1/2} r;  LVA: z = B^T D^{-1/2} r     (Section 3.1.1)
-  T* Rm = S.get<T>((size_t)n * E.ld);
-  T* Zm = S.get<T>((size_t)n * E.ld);
-  T* Um = S.get<T>((size_t)n * E.ld);
-  double* sc64 = S.get<double>(n);
-  T* sc = S.get<T>(n);
-  double* gdev = S.get<double>(t);
-  double* work = S.get<double>((size_t)3 * t * E.lmax);
-  int* bad = S.get<int>(1);
-  if (!Rm || !Zm || !Um || !sc64 || !sc || !gdev || !work || !bad) return fail(c, VL_ERR_OOM, "workspace exhausted (SLQ)");
-  rademacher_kernel<T><<<(n + 127) / 128, 128, 0, VL_STREAM(c)>>>(n, t, E.ld, f->s2u, o->seed, 0, 0, Rm);
-  const int dmode = o->precond == VL_PREC_VADU ? 0 : (o->precond == VL_PREC_LVA ? 1 : 3);
-  diag_fn_kernel<<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, dmode, st->W, f->D64, sc64);
-  convert_kernel<double, T><<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, sc64, sc);
-  VL_CUDA(c, cudaGetLastError());
-  double* r1 = nullptr;
-  if (o->precond == VL_PREC_LRAC) {
-    // z = L r1 + W^{-1/2} r2, r1 in {+-1}^k drawn by rank index on stream 3 (Section 3.1.2)
-    r1 = S.get<double>((size_t)E.kr * t);
-    if (!r1) return fail(c, VL_ERR_OOM, "workspace exhausted (SLQ probes)");
-    rademacher_kernel<double><<<(E.kr + 127) / 128, 128, 0, VL_STREAM(c)>>>(E.kr, t, t, nullptr, o->seed, 3, 0, r1);
-    VL_CUDA(c, cudaGetLastError());
-    VL_TRY(E.lrac_lowrank_plus(r1, Rm, sc, Zm));
-  } else {
-    VL_TRY(E.opBt(Rm, sc, nullptr, nullptr, Zm));
-  }
-  int used = 0;
-  VL_TRY(E.pcg(Zm, Um, o->cg_tol, o->cg_max_iter, &used));
-  VL_CUDA(c, cudaMemsetAsync(bad, 0, sizeof(int), c->stream));
-  slq_quad_kernel<<<(t + 63) / 64, 64, 0, VL_STREAM(c)>>>(t, E.lmax, E.S.Tdiag, E.S.Toff, E.S.iters, E.S.rz0, work, gdev,
-                                                       bad);
-  VL_CUDA(c, cudaGetLastError());
-  std::vector<int> iters;
-  std::vector<double> rel;
-  VL_TRY(E.column_stats(iters, rel));
-  int hbad = 0;
-  gam.resize(t);
-  VL_CUDA(c, cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-  VL_CUDA(c, cudaMemcpyAsync(gam.data(), gdev, sizeof(double) * t, cudaMemcpyDeviceToHost, c->stream));
-  VL_CUDA(c, cudaStreamSynchronize(c->stream));
-  if (hbad) return fail(c, VL_ERR_NOT_CONVERGED, "SLQ: tridiagonal eigen-solve failed (non-positive Ritz value)");
-  const int itmax = *std::max_element(iters.begin(), iters.end());
-  const double relmax = *std::max_element(rel.begin(), rel.end());
-  if (stats) {
-    stats->cg_calls++;
-    stats->cg_iters_max = itmax;
-    stats->cg_iters_total += std::accumulate(iters.begin(), iters.end(), 0);
-    stats->cg_relres_max = relmax;
-  }
-  if (relmax > o->cg_tol && itmax >= o->cg_max_iter)
-    return fail(c, VL_ERR_NOT_CONVERGED, "SLQ probe solves reached cg_max_iter");
-  if (logdetC) *logdetC = (o->precond == VL_PREC_LRAC) ? E.logdetC : 0.0;
-  return probe_residuals<T>(st, o, E, Rm, Zm, Um, r1, stats);
 }
 
 // U = (W + Sigma_tilde^{-1})^{-1} z3 for simulation columns [col0, col0 + sc),
@@ -625,8 +281,8 @@ static vl_status sim_block(State* st, const vl_opts* o, Engine<double>& E64, int
   double* sW = S.get<double>(n);
   double* sD = S.get<double>(n);
   if (!z1 || !z2 || !z3 || !sW || !sD) return fail(c, VL_ERR_OOM, "workspace exhausted (simulation)");
-  gaussian_kernel<<<(n + 127) / 128, 128, 0, VL_STREAM(c)>>>(n, sc, ld, col0, f->s2u, o->seed, 1, z1);
-  gaussian_kernel<<<(n + 127) / 128, 128, 0, VL_STREAM(c)>>>(n, sc, ld, col0, f->s2u, o->seed, 2, z2);
+  gaussian_kernel<<<(n + 127) / 128, 128, 0, VL_STREAM(c)>>>(n, sc, ld, col0, f->s2u_probe(), o->seed, 1, z1);
+  gaussian_kernel<<<(n + 127) / 128, 128, 0, VL_STREAM(c)>>>(n, sc, ld, col0, f->s2u_probe(), o->seed, 2, z2);
   diag_fn_kernel<<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, 2, st->W, f->D64, sW);
   diag_fn_kernel<<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, 1, st->W, f->D64, sD);
   VL_CUDA(c, cudaGetLastError());
@@ -816,8 +472,17 @@ vl_status vl_ctx_create(int device, void* cuda_stream, void* workspace, size_t w
   return VL_OK;
 }
 
-// A context lives until it has been destroyed and every factor and state made on
+// A context lives until it has been destroyed and every factor, state and batch made on
 // it has been destroyed too, in whatever order those calls come.
+static void ctx_release(Ctx* cc);
+
+}  // extern "C"
+namespace vl {
+void ctx_retain(Ctx* c) { ++c->refs; }
+void ctx_release_ref(Ctx* c) { ctx_release(c); }
+}  // namespace vl
+extern "C" {
+
 static void ctx_release(Ctx* cc) {
   if (--cc->refs > 0) return;
   vl_ctx* c = static_cast<vl_ctx*>(cc);
@@ -1133,7 +798,7 @@ vl_status vl_find_mode(vl_factor* f, int lik, const double* y, const double* F, 
     int* bad = S.get<int>(2);
     if (!bad) return bail(fail(c, VL_ERR_OOM, "workspace exhausted (input check)"));
     cudaMemsetAsync(bad, 0x7f, sizeof(int), c->stream);
-    check_inputs_kernel<<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, lik, st->y, st->F, bad);
+    check_inputs_kernel<<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, lik_spec(st), st->y, st->F, bad);
     int hb[2] = {0, 0};
     double hv[2] = {0.0, 0.0};
     if (cudaMemcpyAsync(hb, bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
@@ -1152,69 +817,12 @@ vl_status vl_find_mode(vl_factor* f, int lik, const double* y, const double* F, 
     }
   }
   // Newton iterations (Eq. newton)
-  Scratch S(c);
-  double* g = S.get<double>(n);
-  double* rhs = S.get<double>(n);
-  double* bn = S.get<double>(n);
-  if (!g || !rhs || !bn) return bail(fail(c, VL_ERR_OOM, "workspace exhausted (Newton)"));
-  const bool mixed = opts->precision == VL_FP32_REFINE;
-  Engine<double> E64(c);
-  Engine<float> E32(c);
-  vl_stats stats{};
-  double psi = 0.0;
-  int it = 0;
-  bool converged = false;
-  s = ensure_precond(f, opts);
+  std::vector<vl_stats> ss;
+  std::vector<char> conv;
+  s = newton_run(st, opts, ss, conv);
   if (s != VL_OK) return bail(s);
-  s = E64.init(f, 1, opts->precond, st->W, mixed ? 0 : opts->cg_max_iter + 1);
-  if (s != VL_OK) return bail(s);
-  s = psi_eval(st, E64, S, st->b, &psi, nullptr, nullptr);
-  if (s != VL_OK) return bail(s);
-  // inexact Newton: forcing terms eta_k = 0.9 (||grad psi_k|| / ||grad psi_{k-1}||)^2 with the
-  // safeguard max(eta_k, 0.9 eta_{k-1}^2) while that exceeds 0.1, capped at opts->newton_eta_max
-  // (Eisenstat & Walker 1996, choice 2); the iteration ends only after a full-tolerance solve
-  Forcing fc;
-  fc.eta_max = opts->newton_eta_max > 0.0 ? std::min(opts->newton_eta_max, 0.9) : 0.0;
-  for (it = 1; it <= opts->newton_max_iter; ++it) {
-    lik_kernel<<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, lik, st->shape, st->y, st->F, st->b, st->W, g, rhs, nullptr);
-    s = E64.set_W(st->W);
-    if (s != VL_OK) return bail(s);
-    if (mixed) {
-      s = E32.W ? E32.set_W(st->W) : E32.init(f, 1, opts->precond, st->W, opts->cg_max_iter + 1);
-      if (s != VL_OK) return bail(s);
-    }
-    if (cudaGetLastError() != cudaSuccess) return bail(fail(c, VL_ERR_CUDA, "Newton setup"));
-    cudaMemcpyAsync(bn, st->b, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream);  // the correction form
-    bool full = false;
-    s = solve1(st, opts, E64, mixed ? &E32 : nullptr, rhs, bn, &fc, &stats, &full);
-    if (s != VL_OK) return bail(s);
-    double psi_new = 0.0;
-    s = psi_eval(st, E64, S, bn, &psi_new, nullptr, nullptr);
-    if (s != VL_OK) return bail(s);
-    for (int hlv = 0; hlv < 30 && psi_new < psi - 1e-12 * (1.0 + std::fabs(psi)); ++hlv) {
-      halve_kernel<<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, st->b, bn);
-      s = psi_eval(st, E64, S, bn, &psi_new, nullptr, nullptr);
-      if (s != VL_OK) return bail(s);
-    }
-    double step = 0.0, bmax = 0.0;
-    s = dev_absmax(c, S, n, bn, st->b, &step, &bmax);
-    if (s != VL_OK) return bail(s);
-    cudaMemcpyAsync(st->b, bn, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream);
-    psi = psi_new;
-    if (!std::isfinite(psi)) return bail(fail(c, VL_ERR_NOT_CONVERGED, "Newton: non-finite objective"));
-    if (step <= opts->newton_tol * (1.0 + bmax)) {
-      if (full) {
-        converged = true;
-        break;
-      }
-      fc.force_full = true;   // a small step from an inexact solve: confirm with a full one
-    }
-  }
-  // W at the mode
-  lik_kernel<<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, lik, st->shape, st->y, st->F, st->b, st->W, nullptr, nullptr,
-                                                       nullptr);
-  if (cudaGetLastError() != cudaSuccess) return bail(fail(c, VL_ERR_CUDA, "lik"));
   if (mode_out) {
+    Scratch S(c);
     double* mu = S.get<double>(n);
     if (!mu) return bail(fail(c, VL_ERR_OOM, "workspace exhausted (mode out)"));
     from_storage_kernel<double><<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, 1, 1, f->s2u, st->b, mu);
@@ -1222,11 +830,10 @@ vl_status vl_find_mode(vl_factor* f, int lik, const double* y, const double* F, 
     if (s != VL_OK) return bail(s);
   }
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return bail(fail(c, VL_ERR_CUDA, "sync"));
-  stats.newton_iters = it;
-  st->mode_stats = stats;
+  st->mode_stats = ss[0];
   ++c->refs;
   *out = st;
-  if (!converged) return fail(c, VL_ERR_NOT_CONVERGED, "Newton reached newton_max_iter");
+  if (!conv[0]) return fail(c, VL_ERR_NOT_CONVERGED, "Newton reached newton_max_iter");
   return VL_OK;
 }
 
@@ -1251,52 +858,35 @@ vl_status vl_log_marglik(vl_state* st, const vl_opts* o, double* lml, double* lo
   Ctx* c = st->ctx;
   VL_TRY(check_opts(c, o));
   if (!lml) return fail(c, VL_ERR_INVALID_ARG, "lml is NULL");
-  Factor* f = st->f;
-  const int n = (int)f->n, t = o->t;
+  const int t = o->t;
   VL_CUDA(c, cudaEventRecord(c->ev0, c->stream));
-  vl_stats loc{};
-  std::vector<double> g;
-  double logdetC = 0.0;
+  SlqOut q;
   if (o->precision == VL_FP64)
-    VL_TRY(slq_run<double>(st, o, g, &loc, &logdetC));
+    VL_TRY(slq_run<double>(st, o, q));
   else
-    VL_TRY(slq_run<float>(st, o, g, &loc, &logdetC));
-  double mean = 0.0;
-  for (double v : g) mean += v;
-  mean /= t;
-  double var = 0.0;
-  for (double v : g) var += (v - mean) * (v - mean);
-  const double se = t > 1 ? std::sqrt(var / (t - 1) / t) : 0.0;
-  Scratch S(c);
-  Engine<double> E1(c);
-  VL_TRY(E1.init(f, 1, VL_PREC_VADU, st->W, 0));   // only B products for psi
-  double logp = 0.0, quad = 0.0;
-  VL_TRY(psi_eval(st, E1, S, st->b, nullptr, &logp, &quad));
-  double ld = 0.0;
-  if (o->precond == VL_PREC_LRAC) {
-    ld = logdetC + mean;   // Eq. logdetsplit2 with log det P = log det C - log det W
-  } else {
-    double sum_log_D = 0.0, sum_log_P = 0.0;
-    VL_TRY(dev_sum(c, S, n, 1, f->D64, nullptr, &sum_log_D));
-    if (o->precond == VL_PREC_VADU)
-      VL_TRY(dev_sum(c, S, n, 2, f->D64, st->W, &sum_log_P));   // log det P = log det(W + D^{-1})
-    else
-      sum_log_P = -sum_log_D;                                   // log det P = log det D^{-1}
-    ld = sum_log_D + sum_log_P + mean;                          // Eq. logdetsplit
-  }
-  *lml = -logp + 0.5 * quad + 0.5 * ld;                       // Eq. VLA_loss
-  if (logdet) *logdet = ld;
-  st->h_gammas = g;
+    VL_TRY(slq_run<float>(st, o, q));
+  LmlOut L;
+  VL_TRY(lml_assemble(st, o, q, L));
+  *lml = L.lml[0];
+  if (logdet) *logdet = L.logdet[0];
+  st->h_gammas.assign(q.gam.begin(), q.gam.begin() + t);
   st->last_t = t;
   VL_CUDA(c, cudaEventRecord(c->ev1, c->stream));
   VL_CUDA(c, cudaEventSynchronize(c->ev1));
   float ms = 0.f;
   cudaEventElapsedTime(&ms, c->ev0, c->ev1);
   if (stats) {
-    *stats = loc;
-    stats->slq_mean = mean;
-    stats->slq_stderr = se;
-    stats->logdet = ld;
+    *stats = vl_stats{};
+    stats->cg_calls = 1;
+    stats->cg_iters_max = *std::max_element(q.iters.begin(), q.iters.end());
+    stats->cg_iters_total = (int)(std::accumulate(q.iters.begin(), q.iters.end(), (int64_t)0) + q.extra_iters);
+    stats->cg_relres_max = *std::max_element(q.relres.begin(), q.relres.end());
+    stats->true_relres_max = q.true_rel[0];
+    stats->probe_relres_max = q.true_rel[0];
+    stats->probe_refine_steps = q.passes[0];
+    stats->slq_mean = L.mean[0];
+    stats->slq_stderr = L.se[0];
+    stats->logdet = L.logdet[0];
     stats->ms_total = ms;
   }
   return VL_OK;

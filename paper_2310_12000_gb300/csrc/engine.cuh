@@ -218,6 +218,7 @@ struct Engine {
   int nblk = 1, rpb = 1;
   int nseg = 1, ncol = 1;          // segments (problems of a batch) and nseg * t scalar columns
   BlockRows br{};                  // reduction blocks (segment-aligned)
+  std::vector<int32_t> h_blk_seg;  // segment of each reduction block (batches; empty: all 0)
   unsigned* done = nullptr;        // arrival counter of the fused reductions
   dim3 cb;
   size_t csh = 0;
@@ -300,17 +301,19 @@ struct Engine {
       if (!*p) return fail(c, VL_ERR_OOM, "workspace exhausted (Krylov vectors)");
       VL_CUDA(c, cudaMemsetAsync(*p, 0, sizeof(T) * vec, c->stream));
     }
-    const int cx = (t == 1) ? 1 : (t + 31) / 32 * 32;
-    cb = dim3(cx, 256 / cx);
-    csh = sizeof(double) * 256;
+    // column sweeps: 1024-thread blocks (cx lanes over the columns, a power of two), at most
+    // two per SM, so that the last block's final sums read few partials
+    const int cx = (t == 1) ? 1 : (t <= 32 ? 32 : (t <= 64 ? 64 : (t <= 128 ? 128 : 256)));
+    cb = dim3(cx, 1024 / cx);
+    csh = sizeof(double) * 1024;
     nseg = std::max(1, f->nseg);
     ncol = nseg * t;
     const int64_t want = (n + (int64_t)cb.y * 8 - 1) / ((int64_t)cb.y * 8);
-    nblk = (int)std::max<int64_t>(1, std::min<int64_t>(want, 4LL * c->num_sms));
+    nblk = (int)std::max<int64_t>(1, std::min<int64_t>(want, 2LL * c->num_sms));
     rpb = (n + nblk - 1) / nblk;
     br = BlockRows{n, rpb, nblk, 1, nullptr, nullptr, nullptr, nullptr};
     if (nseg > 1) VL_TRY(segment_blocks());
-    partial = mem.get<double>((size_t)nblk * t);
+    partial = mem.get<double>((size_t)nblk * std::max(t, 2));
     red = mem.get<double>(ncol);
     red2 = mem.get<double>(ncol);
     done = mem.get<unsigned>(1);
@@ -530,6 +533,7 @@ struct Engine {
     VL_CUDA(c, cudaMemcpyAsync(d, all.data(), sizeof(int32_t) * all.size(), cudaMemcpyHostToDevice, c->stream));
     VL_CUDA(c, cudaStreamSynchronize(c->stream));
     br = BlockRows{n, rpb, nblk, nseg, d, d + nblk, d + 2 * nblk, d + 3 * nblk};
+    h_blk_seg = bs;
     return VL_OK;
   }
 
@@ -880,10 +884,10 @@ struct Engine {
 
   // Solves (W + Sigma_tilde^{-1}) D = Rm. VADU / LVA: PCG on form 1. LRAC: PCG on
   // form 2, (Sigma_tilde + W^{-1}) X = Sigma_tilde Rm, then D = W^{-1} X.
-  vl_status solve_A1(const T* Rm, T* Dm, double tol, int max_iter, int* iters_used) {
-    if (prec != VL_PREC_LRAC) return pcg(Rm, Dm, tol, max_iter, iters_used);
+  vl_status solve_A1(const T* Rm, T* Dm, double tol, int max_iter, int* iters_used, const double* tol2v = nullptr) {
+    if (prec != VL_PREC_LRAC) return pcg(Rm, Dm, tol, max_iter, iters_used, tol2v);
     VL_TRY(opSigma(Rm, b2));
-    VL_TRY(pcg(b2, Dm, tol, max_iter, iters_used));
+    VL_TRY(pcg(b2, Dm, tol, max_iter, iters_used, tol2v));
     scale_rows_kernel<T><<<grid_for(c, (int64_t)n * ld), 256, 0, VL_STREAM(c)>>>(n, t, ld, Winv, Dm);
     VL_CUDA(c, cudaGetLastError());
     return VL_OK;

@@ -990,8 +990,22 @@ struct ReduceTail {
   unsigned* done;       // arrival counter of the launch's blocks (zero at launch, reset by the last)
 };
 
-// Runs in the last block to finish: per (segment, column) sums of the block partials in block
-// order, then the epilogue. Every thread of the block calls it.
+// Column sums of a block's per-thread values acc (thread (c, y) of blockDim (cx, ry)) into
+// sh[c] by a fixed pairwise tree over y; ry is a power of two. Every thread calls it.
+__device__ __forceinline__ double block_col_sum(double acc, double* sh) {
+  const int cx = blockDim.x, c = threadIdx.x, y = threadIdx.y;
+  sh[y * cx + c] = acc;
+  __syncthreads();
+  for (int h = blockDim.y >> 1; h > 0; h >>= 1) {
+    if (y < h) sh[y * cx + c] += sh[(y + h) * cx + c];
+    __syncthreads();
+  }
+  return sh[c];
+}
+
+// Runs in the last block to finish: per (segment, column) sums of the block partials, each
+// by one warp (lanes take the segment's blocks at a stride of 32, then a fixed shuffle tree,
+// so the order does not depend on scheduling), then the epilogue. Every thread calls it.
 __device__ __forceinline__ void reduce_tail(const BlockRows& br, int t, const double* __restrict__ partial,
                                             const ReduceTail& rt) {
   __shared__ int last;
@@ -1009,10 +1023,14 @@ __device__ __forceinline__ void reduce_tail(const BlockRows& br, int t, const do
   const PcgScalars& S = rt.S;
   int local = 0;
   const int ncol = br.nseg * t;
-  for (int q = tid; q < ncol; q += nth) {
+  const int lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
+  for (int q = warp; q < ncol; q += nwarp) {
     const int k = q / t, c = q - k * t;
     double sum = 0.0;
-    for (int b = br.blk0(k); b < br.blk1(k); ++b) sum += __ldcg(&partial[(int64_t)b * t + c]);
+    for (int b = br.blk0(k) + lane; b < br.blk1(k); b += 32) sum += __ldcg(&partial[(int64_t)b * t + c]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane != 0) continue;
     if (rt.epi == EPI_NONE) {
       rt.out[q] = sum;
     } else if (rt.epi == EPI_ALPHA) {
@@ -1058,7 +1076,7 @@ __device__ __forceinline__ void reduce_tail(const BlockRows& br, int t, const do
 template <typename T>
 __global__ void coldot_kernel(BlockRows br, int t, int ld, const T* __restrict__ X, const T* __restrict__ Y,
                               const T* __restrict__ w, double* __restrict__ partial, ReduceTail rt) {
-  const int cx = blockDim.x, ry = blockDim.y;
+  const int ry = blockDim.y;
   const int c = threadIdx.x;
   const int r0 = br.row0(blockIdx.x), r1 = br.row1(blockIdx.x);
   double acc = 0.0;
@@ -1079,11 +1097,8 @@ __global__ void coldot_kernel(BlockRows br, int t, int ld, const T* __restrict__
     acc += (double)a;
   }
   extern __shared__ double sh[];
-  sh[threadIdx.y * cx + c] = acc;
-  __syncthreads();
+  const double sum = block_col_sum(acc, sh);
   if (threadIdx.y == 0 && c < t) {
-    double sum = 0.0;
-    for (int y = 0; y < ry; ++y) sum += sh[y * cx + c];
     partial[(int64_t)blockIdx.x * t + c] = sum;
     __threadfence();
   }
@@ -1096,7 +1111,7 @@ template <typename T>
 __global__ void pcg_update1_kernel(BlockRows br, int t, int ld, T* __restrict__ u, T* __restrict__ r,
                                    const T* __restrict__ h, const T* __restrict__ v, double* __restrict__ partial,
                                    ReduceTail rt) {
-  const int cx = blockDim.x, ry = blockDim.y;
+  const int ry = blockDim.y;
   const int c = threadIdx.x;
   const int r0 = br.row0(blockIdx.x), r1 = br.row1(blockIdx.x);
   const int k = br.segment(blockIdx.x);
@@ -1122,11 +1137,8 @@ __global__ void pcg_update1_kernel(BlockRows br, int t, int ld, T* __restrict__ 
     acc += (double)part;
   }
   extern __shared__ double sh[];
-  sh[threadIdx.y * cx + c] = acc;
-  __syncthreads();
+  const double sum = block_col_sum(acc, sh);
   if (threadIdx.y == 0 && c < t) {
-    double sum = 0.0;
-    for (int y = 0; y < ry; ++y) sum += sh[y * cx + c];
     partial[(int64_t)blockIdx.x * t + c] = sum;
     __threadfence();
   }

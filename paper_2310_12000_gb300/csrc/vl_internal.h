@@ -126,6 +126,10 @@ struct Factor {
   // storage rows [seg_row0[k], seg_row0[k + 1]); a single problem is one segment
   int nseg = 1;
   std::vector<int64_t> seg_row0;
+  int32_t* row_seg = nullptr;   // storage row -> segment (device; batches only)
+  int32_t* s2u_loc = nullptr;   // storage row -> caller index within its problem (batches only)
+  // caller index that numbers a row's probe and simulation draws (its problem's own index)
+  const int32_t* s2u_probe() const { return s2u_loc ? s2u_loc : s2u; }
   int cov = 0;
   double sigma2 = 1.0, rho = 1.0, nugget = 0.0;
   int64_t nnz = 0;            // off-diagonal entries of B
@@ -181,6 +185,8 @@ struct State {
   Owned mem;
   int lik = 0;
   double shape = 1.0;   // gamma shape (VL_LIK_GAMMA_LOG)
+  int* d_seg_lik = nullptr;        // batches: likelihood and shape of every problem (device)
+  double* d_seg_shape = nullptr;
   double* y = nullptr;     // storage order
   double* F = nullptr;
   double* b = nullptr;     // mode
