@@ -258,6 +258,19 @@ vl_status vl_slq_gammas(const vl_state* s, double* gammas, int t);
 vl_status vl_pred_var(vl_state* s, const double* test_locs, int64_t np, const double* Fp,
                       const vl_opts* opts, double* mean, double* var, vl_stats* stats);
 
+/* Latent predictive means and variances (Eq. latentpostpredictive) at np test locations with
+ * the variances from a rank-k preconditioned Lanczos factorisation (Section 4, "Predictive
+ * (co-)variances using preconditioned Lanczos algorithms") instead of simulation: k steps of
+ * Lanczos with full reorthogonalisation on P^{-1/2} (W + Sigma_tilde^{-1}) P^{-T/2} from
+ * P^{-1/2} times the mean of the columns of B_po^T, giving
+ * var_p ~ D_p + z_p^T T^{-1} z_p, z_p = Q^T P^{-1/2} B_po^T e_p (fewer than k steps when the
+ * Krylov space closes). precond_l selects the Lanczos preconditioner: 1 = P_L1 =
+ * B^T (W + D^{-1}) B (the only one available; others: VL_ERR_INVALID_ARG). Float64. The
+ * estimate is biased low for small k and exact at k = n. mean/var: np doubles (either may be
+ * NULL); stats->cg_iters_max receives the number of Lanczos steps taken. */
+vl_status vl_pred_var_lanczos(vl_state* s, const double* test_locs, int64_t np, const double* Fp,
+                              int k, int precond_l, double* mean, double* var, vl_stats* stats);
+
 /* Kernel timing. While enabled (enable >= 1), every launch of the library's hot kernels is
  * bracketed by a pair of CUDA events on the context's stream, grouped by kernel
  * class and block width: "sptrsv_fwd", "sptrsv_bwd", "spmv_B", "spmv_Bt",

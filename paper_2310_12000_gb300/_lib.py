@@ -125,6 +125,7 @@ def library():
         "vl_apply_A_noalloc": (st, [vp, vp, i32, vp]),
         "vl_lrac_export": (st, [vp, i32, vp, vp]),
         "vl_lml_grad": (st, [vp, vp, vp, vp, vp]),
+        "vl_pred_var_lanczos": (st, [vp, vp, i64, vp, i32, i32, vp, vp, vp]),
         "vl_batch_create": (st, [vp, i32, vp, vp]),
         "vl_batch_refresh": (st, [vp]),
         "vl_batch_info": (st, [vp, vp, vp, vp]),
@@ -451,6 +452,20 @@ class State:
         self.ctx.check(self.ctx.lib.vl_pred_var(self.h, _ptr(test_locs, np.float64), n_p, _ptr(Fp, np.float64),
                                                 C.byref(opts), _ptr(mean, np.float64), _ptr(var, np.float64),
                                                 C.byref(st)))
+        return (mean, var, st.as_dict()) if with_stats else (mean, var)
+
+    def pred_var_lanczos(self, test_locs, k: int, Fp=None, precond_l: int = 1, with_stats: bool = False):
+        """Predictive mean and variance with rank-k preconditioned Lanczos variances (P_L1)."""
+        test_locs = _host(test_locs, np.float64)
+        Fp = _host(Fp, np.float64)
+        n_p = _points(test_locs, "test_locs")
+        _need(Fp, n_p, "Fp")
+        mean = np.empty(n_p)
+        var = np.empty(n_p)
+        st = Stats()
+        self.ctx.check(self.ctx.lib.vl_pred_var_lanczos(self.h, _ptr(test_locs, np.float64), n_p,
+                                                        _ptr(Fp, np.float64), int(k), int(precond_l),
+                                                        mean.ctypes.data, var.ctypes.data, C.byref(st)))
         return (mean, var, st.as_dict()) if with_stats else (mean, var)
 
     def apply(self, op: int, X, opts: Opts | None = None):

@@ -10,7 +10,7 @@
 #include <string>
 #include <vector>
 
-#include "laplace.cuh"
+#include "lanczos.cuh"
 
 namespace vl {
 
@@ -968,6 +968,178 @@ vl_status vl_pred_var(vl_state* st, const double* test_locs, int64_t np, const d
   cudaEventElapsedTime(&ms, c->ev0, c->ev1);
   loc.ms_total = ms;
   if (stats) *stats = loc;
+  return VL_OK;
+}
+
+vl_status vl_pred_var_lanczos(vl_state* st, const double* test_locs, int64_t np, const double* Fp, int k, int precond_l,
+                              double* mean, double* var, vl_stats* stats) {
+  if (!st) return VL_ERR_INVALID_ARG;
+  Ctx* c = st->ctx;
+  Factor* f = st->f;
+  const int m = f->m, n = (int)f->n;
+  if (np < 0 || (np > 0 && !test_locs) || np > (1LL << 30) || k < 1)
+    return fail(c, VL_ERR_INVALID_ARG, "vl_pred_var_lanczos: invalid argument");
+  if (precond_l != 1)
+    return fail(c, VL_ERR_INVALID_ARG, "vl_pred_var_lanczos: only the Lanczos preconditioner P_L1 is available");
+  if (f->nseg != 1) return fail(c, VL_ERR_INVALID_ARG, "vl_pred_var_lanczos: single problems only");
+  if (np == 0) return VL_OK;
+  k = std::min(k, n);
+  VL_CUDA(c, cudaEventRecord(c->ev0, c->stream));
+  Scratch S(c);
+  const double *dq, *dF = nullptr;
+  VL_TRY(stage_in(c, S, test_locs, (size_t)np * 2, &dq));
+  if (Fp) VL_TRY(stage_in(c, S, Fp, (size_t)np, &dF));
+  const int64_t npm = np * (int64_t)std::max(m, 1);
+  int32_t* Np = S.get<int32_t>(npm);
+  double* Ap = S.get<double>(npm);
+  double* Dp = S.get<double>(np);
+  double* dmean = S.get<double>(np);
+  double* dvar = S.get<double>(np);
+  if (!Np || !Ap || !Dp || !dmean || !dvar) return fail(c, VL_ERR_OOM, "workspace exhausted (prediction)");
+  if (m > 0) {
+    VL_TRY(knn_cross_dev(c, f->locs_v, n, dq, np, m, Np));   // Vecchia indices, Section 4.1
+    translate_kernel<<<grid_for(c, npm), 256, 0, VL_STREAM(c)>>>(npm, f->v2s, Np);
+    VL_CUDA(c, cudaGetLastError());
+  }
+  VL_CUDA(c, status_clear(c));
+  VL_TRY(factor_rows(c, np, m, dq, f->locs_s, Np, f->cov, f->sigma2, f->rho, f->nugget, Ap, Dp, nullptr));
+  VL_TRY(check_dev_status(c, "prediction rows"));
+  const int pg = (int)((np * 32 + 255) / 256);
+  pred_kernel<double><<<pg, 256, 0, VL_STREAM(c)>>>((int)np, m, Np, Ap, Dp, dF, st->b, nullptr, 0, 1, dmean, nullptr);
+  VL_CUDA(c, cudaGetLastError());
+  int kk = 0;
+  if (var) {
+    // CSR of the test neighbours by training row (entries in increasing (p, slot) order)
+    std::vector<int32_t> hN;
+    VL_TRY(to_host(c, hN, (const int32_t*)Np, (size_t)(m > 0 ? npm : 0)));
+    std::vector<int32_t> rp(n + 1, 0), ent;
+    for (int64_t e = 0; e < (int64_t)hN.size(); ++e)
+      if (hN[e] >= 0) ++rp[hN[e] + 1];
+    for (int j = 0; j < n; ++j) rp[j + 1] += rp[j];
+    ent.resize(rp[n]);
+    std::vector<int32_t> fill(rp.begin(), rp.end() - 1);
+    for (int64_t e = 0; e < (int64_t)hN.size(); ++e)
+      if (hN[e] >= 0) ent[fill[hN[e]]++] = (int32_t)e;
+    int32_t* drp = S.get<int32_t>(n + 1);
+    int32_t* dent = S.get<int32_t>(std::max<size_t>(ent.size(), 1));
+    Engine<double> E(c);
+    VL_TRY(E.init(f, 1, VL_PREC_VADU, st->W, 0));
+    const int rows = 4096, nch = (n + rows - 1) / rows;
+    double* Q = S.get<double>((size_t)n * k);
+    double* sv = S.get<double>(n);
+    double* v = S.get<double>(n);
+    double* t1 = S.get<double>(n);
+    double* t2 = S.get<double>(n);
+    double* w = S.get<double>(n);
+    double* h = S.get<double>(k);
+    double* part = S.get<double>((size_t)nch * k);
+    if (!drp || !dent || !Q || !sv || !v || !t1 || !t2 || !w || !h || !part)
+      return fail(c, VL_ERR_OOM, "workspace exhausted (Lanczos)");
+    VL_TRY(to_device(c, drp, rp));
+    VL_TRY(to_device(c, dent, ent));
+    // s = S^{1/2} = (W + D^{-1})^{-1/2}
+    diag_fn_kernel<<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, 0, st->W, f->D64, t1);
+    VL_CUDA(c, cudaGetLastError());
+    {   // sv = 1 / sqrt(W + 1/D)
+      std::vector<double> hs;
+      VL_TRY(to_host(c, hs, (const double*)t1, (size_t)n));
+      for (double& x : hs) x = 1.0 / x;
+      VL_TRY(to_device(c, sv, hs));
+    }
+    // q_0 = P^{-1/2} v / ||P^{-1/2} v||, v = the mean of the columns of B_po^T
+    lanczos_start_kernel<<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, drp, dent, Ap, 1.0 / (double)np, v);
+    VL_TRY(E.solveBt(v, nullptr, t1));
+    lanczos_scale_kernel<<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, sv, t1, 1.0, w);
+    auto norm = [&](const double* x, double* out) -> vl_status {
+      VL_TRY(E.coldot(x, x, nullptr, E.red));
+      std::vector<double> hr;
+      VL_TRY(to_host(c, hr, (const double*)E.red, 1));
+      *out = std::sqrt(hr[0]);
+      return VL_OK;
+    };
+    // h[0 .. ncol) = Q[:, c0 .. c0 + ncol)^T x
+    auto qtw = [&](int c0, int ncol, const double* x) -> vl_status {
+      lanczos_qtw_kernel<<<dim3(nch, ncol), 256, 0, VL_STREAM(c)>>>(n, ncol, rows, Q + (size_t)c0 * n, x, part);
+      lanczos_sum_kernel<<<(ncol + 255) / 256, 256, 0, VL_STREAM(c)>>>(nch, ncol, part, h);
+      VL_CUDA(c, cudaGetLastError());
+      return VL_OK;
+    };
+    double nrm = 0.0;
+    VL_TRY(norm(w, &nrm));
+    if (!(nrm > 0.0)) return fail(c, VL_ERR_INVALID_ARG, "vl_pred_var_lanczos: the start vector is zero");
+    lanczos_scale_kernel<<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, nullptr, w, nrm, Q);
+    std::vector<double> alpha, beta;
+    for (int j = 0; j < k; ++j) {
+      double* qj = Q + (size_t)j * n;
+      // w = M q_j = S^{1/2} B^{-T} A B^{-1} S^{1/2} q_j
+      VL_TRY(E.solveB(qj, sv, t1));
+      VL_TRY(E.opA(t1, t2));
+      VL_TRY(E.solveBt(t2, nullptr, t1));
+      lanczos_scale_kernel<<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, sv, t1, 1.0, w);
+      VL_TRY(qtw(j, 1, w));
+      std::vector<double> ha;
+      VL_TRY(to_host(c, ha, (const double*)h, 1));
+      alpha.push_back(ha[0]);
+      for (int pass = 0; pass < 2; ++pass) {   // full reorthogonalisation, twice
+        VL_TRY(qtw(0, j + 1, w));
+        lanczos_axpy_kernel<<<grid_for(c, n), 256, sizeof(double) * (j + 1), VL_STREAM(c)>>>(n, j + 1, Q, h, w);
+        VL_CUDA(c, cudaGetLastError());
+      }
+      double bj = 0.0;
+      VL_TRY(norm(w, &bj));
+      kk = j + 1;
+      if (j + 1 == k || !(bj > 1e-13 * std::max(std::fabs(alpha[0]), 1e-300))) break;
+      beta.push_back(bj);
+      lanczos_scale_kernel<<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, nullptr, w, bj, Q + (size_t)(j + 1) * n);
+    }
+    // T = L diag(d) L^T
+    std::vector<double> d(kk), l(std::max(kk - 1, 1), 0.0);
+    d[0] = alpha[0];
+    for (int i = 0; i + 1 < kk; ++i) {
+      l[i] = beta[i] / d[i];
+      d[i + 1] = alpha[i + 1] - l[i] * beta[i];
+    }
+    for (double x : d)
+      if (!(x > 0.0)) return fail(c, VL_ERR_NOT_SPD, "vl_pred_var_lanczos: the Lanczos tridiagonal is not positive definite");
+    double* dd = S.get<double>(kk);
+    double* dl = S.get<double>(std::max(kk - 1, 1));
+    double* Z = S.get<double>((size_t)np * kk);
+    if (!dd || !dl || !Z) return fail(c, VL_ERR_OOM, "workspace exhausted (Lanczos)");
+    VL_TRY(to_device(c, dd, d));
+    VL_TRY(to_device(c, dl, l));
+    // U = B^{-1} S^{1/2} Q in blocks of at most 128 columns, then z_p = U^T B_po^T e_p
+    for (int c0 = 0; c0 < kk; c0 += 128) {
+      const int kc = std::min(128, kk - c0);
+      Engine<double> Ek(c);
+      VL_TRY(Ek.init(f, kc, VL_PREC_VADU, st->W, 0, /*ops_only=*/true));
+      double* X = S.get<double>((size_t)n * Ek.ld);
+      double* U = S.get<double>((size_t)n * Ek.ld);
+      if (!X || !U) return fail(c, VL_ERR_OOM, "workspace exhausted (Lanczos blocks)");
+      lanczos_rows_kernel<<<grid_for(c, (int64_t)n * Ek.ld), 256, 0, VL_STREAM(c)>>>(n, kc, Ek.ld, c0, sv, Q, X);
+      VL_TRY(Ek.solveB(X, nullptr, U));
+      lanczos_gather_kernel<<<(unsigned)np, 128, 0, VL_STREAM(c)>>>((int)np, m, kc, Ek.ld, c0, kk, Np, Ap, U, Z);
+      VL_CUDA(c, cudaGetLastError());
+      VL_CUDA(c, cudaStreamSynchronize(c->stream));
+      c->arena.release(U);
+      c->arena.release(X);
+      S.blocks.erase(std::remove_if(S.blocks.begin(), S.blocks.end(), [&](void* p) { return p == U || p == X; }),
+                     S.blocks.end());
+    }
+    lanczos_quad_kernel<<<grid_for(c, np), 256, 0, VL_STREAM(c)>>>((int)np, kk, Z, dl, dd, Dp, dvar);
+    VL_CUDA(c, cudaGetLastError());
+    VL_TRY(check_dev_status(c, "Lanczos predictive variances"));
+  }
+  VL_TRY(stage_out(c, dmean, mean, np));
+  VL_TRY(stage_out(c, dvar, var, np));
+  VL_CUDA(c, cudaEventRecord(c->ev1, c->stream));
+  VL_CUDA(c, cudaEventSynchronize(c->ev1));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+  if (stats) {
+    *stats = vl_stats{};
+    stats->cg_iters_max = kk;
+    stats->ms_total = ms;
+  }
   return VL_OK;
 }
 
