@@ -170,6 +170,17 @@ vl_status vl_ctx_set_wait_limit(vl_ctx* ctx, long long cycles);
  * shares; the paper has no counterpart. */
 vl_status vl_ctx_wait_probe(vl_ctx* ctx);
 
+/* Launch tuning (on by default): launch parameters that change no result (blocks per SM
+ * of a grid triangular solve, dependency rows in flight per lane of a block solve) are tuned
+ * at first use for each (kernel class, value size, row width, size bucket): every candidate
+ * runs once on the live call, timed with CUDA events, and the fastest is kept for the
+ * process. enable = 0 keeps the defaults for calls on this context. */
+vl_status vl_ctx_set_autotune(vl_ctx* ctx, int enable);
+/* The tuner's choices so far as a JSON list (key, chosen candidate, candidate times in ms),
+ * written to buf (len bytes, always NUL-terminated when len > 0); returns the bytes the
+ * whole report needs, terminator included. */
+size_t vl_tune_report(char* buf, size_t len);
+
 /* Form of the level-scheduled triangular solves with B and B^T (the two solves of the
  * VADU / LVA preconditioners, Section 3.1.1, and of Sigma_tilde = B^{-1} D B^{-T}).
  * By default each solve picks its form from n, t and the widest level; forcing one

@@ -103,6 +103,8 @@ def library():
         "vl_ctx_mem": (st, [vp, vp, vp]),
         "vl_ctx_set_solve_form": (st, [vp, i32]),
         "vl_ctx_set_wait_limit": (st, [vp, C.c_longlong]),
+        "vl_ctx_set_autotune": (st, [vp, i32]),
+        "vl_tune_report": (C.c_size_t, [vp, C.c_size_t]),
         "vl_ctx_wait_probe": (st, [vp]),
         "vl_profile_enable": (st, [vp, i32]),
         "vl_profile_read": (st, [vp, C.c_char_p, i32, vp, vp, i32]),
@@ -276,6 +278,10 @@ class Context:
         """Cycle limit of every bounded device-side wait on this context (0: the default,
         about 2 s); a wait that runs out makes the call fail with VL_ERR_TIMEOUT."""
         self.check(self.lib.vl_ctx_set_wait_limit(self.h, int(cycles)))
+
+    def set_autotune(self, enable: bool):
+        """Tune result-neutral launch parameters at first use (default on)."""
+        self.check(self.lib.vl_ctx_set_autotune(self.h, 1 if enable else 0))
 
     def wait_probe(self):
         """One bounded wait on a flag nothing sets: raises VLError(VL_ERR_TIMEOUT)."""
@@ -581,3 +587,13 @@ class Batch:
         g = np.empty(len(self.sizes) * t)
         self.ctx.check(self.ctx.lib.vl_batch_gammas(self.h, g.ctypes.data, t))
         return g.reshape(len(self.sizes), t)
+
+
+def tune_report() -> list:
+    """The launch tuner's choices so far (vl_tune_report)."""
+    import json
+    L = library()
+    need = L.vl_tune_report(None, 0)
+    buf = C.create_string_buffer(int(need))
+    L.vl_tune_report(buf, need)
+    return json.loads(buf.value.decode() or "[]")

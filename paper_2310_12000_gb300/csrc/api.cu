@@ -584,6 +584,42 @@ vl_status vl_ctx_wait_probe(vl_ctx* c) {
   return check_dev_status(c, "wait probe");
 }
 
+vl_status vl_ctx_set_autotune(vl_ctx* c, int enable) {
+  if (!c) return VL_ERR_INVALID_ARG;
+  c->autotune = enable != 0;
+  return VL_OK;
+}
+
+size_t vl_tune_report(char* buf, size_t len) {
+  std::string out = "[";
+  {
+    std::lock_guard<std::mutex> lk(tuner().mu);
+    bool first = true;
+    for (auto& kv : tuner().best) {
+      const TuneKey& k = kv.first;
+      char head[160];
+      snprintf(head, sizeof head, "%s{\"device\": %d, \"class\": %d, \"value_bytes\": %d, \"ld\": %d, \"log2_n\": %d, "
+               "\"choice\": %d, \"ms\": [", first ? "" : ", ", k.device, k.cls, k.vbytes, k.ld, k.nbucket, kv.second);
+      out += head;
+      const std::vector<float>& ms = tuner().times[k];
+      for (size_t i = 0; i < ms.size(); ++i) {
+        char v[32];
+        snprintf(v, sizeof v, "%s%.4f", i ? ", " : "", ms[i]);
+        out += v;
+      }
+      out += "]}";
+      first = false;
+    }
+  }
+  out += "]";
+  if (buf && len > 0) {
+    const size_t k = std::min(len - 1, out.size());
+    std::memcpy(buf, out.data(), k);
+    buf[k] = 0;
+  }
+  return out.size() + 1;
+}
+
 vl_status vl_ctx_set_solve_form(vl_ctx* c, int form) {
   if (!c) return VL_ERR_INVALID_ARG;
   if (form < VL_SOLVE_AUTO || form > VL_SOLVE_GRID) return fail(c, VL_ERR_INVALID_ARG, "unknown solve form");

@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <map>
+#include <tuple>
 #include <mutex>
 #include <set>
 #include <string>
@@ -203,6 +204,71 @@ inline vl_status chunk_plan(Ctx* c, Factor* f, bool fwd, int ch, const Factor::C
   return VL_OK;
 }
 
+// ----------------------------------------------------------------------------- launch tuner
+// Launch parameters that do not change any result (blocks per SM of a grid solve, dependency
+// rows in flight per lane, lanes per row of a block product) are tuned at first use: every
+// candidate is run on the live call and timed with CUDA events, and the fastest is kept for
+// later calls of the same key (kernel class and direction, value size, row width, size bucket).
+struct TuneKey {
+  int device, cls, vbytes, ld, nbucket;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(device, cls, vbytes, ld, nbucket) < std::tie(o.device, o.cls, o.vbytes, o.ld, o.nbucket);
+  }
+};
+
+inline int log2_bucket(int64_t n) {
+  int b = 0;
+  while ((1LL << (b + 1)) <= n) ++b;
+  return b;
+}
+
+struct Tuner {
+  std::mutex mu;
+  std::map<TuneKey, int> best;          // key -> candidate
+  std::map<TuneKey, std::vector<float>> times;
+};
+inline Tuner& tuner() {
+  static Tuner t;
+  return t;
+}
+
+// Runs candidate `best` of key (tuning it first when the context allows and no choice is
+// cached): run(cand) launches candidate cand on the context's stream.
+template <typename Run>
+vl_status tuned_call(Ctx* c, const TuneKey& key, int ncand, Run run) {
+  if (!c->autotune || ncand < 2) return run(0);   // the defaults
+  int choice = -1;
+  {
+    std::lock_guard<std::mutex> lk(tuner().mu);
+    auto it = tuner().best.find(key);
+    if (it != tuner().best.end()) choice = it->second;
+  }
+  if (choice >= 0) return run(choice);
+  cudaEvent_t a = nullptr, b = nullptr;
+  VL_CUDA(c, cudaEventCreate(&a));
+  VL_CUDA(c, cudaEventCreate(&b));
+  std::vector<float> ms(ncand, 0.f);
+  vl_status st = VL_OK;
+  for (int k = 0; k < ncand && st == VL_OK; ++k) {
+    cudaEventRecord(a, c->stream);
+    st = run(k);
+    cudaEventRecord(b, c->stream);
+    if (cudaEventSynchronize(b) != cudaSuccess) st = cuda_fail(c, cudaGetLastError(), "tuning");
+    cudaEventElapsedTime(&ms[k], a, b);
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  VL_TRY(st);
+  const int pick = (int)(std::min_element(ms.begin(), ms.end()) - ms.begin());
+  {
+    std::lock_guard<std::mutex> lk(tuner().mu);
+    tuner().best[key] = pick;
+    tuner().times[key] = ms;
+  }
+  // every candidate computed the same result; the last run stands
+  return VL_OK;
+}
+
 // ----------------------------------------------------------------------------- engine
 template <typename T>
 struct Engine {
@@ -245,6 +311,11 @@ struct Engine {
   int part_slots = 0, cnt_len = 0;
 
   explicit Engine(Ctx* ctx) : c(ctx), mem(ctx) {}
+
+  template <typename Run>
+  vl_status tuned(const TuneKey& key, int ncand, Run run) {
+    return tuned_call(c, key, ncand, run);
+  }
 
   // Heavy-row chunk plan of a grid solve, with partial slots and zeroed counters.
   vl_status chunk_setup(bool fwd, int ch, LevelPlan& L) {
@@ -683,11 +754,11 @@ struct Engine {
     const T* val = FWD ? Aval : valT;
     const int32_t* rp = FWD ? nullptr : f->rowptrT;
     VL_CUDA(c, cudaMemsetAsync(c->gbar, 0, 2 * sizeof(unsigned), c->stream));
-    auto launch = [&](const void* fn, void** args, int lpv) -> vl_status {
+    auto launch = [&](const void* fn, void** args, int lpv, int bps) -> vl_status {
       const int tpb = 16 * (32 / lpv);   // row teams per 512-thread block
       // heavy rows of the grid body in chunks: one round of loads of a team
-      // (t = 1: lpv lanes x 4 loads; blocks: lpv dependency rows)
-      VL_TRY(chunk_setup(FWD, t == 1 ? lpv * 4 : lpv, L));
+      // (t = 1: lpv lanes x 4 loads; blocks: 16 dependency rows, whatever the row shape)
+      VL_TRY(chunk_setup(FWD, t == 1 ? lpv * 4 : 16, L));
       const size_t smem = sizeof(T) * (size_t)tpb * (t == 1 ? 1 : ld);   // heavy-row partials
       level_cut(hl, hh, hw, t == 1 ? 1 : ld / VecT<T>::n, &L.l_head, &L.l_tail);
       if (form == VL_SOLVE_GRID) {   // forced: every level on the whole grid (no single-block head / tail)
@@ -695,8 +766,8 @@ struct Engine {
         L.l_tail = L.nlev;
       }
       const int body_rows = hl[L.l_tail] - hl[L.l_head];
-      // at most two blocks per SM: fewer arrivals per grid barrier
-      const int maxb = std::min(resident_blocks(c, fn, 512, smem), 2 * c->num_sms);
+      // at most bps blocks per SM: fewer arrivals per grid barrier
+      const int maxb = std::min(resident_blocks(c, fn, 512, smem), bps * c->num_sms);
       const int grid = std::max(1, std::min(maxb, (body_rows + tpb - 1) / tpb));
       {
         ProfScope ps(c, cls, t);
@@ -844,14 +915,22 @@ struct Engine {
       void* args[] = {&L, &mm, &idx, &val, &rp, &rhs, &q, &x};
       // backward rows list up to 48 light dependents: 16 lanes keep them to one round of loads
       constexpr int LPVG = FWD ? 8 : 16;
-      return launch((const void*)sptrsv_t1_kernel<T, FWD, LPVG>, args, LPVG);
+      const void* fn1 = (const void*)sptrsv_t1_kernel<T, FWD, LPVG>;
+      return tuned(TuneKey{c->device, FWD ? 0 : 1, (int)sizeof(T), 1, log2_bucket(n)}, 2,
+                   [&](int cand) { return launch(fn1, args, LPVG, cand == 0 ? 2 : 1); });
     }
     // block kernels read rows as float4 / double2 words: ld must be a multiple of 8
     if (ld % 8 != 0) return fail(c, VL_ERR_STATE, "block solve with a row width that is not a multiple of 8");
     void* args[] = {&L, &mm, &idx, &val, &rp, &rhs, &q, &x, &l};
-    return with_shape<T>(ld, [&](auto Lc, auto N, auto U) {
-      constexpr int LPV = decltype(Lc)::value;
-      return launch((const void*)sptrsv_kernel<T, FWD, LPV, decltype(N)::value, decltype(U)::value>, args, LPV);
+    // candidates (all give the same numbers): dependency rows in flight per lane (the shape's
+    // UNR or twice it) x blocks per SM (2 or 1)
+    return tuned(TuneKey{c->device, FWD ? 0 : 1, (int)sizeof(T), ld, log2_bucket(n)}, 4, [&](int cand) {
+      return with_shape<T>(ld, [&](auto Lc, auto N, auto U) {
+        constexpr int LPV = decltype(Lc)::value, NV = decltype(N)::value, UNR = decltype(U)::value;
+        const int bps = (cand & 1) ? 1 : 2;
+        if (cand & 2) return launch((const void*)sptrsv_kernel<T, FWD, LPV, NV, 2 * UNR>, args, LPV, bps);
+        return launch((const void*)sptrsv_kernel<T, FWD, LPV, NV, UNR>, args, LPV, bps);
+      });
     });
   }
   // x = B^{-1} (q o rhs)

@@ -84,6 +84,7 @@ struct Ctx {
   int64_t launches = 0;           // kernels launched on this context
   unsigned* gbar = nullptr;       // grid-barrier state {count, generation} (device)
   int solve_form = 0;             // vl_solve_form: 0 = chosen per solve, else forced
+  bool autotune = true;           // tune result-neutral launch parameters at first use
   int refs = 1;                   // the context itself + every live factor and state
   bool closed = false;            // vl_ctx_destroy was called
 };

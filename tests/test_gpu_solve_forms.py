@@ -210,3 +210,30 @@ def test_large_solves_by_form(ctx, vl, form):
                 assert wt <= eb.BOUND_SLACK * (eb.gamma(kb, u) + 2 * u), (prec, t, wt)
     finally:
         ctx.set_solve_form(vl.SOLVE_AUTO)
+
+
+def test_tuned_launches_give_identical_results(vl):
+    """The launch tuner only picks among parameters that change no result (blocks per SM,
+    dependency rows in flight): a tuned context and an untuned one give bit-identical solves,
+    before and after the choice is cached."""
+    P = wl.make_problem("c3_grid1m", n=300_000)
+    outs = []
+    for tune in (True, False):
+        c = vl.Context(0, ws_bytes=4 << 30)
+        c.set_autotune(tune)
+        fac = c.build_factor(P.locs, P.order, P.cov, P.sigma2, P.rho, P.m)
+        st = fac.find_mode(P.lik, P.y, P.F, vl.Opts.make(precision=vl.FP32_REFINE, cg_tol=1e-6, newton_tol=1e-6,
+                                                          cg_max_iter=3000))
+        res = []
+        for t in (1, 50):
+            X = np.random.default_rng(t).standard_normal((P.n, t))
+            o = vl.Opts.make(precision=vl.FP32_REFINE)
+            for _ in range(2):
+                res.append(st.apply(vl.OP_BINV, X, o))
+                res.append(st.apply(vl.OP_BTINV, X, o))
+        outs.append(res)
+        c.close()
+    for a, b in zip(outs[0], outs[1]):
+        assert np.array_equal(a, b)
+    rep = vl.tune_report()
+    assert rep and all(len(r["ms"]) >= 2 and 0 <= r["choice"] < len(r["ms"]) for r in rep)
