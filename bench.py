@@ -492,7 +492,42 @@ def run_ours(args):
                 "rel_diff_mixed_vs_fp64": abs(lmls[-1] - L64) / abs(L64),
                 "newton": newton_summary(s64["mode"]), "slq_cg_iters_max": s64.get("cg_iters_max")}
 
+    # ---------------- the config's second run: the low-rank preconditioner (rank k) on the same step
+    lrac = None
+    if args.precond != "lrac" and args.lrac_k > 0:
+        olr = vl.Opts.make(precision=vl.FP32_REFINE, t=50, cg_tol=1e-6, newton_tol=1e-7, cg_max_iter=3000,
+                           precond=vl.PREC_LRAC, k=args.lrac_k, newton_eta_max=args.newton_eta_max)
+        barrier()
+        ctx.profile(True)
+        ctx.profile_read("all", reset=True)
+        t0 = time.perf_counter()
+        Llr, slr = step(olr)
+        barrier()
+        sec = max_over_ranks(time.perf_counter() - t0)
+        lprof = {}
+        for cls, tt in (("woodbury", 1), ("woodbury", 50), ("pivoted_cholesky", args.lrac_k),
+                        ("lrac_gram", args.lrac_k), ("lrac_kxk", args.lrac_k)):
+            ms, cnt = ctx.profile_read(cls, tt)
+            if cnt:
+                lprof[f"{cls}/t={tt}"] = {"ms": ms, "launches": cnt}
+        ctx.profile(False)
+        wb = lprof.get("woodbury/t=50")
+        wroof = None
+        if wb:
+            byt = algorithmic_bytes("woodbury", n, P.m, 50, 4, args.lrac_k)
+            ach = byt / (wb["ms"] / wb["launches"] / 1000.0) / 1e9
+            wroof = {"bound": "hbm", "kernel": "woodbury/t=50 (two tcgen05 rank-k products + k x k)",
+                     "achieved": ach, "peak": _peaks()[0], "unit": "GB/s", "frac": ach / _peaks()[0],
+                     "algorithmic_bytes_per_launch": byt, "avg_launch_ms": wb["ms"] / wb["launches"]}
+        lrac = {"k": args.lrac_k, "evals_per_s": ws / sec, "seconds_per_eval": sec, "lml": Llr,
+                "rel_diff_vs_vadu": abs(Llr - lmls[-1]) / abs(lmls[-1]), "slq_stderr": slr.get("slq_stderr"),
+                "newton": newton_summary(slr["mode"]), "slq_cg_iters_max": slr.get("cg_iters_max"),
+                "probe_relres_max": slr.get("probe_relres_max"), "kernel_profile_ms": lprof,
+                "woodbury_roofline": wroof,
+                "note": "one evaluation (the pivoted Cholesky of Sigma is built in it: the factor is refit first)"}
+
     # ---------------- batched and serving legs (their own slot contexts)
+    tune = vl.tune_report()
     ctx.close()
     del ctx, fac
     torch.cuda.empty_cache()
@@ -542,7 +577,7 @@ def run_ours(args):
             "roofline": roofline,
             "kernel_profile_ms": prof, "clocks": clk.summary(), "cpu_baseline": cb,
             "p99_latency_ms": serving_out["p99_latency_ms"] if serving_out else None,
-            "batched": batched, "serving": serving_out,
+            "batched": batched, "serving": serving_out, "lrac": lrac, "launch_tuner": tune,
         }
         try:
             out.update(derived_metrics(prof, n, P.m, out["ms_per_step"], graph_ms))
@@ -568,6 +603,8 @@ def main():
     ap.add_argument("--ws-gb", type=float, default=None, help="workspace size in GiB (default: 60%% of free memory)")
     ap.add_argument("--precond", default="vadu", choices=["vadu", "lrac"], help="preconditioner of the timed step")
     ap.add_argument("--k", type=int, default=500, help="LRAC rank")
+    ap.add_argument("--lrac-k", type=int, default=500,
+                    help="rank of the extra low-rank-preconditioner evaluation (0: skip it)")
     ap.add_argument("--newton-eta-max", type=float, default=0.1,
                     help="largest inexact-Newton forcing term (0: every Newton solve to cg_tol)")
     ap.add_argument("--batch", type=int, default=256, help="problems in the batched leg (0: skip)")
