@@ -190,7 +190,10 @@ typedef enum vl_solve_form {
   VL_SOLVE_SHARED = 1,  /* t = 1: one block, x in shared memory (n * sizeof <= 200 KiB);
                            block solves (t > 1) keep the automatic choice              */
   VL_SOLVE_CLUSTER = 2, /* one thread-block cluster, hardware cluster barrier per level */
-  VL_SOLVE_GRID = 3     /* cooperative grid, bounded software grid barrier per level   */
+  VL_SOLVE_GRID = 3,    /* cooperative grid, bounded software grid barrier per level; the
+                           narrow leading and trailing levels in one block (the leading ones of
+                           single-column forward solves with x in shared memory)           */
+  VL_SOLVE_GRID_ALL = 4 /* cooperative grid with every level on the grid barrier          */
 } vl_solve_form;
 /* Sets the form for every later solve on this context (VL_ERR_INVALID_ARG for an
  * unknown form). A solve the forced form cannot run (VL_SOLVE_SHARED with too many

@@ -622,7 +622,7 @@ size_t vl_tune_report(char* buf, size_t len) {
 
 vl_status vl_ctx_set_solve_form(vl_ctx* c, int form) {
   if (!c) return VL_ERR_INVALID_ARG;
-  if (form < VL_SOLVE_AUTO || form > VL_SOLVE_GRID) return fail(c, VL_ERR_INVALID_ARG, "unknown solve form");
+  if (form < VL_SOLVE_AUTO || form > VL_SOLVE_GRID_ALL) return fail(c, VL_ERR_INVALID_ARG, "unknown solve form");
   c->solve_form = form;
   return VL_OK;
 }

@@ -204,6 +204,61 @@ inline vl_status chunk_plan(Ctx* c, Factor* f, bool fwd, int ch, const Factor::C
   return VL_OK;
 }
 
+// out[p * m + c] = nbr[task[p] * m + c] for the first `rows` task positions
+static __global__ void head_nbr_kernel(int rows, int m, const int32_t* __restrict__ task, const int32_t* __restrict__ nbr,
+                                       int32_t* __restrict__ out) {
+  const int64_t total = (int64_t)rows * m;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int p = (int)(e / m), c = (int)(e % m);
+    out[e] = nbr[(int64_t)task[p] * m + c];
+  }
+}
+
+// Dependencies of the forward head's rows (levels [0, l_head)) as task positions; unusable if a
+// dependency lay outside the head (it cannot: a row depends only on rows of earlier levels).
+inline vl_status head_plan(Ctx* c, Factor* f, int l_head, const Factor::HeadPlan** out) {
+  auto it = f->head_plans.find(l_head);
+  if (it != f->head_plans.end()) {
+    *out = &it->second;
+    return VL_OK;
+  }
+  Factor::HeadPlan plan;
+  const int H = f->h_lptr_fwd[l_head], m = f->m;
+  plan.rows = H;
+  if (H > 0 && m > 0) {
+    Scratch S(c);
+    int32_t* dn = S.get<int32_t>((size_t)H * m);
+    if (!dn) return fail(c, VL_ERR_OOM, "workspace exhausted (head plan)");
+    head_nbr_kernel<<<grid_for(c, (int64_t)H * m), 256, 0, VL_STREAM(c)>>>(H, m, f->task_fwd, f->nbr, dn);
+    VL_CUDA(c, cudaGetLastError());
+    std::vector<int32_t> hn((size_t)H * m), task(H);
+    VL_CUDA(c, cudaMemcpyAsync(hn.data(), dn, sizeof(int32_t) * hn.size(), cudaMemcpyDeviceToHost, c->stream));
+    VL_CUDA(c, cudaMemcpyAsync(task.data(), f->task_fwd, sizeof(int32_t) * H, cudaMemcpyDeviceToHost, c->stream));
+    VL_CUDA(c, cudaStreamSynchronize(c->stream));
+    std::map<int32_t, int32_t> pos;
+    for (int p = 0; p < H; ++p) pos[task[p]] = p;
+    bool ok = true;
+    for (int32_t& j : hn) {
+      if (j < 0) continue;
+      auto q = pos.find(j);
+      if (q == pos.end()) {
+        ok = false;
+        break;
+      }
+      j = q->second;
+    }
+    if (ok) {
+      plan.hpos = f->mem.get<int32_t>(hn.size());
+      if (!plan.hpos) return fail(c, VL_ERR_OOM, "workspace exhausted (head plan)");
+      VL_CUDA(c, cudaMemcpyAsync(plan.hpos, hn.data(), sizeof(int32_t) * hn.size(), cudaMemcpyHostToDevice, c->stream));
+      VL_CUDA(c, cudaStreamSynchronize(c->stream));
+      plan.usable = true;
+    }
+  }
+  *out = &(f->head_plans[l_head] = plan);
+  return VL_OK;
+}
+
 // ----------------------------------------------------------------------------- launch tuner
 // Launch parameters that do not change any result (blocks per SM of a grid solve, dependency
 // rows in flight per lane, lanes per row of a block product) are tuned at first use: every
@@ -736,7 +791,7 @@ struct Engine {
     const std::vector<int64_t>& hw = FWD ? f->h_lwork_fwd : f->h_lwork_bwd;
     const std::vector<int32_t>& hh = FWD ? f->h_hptr_fwd : f->h_hptr_bwd;
     LevelPlan L{FWD ? f->task_fwd : f->task_bwd, FWD ? f->lptr_fwd : f->lptr_bwd, FWD ? f->hptr_fwd : f->hptr_bwd, 0, 0,
-                (int)hl.size() - 1, c->gbar, c->dstatus, nullptr, nullptr, nullptr, nullptr, nullptr};
+                (int)hl.size() - 1, c->gbar, c->dstatus, nullptr, nullptr, nullptr, nullptr, nullptr, 0};
     const char* cls = FWD ? "sptrsv_fwd" : "sptrsv_bwd";
     // form: chosen from n, t and the widest level, or forced by vl_ctx_set_solve_form
     // (VL_SOLVE_SHARED concerns single-column solves; block solves keep the automatic choice)
@@ -761,19 +816,30 @@ struct Engine {
       VL_TRY(chunk_setup(FWD, t == 1 ? lpv * 4 : 16, L));
       const size_t smem = sizeof(T) * (size_t)tpb * (t == 1 ? 1 : ld);   // heavy-row partials
       level_cut(hl, hh, hw, t == 1 ? 1 : ld / VecT<T>::n, &L.l_head, &L.l_tail);
-      if (form == VL_SOLVE_GRID) {   // forced: every level on the whole grid (no single-block head / tail)
+      if (form == VL_SOLVE_GRID_ALL) {   // forced: every level on the whole grid (no single-block head / tail)
         L.l_head = 0;
         L.l_tail = L.nlev;
+      }
+      L.head_done = 0;
+      ProfScope ps(c, cls, t);
+      if (t == 1 && FWD && L.l_head > 0 && (size_t)hl[L.l_head] * sizeof(T) <= kSmemSolveBytes) {
+        // the narrow leading levels in one block with x in shared memory, then the grid from l_head
+        const Factor::HeadPlan* hp = nullptr;
+        VL_TRY(head_plan(c, f, L.l_head, &hp));
+        if (hp->usable) {
+          auto hfn = sptrsv_t1_head_kernel<T, 8>;
+          VL_TRY(smem_limit_once(c, (const void*)hfn, kSmemSolveBytes));
+          hfn<<<1, 1024, sizeof(T) * (size_t)hp->rows, VL_STREAM(c)>>>(L, m, hp->hpos, val, rhs, q, x);
+          VL_CUDA(c, cudaGetLastError());
+          L.head_done = 1;
+        }
       }
       const int body_rows = hl[L.l_tail] - hl[L.l_head];
       // at most bps blocks per SM: fewer arrivals per grid barrier
       const int maxb = std::min(resident_blocks(c, fn, 512, smem), bps * c->num_sms);
       const int grid = std::max(1, std::min(maxb, (body_rows + tpb - 1) / tpb));
-      {
-        ProfScope ps(c, cls, t);
-        ++c->launches;
-        VL_CUDA(c, cudaLaunchCooperativeKernel(fn, grid, 512, args, smem, c->stream));
-      }
+      ++c->launches;
+      VL_CUDA(c, cudaLaunchCooperativeKernel(fn, grid, 512, args, smem, c->stream));
       if (L.trace) {
         std::vector<long long>& h = c->prof.traces[{cls, t}];
         h.resize(hl.size());
@@ -811,7 +877,7 @@ struct Engine {
       }
       return VL_OK;
     }
-    if (t > 1 && form != VL_SOLVE_GRID) {
+    if (t > 1 && form != VL_SOLVE_GRID && form != VL_SOLVE_GRID_ALL) {
       // narrow level profile: one thread-block cluster (see sptrsv_cluster_kernel)
       vl_status out = VL_OK;
       bool done = false;
@@ -880,7 +946,7 @@ struct Engine {
       const int rounds = n <= kSharedRows ? VL_SHARED_CLUSTER_ROUNDS : VL_T1_CLUSTER_ROUNDS;
       if (form == VL_SOLVE_CLUSTER && cs_max < 1)
         return fail(c, VL_ERR_INVALID_ARG, "no thread-block cluster fits this solve");
-      if (form != VL_SOLVE_GRID && ((form == VL_SOLVE_CLUSTER && cs_max >= 1) ||
+      if (form != VL_SOLVE_GRID && form != VL_SOLVE_GRID_ALL && ((form == VL_SOLVE_CLUSTER && cs_max >= 1) ||
                                     (form == VL_SOLVE_AUTO && cs_max >= 2 && widest <= rounds * cs_max * cta_teams))) {
         const int cs = fit_cluster(widest, cta_teams, cs_max);
         L.l_head = 0;

@@ -290,6 +290,7 @@ struct LevelPlan {
   const int32_t* cptr;
   void* part;
   int* cnt;
+  int head_done;               // levels [0, l_head) were solved by sptrsv_t1_head_kernel before
 };
 
 // Grid barrier with a bounded wait on a monotonic arrival counter (zero at launch):
@@ -697,8 +698,10 @@ __device__ __forceinline__ void level_walk(const LevelPlan& L, Pre pre, Run run,
     }
   };
   unsigned epoch = 0;
-  if (blockIdx.x == 0) solo(0, L.l_head);
-  if (L.l_head > 0 && L.l_head < L.nlev) grid_barrier<COUNTER>(L.bar, L.st, epoch);
+  if (!L.head_done) {
+    if (blockIdx.x == 0) solo(0, L.l_head);
+    if (L.l_head > 0 && L.l_head < L.nlev) grid_barrier<COUNTER>(L.bar, L.st, epoch);
+  }
   {
     int p = 0;
     bool has = L.l_head < L.l_tail && first_light(L.l_head, g, p);
@@ -841,6 +844,96 @@ __global__ void __launch_bounds__(1024) sptrsv_t1_smem_kernel(LevelPlan L, int n
   }
   if (tr) L.trace[L.nlev] = clock64();
   for (int s = threadIdx.x; s < n; s += blockDim.x) x[s] = xs[s];
+}
+
+// The leading levels [0, L.l_head) of a scalar forward solve by one block with x in shared
+// memory, indexed by task position (the head's rows depend only on rows of earlier head
+// levels): hpos[p * m + c] is the task position of dependency c of the row at position p (-1:
+// none), its weight val[s * m + c] (s = task[p]). Rows of the next D levels are loaded D levels
+// ahead into ring slots with fixed indices, as in sptrsv_t1_smem_kernel; every row is also
+// written to x for the levels after the head (the grid kernel that follows).
+template <typename T, int LPV>
+__device__ __forceinline__ void head_pre(RowPre1<T, LPV>& r, int p, int m, const LevelPlan& L,
+                                         const int32_t* __restrict__ hpos, const T* __restrict__ val,
+                                         const T* __restrict__ rhs, const T* __restrict__ q) {
+  const int sl = (threadIdx.x & 31) % LPV;
+  r.s = L.task[p];
+  r.beg = p * m;
+  r.end = p * m + m;
+#pragma unroll
+  for (int u = 0; u < RowPre1<T, LPV>::K; ++u) {
+    const int c = sl + u * LPV;
+    r.j[u] = c < m ? hpos[r.beg + c] : -1;
+    r.a[u] = r.j[u] >= 0 ? val[(int64_t)r.s * m + c] : T(0);
+  }
+  r.b = (q ? q[r.s] : T(1)) * rhs[r.s];
+}
+
+template <typename T, int LPV>
+__device__ __forceinline__ void head_run(RowPre1<T, LPV>& r, int p, int m, const int32_t* __restrict__ hpos,
+                                         const T* __restrict__ val, T* xs, T* x) {
+  constexpr int K = RowPre1<T, LPV>::K;
+  const unsigned mask = team_mask<LPV>();
+  const int sl = (threadIdx.x & 31) % LPV;
+  T acc = T(0);
+#pragma unroll
+  for (int u = 0; u < K; ++u) acc += r.j[u] >= 0 ? r.a[u] * xs[r.j[u]] : T(0);
+  for (int c = sl + LPV * K; c < m; c += LPV) {
+    const int j = hpos[r.beg + c];
+    if (j >= 0) acc += val[(int64_t)r.s * m + c] * xs[j];
+  }
+#pragma unroll
+  for (int off = LPV / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(mask, acc, off, LPV);
+  if (sl == 0) {
+    const T v = r.b + acc;
+    xs[p] = v;
+    x[r.s] = v;
+  }
+}
+
+template <typename T, int LPV>
+__global__ void __launch_bounds__(1024) sptrsv_t1_head_kernel(LevelPlan L, int m, const int32_t* __restrict__ hpos,
+                                                              const T* __restrict__ val, const T* __restrict__ rhs,
+                                                              const T* __restrict__ q, T* x) {
+  extern __shared__ unsigned char vl_smem[];
+  T* xs = reinterpret_cast<T*>(vl_smem);
+  constexpr int RPW = 32 / LPV;
+  constexpr int D = sizeof(T) == 4 ? 3 : 2;
+  const int tpb = (blockDim.x >> 5) * RPW;
+  const int tib = (threadIdx.x >> 5) * RPW + (threadIdx.x & 31) / LPV;
+  const int nl = L.l_head;
+  const bool tr = L.trace && threadIdx.x == 0;
+  RowPre1<T, LPV> r[D];
+  bool h[D];
+  int pr[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    pr[d] = d < nl ? L.lptr[d] + tib : 0;
+    h[d] = d < nl && pr[d] < L.lptr[d + 1];
+    if (h[d]) head_pre<T, LPV>(r[d], pr[d], m, L, hpos, val, rhs, q);
+  }
+  for (int l0 = 0; l0 < nl; l0 += D) {
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      const int l = l0 + d;
+      if (l < nl) {   // uniform across the block
+        if (tr) L.trace[l] = clock64();
+        if (h[d]) {
+          head_run<T, LPV>(r[d], pr[d], m, hpos, val, xs, x);
+          for (int p = pr[d] + tpb; p < L.lptr[l + 1]; p += tpb) {
+            RowPre1<T, LPV> e;
+            head_pre<T, LPV>(e, p, m, L, hpos, val, rhs, q);
+            head_run<T, LPV>(e, p, m, hpos, val, xs, x);
+          }
+        }
+        const int ln = l + D;
+        pr[d] = ln < nl ? L.lptr[ln] + tib : 0;
+        h[d] = ln < nl && pr[d] < L.lptr[ln + 1];
+        if (h[d]) head_pre<T, LPV>(r[d], pr[d], m, L, hpos, val, rhs, q);
+        __syncthreads();
+      }
+    }
+  }
 }
 
 // Block (t > 1) solve by one thread-block cluster: the level walk of the grid

@@ -170,6 +170,14 @@ struct Factor {
     int max_slots = 0, max_rows = 0;
   };
   std::map<std::pair<int, int>, ChunkPlan> chunk_plans;   // (fwd, chunk size) -> plan
+  // the leading levels [0, l_head) of the forward solve in task-position space: hpos[p * m + c]
+  // is the position of dependency c of the row at position p (built on first use per l_head)
+  struct HeadPlan {
+    int32_t* hpos = nullptr;
+    int rows = 0;
+    bool usable = false;
+  };
+  std::map<int, HeadPlan> head_plans;
   // LRAC (Section 3.1.2): rank-k pivoted Cholesky factor of Sigma, built on first use
   // and dropped when the covariance parameters change
   Owned lrac_mem;

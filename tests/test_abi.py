@@ -76,7 +76,8 @@ def test_binding_structs_and_constants_match_the_c_header(tmp_path):
             lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
     consts = ["COV_EXPONENTIAL", "COV_MATERN15", "LIK_BERNOULLI_LOGIT", "LIK_POISSON_LOG", "LIK_GAMMA_LOG", "PREC_VADU",
               "PREC_LVA", "PREC_LRAC", "FP64", "FP32_REFINE", "OP_A", "OP_PINV", "OP_B", "OP_BT", "OP_BINV",
-              "OP_BTINV", "OP_SIGMA", "OP_A2", "SOLVE_AUTO", "SOLVE_SHARED", "SOLVE_CLUSTER", "SOLVE_GRID"]
+              "OP_BTINV", "OP_SIGMA", "OP_A2", "SOLVE_AUTO", "SOLVE_SHARED", "SOLVE_CLUSTER", "SOLVE_GRID",
+              "SOLVE_GRID_ALL"]
     for name in consts:
         lines.append(f'  printf("const {name} %d\\n", (int)VL_{name});')
     lines += ["  return 0;", "}"]

@@ -3,9 +3,11 @@
 The preconditioners of Section 3.1.1 and Sigma_tilde = B^{-1} D B^{-T} are applied by solves
 with B and B^T. A solve runs in one of three forms: one block with x in shared memory
 (single-column solves of small systems), one thread-block cluster, or the cooperative grid
-with a bounded software barrier per level (large problems). The automatic choice depends
-on n, t and the widest level, so the small parity cases elsewhere reach only the first two;
-here each form is forced (vl_ctx_set_solve_form) and checked:
+with a bounded software barrier per level (large problems; its narrow leading and trailing
+levels run in one block, the leading ones of single-column forward solves with x in shared
+memory). The automatic choice depends on n, t and the widest level, so the small parity cases
+elsewhere reach only the first two; here each form is forced (vl_ctx_set_solve_form; "grid_all"
+puts every level on the grid barrier) and checked:
 
 * every operator of vl_apply at t = 1, 5, 40 and 50, in float64 and float32, element by
   element against dense float64 algebra on the library's own factor under the rounding-error
@@ -13,10 +15,10 @@ here each form is forced (vl_ctx_set_solve_form) and checked:
   through |B^{-1}| for the solves), and float64 results within 1e-9 of the oracle's operator;
 * the Laplace mode, L^VLA, every SLQ term (float64, 1e-9) and the mixed-precision L^VLA
   (1e-4) with the whole path in that form;
-* at n = 300,000 of the grid workload, where the automatic choice takes the grid (or cluster)
-  form with the single-block head and tail: neighbour sets and factor rows of sampled rows
-  against the oracle, and the componentwise backward error of B^{-1} X and B^{-T} X on every
-  element (Higham, Thm 8.5: below gamma_k, rows of at most k terms).
+* at n = 300,000 of the grid workload: neighbour sets and factor rows of sampled rows against
+  the oracle, and the componentwise backward error of B^{-1} X and B^{-T} X on every element
+  (Higham, Thm 8.5: below gamma_k, rows of at most k terms);
+* a tuned and an untuned context give bit-identical solves.
 """
 import numpy as np
 import pytest
@@ -30,7 +32,7 @@ from oracle import laplace as la, vecchia
 
 pytestmark = pytest.mark.gpu
 
-FORMS = ["shared", "cluster", "grid"]
+FORMS = ["shared", "cluster", "grid", "grid_all"]
 FP64_TIGHT = dict(cg_tol=1e-12, newton_tol=1e-10, cg_max_iter=2000)
 
 
@@ -50,7 +52,7 @@ def ctx(vl):
 
 def _form(vl, name):
     return {"auto": vl.SOLVE_AUTO, "shared": vl.SOLVE_SHARED, "cluster": vl.SOLVE_CLUSTER,
-            "grid": vl.SOLVE_GRID}[name]
+            "grid": vl.SOLVE_GRID, "grid_all": vl.SOLVE_GRID_ALL}[name]
 
 
 _CACHE = {}
@@ -177,7 +179,7 @@ def test_forced_form_that_cannot_run_is_refused(ctx, vl, op_case):
     assert np.all(np.isfinite(Y))
 
 
-@pytest.mark.parametrize("form", ["auto", "grid", "cluster"])
+@pytest.mark.parametrize("form", ["auto", "grid", "grid_all", "cluster"])
 def test_large_solves_by_form(ctx, vl, form):
     """n = 300,000 of the grid-with-gaps workload (m = 20, hundreds of levels)."""
     P = wl.make_problem("c3_grid1m", n=300_000)
