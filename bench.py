@@ -198,14 +198,23 @@ def _oracle_eval_seconds(n_sub: int, seed: int) -> tuple[float, float]:
     return time.perf_counter() - t0, L
 
 
+ARM_PARTS = {"0xd4f": "Arm Neoverse V2", "0xd40": "Arm Neoverse V1", "0xd0c": "Arm Neoverse N1",
+             "0xd49": "Arm Neoverse N2", "0xd8e": "Arm Neoverse N3", "0xd84": "Arm Neoverse V3"}
+
+
 def cpu_model() -> str:
+    part = None
     try:
         for line in open("/proc/cpuinfo"):
             key = line.split(":")[0].strip().lower()
-            if key in ("model name", "cpu part", "hardware"):
+            if key == "model name":
                 return line.split(":", 1)[1].strip()
+            if key == "cpu part" and part is None:
+                part = line.split(":", 1)[1].strip()
     except OSError:
         pass
+    if part:
+        return f"{ARM_PARTS.get(part.lower(), 'Arm')} (CPU part {part})"
     import platform
     return platform.processor() or platform.machine()
 
