@@ -380,6 +380,34 @@ struct Engine {
     return tuned_call(c, key, ncand, run);
   }
 
+  // Whether cooperative launches in thread-block clusters are accepted on this process
+  // (cleared after the first refusal).
+  static bool& cluster_grid_ok() {
+    static bool ok = true;
+    return ok;
+  }
+  // Most clusters of csize blocks (config cfg) co-resident, cached per (device, kernel, smem).
+  int cluster_capacity(const void* fn, const cudaLaunchConfig_t& cfg, int csize) {
+    static std::mutex mu;
+    static std::map<std::tuple<int, const void*, size_t, int>, int> cache;
+    const auto key = std::make_tuple(c->device, fn, cfg.dynamicSmemBytes, csize);
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      auto it = cache.find(key);
+      if (it != cache.end()) return it->second;
+    }
+    cudaLaunchConfig_t q = cfg;
+    q.gridDim = dim3(csize);
+    int ncl = 0;
+    if (cudaOccupancyMaxActiveClusters(&ncl, fn, &q) != cudaSuccess) {
+      cudaGetLastError();
+      ncl = 0;
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    cache[key] = ncl;
+    return ncl;
+  }
+
   // Heavy-row chunk plan of a grid solve, with partial slots and zeroed counters.
   vl_status chunk_setup(bool fwd, int ch, LevelPlan& L) {
     const Factor::ChunkPlan* pl = nullptr;
@@ -817,7 +845,7 @@ struct Engine {
     const T* val = FWD ? Aval : valT;
     const int32_t* rp = FWD ? nullptr : f->rowptrT;
     VL_CUDA(c, cudaMemsetAsync(c->gbar, 0, 2 * sizeof(unsigned), c->stream));
-    auto launch = [&](const void* fn, void** args, int lpv, int bps) -> vl_status {
+    auto launch = [&](const void* fn, void** args, int lpv, int bps, int csize = 0) -> vl_status {
       const int tpb = 16 * (32 / lpv);   // row teams per 512-thread block
       // heavy rows of the grid body in chunks: one round of loads of a team
       // (t = 1: lpv lanes x 4 loads; blocks: 16 dependency rows, whatever the row shape)
@@ -847,6 +875,32 @@ struct Engine {
       const int maxb = std::min(resident_blocks(c, fn, 512, smem), bps * c->num_sms);
       const int grid = std::max(1, std::min(maxb, (body_rows + tpb - 1) / tpb));
       ++c->launches;
+      if (csize > 0 && cluster_grid_ok()) {
+        // thread-block clusters of csize blocks, cooperative: as many whole clusters as can be
+        // co-resident and the body needs; a configuration the device refuses falls back to
+        // the plain cooperative launch below (a refused launch changes nothing)
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[2];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = csize;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        at[1].id = cudaLaunchAttributeCooperative;
+        at[1].val.cooperative = 1;
+        cfg.blockDim = dim3(512);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = c->stream;
+        cfg.attrs = at;
+        cfg.numAttrs = 2;
+        const int ncl = cluster_capacity(fn, cfg, csize);
+        const int want = std::max(1, (grid + csize - 1) / csize);
+        if (ncl >= 1) {
+          cfg.gridDim = dim3(csize * std::min(ncl, want));
+          if (cudaLaunchKernelExC(&cfg, fn, args) == cudaSuccess) return VL_OK;
+          cudaGetLastError();
+          cluster_grid_ok() = false;
+        }
+      }
       VL_CUDA(c, cudaLaunchCooperativeKernel(fn, grid, 512, args, smem, c->stream));
       if (L.trace) {
         std::vector<long long>& h = c->prof.traces[{cls, t}];
@@ -990,17 +1044,23 @@ struct Engine {
       // backward rows list up to 48 light dependents: 16 lanes keep them to one round of loads
       constexpr int LPVG = FWD ? 8 : 16;
       const void* fn1 = (const void*)sptrsv_t1_kernel<T, FWD, LPVG>;
-      return tuned(TuneKey{c->device, FWD ? 0 : 1, (int)sizeof(T), 1, log2_bucket(n)}, 2,
-                   [&](int cand) { return launch(fn1, args, LPVG, cand == 0 ? 2 : 1); });
+      const void* fn1c = (const void*)sptrsv_t1_kernel<T, FWD, LPVG, 2>;
+      // candidates: 2 or 1 blocks per SM with the counter barrier; clusters of 8 blocks with
+      // the two-stage barrier
+      return tuned(TuneKey{c->device, FWD ? 0 : 1, (int)sizeof(T), 1, log2_bucket(n)}, 3, [&](int cand) {
+        return cand == 2 ? launch(fn1c, args, LPVG, 1, 8) : launch(fn1, args, LPVG, cand == 0 ? 2 : 1);
+      });
     }
     // block kernels read rows as float4 / double2 words: ld must be a multiple of 8
     if (ld % 8 != 0) return fail(c, VL_ERR_STATE, "block solve with a row width that is not a multiple of 8");
     void* args[] = {&L, &mm, &idx, &val, &rp, &rhs, &q, &x, &l};
     // candidates (all give the same numbers): dependency rows in flight per lane (the shape's
     // UNR or twice it) x blocks per SM (2 or 1)
-    return tuned(TuneKey{c->device, FWD ? 0 : 1, (int)sizeof(T), ld, log2_bucket(n)}, 4, [&](int cand) {
+    return tuned(TuneKey{c->device, FWD ? 0 : 1, (int)sizeof(T), ld, log2_bucket(n)}, 5, [&](int cand) {
       return with_shape<T>(ld, [&](auto Lc, auto N, auto U) {
         constexpr int LPV = decltype(Lc)::value, NV = decltype(N)::value, UNR = decltype(U)::value;
+        if (cand == 4)   // clusters of 8 blocks with the two-stage barrier
+          return launch((const void*)sptrsv_kernel<T, FWD, LPV, NV, 2 * UNR, 2>, args, LPV, 1, 8);
         const int bps = (cand & 1) ? 1 : 2;
         if (cand & 2) return launch((const void*)sptrsv_kernel<T, FWD, LPV, NV, 2 * UNR>, args, LPV, bps);
         return launch((const void*)sptrsv_kernel<T, FWD, LPV, NV, UNR>, args, LPV, bps);

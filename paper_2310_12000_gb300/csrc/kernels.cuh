@@ -346,9 +346,37 @@ __device__ __forceinline__ void grid_barrier_generation(unsigned* bar, DevStatus
   __syncthreads();
 }
 
-template <bool COUNTER>
+// Grid barrier in two stages for a grid launched in thread-block clusters: the hardware
+// cluster barrier (release / acquire at cluster scope), then one arrival per cluster on the
+// monotonic counter (release at gpu scope, after the cluster barrier, so it publishes the whole
+// cluster's writes), polled by the cluster's first thread; the cluster barrier again releases
+// the cluster. A grid of C clusters makes C arrivals on the counter per level instead of one
+// per block. Bounded like grid_barrier_counter; after an abort the counter is skipped.
+__device__ __forceinline__ void grid_barrier_cluster(unsigned* bar, DevStatus* st, unsigned& epoch) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  cl.sync();
+  if (cl.block_rank() == 0 && threadIdx.x == 0) {
+    ++epoch;
+    if (!ld_volatile(&st->abort)) {
+      const unsigned target = epoch * (gridDim.x / cl.num_blocks());
+      red_release_add(&bar[0], 1u);
+      int spins = 0;
+      while (ld_acquire(&bar[0]) < target && ++spins < 4096) {
+        if (spins > 4) __nanosleep(40);
+      }
+      if (spins >= 4096) bounded_wait([&] { return ld_acquire(&bar[0]) >= target; }, st, -1);
+    }
+  }
+  cl.sync();
+}
+
+// BAR: 0 generation word, 1 monotonic counter, 2 counter per thread-block cluster
+template <int BAR>
 __device__ __forceinline__ void grid_barrier(unsigned* bar, DevStatus* st, unsigned& epoch) {
-  if constexpr (COUNTER)
+  if constexpr (BAR == 2)
+    grid_barrier_cluster(bar, st, epoch);
+  else if constexpr (BAR == 1)
     grid_barrier_counter(bar, st, epoch);
   else
     grid_barrier_generation(bar, st);
@@ -665,7 +693,7 @@ __device__ __forceinline__ void chunk_run1(const HeavyChunk& hc, const LevelPlan
 // light row (pre) before the barrier that precedes it and finishes it after
 // (run); the heavy rows that lead each level are done first, a block per row
 // (heavy(p), called by every thread of the block).
-template <int LPV, bool COUNTER, typename Pre, typename Run, typename Heavy, typename Chunk>
+template <int LPV, int BAR, typename Pre, typename Run, typename Heavy, typename Chunk>
 __device__ __forceinline__ void level_walk(const LevelPlan& L, Pre pre, Run run, Heavy heavy, Chunk chunk) {
   constexpr int RPW = 32 / LPV;
   const int tpb = (blockDim.x >> 5) * RPW;
@@ -700,7 +728,7 @@ __device__ __forceinline__ void level_walk(const LevelPlan& L, Pre pre, Run run,
   unsigned epoch = 0;
   if (!L.head_done) {
     if (blockIdx.x == 0) solo(0, L.l_head);
-    if (L.l_head > 0 && L.l_head < L.nlev) grid_barrier<COUNTER>(L.bar, L.st, epoch);
+    if (L.l_head > 0 && L.l_head < L.nlev) grid_barrier<BAR>(L.bar, L.st, epoch);
   }
   {
     int p = 0;
@@ -724,7 +752,7 @@ __device__ __forceinline__ void level_walk(const LevelPlan& L, Pre pre, Run run,
         has = first_light(l + 1, g, p);
         if (has) pre(p);
       }
-      grid_barrier<COUNTER>(L.bar, L.st, epoch);
+      grid_barrier<BAR>(L.bar, L.st, epoch);
     }
   }
   if (blockIdx.x == 0) solo(L.l_tail, L.nlev);
@@ -980,28 +1008,28 @@ __global__ void __launch_bounds__(1024) sptrsv_cluster_kernel(LevelPlan L, int m
   if (tr) L.trace[L.nlev] = clock64();
 }
 
-template <typename T, bool FWD, int LPV, int NV, int UNR>
+template <typename T, bool FWD, int LPV, int NV, int UNR, int BAR = 0>
 __global__ void __launch_bounds__(512) sptrsv_kernel(LevelPlan L, int m, const int32_t* __restrict__ idx,
                                                      const T* __restrict__ val, const int32_t* __restrict__ rowptr,
                                                      const T* __restrict__ rhs, const T* __restrict__ q, T* x, int ld) {
   extern __shared__ unsigned char vl_smem[];
   T* part = reinterpret_cast<T*>(vl_smem);
   RowPre<T, LPV, NV> r;
-  level_walk<LPV, false>(
+  level_walk<LPV, BAR>(
       L, [&](int p) { row_pre<T, FWD, LPV, NV>(r, p, m, L, idx, val, rowptr, rhs, q, ld); },
       [&]() { row_run<T, LPV, NV, UNR>(r, idx, val, x, ld); },
       [&](int p) { heavy_row<T, FWD, LPV, NV, UNR>(p, m, L, idx, val, rowptr, rhs, q, x, ld, part); },
       [&](const HeavyChunk& hc) { chunk_run<T, LPV, NV, UNR>(hc, L, idx, val, rhs, q, x, ld); });
 }
 
-template <typename T, bool FWD, int LPV>
+template <typename T, bool FWD, int LPV, int BAR = 1>
 __global__ void __launch_bounds__(512) sptrsv_t1_kernel(LevelPlan L, int m, const int32_t* __restrict__ idx,
                                                         const T* __restrict__ val, const int32_t* __restrict__ rowptr,
                                                         const T* __restrict__ rhs, const T* __restrict__ q, T* x) {
   extern __shared__ unsigned char vl_smem[];
   T* part = reinterpret_cast<T*>(vl_smem);
   RowPre1<T, LPV> r;
-  level_walk<LPV, true>(
+  level_walk<LPV, BAR>(
       L, [&](int p) { row_pre1<T, FWD, LPV>(r, p, m, L, idx, val, rowptr, rhs, q); },
       [&]() { row_run1<T, LPV>(r, idx, val, x); },
       [&](int p) { heavy_row1<T, FWD, LPV>(p, m, L, idx, val, rowptr, rhs, q, x, part); },
