@@ -398,6 +398,14 @@ vl_status vl_batch_find_mode(vl_batch* b, const int* lik, const double* y, const
  * probes): lml[k] (host, nprob), logdet (NULL or nprob), stats (NULL or nprob). */
 vl_status vl_batch_log_marglik(vl_batch* b, const vl_opts* opts, double* lml, double* logdet,
                                vl_stats* stats);
+/* Predictive means and simulated variances of every problem (as vl_pred_var: Eq.
+ * latentpostpredictive, Algorithm simAlgo with opts->s vectors drawn by each problem's own
+ * caller indices): np[k] test points of problem k, their locations (sum np x 2) and offsets Fp
+ * (sum np, may be NULL) concatenated in problem order; mean and var (sum np each, host or
+ * device, either may be NULL). Each test point conditions on the m_k nearest training points of
+ * its own problem. Call after vl_batch_find_mode. */
+vl_status vl_batch_pred_var(vl_batch* b, const int64_t* np, const double* test_locs, const double* Fp,
+                            const vl_opts* opts, double* mean, double* var);
 /* SLQ values of the last vl_batch_log_marglik: nprob x t host doubles, problem-major. */
 vl_status vl_batch_gammas(const vl_batch* b, double* gammas, int t);
 void vl_batch_destroy(vl_batch* b);

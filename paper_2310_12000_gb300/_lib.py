@@ -134,6 +134,7 @@ def library():
         "vl_batch_find_mode": (st, [vp, vp, vp, vp, vp, vp, vp]),
         "vl_batch_log_marglik": (st, [vp, vp, vp, vp, vp]),
         "vl_batch_gammas": (st, [vp, vp, i32]),
+        "vl_batch_pred_var": (st, [vp, vp, vp, vp, vp, vp, vp]),
         "vl_batch_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -582,6 +583,29 @@ class Batch:
         st = (Stats * P)()
         self.ctx.check(self.ctx.lib.vl_batch_log_marglik(self.h, C.byref(opts), lml.ctypes.data, ld.ctypes.data, st))
         return (lml, [x.as_dict() for x in st]) if with_stats else lml
+
+    def pred_var(self, test_locs, Fps=None, opts: Opts | None = None):
+        """Predictive means and simulated variances per problem (lists of arrays): test_locs is a
+        list of (np_k, 2) arrays, Fps a list of offsets or None."""
+        P = len(self.sizes)
+        if len(test_locs) != P or (Fps is not None and len(Fps) != P):
+            raise ValueError(f"expected {P} problems")
+        counts = np.array([_points(np.asarray(q, np.float64), f"test_locs[{k}]") for k, q in enumerate(test_locs)],
+                          np.int64)
+        q = np.ascontiguousarray(np.concatenate([np.asarray(v, np.float64).reshape(-1, 2) for v in test_locs]))
+        Fp = None
+        if Fps is not None:
+            for k, v in enumerate(Fps):
+                _need(v, int(counts[k]), f"Fp[{k}]")
+            Fp = np.ascontiguousarray(np.concatenate([np.asarray(v, np.float64) for v in Fps]))
+        opts = opts or Opts.make()
+        tot = int(counts.sum())
+        mean = np.empty(tot)
+        var = np.empty(tot)
+        self.ctx.check(self.ctx.lib.vl_batch_pred_var(self.h, counts.ctypes.data, q.ctypes.data, _ptr(Fp, np.float64),
+                                                      C.byref(opts), mean.ctypes.data, var.ctypes.data))
+        off = np.concatenate([[0], np.cumsum(counts)])
+        return ([mean[off[k]:off[k + 1]] for k in range(P)], [var[off[k]:off[k + 1]] for k in range(P)])
 
     def gammas(self, t: int):
         g = np.empty(len(self.sizes) * t)

@@ -251,7 +251,7 @@ static vl_status cg_converged(Engine<T>& E, const vl_opts* o, const char* what) 
   std::vector<int> iters;
   std::vector<double> rel;
   VL_TRY(E.column_stats(iters, rel));
-  for (int k = 0; k < E.t; ++k)
+  for (int k = 0; k < E.ncol; ++k)
     if (rel[k] > o->cg_tol && iters[k] >= o->cg_max_iter)
       return fail(E.c, VL_ERR_NOT_CONVERGED, std::string(what) + ": PCG reached cg_max_iter above cg_tol");
   return VL_OK;
@@ -305,18 +305,20 @@ static vl_status sim_block(State* st, const vl_opts* o, Engine<double>& E64, int
   if (!res || !r32 || !d32) return fail(c, VL_ERR_OOM, "workspace exhausted (simulation refinement)");
   VL_CUDA(c, cudaMemsetAsync(res, 0, sizeof(double) * vec, c->stream));
   VL_CUDA(c, cudaMemsetAsync(U, 0, sizeof(double) * vec, c->stream));
+  // per (problem, column) norms: a batch has nseg * sc columns
+  const int ncol = E64.ncol;
   VL_TRY(E64.coldot(z3, z3, nullptr, E64.red2));
-  std::vector<double> bn(sc), rn(sc);
-  VL_CUDA(c, cudaMemcpyAsync(bn.data(), E64.red2, sizeof(double) * sc, cudaMemcpyDeviceToHost, c->stream));
+  std::vector<double> bn(ncol), rn(ncol);
+  VL_CUDA(c, cudaMemcpyAsync(bn.data(), E64.red2, sizeof(double) * ncol, cudaMemcpyDeviceToHost, c->stream));
   double worst = 1.0;
   for (int pass = 0; pass < 12; ++pass) {
     VL_TRY(E64.opA(U, res));
     residual_kernel<<<grid_for(c, vec), 256, 0, VL_STREAM(c)>>>(vec, z3, res);
     VL_TRY(E64.coldot(res, res, nullptr, E64.red));
-    VL_CUDA(c, cudaMemcpyAsync(rn.data(), E64.red, sizeof(double) * sc, cudaMemcpyDeviceToHost, c->stream));
+    VL_CUDA(c, cudaMemcpyAsync(rn.data(), E64.red, sizeof(double) * ncol, cudaMemcpyDeviceToHost, c->stream));
     VL_CUDA(c, cudaStreamSynchronize(c->stream));
     worst = 0.0;
-    for (int k = 0; k < sc; ++k) worst = std::max(worst, bn[k] > 0 ? std::sqrt(rn[k] / bn[k]) : 0.0);
+    for (int k = 0; k < ncol; ++k) worst = std::max(worst, bn[k] > 0 ? std::sqrt(rn[k] / bn[k]) : 0.0);
     if (worst <= o->cg_tol) break;
     repack_kernel<<<grid_for(c, vec), 256, 0, VL_STREAM(c)>>>(vec, res, r32);
     VL_CUDA(c, cudaGetLastError());
@@ -332,6 +334,42 @@ static vl_status sim_block(State* st, const vl_opts* o, Engine<double>& E64, int
   }
   if (stats) stats->true_relres_max = std::max(stats->true_relres_max, worst);
   if (worst > o->cg_tol) return fail(c, VL_ERR_NOT_CONVERGED, "simulation solves: refinement did not reach cg_tol");
+  return VL_OK;
+}
+
+// Predictive mean and simulated variances at np test points whose neighbours (storage rows of
+// st->f, -1 padding, m per point), weights Ap and conditional variances Dp are given (Eq.
+// latentpostpredictive, Algorithm simAlgo); mean/var device arrays of np. Shared by single
+// problems and batches.
+vl_status pred_from_rows(State* st, const vl_opts* o, int64_t np, int m, const int32_t* Np, const double* Ap,
+                         const double* Dp, const double* dF, double* dmean, double* dvar, vl_stats* loc) {
+  Ctx* c = st->ctx;
+  Factor* f = st->f;
+  const int n = (int)f->n;
+  Scratch S(c);
+  const int pg = (int)((np * 32 + 255) / 256);
+  if (dmean) {
+    pred_kernel<double><<<pg, 256, 0, VL_STREAM(c)>>>((int)np, m, Np, Ap, Dp, dF, st->b, nullptr, 0, 1, dmean, nullptr);
+    VL_CUDA(c, cudaGetLastError());
+  }
+  if (!dvar) return VL_OK;
+  VL_CUDA(c, cudaMemsetAsync(dvar, 0, sizeof(double) * np, c->stream));
+  if (o->precond == VL_PREC_LRAC) VL_TRY(lrac_build(f, o->k));
+  for (int col0 = 0; col0 < o->s; col0 += 128) {
+    const int sc = std::min(128, o->s - col0);
+    Engine<double> E64(c);
+    VL_TRY(E64.init(f, sc, o->precond, st->W, o->precision == VL_FP64 ? o->cg_max_iter + 1 : 0));
+    double* U = S.get<double>((size_t)n * E64.ld);
+    if (!U) return fail(c, VL_ERR_OOM, "workspace exhausted (simulation)");
+    VL_TRY(sim_block(st, o, E64, sc, col0, U, loc));
+    pred_kernel<double><<<pg, 256, 0, VL_STREAM(c)>>>((int)np, m, Np, Ap, Dp, nullptr, st->b, U, sc, E64.ld, nullptr, dvar);
+    VL_CUDA(c, cudaGetLastError());
+    VL_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->arena.release(U);
+    S.blocks.erase(std::find(S.blocks.begin(), S.blocks.end(), (void*)U));
+  }
+  pred_finish_kernel<<<(int)((np + 255) / 256), 256, 0, VL_STREAM(c)>>>((int)np, Dp, 1.0 / o->s, dvar);
+  VL_CUDA(c, cudaGetLastError());
   return VL_OK;
 }
 
@@ -973,29 +1011,7 @@ vl_status vl_pred_var(vl_state* st, const double* test_locs, int64_t np, const d
   VL_CUDA(c, status_clear(c));
   VL_TRY(factor_rows(c, np, m, dq, f->locs_s, Np, f->cov, f->sigma2, f->rho, f->nugget, Ap, Dp, nullptr));
   VL_TRY(check_dev_status(c, "prediction rows"));
-  VL_CUDA(c, cudaMemsetAsync(dvar, 0, sizeof(double) * np, c->stream));
-  const int pg = (int)((np * 32 + 255) / 256);
-  pred_kernel<double><<<pg, 256, 0, VL_STREAM(c)>>>((int)np, m, Np, Ap, Dp, dF, st->b, nullptr, 0, 1, dmean, nullptr);
-  VL_CUDA(c, cudaGetLastError());
-  if (var) {
-    VL_TRY(ensure_precond(f, o));
-    for (int col0 = 0; col0 < o->s; col0 += 128) {
-      const int sc = std::min(128, o->s - col0);
-      Engine<double> E64(c);
-      VL_TRY(E64.init(f, sc, o->precond, st->W, o->precision == VL_FP64 ? o->cg_max_iter + 1 : 0));
-      double* U = S.get<double>((size_t)n * E64.ld);
-      if (!U) return fail(c, VL_ERR_OOM, "workspace exhausted (simulation)");
-      VL_TRY(sim_block(st, o, E64, sc, col0, U, &loc));
-      pred_kernel<double><<<pg, 256, 0, VL_STREAM(c)>>>((int)np, m, Np, Ap, Dp, nullptr, st->b, U, sc, E64.ld, nullptr,
-                                                      dvar);
-      VL_CUDA(c, cudaGetLastError());
-      VL_CUDA(c, cudaStreamSynchronize(c->stream));
-      c->arena.release(U);
-      S.blocks.erase(std::find(S.blocks.begin(), S.blocks.end(), (void*)U));
-    }
-    pred_finish_kernel<<<(int)((np + 255) / 256), 256, 0, VL_STREAM(c)>>>((int)np, Dp, 1.0 / o->s, dvar);
-    VL_CUDA(c, cudaGetLastError());
-  }
+  VL_TRY(pred_from_rows(st, o, np, m, Np, Ap, Dp, dF, dmean, var ? dvar : nullptr, &loc));
   VL_TRY(stage_out(c, dmean, mean, np));
   VL_TRY(stage_out(c, dvar, var, np));
   VL_CUDA(c, cudaEventRecord(c->ev1, c->stream));

@@ -22,6 +22,8 @@ namespace vl {
 
 void ctx_retain(Ctx* c);
 void ctx_release_ref(Ctx* c);
+vl_status pred_from_rows(State* st, const vl_opts* o, int64_t np, int m, const int32_t* Np, const double* Ap,
+                         const double* Dp, const double* dF, double* dmean, double* dvar, vl_stats* loc);
 
 struct Batch {
   Ctx* ctx = nullptr;
@@ -77,6 +79,25 @@ __global__ void gather_rows_kernel(int n, const int32_t* __restrict__ s2u, const
 __global__ void scatter_rows_kernel(int n, const int32_t* __restrict__ s2u, const double* __restrict__ Xs,
                                     double* __restrict__ Xu) {
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) Xu[s2u[s]] = Xs[s];
+}
+
+// Test-point rows of one member into the merged rows of width mm: neighbour Vecchia indices
+// of the member -> member storage rows (v2s) for its own factor rows (Nloc), and -> merged
+// storage rows (+ off) with -1 / 0 padding (Nm, Am).
+__global__ void pred_rows_local_kernel(int64_t total, const int32_t* __restrict__ v2s, int32_t* __restrict__ N) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
+    N[e] = N[e] >= 0 ? v2s[N[e]] : -1;
+}
+__global__ void pred_rows_merge_kernel(int np, int m, int mm, int32_t off, const int32_t* __restrict__ Nloc,
+                                       const double* __restrict__ Aloc, int32_t* __restrict__ Nm,
+                                       double* __restrict__ Am) {
+  const int64_t total = (int64_t)np * mm;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int p = (int)(e / mm), c = (int)(e % mm);
+    const int j = c < m ? Nloc[(int64_t)p * m + c] : -1;
+    Nm[e] = j >= 0 ? j + off : -1;
+    Am[e] = j >= 0 ? Aloc[(int64_t)p * m + c] : 0.0;
+  }
 }
 
 bool on_device(const void* p) {
@@ -426,6 +447,76 @@ vl_status vl_batch_log_marglik(vl_batch* b, const vl_opts* o, double* lml, doubl
       s.logdet = L.logdet[k];
     }
   }
+  return VL_OK;
+}
+
+vl_status vl_batch_pred_var(vl_batch* b, const int64_t* np, const double* test_locs, const double* Fp,
+                            const vl_opts* o, double* mean, double* var) {
+  if (!b) return VL_ERR_INVALID_ARG;
+  Ctx* c = b->ctx;
+  VL_TRY(batch_opts(c, o));
+  if (!np || o->s < 1) return fail(c, VL_ERR_INVALID_ARG, "vl_batch_pred_var: invalid argument");
+  if (!b->has_state) return fail(c, VL_ERR_STATE, "vl_batch_pred_var: call vl_batch_find_mode first");
+  const int P = (int)b->members.size();
+  Factor& M = b->merged;
+  std::vector<int64_t> p0(P + 1, 0);
+  for (int k = 0; k < P; ++k) {
+    if (np[k] < 0) return fail(c, VL_ERR_INVALID_ARG, "vl_batch_pred_var: negative test count");
+    p0[k + 1] = p0[k] + np[k];
+  }
+  const int64_t ntot = p0[P];
+  if (ntot == 0) return VL_OK;
+  if (!test_locs || ntot > (1LL << 30)) return fail(c, VL_ERR_INVALID_ARG, "vl_batch_pred_var: invalid argument");
+  const int mm = std::max(M.m, 1);
+  Scratch S(c);
+  const double* dq = test_locs;
+  const double* dF = Fp;
+  if (!on_device(test_locs)) {
+    double* t = S.get<double>((size_t)ntot * 2);
+    if (!t) return fail(c, VL_ERR_OOM, "workspace exhausted (staging test locations)");
+    VL_CUDA(c, cudaMemcpyAsync(t, test_locs, sizeof(double) * ntot * 2, cudaMemcpyHostToDevice, c->stream));
+    dq = t;
+  }
+  if (Fp && !on_device(Fp)) {
+    double* t = S.get<double>(ntot);
+    if (!t) return fail(c, VL_ERR_OOM, "workspace exhausted (staging Fp)");
+    VL_CUDA(c, cudaMemcpyAsync(t, Fp, sizeof(double) * ntot, cudaMemcpyHostToDevice, c->stream));
+    dF = t;
+  }
+  int32_t* Nm = S.get<int32_t>((size_t)ntot * mm);
+  double* Am = S.get<double>((size_t)ntot * mm);
+  double* Dp = S.get<double>(ntot);
+  double* dmean = S.get<double>(ntot);
+  double* dvar = S.get<double>(ntot);
+  if (!Nm || !Am || !Dp || !dmean || !dvar) return fail(c, VL_ERR_OOM, "workspace exhausted (batch prediction)");
+  // each problem's test points condition on its own m nearest training points (Section 4.1)
+  for (int k = 0; k < P; ++k) {
+    const int64_t npk = np[k];
+    if (npk == 0) continue;
+    Factor* f = b->members[k];
+    const int m = f->m;
+    Scratch T(c);
+    int32_t* Nl = T.get<int32_t>((size_t)npk * std::max(m, 1));
+    double* Al = T.get<double>((size_t)npk * std::max(m, 1));
+    if (!Nl || !Al) return fail(c, VL_ERR_OOM, "workspace exhausted (batch prediction rows)");
+    const double* q = dq + 2 * p0[k];
+    if (m > 0) {
+      VL_TRY(knn_cross_dev(c, f->locs_v, f->n, q, npk, m, Nl));
+      pred_rows_local_kernel<<<grid_for(c, npk * m), 256, 0, VL_STREAM(c)>>>(npk * m, f->v2s, Nl);
+      VL_CUDA(c, cudaGetLastError());
+    }
+    VL_CUDA(c, status_clear(c));
+    VL_TRY(factor_rows(c, npk, m, q, f->locs_s, Nl, f->cov, f->sigma2, f->rho, f->nugget, Al, Dp + p0[k], nullptr));
+    VL_TRY(check_dev_status(c, "batch prediction rows"));
+    pred_rows_merge_kernel<<<grid_for(c, npk * mm), 256, 0, VL_STREAM(c)>>>((int)npk, m, mm, (int32_t)b->row0[k], Nl,
+                                                                           Al, Nm + p0[k] * mm, Am + p0[k] * mm);
+    VL_CUDA(c, cudaGetLastError());
+    VL_CUDA(c, cudaStreamSynchronize(c->stream));
+  }
+  VL_TRY(pred_from_rows(&b->state, o, ntot, mm, Nm, Am, Dp, dF, dmean, var ? dvar : nullptr, nullptr));
+  if (mean) VL_CUDA(c, cudaMemcpyAsync(mean, dmean, sizeof(double) * ntot, cudaMemcpyDefault, c->stream));
+  if (var) VL_CUDA(c, cudaMemcpyAsync(var, dvar, sizeof(double) * ntot, cudaMemcpyDefault, c->stream));
+  VL_CUDA(c, cudaStreamSynchronize(c->stream));
   return VL_OK;
 }
 

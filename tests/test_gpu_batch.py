@@ -124,3 +124,43 @@ def test_batch_after_refit_and_refusals(vl):
         b.log_marglik(vl.Opts.make(t=8, precond=vl.PREC_LRAC, k=5))
     b.close()
     ctx.close()
+
+
+def test_batch_pred_var_equals_problems_alone(vl):
+    """vl_batch_pred_var: each problem's test points condition on its own training points and its
+    simulated variances use its own probes, so every problem gets what vl_pred_var gives it alone
+    (float64, 1e-9), and two members match the oracle's simAlgo with the same probes. One problem
+    has no test points."""
+    probs = _problems()
+    rng = np.random.default_rng(77)
+    counts = [13, 0, 40, 7, 3, 25]
+    tl = [rng.random((c, 2)) for c in counts]
+    Fps = [np.full(c, 0.3) for c in counts]
+    ctx = vl.Context(0, ws_bytes=4 << 30)
+    s = 24
+    opts = vl.Opts.make(s=s, lik_shape=5.0, **FP64_TIGHT)
+    facs = [ctx.build_factor(P.locs, P.order, P.cov, P.sigma2, P.rho, P.m, opts) for P in probs]
+    alone = []
+    for P, f, q, Fp in zip(probs, facs, tl, Fps):
+        st = f.find_mode(P.lik, P.y, P.F, opts)
+        alone.append(st.pred_var(q, Fp, opts) if len(q) else (np.zeros(0), np.zeros(0)))
+        st.close()
+    b = vl.Batch(ctx, facs)
+    b.find_mode([P.lik for P in probs], [P.y for P in probs], [P.F for P in probs], opts)
+    means, vars_ = b.pred_var(tl, Fps, opts)
+    for k, (m_a, v_a) in enumerate(alone):
+        assert means[k].shape == (counts[k],) and vars_[k].shape == (counts[k],)
+        if counts[k] == 0:
+            continue
+        assert np.max(np.abs(means[k] - m_a)) <= 1e-9 * (1 + np.max(np.abs(m_a))), k
+        assert np.max(np.abs(vars_[k] - v_a) / v_a) <= 1e-9, k
+    for k in (0, 5):
+        P = probs[k]
+        f = la.build_factor(P.locs, P.order, P.cov, P.sigma2, P.rho, P.m, P.nugget)
+        md = la.find_mode(f, P.y, P.F, P.lik, newton_tol=1e-12, xi=5.0)
+        pf = la.pred_factor(f, tl[k], P.m)
+        assert np.max(np.abs(means[k] - la.pred_mean(pf, md, Fps[k]))) <= 1e-9 * (1 + np.max(np.abs(means[k])))
+        v_ref = la.pred_var_sim(f, md, pf, s, 1)
+        assert np.max(np.abs(vars_[k] - v_ref) / v_ref) <= 1e-9, k
+    b.close()
+    ctx.close()
