@@ -19,8 +19,10 @@ Two more legs run on rank 0 of a single-GPU run, after the timed steps:
   slot contexts on separate streams; reported as evaluations/s.
 * serving: a Poisson stream of fresh problems at 50 requests/s (n log-uniform in
   [1e3, 2e5], Matern-1.5, Bernoulli or Poisson, mode + L^VLA + predictive
-  variances at 1000 points) admitted by device-memory footprint; reported as
-  p50 / p99 latency (arrival to completion) and throughput.
+  variances at 1000 points) admitted by device-memory footprint and served by
+  continuous batching (a free slot merges every queued request that fits into one
+  block-diagonal system); reported as p50 / p99 latency (arrival to completion),
+  service time and throughput, with the arrival window stated.
 
 Multi-GPU (torchrun, one rank per GPU): independent replicas, each rank solving its
 own seeded problem of the same shape (weak scaling); no collective on the data path.
@@ -272,17 +274,31 @@ def pregenerate(kind: str, count: int, procs: int = 12):
         return pool.map(fn, range(count), chunksize=4)
 
 
-def serving_leg(vl, problems, arrivals, duration: float, slots: int, device: int, small: int = 0) -> dict:
+def serving_leg(vl, problems, arrivals, duration: float, slots: int, device: int, small: int = 0,
+                form: str = "groups", group_slots: int = 2, group_gb: float = 60.0) -> dict:
+    """The serving stream. form "groups": continuous batching, `group_slots` slot contexts of
+    group_gb GiB each, a free slot merging every queued request that fits into one
+    block-diagonal system; form "slots": one request per slot context, `slots` of them."""
     import numpy as np
     from paper_2310_12000_gb300 import serving
     opts = dict(precision=1, t=50, s=100, cg_tol=1e-6, newton_tol=1e-7)
     reqs = [serving.Request.from_problem(i, P, opts) for i, P in enumerate(problems)]
-    # slot classes: `small` slots sized for n <= 6e4, the rest for the largest requests (n = 2e5)
-    big = slots - small
-    caps = [serving.footprint_bytes(200_000, 20)] * big + [serving.footprint_bytes(60_000, 20)] * small
-    srv = serving.Server(slots=caps, budget_bytes=sum(caps), slot_capacity=None,
-                         make_ctx=serving.gpu_slots(vl, device),
-                         runner=lambda ctx, req: serving.run_request(vl, ctx, req)).start()
+    if form == "groups":
+        cap = int(group_gb * (1 << 30))
+        caps = [cap] * group_slots
+        srv = serving.Server(slots=caps, budget_bytes=sum(caps), slot_capacity=None,
+                             make_ctx=serving.gpu_slots(vl, device), max_group=256,
+                             group_footprint=serving.batch_footprint_bytes,
+                             batch_runner=lambda ctx, g: serving.run_batch(vl, ctx, g)).start()
+        classes = {f"{group_gb:g} GiB merged-group slots": group_slots}
+    else:
+        # slot classes: `small` slots sized for n <= 6e4, the rest for the largest requests (n = 2e5)
+        big = slots - small
+        caps = [serving.footprint_bytes(200_000, 20)] * big + [serving.footprint_bytes(60_000, 20)] * small
+        srv = serving.Server(slots=caps, budget_bytes=sum(caps), slot_capacity=None,
+                             make_ctx=serving.gpu_slots(vl, device),
+                             runner=lambda ctx, req: serving.run_request(vl, ctx, req)).start()
+        classes = {"n<=2e5": big, "n<=6e4": small}
     for r, t in zip(reqs, arrivals):
         now = srv.now()
         if t > now:
@@ -291,8 +307,14 @@ def serving_leg(vl, problems, arrivals, duration: float, slots: int, device: int
     res = srv.drain()
     wall = srv.now()
     out = serving.latency_summary(res, wall)
-    out.update({"offered_rps": len(arrivals) / duration, "arrival_window_s": duration, "slots": slots,
-                "slot_classes": {"n<=2e5": big, "n<=6e4": small},
+    out.update({"form": "continuous batching (merged groups)" if form == "groups" else "one request per slot",
+                "offered_rps": len(arrivals) / duration, "arrival_window_s": duration, "slots": len(caps),
+                "slot_classes": classes,
+                "groups": ({"count": len(srv.groups), "mean": float(np.mean(srv.groups)), "max": max(srv.groups)}
+                           if srv.groups else None),
+                "note": (f"arrivals offered for {duration:g} s at {len(arrivals) / duration:.1f} req/s, then "
+                         f"drained: p50/p99 latency include the queueing behind that backlog; "
+                         f"p50/p99_service_ms exclude it"),
                 "peak_concurrent": srv.sched.peak_running, "wall_s": wall,
                 "mean_n": float(np.mean([r.n for r in reqs])) if reqs else None,
                 "max_true_relres": max((r.stats.get("mode", {}).get("true_relres_max", 0.0) for r in res
@@ -557,7 +579,7 @@ def run_ours(args):
                                f"float32 + float64 refinement, merged into one block-diagonal system")
     if serve_problems:
         serving_out = serving_leg(vl, serve_problems, serve_arrivals, args.serve_seconds, args.slots, dev,
-                                  args.small_slots)
+                                  args.small_slots, args.serve_form, args.group_slots, args.group_gb)
         print(f"[bench] serving: {serving_out['completed']} requests, p99 {serving_out['p99_latency_ms']} ms, "
               f"wall {serving_out['wall_s']:.1f} s", file=sys.stderr, flush=True)
 
@@ -622,6 +644,10 @@ def main():
     ap.add_argument("--slots", type=int, default=16, help="slot contexts of the batched and serving legs")
     ap.add_argument("--batch-streams", action="store_true",
                     help="also run the batched problems on slot contexts (one stream each)")
+    ap.add_argument("--serve-form", default="groups", choices=["groups", "slots"],
+                    help="serving by merged groups (continuous batching) or one request per slot context")
+    ap.add_argument("--group-slots", type=int, default=2, help="slot contexts of the merged-group serving form")
+    ap.add_argument("--group-gb", type=float, default=60.0, help="workspace GiB of each merged-group slot")
     ap.add_argument("--small-slots", type=int, default=0,
                     help="of the serving slots, how many are sized for n <= 6e4 only (the rest for n = 2e5)")
     args = ap.parse_args()

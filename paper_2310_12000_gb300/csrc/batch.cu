@@ -100,13 +100,22 @@ __global__ void pred_rows_merge_kernel(int np, int m, int mm, int32_t off, const
   }
 }
 
-bool on_device(const void* p) {
+// Where a caller's pointer lives: *dev is set for memory that kernels on the context's device
+// may use directly; another GPU's memory is refused (VL_ERR_INVALID_ARG).
+vl_status locate(Ctx* c, const void* p, bool* dev) {
+  *dev = false;
+  if (!p) return VL_OK;
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
-    return false;
+    return VL_OK;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) {
+    if (!device_memory_usable(a.type, a.device, c->device))
+      return fail(c, VL_ERR_INVALID_ARG, "a device pointer is not on the context's device");
+    *dev = true;
+  }
+  return VL_OK;
 }
 
 // Copies values (A, D, B^T values) of every member into the merged arrays.
@@ -355,13 +364,16 @@ vl_status vl_batch_find_mode(vl_batch* b, const int* lik, const double* y, const
   {
     Scratch S(c);
     const double *dy = y, *dF = F;
-    if (!on_device(y)) {
+    bool y_dev, F_dev;
+    VL_TRY(locate(c, y, &y_dev));
+    VL_TRY(locate(c, F, &F_dev));
+    if (!y_dev) {
       double* t = S.get<double>(n);
       if (!t) return fail(c, VL_ERR_OOM, "workspace exhausted (staging y)");
       VL_CUDA(c, cudaMemcpyAsync(t, y, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
       dy = t;
     }
-    if (F && !on_device(F)) {
+    if (F && !F_dev) {
       double* t = S.get<double>(n);
       if (!t) return fail(c, VL_ERR_OOM, "workspace exhausted (staging F)");
       VL_CUDA(c, cudaMemcpyAsync(t, F, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
@@ -392,7 +404,9 @@ vl_status vl_batch_find_mode(vl_batch* b, const int* lik, const double* y, const
   }
   VL_TRY(newton_run(&st, opts, b->mode_stats, b->conv));
   if (mode_out) {
-    if (on_device(mode_out)) {
+    bool out_dev;
+    VL_TRY(locate(c, mode_out, &out_dev));
+    if (out_dev) {
       scatter_rows_kernel<<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, M.s2u, st.b, mode_out);
     } else {
       Scratch S(c);
@@ -471,13 +485,18 @@ vl_status vl_batch_pred_var(vl_batch* b, const int64_t* np, const double* test_l
   Scratch S(c);
   const double* dq = test_locs;
   const double* dF = Fp;
-  if (!on_device(test_locs)) {
+  bool q_dev, F_dev, mean_dev, var_dev;
+  VL_TRY(locate(c, test_locs, &q_dev));
+  VL_TRY(locate(c, Fp, &F_dev));
+  VL_TRY(locate(c, mean, &mean_dev));
+  VL_TRY(locate(c, var, &var_dev));
+  if (!q_dev) {
     double* t = S.get<double>((size_t)ntot * 2);
     if (!t) return fail(c, VL_ERR_OOM, "workspace exhausted (staging test locations)");
     VL_CUDA(c, cudaMemcpyAsync(t, test_locs, sizeof(double) * ntot * 2, cudaMemcpyHostToDevice, c->stream));
     dq = t;
   }
-  if (Fp && !on_device(Fp)) {
+  if (Fp && !F_dev) {
     double* t = S.get<double>(ntot);
     if (!t) return fail(c, VL_ERR_OOM, "workspace exhausted (staging Fp)");
     VL_CUDA(c, cudaMemcpyAsync(t, Fp, sizeof(double) * ntot, cudaMemcpyHostToDevice, c->stream));
@@ -514,8 +533,12 @@ vl_status vl_batch_pred_var(vl_batch* b, const int64_t* np, const double* test_l
     VL_CUDA(c, cudaStreamSynchronize(c->stream));
   }
   VL_TRY(pred_from_rows(&b->state, o, ntot, mm, Nm, Am, Dp, dF, dmean, var ? dvar : nullptr, nullptr));
-  if (mean) VL_CUDA(c, cudaMemcpyAsync(mean, dmean, sizeof(double) * ntot, cudaMemcpyDefault, c->stream));
-  if (var) VL_CUDA(c, cudaMemcpyAsync(var, dvar, sizeof(double) * ntot, cudaMemcpyDefault, c->stream));
+  if (mean)
+    VL_CUDA(c, cudaMemcpyAsync(mean, dmean, sizeof(double) * ntot,
+                               mean_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+  if (var)
+    VL_CUDA(c, cudaMemcpyAsync(var, dvar, sizeof(double) * ntot,
+                               var_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
   VL_CUDA(c, cudaStreamSynchronize(c->stream));
   return VL_OK;
 }

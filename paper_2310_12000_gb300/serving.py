@@ -21,6 +21,13 @@ Execution model
   the device as requests arrive and leave.
 * Every kernel of the library is deterministic and requests share no device state,
   so a request's results are the same whether it runs alone or in the mix.
+* Continuous batching (``batch_runner``): a slot that frees up takes the first queued
+  request that fits and, in queue order, every further queued request with the same
+  options while the group's footprint stays within the slot and the budget. The group
+  runs as one merged block-diagonal system (``run_batch``: one launch of every kernel
+  for all of its requests, each request with its own Newton iteration, PCG stopping
+  rule and probes), so a request gets the same results alone and in a group up to the
+  rounding of reductions taken over other block partitions.
 
 The scheduler (admission, FIFO order, budget accounting) is plain host logic and
 can be driven with any runner; ``run_request`` is the runner that calls the library.
@@ -52,6 +59,20 @@ def footprint_bytes(n: int, m: int, t: int = 50, s: int = 100, n_test: int = 100
     test = n_test * (16 * m + 96)
     lrac = n * k * 12 + n * lt * 4 + 6 * k * k * 8 if k else 0
     return int(1.15 * (factor + max(sim, slq) + test + lrac)) + (32 << 20)
+
+
+def batch_footprint_bytes(reqs) -> int:
+    """Upper estimate of the workspace a merged group of requests needs (bytes): every
+    member's own factor, plus the merged system (its factor, state and largest phase) as
+    one request of the group's total size and largest m."""
+    if not reqs:
+        return 0
+    o = reqs[0].opts
+    N = sum(r.n for r in reqs)
+    m = max(r.m for r in reqs)
+    nt = sum(0 if r.test_locs is None else len(r.test_locs) for r in reqs)
+    members = sum(int(1.15 * r.n * (200 + 40 * r.m)) for r in reqs)
+    return footprint_bytes(N, m, o.get("t", 50), o.get("s", 100), nt) + members
 
 
 @dataclasses.dataclass
@@ -106,11 +127,14 @@ class Result:
 
 
 class Scheduler:
-    """FIFO admission by footprint against a device-memory budget."""
+    """FIFO admission by footprint against a device-memory budget. ``group_footprint``
+    (a list of requests -> bytes) prices the groups of continuous batching; by default a
+    group costs the sum of its requests' footprints."""
 
-    def __init__(self, budget_bytes: int, slot_capacity: int):
+    def __init__(self, budget_bytes: int, slot_capacity: int, group_footprint: Callable | None = None):
         self.budget = int(budget_bytes)
         self.capacity = int(slot_capacity)   # bytes the largest slot can hold
+        self.group_footprint = group_footprint or (lambda reqs: sum(r.footprint for r in reqs))
         self.q: collections.deque[Request] = collections.deque()
         self.cv = threading.Condition()
         self.in_use = 0
@@ -120,9 +144,10 @@ class Scheduler:
         self.closed = False
         self.rejected: list[Request] = []
 
-    def submit(self, req: Request) -> bool:
+    def submit(self, req: Request, grouped: bool = False) -> bool:
         with self.cv:
-            if req.footprint > min(self.budget, self.capacity):
+            fp = self.group_footprint([req]) if grouped else req.footprint
+            if fp > min(self.budget, self.capacity):
                 self.rejected.append(req)
                 return False
             self.q.append(req)
@@ -160,16 +185,100 @@ class Scheduler:
                     return None
                 self.cv.wait(left)
 
+    def acquire_group(self, capacity: int | None = None, max_group: int = 64,
+                      timeout: float | None = None) -> tuple[list[Request], int]:
+        """Continuous batching: block until the first queued request that fits a slot of
+        `capacity` bytes, alone, also fits the budget; take it and then, in queue order,
+        every further queued request with the same options while the group's footprint
+        stays within the slot and the budget (at most max_group requests). Returns the
+        group (removed from the queue, admitted) and its footprint, or ([], 0) once the
+        scheduler is closed and no queued request fits this slot."""
+        cap = self.capacity if capacity is None else int(capacity)
+        deadline = None if timeout is None else time.perf_counter() + timeout
+        with self.cv:
+            while True:
+                group: list[Request] = []
+                fp = 0
+                first_fits = False
+                for r in self.q:
+                    if len(group) >= max_group:
+                        break
+                    if group and r.opts != group[0].opts:
+                        continue
+                    f = self.group_footprint(group + [r])
+                    if not group:
+                        if f > cap:
+                            continue           # not for this slot's size class
+                        first_fits = True
+                        if self.in_use + f > self.budget:
+                            break              # first come, first served: the head waits for room
+                        group.append(r)
+                        fp = f
+                    elif f <= cap and self.in_use + f <= self.budget:
+                        group.append(r)
+                        fp = f
+                if group:
+                    for r in group:
+                        self.q.remove(r)
+                    self.in_use += fp
+                    self.running += len(group)
+                    self.peak_in_use = max(self.peak_in_use, self.in_use)
+                    self.peak_running = max(self.peak_running, self.running)
+                    self.cv.notify_all()
+                    return group, fp
+                if self.closed and not first_fits:
+                    return [], 0
+                left = None if deadline is None else deadline - time.perf_counter()
+                if left is not None and left <= 0:
+                    return [], 0
+                self.cv.wait(left)
+
     def release(self, req: Request):
         with self.cv:
             self.in_use -= req.footprint
             self.running -= 1
             self.cv.notify_all()
 
+    def release_group(self, group: list[Request], footprint: int):
+        with self.cv:
+            self.in_use -= footprint
+            self.running -= len(group)
+            self.cv.notify_all()
+
     def close(self):
         with self.cv:
             self.closed = True
             self.cv.notify_all()
+
+
+def run_batch(vl, ctx, reqs: list[Request]) -> list[dict]:
+    """The whole path for a group of requests with the same options, merged into one
+    block-diagonal system on one slot context (vl.Batch): factors, modes, L^VLA,
+    predictive means and variances. A failure fails the whole group."""
+    o = vl.Opts.make(**reqs[0].opts)
+    facs, b = [], None
+    try:
+        for r in reqs:
+            facs.append(ctx.build_factor(r.locs, r.order, r.cov, r.sigma2, r.rho, r.m, o))
+        b = vl.Batch(ctx, facs)
+        Fs = None if all(r.F is None for r in reqs) else [np.zeros(r.n) if r.F is None else r.F for r in reqs]
+        modes, mstats = b.find_mode([r.lik for r in reqs], [r.y for r in reqs], Fs, o, with_stats=True)
+        lml, lstats = b.log_marglik(o, with_stats=True)
+        outs = [{"lml": float(lml[k]), "mode": modes[k], "stats": {"mode": mstats[k], "lml": lstats[k],
+                                                                  "group": len(reqs)}}
+                for k in range(len(reqs))]
+        tl = [np.zeros((0, 2)) if r.test_locs is None else np.asarray(r.test_locs, np.float64) for r in reqs]
+        if any(len(q) for q in tl):
+            means, vars_ = b.pred_var(tl, None, o)
+            for k, r in enumerate(reqs):
+                if len(tl[k]):
+                    outs[k]["mean"], outs[k]["var"] = means[k], vars_[k]
+        return outs
+    finally:
+        if b is not None:
+            b.close()
+        for f in facs:
+            f.close()
 
 
 def run_request(vl, ctx, req: Request) -> dict:
@@ -199,11 +308,17 @@ class Server:
     count (every slot holds ``slot_capacity`` bytes) or a list of per-slot capacities."""
 
     def __init__(self, slots, budget_bytes: int, slot_capacity: int | None, make_ctx: Callable[..., object],
-                 runner: Callable[[object, Request], dict], clock: Callable[[], float] = time.perf_counter):
+                 runner: Callable[[object, Request], dict] | None = None, clock: Callable[[], float] = time.perf_counter,
+                 batch_runner: Callable[[object, list], list] | None = None, max_group: int = 64,
+                 group_footprint: Callable | None = None):
         caps = [int(slot_capacity)] * slots if isinstance(slots, int) else [int(c) for c in slots]
+        if (runner is None) == (batch_runner is None):
+            raise ValueError("give exactly one of runner and batch_runner")
         self.caps = caps
-        self.sched = Scheduler(budget_bytes, max(caps))
+        self.sched = Scheduler(budget_bytes, max(caps), group_footprint)
         self.make_ctx, self.runner, self.clock = make_ctx, runner, clock
+        self.batch_runner, self.max_group = batch_runner, int(max_group)
+        self.groups: list[int] = []          # sizes of the groups served (continuous batching)
         self._sized = not isinstance(slots, int)
         self.results: list[Result] = []
         self._lock = threading.Lock()
@@ -230,7 +345,7 @@ class Server:
     def submit(self, req: Request, stamp: bool = True) -> bool:
         if stamp:
             req.arrival = self.now()
-        ok = self.sched.submit(req)
+        ok = self.sched.submit(req, grouped=self.batch_runner is not None)
         if not ok:
             with self._lock:
                 self.results.append(Result(req.rid, req.n, -1, req.arrival, req.arrival, req.arrival,
@@ -245,7 +360,9 @@ class Server:
             self._ready.wait()
             return
         self._ready.wait()
-        while True:
+        if self.batch_runner is not None:
+            self._serve_groups(slot, ctx)
+        while self.batch_runner is None:
             req = self.sched.acquire(capacity=self.caps[slot])
             if req is None:
                 break
@@ -265,6 +382,30 @@ class Server:
         close = getattr(ctx, "close", None)
         if close:
             close()
+
+    def _serve_groups(self, slot: int, ctx):
+        while True:
+            group, fp = self.sched.acquire_group(capacity=self.caps[slot], max_group=self.max_group)
+            if not group:
+                return
+            t_admit = self.now()
+            res = [Result(r.rid, r.n, slot, r.arrival, t_admit, t_admit) for r in group]
+            try:
+                outs = self.batch_runner(ctx, group)
+                for x, out in zip(res, outs):
+                    x.lml = out.get("lml", float("nan"))
+                    x.mode, x.mean, x.var = out.get("mode"), out.get("mean"), out.get("var")
+                    x.stats = out.get("stats", {})
+            except Exception as e:      # noqa: BLE001 - recorded for every request of the group
+                for x in res:
+                    x.error = f"{type(e).__name__}: {e}"
+            t_done = self.now()
+            self.sched.release_group(group, fp)
+            with self._lock:
+                for x in res:
+                    x.t_done = t_done
+                    self.results.append(x)
+                self.groups.append(len(group))
 
     def drain(self):
         """Stop taking requests once the queue is empty and wait for the workers."""

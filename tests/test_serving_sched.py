@@ -105,3 +105,75 @@ def test_start_fails_loudly_when_a_slot_cannot_be_made():
     srv = serving.Server(slots=3, budget_bytes=100, slot_capacity=100, make_ctx=make, runner=lambda c, r: {})
     with pytest.raises(RuntimeError, match="slot 1"):
         srv.start()
+
+
+def test_continuous_batching_groups_within_slot_and_budget():
+    """Grouped admission: a free slot takes the head of the queue and every later queued
+    request with the same options while the group's footprint fits the slot and the budget;
+    every request is served exactly once and gets its own result."""
+    lock = threading.Lock()
+    live = {"bytes": 0, "peak": 0}
+    groups = []
+
+    def batch_runner(ctx, reqs):
+        fp = sum(r.footprint for r in reqs)
+        with lock:
+            live["bytes"] += fp
+            live["peak"] = max(live["peak"], live["bytes"])
+            groups.append([r.rid for r in reqs])
+        assert fp <= ctx                          # the slot's capacity
+        assert len({str(r.opts) for r in reqs}) == 1
+        time.sleep(0.01)
+        with lock:
+            live["bytes"] -= fp
+        return [{"lml": float(r.rid)} for r in reqs]
+
+    srv = serving.Server(slots=[100, 60], budget_bytes=140, slot_capacity=None, make_ctx=lambda s, cap: cap,
+                         batch_runner=batch_runner, max_group=5).start()
+    sizes = [30, 20, 10, 50, 40, 5, 25, 60, 15, 10, 35, 20] * 2
+    for i, fp in enumerate(sizes):
+        r = _req(i, fp)
+        r.opts = {"t": 8} if i % 7 else {"t": 16}   # two option sets never share a group
+        assert srv.submit(r)
+    assert not srv.submit(_req(99, 101))
+    res = {r.rid: r for r in srv.drain()}
+    assert sorted(res) == list(range(len(sizes))) + [99]
+    assert all(res[i].error is None and res[i].lml == i for i in range(len(sizes)))
+    served = sorted(x for g in groups for x in g)
+    assert served == list(range(len(sizes)))       # each request exactly once
+    assert max(len(g) for g in groups) > 1 and max(len(g) for g in groups) <= 5
+    assert live["peak"] <= 140 and srv.sched.peak_in_use <= 140
+    assert srv.groups and sum(srv.groups) == len(sizes)
+    for g in groups:                               # each group's head is the oldest request it could take
+        assert g[0] == min(g)
+    assert all(r.t_done >= r.t_admit >= r.t_arrival for r in res.values() if r.slot >= 0)
+
+
+def test_group_failure_fails_every_member_and_drain_ends():
+    def batch_runner(ctx, reqs):
+        if any(r.rid == 3 for r in reqs):
+            raise RuntimeError("group boom")
+        return [{"lml": 1.0} for _ in reqs]
+
+    srv = serving.Server(slots=1, budget_bytes=100, slot_capacity=100, make_ctx=lambda s: None,
+                         batch_runner=batch_runner, max_group=2)
+    import pytest
+    with pytest.raises(ValueError):
+        serving.Server(slots=1, budget_bytes=1, slot_capacity=1, make_ctx=lambda s: None)
+    srv.start()
+    for i in range(6):
+        srv.submit(_req(i, 10))
+    res = srv.drain()
+    bad = [r.rid for r in res if r.error]
+    assert 3 in bad and all("group boom" in r.error for r in res if r.error)
+    assert len(bad) <= 2 and len(res) == 6
+
+
+def test_batch_footprint_covers_members_and_merged_system():
+    a = _req(0, 0)
+    b = _req(1, 0)
+    a.opts = b.opts = {"t": 50, "s": 100}
+    one = serving.batch_footprint_bytes([a])
+    two = serving.batch_footprint_bytes([a, b])
+    assert serving.footprint_bytes(10, 5, n_test=0) < one < two
+    assert serving.batch_footprint_bytes([]) == 0
