@@ -180,6 +180,10 @@ vl_status vl_ctx_set_autotune(vl_ctx* ctx, int enable);
  * written to buf (len bytes, always NUL-terminated when len > 0); returns the bytes the
  * whole report needs, terminator included. */
 size_t vl_tune_report(char* buf, size_t len);
+/* Forgets every choice of the tuner: the next call of each kind tunes again (for example
+ * after the device's clocks or its other load have changed). Not to be called while another
+ * thread is inside a library call. */
+void vl_tune_reset(void);
 
 /* Form of the level-scheduled triangular solves with B and B^T (the two solves of the
  * VADU / LVA preconditioners, Section 3.1.1, and of Sigma_tilde = B^{-1} D B^{-T}).

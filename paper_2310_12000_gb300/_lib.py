@@ -105,6 +105,7 @@ def library():
         "vl_ctx_set_wait_limit": (st, [vp, C.c_longlong]),
         "vl_ctx_set_autotune": (st, [vp, i32]),
         "vl_tune_report": (C.c_size_t, [vp, C.c_size_t]),
+        "vl_tune_reset": (None, []),
         "vl_ctx_wait_probe": (st, [vp]),
         "vl_profile_enable": (st, [vp, i32]),
         "vl_profile_read": (st, [vp, C.c_char_p, i32, vp, vp, i32]),
@@ -611,6 +612,11 @@ class Batch:
         g = np.empty(len(self.sizes) * t)
         self.ctx.check(self.ctx.lib.vl_batch_gammas(self.h, g.ctypes.data, t))
         return g.reshape(len(self.sizes), t)
+
+
+def tune_reset():
+    """Forget the launch tuner's choices (vl_tune_reset)."""
+    library().vl_tune_reset()
 
 
 def tune_report() -> list:

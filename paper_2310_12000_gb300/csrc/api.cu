@@ -658,6 +658,12 @@ size_t vl_tune_report(char* buf, size_t len) {
   return out.size() + 1;
 }
 
+void vl_tune_reset(void) {
+  std::lock_guard<std::mutex> lk(tuner().mu);
+  tuner().best.clear();
+  tuner().times.clear();
+}
+
 vl_status vl_ctx_set_solve_form(vl_ctx* c, int form) {
   if (!c) return VL_ERR_INVALID_ARG;
   if (form < VL_SOLVE_AUTO || form > VL_SOLVE_GRID_ALL) return fail(c, VL_ERR_INVALID_ARG, "unknown solve form");

@@ -844,8 +844,10 @@ struct Engine {
     const int32_t* idx = FWD ? f->nbr : f->colT;
     const T* val = FWD ? Aval : valT;
     const int32_t* rp = FWD ? nullptr : f->rowptrT;
-    VL_CUDA(c, cudaMemsetAsync(c->gbar, 0, 2 * sizeof(unsigned), c->stream));
     auto launch = [&](const void* fn, void** args, int lpv, int bps, int csize = 0) -> vl_status {
+      // the grid barriers start from a zeroed arrival counter and generation word in every
+      // launch (the tuner launches one solve several times)
+      VL_CUDA(c, cudaMemsetAsync(c->gbar, 0, 2 * sizeof(unsigned), c->stream));
       const int tpb = 16 * (32 / lpv);   // row teams per 512-thread block
       // heavy rows of the grid body in chunks: one round of loads of a team
       // (t = 1: lpv lanes x 4 loads; blocks: 16 dependency rows, whatever the row shape)
