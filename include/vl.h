@@ -197,12 +197,17 @@ typedef enum vl_solve_form {
   VL_SOLVE_GRID = 3,    /* cooperative grid, bounded software grid barrier per level; the
                            narrow leading and trailing levels in one block (the leading ones of
                            single-column forward solves with x in shared memory)           */
-  VL_SOLVE_GRID_ALL = 4 /* cooperative grid with every level on the grid barrier          */
+  VL_SOLVE_GRID_ALL = 4, /* cooperative grid with every level on the grid barrier         */
+  VL_SOLVE_TILE = 5      /* cooperative grid of storage-row tiles, one block each, walking
+                            its own rows level by level and waiting only for the progress
+                            of the tiles its rows depend on (t = 1: the tile's x in shared
+                            memory)                                                     */
 } vl_solve_form;
 /* Sets the form for every later solve on this context (VL_ERR_INVALID_ARG for an
  * unknown form). A solve the forced form cannot run (VL_SOLVE_SHARED with too many
  * rows; VL_SOLVE_CLUSTER when no cluster fits the kernel, or float64 blocks wider
- * than 128 columns) fails with VL_ERR_INVALID_ARG. */
+ * than 128 columns; VL_SOLVE_TILE when a tile of a single-column x does not fit shared
+ * memory) fails with VL_ERR_INVALID_ARG. */
 vl_status vl_ctx_set_solve_form(vl_ctx* ctx, int form);
 
 /* Vecchia factor (Section 2.1): for locations `locs` (n x 2, caller order) and the

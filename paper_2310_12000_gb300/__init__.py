@@ -19,7 +19,7 @@ from __future__ import annotations
 
 from ._lib import (COV_EXPONENTIAL, COV_MATERN15, FP32_REFINE, FP64, LIK_BERNOULLI_LOGIT, LIK_GAMMA_LOG,
                    LIK_POISSON_LOG, OP_A, OP_A2, OP_B, OP_BINV, OP_BT, OP_BTINV, OP_PINV, OP_SIGMA,
-                   PREC_LRAC, PREC_LVA, PREC_VADU, SOLVE_AUTO, SOLVE_CLUSTER, SOLVE_GRID, SOLVE_GRID_ALL, SOLVE_SHARED,
+                   PREC_LRAC, PREC_LVA, PREC_VADU, SOLVE_AUTO, SOLVE_CLUSTER, SOLVE_GRID, SOLVE_GRID_ALL, SOLVE_SHARED, SOLVE_TILE,
                    Batch, Context, Factor, Opts, State, Stats, VLError, lib_path, library, tune_report,
                    tune_reset)
 
@@ -28,5 +28,5 @@ __all__ = [
     "COV_EXPONENTIAL", "COV_MATERN15", "LIK_BERNOULLI_LOGIT", "LIK_POISSON_LOG", "LIK_GAMMA_LOG",
     "PREC_VADU", "PREC_LVA", "PREC_LRAC", "FP64", "FP32_REFINE",
     "OP_A", "OP_PINV", "OP_B", "OP_BT", "OP_BINV", "OP_BTINV", "OP_SIGMA", "OP_A2",
-    "SOLVE_AUTO", "SOLVE_SHARED", "SOLVE_CLUSTER", "SOLVE_GRID", "SOLVE_GRID_ALL",
+    "SOLVE_AUTO", "SOLVE_SHARED", "SOLVE_CLUSTER", "SOLVE_GRID", "SOLVE_GRID_ALL", "SOLVE_TILE",
 ]

@@ -13,7 +13,7 @@ LIK_BERNOULLI_LOGIT, LIK_POISSON_LOG, LIK_GAMMA_LOG = 0, 1, 2
 PREC_VADU, PREC_LVA, PREC_LRAC = 0, 1, 2
 FP64, FP32_REFINE = 0, 1
 OP_A, OP_PINV, OP_B, OP_BT, OP_BINV, OP_BTINV, OP_SIGMA, OP_A2 = range(8)
-SOLVE_AUTO, SOLVE_SHARED, SOLVE_CLUSTER, SOLVE_GRID, SOLVE_GRID_ALL = range(5)
+SOLVE_AUTO, SOLVE_SHARED, SOLVE_CLUSTER, SOLVE_GRID, SOLVE_GRID_ALL, SOLVE_TILE = range(6)
 
 _STATUS = {0: "VL_OK", 1: "VL_ERR_INVALID_ARG", 2: "VL_ERR_OOM", 3: "VL_ERR_NOT_SPD",
            4: "VL_ERR_NOT_CONVERGED", 5: "VL_ERR_TIMEOUT", 6: "VL_ERR_CUDA", 7: "VL_ERR_STATE"}
@@ -272,7 +272,7 @@ class Context:
 
     def set_solve_form(self, form: int):
         """Force the triangular-solve form (SOLVE_AUTO, SOLVE_SHARED, SOLVE_CLUSTER,
-        SOLVE_GRID, SOLVE_GRID_ALL) of every later solve on this context; SOLVE_AUTO restores
+        SOLVE_GRID, SOLVE_GRID_ALL, SOLVE_TILE) of every later solve on this context; SOLVE_AUTO restores
         the per-solve choice."""
         self.check(self.lib.vl_ctx_set_solve_form(self.h, int(form)))
 

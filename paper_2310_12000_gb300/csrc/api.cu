@@ -666,7 +666,7 @@ void vl_tune_reset(void) {
 
 vl_status vl_ctx_set_solve_form(vl_ctx* c, int form) {
   if (!c) return VL_ERR_INVALID_ARG;
-  if (form < VL_SOLVE_AUTO || form > VL_SOLVE_GRID_ALL) return fail(c, VL_ERR_INVALID_ARG, "unknown solve form");
+  if (form < VL_SOLVE_AUTO || form > VL_SOLVE_TILE) return fail(c, VL_ERR_INVALID_ARG, "unknown solve form");
   c->solve_form = form;
   return VL_OK;
 }

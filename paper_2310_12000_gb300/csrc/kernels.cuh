@@ -394,18 +394,25 @@ struct RowPre {
 };
 
 template <typename T, bool FWD, int LPV, int NV>
-__device__ __forceinline__ void row_pre(RowPre<T, LPV, NV>& r, int p, int m, const LevelPlan& L,
-                                        const int32_t* __restrict__ idx, const T* __restrict__ val,
-                                        const int32_t* __restrict__ rowptr, const T* __restrict__ rhs,
-                                        const T* __restrict__ q, int ld) {
+__device__ __forceinline__ void row_pre_s(RowPre<T, LPV, NV>& r, int s, int m, const int32_t* __restrict__ idx,
+                                          const T* __restrict__ val, const int32_t* __restrict__ rowptr,
+                                          const T* __restrict__ rhs, const T* __restrict__ q, int ld) {
   const int sl = (threadIdx.x & 31) % LPV;
-  r.s = L.task[p];
+  r.s = s;
   r.beg = FWD ? r.s * m : rowptr[r.s];
   r.end = FWD ? r.s * m + m : rowptr[r.s + 1];
   const int e = r.beg + sl;
   r.jl = e < r.end ? idx[e] : -1;
   r.al = r.jl >= 0 ? val[e] : T(0);
   team_init<T, LPV, NV>(r.acc, r.s, ld, q ? q[r.s] : T(1), rhs, T(0), nullptr);
+}
+
+template <typename T, bool FWD, int LPV, int NV>
+__device__ __forceinline__ void row_pre(RowPre<T, LPV, NV>& r, int p, int m, const LevelPlan& L,
+                                        const int32_t* __restrict__ idx, const T* __restrict__ val,
+                                        const int32_t* __restrict__ rowptr, const T* __restrict__ rhs,
+                                        const T* __restrict__ q, int ld) {
+  row_pre_s<T, FWD, LPV, NV>(r, L.task[p], m, idx, val, rowptr, rhs, q, ld);
 }
 
 // Finishes a prefetched row: gathers its dependencies (first chunk already in
@@ -1034,6 +1041,135 @@ __global__ void __launch_bounds__(512) sptrsv_t1_kernel(LevelPlan L, int m, cons
       [&]() { row_run1<T, LPV>(r, idx, val, x); },
       [&](int p) { heavy_row1<T, FWD, LPV>(p, m, L, idx, val, rowptr, rhs, q, x, part); },
       [&](const HeavyChunk& hc) { chunk_run1<T, LPV>(hc, L, idx, val, rhs, q, x); });
+}
+
+// ----------------------------------------------------------------------------- tiled solves
+// Triangular solve by storage-row tiles with point-to-point progress instead of a grid barrier
+// per level. Tile b (one block) owns the storage rows [b R, min(n, (b + 1) R)): the rows are in
+// Morton order, so a tile is a compact patch of the domain and most dependencies of its rows lie
+// inside it. The block walks its own rows level by level (its "segments": the runs of equal
+// level in its rows sorted by (level, row)) with a block barrier between segments, and after
+// each segment publishes prog[b] = the level of its next segment (every row of the tile below
+// that level is solved; release at gpu scope after the block barrier). Before a segment it waits
+// for the tiles its rows depend on: the plan lists, per segment, the neighbouring tiles and the
+// progress each must have reached (one more than the highest level among the segment's
+// dependencies in that tile, only where it rises above what the tile already waited for).
+// Waits are only on strictly lower levels and every block publishes before it waits, so the
+// block at the lowest level always proceeds: with every block resident (cooperative launch) the
+// walk cannot deadlock. prog is zero at launch.
+struct TileArgs {
+  const int32_t* ttask;     // n: each tile's rows sorted by (level, row), tiles in order
+  const int32_t* sp;        // G + 1: segments of tile b are [sp[b], sp[b + 1])
+  const int32_t* seg_lev;   // nseg: level of each segment
+  const int32_t* seg_beg;   // nseg + 1: ttask range of each segment (seg_beg[nseg] = n)
+  const int32_t* wptr;      // nseg + 1: waits of each segment
+  const int32_t* wtile;     // tile waited for
+  const int32_t* wneed;     // progress it must have reached
+  int* prog;                // G, zero at launch
+  DevStatus* st;
+  int n, R;
+};
+
+__device__ __forceinline__ void tile_wait(const int* p, int need, DevStatus* st, int row) {
+  int spins = 0;
+  while (ld_acquire(p) < need) {
+    if (++spins > 64) {
+      bounded_wait([&] { return ld_acquire(p) >= need; }, st, row);
+      return;
+    }
+    __nanosleep(20);
+  }
+}
+
+// Waits of segment k (threads of the block in parallel), then a block barrier.
+__device__ __forceinline__ void tile_segment_waits(const TileArgs& A, int k) {
+  if (!ld_volatile(&A.st->abort))
+    for (int w = A.wptr[k] + threadIdx.x; w < A.wptr[k + 1]; w += blockDim.x)
+      tile_wait(&A.prog[A.wtile[w]], A.wneed[w], A.st, -2);
+  __syncthreads();
+}
+
+// After segment k: block barrier, then publish the tile's progress.
+__device__ __forceinline__ void tile_publish(const TileArgs& A, int k, int k1) {
+  __syncthreads();
+  if (threadIdx.x == 0) st_release(&A.prog[blockIdx.x], k + 1 < k1 ? A.seg_lev[k + 1] : 0x7fffffff);
+}
+
+// Scalar rows (t = 1): the tile's x lives in shared memory (R values); a dependency in another
+// tile is read from x through L2 (the wait made it visible); every solved row is also written to
+// x. Team lanes split a row's dependencies (K loads in flight each) as in the grid walk.
+template <typename T, bool FWD, int LPV>
+__global__ void __launch_bounds__(1024) sptrsv_tile1_kernel(TileArgs A, int m, const int32_t* __restrict__ idx,
+                                                            const T* __restrict__ val,
+                                                            const int32_t* __restrict__ rowptr,
+                                                            const T* __restrict__ rhs, const T* __restrict__ q, T* x) {
+  extern __shared__ unsigned char vl_smem[];
+  T* xs = reinterpret_cast<T*>(vl_smem);
+  constexpr int RPW = 32 / LPV, K = 4;
+  const unsigned mask = team_mask<LPV>();
+  const int tpb = (blockDim.x >> 5) * RPW;
+  const int tib = (threadIdx.x >> 5) * RPW + (threadIdx.x & 31) / LPV;
+  const int sl = (threadIdx.x & 31) % LPV;
+  const int b = blockIdx.x;
+  const int r0 = b * A.R, r1 = min(A.n, r0 + A.R);
+  const int k0 = A.sp[b], k1 = A.sp[b + 1];
+  for (int k = k0; k < k1; ++k) {
+    tile_segment_waits(A, k);
+    for (int p = A.seg_beg[k] + tib; p < A.seg_beg[k + 1]; p += tpb) {
+      const int s = A.ttask[p];
+      const int beg = FWD ? s * m : rowptr[s];
+      const int end = FWD ? s * m + m : rowptr[s + 1];
+      T acc = T(0);
+      for (int e0 = beg + sl; e0 < end; e0 += LPV * K) {
+        int j[K];
+        T a[K], xv[K];
+#pragma unroll
+        for (int u = 0; u < K; ++u) {
+          const int e = e0 + u * LPV;
+          j[u] = e < end ? idx[e] : -1;
+          a[u] = j[u] >= 0 ? val[e] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < K; ++u)
+          xv[u] = j[u] < 0 ? T(0) : ((j[u] >= r0 && j[u] < r1) ? xs[j[u] - r0] : __ldcg(&x[j[u]]));
+#pragma unroll
+        for (int u = 0; u < K; ++u) acc += a[u] * xv[u];
+      }
+#pragma unroll
+      for (int off = LPV / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(mask, acc, off, LPV);
+      if (sl == 0) {
+        const T v = (q ? q[s] : T(1)) * rhs[s] + acc;
+        xs[s - r0] = v;
+        x[s] = v;
+      }
+    }
+    tile_publish(A, k, k1);
+  }
+}
+
+// Block rows (t > 1): x stays in global memory (a tile's rows are too wide for shared memory);
+// rows go to teams as in the grid walk (row_pre / row_run), dependencies inside the tile are
+// visible after the block barrier, those in other tiles after the segment's waits.
+template <typename T, bool FWD, int LPV, int NV, int UNR>
+__global__ void __launch_bounds__(512) sptrsv_tile_kernel(TileArgs A, int m,
+                                                          const int32_t* __restrict__ idx, const T* __restrict__ val,
+                                                          const int32_t* __restrict__ rowptr,
+                                                          const T* __restrict__ rhs, const T* __restrict__ q, T* x,
+                                                          int ld) {
+  constexpr int RPW = 32 / LPV;
+  const int tpb = (blockDim.x >> 5) * RPW;
+  const int tib = (threadIdx.x >> 5) * RPW + (threadIdx.x & 31) / LPV;
+  const int b = blockIdx.x;
+  const int k0 = A.sp[b], k1 = A.sp[b + 1];
+  for (int k = k0; k < k1; ++k) {
+    tile_segment_waits(A, k);
+    for (int p = A.seg_beg[k] + tib; p < A.seg_beg[k + 1]; p += tpb) {
+      RowPre<T, LPV, NV> r;
+      row_pre_s<T, FWD, LPV, NV>(r, A.ttask[p], m, idx, val, rowptr, rhs, q, ld);
+      row_run<T, LPV, NV, UNR>(r, idx, val, x, ld);
+    }
+    tile_publish(A, k, k1);
+  }
 }
 
 // ----------------------------------------------------------------------------- column reductions

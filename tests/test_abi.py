@@ -77,7 +77,7 @@ def test_binding_structs_and_constants_match_the_c_header(tmp_path):
     consts = ["COV_EXPONENTIAL", "COV_MATERN15", "LIK_BERNOULLI_LOGIT", "LIK_POISSON_LOG", "LIK_GAMMA_LOG", "PREC_VADU",
               "PREC_LVA", "PREC_LRAC", "FP64", "FP32_REFINE", "OP_A", "OP_PINV", "OP_B", "OP_BT", "OP_BINV",
               "OP_BTINV", "OP_SIGMA", "OP_A2", "SOLVE_AUTO", "SOLVE_SHARED", "SOLVE_CLUSTER", "SOLVE_GRID",
-              "SOLVE_GRID_ALL"]
+              "SOLVE_GRID_ALL", "SOLVE_TILE"]
     for name in consts:
         lines.append(f'  printf("const {name} %d\\n", (int)VL_{name});')
     lines += ["  return 0;", "}"]

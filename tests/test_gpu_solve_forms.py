@@ -32,7 +32,7 @@ from oracle import laplace as la, vecchia
 
 pytestmark = pytest.mark.gpu
 
-FORMS = ["shared", "cluster", "grid", "grid_all"]
+FORMS = ["shared", "cluster", "grid", "grid_all", "tile"]
 FP64_TIGHT = dict(cg_tol=1e-12, newton_tol=1e-10, cg_max_iter=2000)
 
 
@@ -52,7 +52,7 @@ def ctx(vl):
 
 def _form(vl, name):
     return {"auto": vl.SOLVE_AUTO, "shared": vl.SOLVE_SHARED, "cluster": vl.SOLVE_CLUSTER,
-            "grid": vl.SOLVE_GRID, "grid_all": vl.SOLVE_GRID_ALL}[name]
+            "grid": vl.SOLVE_GRID, "grid_all": vl.SOLVE_GRID_ALL, "tile": vl.SOLVE_TILE}[name]
 
 
 _CACHE = {}
@@ -179,7 +179,7 @@ def test_forced_form_that_cannot_run_is_refused(ctx, vl, op_case):
     assert np.all(np.isfinite(Y))
 
 
-@pytest.mark.parametrize("form", ["auto", "grid", "grid_all", "cluster"])
+@pytest.mark.parametrize("form", ["auto", "grid", "grid_all", "cluster", "tile"])
 def test_large_solves_by_form(ctx, vl, form):
     """n = 300,000 of the grid-with-gaps workload (m = 20, hundreds of levels)."""
     P = wl.make_problem("c3_grid1m", n=300_000)
