@@ -466,7 +466,8 @@ def run_ours(args):
         barrier()
     elapsed_s, value = replica_throughput(e0.elapsed_time(e1) / 1000.0, args.steps)
     launches = ctx.profile_read("all")[1]
-    classes = ["sptrsv_fwd", "sptrsv_bwd", "spmv_B", "spmv_Bt", "coldot", "pcg_update", "factor", "woodbury"]
+    classes = ["sptrsv_fwd", "sptrsv_bwd", "spmv_B", "spmv_Bt", "coldot", "pcg_update", "factor", "woodbury",
+               "slq_quad"]
     prof = {}
     for cls in classes:
         for t in (1, 50):

@@ -218,7 +218,7 @@ static __global__ void head_nbr_kernel(int rows, int m, const int32_t* __restric
 // Dependencies of the forward head's rows (levels [0, l_head)) as task positions; unusable if a
 // dependency lay outside the head (it cannot: a row depends only on rows of earlier levels).
 // Plan of the tiled solve in one direction over G tiles (tile_plan.h), built on the host from
-// the task list, the level pointers and the dependency lists, and kept on the device.
+// the task list and the dependency lists, and kept on the device.
 inline vl_status tile_plan(Ctx* c, Factor* f, bool fwd, int G, const Factor::TilePlan** out) {
   const std::pair<int, int> key{fwd ? 1 : 0, G};
   auto it = f->tile_plans.find(key);
@@ -242,31 +242,23 @@ inline vl_status tile_plan(Ctx* c, Factor* f, bool fwd, int G, const Factor::Til
       VL_CUDA(c, cudaMemcpyAsync(col.data(), f->colT, sizeof(int32_t) * f->nnz, cudaMemcpyDeviceToHost, c->stream));
   }
   VL_CUDA(c, cudaStreamSynchronize(c->stream));
-  const std::vector<int32_t>& lp = fwd ? f->h_lptr_fwd : f->h_lptr_bwd;
-  const TilePlanHost H = build_tile_plan(n, G, task.data(), lp.data(), (int)lp.size() - 1, m,
-                                         fwd ? nbr.data() : nullptr, fwd ? nullptr : rp.data(),
-                                         fwd ? nullptr : col.data());
+  const TilePlanHost H = build_tile_plan(n, G, task.data(), m, fwd ? nbr.data() : nullptr,
+                                         fwd ? nullptr : rp.data(), fwd ? nullptr : col.data());
   Factor::TilePlan plan;
   plan.G = G;
   plan.R = H.R;
-  plan.nseg = (int)H.seg_lev.size();
-  plan.nwait = (int)H.wtile.size();
-  auto up = [&](const std::vector<int32_t>& h, int32_t** d) -> vl_status {
-    *d = f->mem.get<int32_t>(std::max<size_t>(h.size(), 1));
+  auto up = [&](const void* h, size_t bytes, void** d) -> vl_status {
+    *d = f->mem.get<uint8_t>(std::max<size_t>(bytes, 16));
     if (!*d) return fail(c, VL_ERR_OOM, "workspace exhausted (tile plan)");
-    if (!h.empty())
-      VL_CUDA(c, cudaMemcpyAsync(*d, h.data(), sizeof(int32_t) * h.size(), cudaMemcpyHostToDevice, c->stream));
+    if (bytes) VL_CUDA(c, cudaMemcpyAsync(*d, h, bytes, cudaMemcpyHostToDevice, c->stream));
     return VL_OK;
   };
-  VL_TRY(up(H.ttask, &plan.ttask));
-  VL_TRY(up(H.sp, &plan.sp));
-  VL_TRY(up(H.seg_lev, &plan.seg_lev));
-  VL_TRY(up(H.seg_beg, &plan.seg_beg));
-  VL_TRY(up(H.wptr, &plan.wptr));
-  VL_TRY(up(H.wtile, &plan.wtile));
-  VL_TRY(up(H.wneed, &plan.wneed));
-  plan.prog = f->mem.get<int>(G);
-  if (!plan.prog) return fail(c, VL_ERR_OOM, "workspace exhausted (tile plan)");
+  VL_TRY(up(H.ttask.data(), sizeof(int32_t) * H.ttask.size(), (void**)&plan.ttask));
+  VL_TRY(up(H.toff.data(), sizeof(int32_t) * H.toff.size(), (void**)&plan.toff));
+  VL_TRY(up(H.exported.data(), H.exported.size(), (void**)&plan.exported));
+  plan.flag = f->mem.get<int>(std::max(n, 1));
+  if (!plan.flag) return fail(c, VL_ERR_OOM, "workspace exhausted (tile plan)");
+  VL_CUDA(c, cudaMemsetAsync(plan.flag, 0, sizeof(int) * std::max(n, 1), c->stream));
   VL_CUDA(c, cudaStreamSynchronize(c->stream));
   *out = &(f->tile_plans[key] = plan);
   return VL_OK;
@@ -970,13 +962,10 @@ struct Engine {
       return VL_OK;
     };
     if (form == VL_SOLVE_TILE) {
-      // storage-row tiles with point-to-point progress waits (see TileArgs)
-      auto tile_launch = [&](const void* fn, int block, int G, size_t smem, const Factor::TilePlan* tp,
-                             void** args) -> vl_status {
-        VL_CUDA(c, cudaMemsetAsync(tp->prog, 0, sizeof(int) * G, c->stream));
-        ++c->launches;
-        ProfScope ps(c, cls, t);
-        return cuda_ok(c, cudaLaunchCooperativeKernel(fn, G, block, args, smem, c->stream));
+      // storage-row tiles, each row waiting only for its own dependencies (see TileArgs)
+      if (x == rhs) return fail(c, VL_ERR_STATE, "tiled solve in place");
+      auto args_of = [&](const Factor::TilePlan* tp) {
+        return TileArgs{tp->ttask, tp->toff, tp->exported, tp->flag, c->dstatus, n, tp->R, tp->epoch};
       };
       if (t == 1) {
         constexpr int LPVT = FWD ? 8 : 16;
@@ -986,30 +975,46 @@ struct Engine {
           const int G = bps * c->num_sms;
           const size_t smem = sizeof(T) * (size_t)((n + G - 1) / G);
           if (smem > kSmemSolveBytes || resident_blocks(c, fn, 1024, smem) < G) continue;
-          const Factor::TilePlan* tp = nullptr;
-          VL_TRY(tile_plan(c, f, FWD, G, &tp));
-          TileArgs A{tp->ttask, tp->sp, tp->seg_lev, tp->seg_beg, tp->wptr, tp->wtile, tp->wneed, tp->prog,
-                     c->dstatus, n, tp->R};
+          Factor::TilePlan* tp = nullptr;
+          VL_TRY(tile_plan(c, f, FWD, G, (const Factor::TilePlan**)&tp));
+          TileArgs A = args_of(tp);
           void* args[] = {&A, &mm, &idx, &val, &rp, &rhs, &q, &x};
-          return tile_launch(fn, 1024, G, smem, tp, args);
+          // every value starts "unsolved" (all bits set): it is its own ready flag
+          VL_CUDA(c, cudaMemsetAsync(x, 0xff, sizeof(T) * (size_t)n, c->stream));
+          ++c->launches;
+          ProfScope ps(c, cls, t);
+          return cuda_ok(c, cudaLaunchCooperativeKernel(fn, G, 1024, args, smem, c->stream));
         }
         return fail(c, VL_ERR_INVALID_ARG, "solve form VL_SOLVE_TILE: a tile of x does not fit shared memory");
       }
       if (ld % 8 != 0) return fail(c, VL_ERR_STATE, "block solve with a row width that is not a multiple of 8");
-      // candidates (all give the same numbers: a row's sum does not depend on its tile):
+      // candidates (all give the same numbers: a row's sum does not depend on its tile or team):
       // tiles of 512 threads, 2 or 1 per SM, x the shape's UNR or twice it
       return tuned(TuneKey{c->device, FWD ? 2 : 3, (int)sizeof(T), ld, log2_bucket(n)}, 4, [&](int cand) {
         return with_shape<T>(ld, [&](auto Lc, auto N, auto U) {
           constexpr int LPV = decltype(Lc)::value, NV = decltype(N)::value, UNR = decltype(U)::value;
           const void* fn = (cand & 2) ? (const void*)sptrsv_tile_kernel<T, FWD, LPV, NV, 2 * UNR>
                                       : (const void*)sptrsv_tile_kernel<T, FWD, LPV, NV, UNR>;
-          const int G = std::min(resident_blocks(c, fn, 512, 0), ((cand & 1) ? 1 : 2) * c->num_sms);
-          const Factor::TilePlan* tp = nullptr;
-          VL_TRY(tile_plan(c, f, FWD, G, &tp));
-          TileArgs A{tp->ttask, tp->sp, tp->seg_lev, tp->seg_beg, tp->wptr, tp->wtile, tp->wneed, tp->prog,
-                     c->dstatus, n, tp->R};
+          const int per_sm = (cand & 1) ? 1 : 2;
+          const int G = per_sm * c->num_sms;
+          const size_t smem = sizeof(int) * (size_t)((n + G - 1) / G);
+          if (smem > kSmemSolveBytes)
+            return fail(c, VL_ERR_INVALID_ARG, "solve form VL_SOLVE_TILE: a tile's flags do not fit shared memory");
+          VL_TRY(smem_limit_once(c, fn, kSmemSolveBytes));
+          if (resident_blocks(c, fn, 512, smem) < G)
+            return fail(c, VL_ERR_INVALID_ARG, "solve form VL_SOLVE_TILE: the tiles are not all resident");
+          Factor::TilePlan* tp = nullptr;
+          VL_TRY(tile_plan(c, f, FWD, G, (const Factor::TilePlan**)&tp));
+          if (tp->epoch == 0x7fffffff) {   // flags of earlier launches hold older epochs
+            VL_CUDA(c, cudaMemsetAsync(tp->flag, 0, sizeof(int) * (size_t)std::max(n, 1), c->stream));
+            tp->epoch = 0;
+          }
+          ++tp->epoch;
+          TileArgs A = args_of(tp);
           void* args[] = {&A, &mm, &idx, &val, &rp, &rhs, &q, &x, &l};
-          return tile_launch(fn, 512, G, 0, tp, args);
+          ++c->launches;
+          ProfScope ps(c, cls, t);
+          return cuda_ok(c, cudaLaunchCooperativeKernel(fn, G, 512, args, smem, c->stream));
         });
       });
     }

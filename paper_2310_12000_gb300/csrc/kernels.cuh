@@ -1044,60 +1044,63 @@ __global__ void __launch_bounds__(512) sptrsv_t1_kernel(LevelPlan L, int m, cons
 }
 
 // ----------------------------------------------------------------------------- tiled solves
-// Triangular solve by storage-row tiles with point-to-point progress instead of a grid barrier
-// per level. Tile b (one block) owns the storage rows [b R, min(n, (b + 1) R)): the rows are in
-// Morton order, so a tile is a compact patch of the domain and most dependencies of its rows lie
-// inside it. The block walks its own rows level by level (its "segments": the runs of equal
-// level in its rows sorted by (level, row)) with a block barrier between segments, and after
-// each segment publishes prog[b] = the level of its next segment (every row of the tile below
-// that level is solved; release at gpu scope after the block barrier). Before a segment it waits
-// for the tiles its rows depend on: the plan lists, per segment, the neighbouring tiles and the
-// progress each must have reached (one more than the highest level among the segment's
-// dependencies in that tile, only where it rises above what the tile already waited for).
-// Waits are only on strictly lower levels and every block publishes before it waits, so the
-// block at the lowest level always proceeds: with every block resident (cooperative launch) the
-// walk cannot deadlock. prog is zero at launch.
+// Triangular solve by storage-row tiles with no barrier at all (plan: tile_plan.h). Tile b (one
+// block) owns the storage rows [b R, min(n, (b + 1) R)); the block's teams take the tile's rows,
+// listed by level, round robin, and a row waits only for its own dependencies: a dependency in
+// the tile through shared memory, one in another tile through global memory. In a random
+// ordering the dependency chain is hundreds of rows long but most of its links stay inside a
+// tile (the rows are in Morton order, a tile is a compact patch), so most links cost a
+// shared-memory hand-off instead of a grid-wide barrier. Every wait is bounded (a timeout
+// records VL_ERR_TIMEOUT and every other wait then returns at once).
 struct TileArgs {
-  const int32_t* ttask;     // n: each tile's rows sorted by (level, row), tiles in order
-  const int32_t* sp;        // G + 1: segments of tile b are [sp[b], sp[b + 1])
-  const int32_t* seg_lev;   // nseg: level of each segment
-  const int32_t* seg_beg;   // nseg + 1: ttask range of each segment (seg_beg[nseg] = n)
-  const int32_t* wptr;      // nseg + 1: waits of each segment
-  const int32_t* wtile;     // tile waited for
-  const int32_t* wneed;     // progress it must have reached
-  int* prog;                // G, zero at launch
+  const int32_t* ttask;      // n: each tile's rows by level, tiles in order
+  const int32_t* toff;       // G + 1
+  const uint8_t* exported;   // n: a row of another tile depends on this row (t > 1 flags)
+  int* flag;                 // n: epoch of the last solve that finished the row (t > 1)
   DevStatus* st;
   int n, R;
+  int epoch;
 };
 
-__device__ __forceinline__ void tile_wait(const int* p, int need, DevStatus* st, int row) {
-  int spins = 0;
-  while (ld_acquire(p) < need) {
-    if (++spins > 64) {
-      bounded_wait([&] { return ld_acquire(p) >= need; }, st, row);
-      return;
+// float / double "not yet solved" marker: all bits set (a NaN no solve produces: results equal
+// to it are replaced by the canonical quiet NaN)
+__device__ __forceinline__ bool is_unsolved(float v) { return __float_as_uint(v) == 0xffffffffu; }
+__device__ __forceinline__ bool is_unsolved(double v) { return __double_as_longlong(v) == -1LL; }
+__device__ __forceinline__ float unsolved_value(float) { return __uint_as_float(0xffffffffu); }
+__device__ __forceinline__ double unsolved_value(double) { return __longlong_as_double(-1LL); }
+__device__ __forceinline__ float solved_value(float v) { return is_unsolved(v) ? __uint_as_float(0x7fc00000u) : v; }
+__device__ __forceinline__ double solved_value(double v) {
+  return is_unsolved(v) ? __longlong_as_double(0x7ff8000000000000LL) : v;
+}
+
+// Value of a dependency once it is solved (bounded: after a timeout or an abort the value read
+// last is returned and the solve's result is void).
+template <typename T>
+__device__ __forceinline__ T tile_wait_value(const T* p, DevStatus* st, int row) {
+  T v = *(volatile const T*)p;
+  if (!is_unsolved(v)) return v;
+  long long t0 = 0, limit = 0;
+  for (int it = 1;; ++it) {
+    __nanosleep(20);   // leave issue slots to the warps that produce the value
+    v = *(volatile const T*)p;
+    if (!is_unsolved(v)) return v;
+    if ((it & 63) == 0) {
+      if (ld_volatile(&st->abort)) return v;
+      if (t0 == 0) {
+        t0 = clock64();
+        const long long set = *(volatile const long long*)&st->limit;
+        limit = set > 0 ? set : kSpinLimitCycles;
+      } else if (clock64() - t0 > limit) {
+        raise_error(st, VL_ERR_TIMEOUT, row);
+        return v;
+      }
     }
-    __nanosleep(20);
   }
 }
 
-// Waits of segment k (threads of the block in parallel), then a block barrier.
-__device__ __forceinline__ void tile_segment_waits(const TileArgs& A, int k) {
-  if (!ld_volatile(&A.st->abort))
-    for (int w = A.wptr[k] + threadIdx.x; w < A.wptr[k + 1]; w += blockDim.x)
-      tile_wait(&A.prog[A.wtile[w]], A.wneed[w], A.st, -2);
-  __syncthreads();
-}
-
-// After segment k: block barrier, then publish the tile's progress.
-__device__ __forceinline__ void tile_publish(const TileArgs& A, int k, int k1) {
-  __syncthreads();
-  if (threadIdx.x == 0) st_release(&A.prog[blockIdx.x], k + 1 < k1 ? A.seg_lev[k + 1] : 0x7fffffff);
-}
-
-// Scalar rows (t = 1): the tile's x lives in shared memory (R values); a dependency in another
-// tile is read from x through L2 (the wait made it visible); every solved row is also written to
-// x. Team lanes split a row's dependencies (K loads in flight each) as in the grid walk.
+// Scalar rows (t = 1): the tile's x in shared memory, every row also stored to x for the other
+// tiles; x starts all "unsolved" (the host sets it before the launch), so a value is its own
+// ready flag and no fence is needed. Team lanes split a row's dependencies (K loads each).
 template <typename T, bool FWD, int LPV>
 __global__ void __launch_bounds__(1024) sptrsv_tile1_kernel(TileArgs A, int m, const int32_t* __restrict__ idx,
                                                             const T* __restrict__ val,
@@ -1112,63 +1115,95 @@ __global__ void __launch_bounds__(1024) sptrsv_tile1_kernel(TileArgs A, int m, c
   const int sl = (threadIdx.x & 31) % LPV;
   const int b = blockIdx.x;
   const int r0 = b * A.R, r1 = min(A.n, r0 + A.R);
-  const int k0 = A.sp[b], k1 = A.sp[b + 1];
-  for (int k = k0; k < k1; ++k) {
-    tile_segment_waits(A, k);
-    for (int p = A.seg_beg[k] + tib; p < A.seg_beg[k + 1]; p += tpb) {
-      const int s = A.ttask[p];
-      const int beg = FWD ? s * m : rowptr[s];
-      const int end = FWD ? s * m + m : rowptr[s + 1];
-      T acc = T(0);
-      for (int e0 = beg + sl; e0 < end; e0 += LPV * K) {
-        int j[K];
-        T a[K], xv[K];
+  for (int i = threadIdx.x; i < r1 - r0; i += blockDim.x) xs[i] = unsolved_value(T(0));
+  __syncthreads();
+  for (int p = A.toff[b] + tib; p < A.toff[b + 1]; p += tpb) {
+    const int s = A.ttask[p];
+    const int beg = FWD ? s * m : rowptr[s];
+    const int end = FWD ? s * m + m : rowptr[s + 1];
+    const T bs = (q ? q[s] : T(1)) * rhs[s];
+    T acc = T(0);
+    for (int e0 = beg + sl; e0 < end; e0 += LPV * K) {
+      int j[K];
+      T a[K], xv[K];
 #pragma unroll
-        for (int u = 0; u < K; ++u) {
-          const int e = e0 + u * LPV;
-          j[u] = e < end ? idx[e] : -1;
-          a[u] = j[u] >= 0 ? val[e] : T(0);
-        }
-#pragma unroll
-        for (int u = 0; u < K; ++u)
-          xv[u] = j[u] < 0 ? T(0) : ((j[u] >= r0 && j[u] < r1) ? xs[j[u] - r0] : __ldcg(&x[j[u]]));
-#pragma unroll
-        for (int u = 0; u < K; ++u) acc += a[u] * xv[u];
+      for (int u = 0; u < K; ++u) {
+        const int e = e0 + u * LPV;
+        j[u] = e < end ? idx[e] : -1;
+        a[u] = j[u] >= 0 ? val[e] : T(0);
       }
 #pragma unroll
-      for (int off = LPV / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(mask, acc, off, LPV);
-      if (sl == 0) {
-        const T v = (q ? q[s] : T(1)) * rhs[s] + acc;
-        xs[s - r0] = v;
-        x[s] = v;
-      }
+      for (int u = 0; u < K; ++u)
+        xv[u] = j[u] < 0 ? T(0)
+                         : tile_wait_value((j[u] >= r0 && j[u] < r1) ? xs + (j[u] - r0) : x + j[u], A.st, s);
+#pragma unroll
+      for (int u = 0; u < K; ++u) acc += a[u] * xv[u];
     }
-    tile_publish(A, k, k1);
+#pragma unroll
+    for (int off = LPV / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(mask, acc, off, LPV);
+    if (sl == 0) {
+      const T v = solved_value(bs + acc);
+      *(volatile T*)(xs + (s - r0)) = v;
+      *(volatile T*)(x + s) = v;
+    }
   }
 }
 
-// Block rows (t > 1): x stays in global memory (a tile's rows are too wide for shared memory);
-// rows go to teams as in the grid walk (row_pre / row_run), dependencies inside the tile are
-// visible after the block barrier, those in other tiles after the segment's waits.
+// Block rows (t > 1): x in global memory (a tile's rows are too wide for shared memory), ready
+// flags per row: in shared memory for the tile, and in global memory (the launch's epoch) for
+// the rows that another tile depends on, written after a gpu-scope fence of the team's stores.
+// Each lane waits for the dependency it holds, the team meets (__syncwarp), then every lane
+// gathers its words of the chunk's rows as in the grid walk.
 template <typename T, bool FWD, int LPV, int NV, int UNR>
 __global__ void __launch_bounds__(512) sptrsv_tile_kernel(TileArgs A, int m,
                                                           const int32_t* __restrict__ idx, const T* __restrict__ val,
                                                           const int32_t* __restrict__ rowptr,
                                                           const T* __restrict__ rhs, const T* __restrict__ q, T* x,
                                                           int ld) {
+  extern __shared__ unsigned char vl_smem[];
+  int* rf = reinterpret_cast<int*>(vl_smem);
   constexpr int RPW = 32 / LPV;
+  const unsigned mask = team_mask<LPV>();
   const int tpb = (blockDim.x >> 5) * RPW;
   const int tib = (threadIdx.x >> 5) * RPW + (threadIdx.x & 31) / LPV;
+  const int sl = (threadIdx.x & 31) % LPV;
   const int b = blockIdx.x;
-  const int k0 = A.sp[b], k1 = A.sp[b + 1];
-  for (int k = k0; k < k1; ++k) {
-    tile_segment_waits(A, k);
-    for (int p = A.seg_beg[k] + tib; p < A.seg_beg[k + 1]; p += tpb) {
-      RowPre<T, LPV, NV> r;
-      row_pre_s<T, FWD, LPV, NV>(r, A.ttask[p], m, idx, val, rowptr, rhs, q, ld);
-      row_run<T, LPV, NV, UNR>(r, idx, val, x, ld);
+  const int r0 = b * A.R, r1 = min(A.n, r0 + A.R);
+  for (int i = threadIdx.x; i < r1 - r0; i += blockDim.x) rf[i] = 0;
+  __syncthreads();
+  for (int p = A.toff[b] + tib; p < A.toff[b + 1]; p += tpb) {
+    const int s = A.ttask[p];
+    RowPre<T, LPV, NV> r;
+    row_pre_s<T, FWD, LPV, NV>(r, s, m, idx, val, rowptr, rhs, q, ld);
+    for (int e0 = r.beg; e0 < r.end; e0 += LPV) {
+      const int cnt = min(LPV, r.end - e0);
+      int jl = r.jl;
+      T al = r.al;
+      if (e0 != r.beg) {
+        jl = sl < cnt ? idx[e0 + sl] : -1;
+        al = jl >= 0 ? val[e0 + sl] : T(0);
+      }
+      if (jl >= 0) {
+        if (jl >= r0 && jl < r1) {
+          const int* f = rf + (jl - r0);
+          bounded_wait([&] { return *(volatile const int*)f != 0; }, A.st, s);
+        } else {
+          const int* f = A.flag + jl;
+          bounded_wait([&] { return ld_acquire(f) == A.epoch; }, A.st, s);
+        }
+      }
+      __syncwarp(mask);
+      chunk_gather<T, LPV, NV, UNR>(r.acc, jl, al, cnt, x, ld);
     }
-    tile_publish(A, k, k1);
+    team_store<T, LPV, NV>(x, r.s, ld, T(1), r.acc);
+    const bool ex = A.exported[s] != 0;
+    if (ex) __threadfence();
+    else __threadfence_block();
+    __syncwarp(mask);
+    if (sl == 0) {
+      *(volatile int*)(rf + (s - r0)) = 1;
+      if (ex) st_release(A.flag + s, A.epoch);
+    }
   }
 }
 

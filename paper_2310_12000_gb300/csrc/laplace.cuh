@@ -567,8 +567,14 @@ inline vl_status slq_run(State* st, const vl_opts* o, SlqOut& out) {
   int used = 0;
   VL_TRY(E.pcg(Zm, Um, o->cg_tol, o->cg_max_iter, &used));
   VL_CUDA(c, cudaMemsetAsync(bad, 0, sizeof(int), c->stream));
-  slq_quad_kernel<<<(ncol + 63) / 64, 64, 0, VL_STREAM(c)>>>(ncol, E.lmax, E.S.Tdiag, E.S.Toff, E.S.iters, E.S.rz0,
-                                                             work, gdev, bad);
+  // one column per block: the QR sweeps are a serial float64 chain per column, and columns
+  // packed into one block shared that SM's few float64 units (measured 0.7 s for 50 columns of
+  // l = 421 in one block)
+  {
+    ProfScope ps(c, "slq_quad", t);
+    slq_quad_kernel<<<ncol, 1, 0, VL_STREAM(c)>>>(ncol, E.lmax, E.S.Tdiag, E.S.Toff, E.S.iters, E.S.rz0, work, gdev,
+                                                  bad);
+  }
   VL_CUDA(c, cudaGetLastError());
   VL_TRY(E.column_stats(out.iters, out.relres));
   std::vector<int> hbad;

@@ -178,19 +178,16 @@ struct Factor {
     bool usable = false;
   };
   std::map<int, HeadPlan> head_plans;
-  // tiled solves (sptrsv_tile*_kernel): G tiles of R storage rows, each tile's rows by (level,
-  // row), its segments (runs of one level) and the progress waits of each segment; built on
-  // first use per (direction, G)
+  // tiled solves (sptrsv_tile*_kernel): G tiles of R storage rows, each tile's rows by level,
+  // the rows another tile depends on, and the ready flags of block solves (epoch per launch);
+  // built on first use per (direction, G)
   struct TilePlan {
-    int G = 0, R = 0, nseg = 0, nwait = 0;
+    int G = 0, R = 0;
     int32_t* ttask = nullptr;
-    int32_t* sp = nullptr;
-    int32_t* seg_lev = nullptr;
-    int32_t* seg_beg = nullptr;
-    int32_t* wptr = nullptr;
-    int32_t* wtile = nullptr;
-    int32_t* wneed = nullptr;
-    int* prog = nullptr;
+    int32_t* toff = nullptr;
+    uint8_t* exported = nullptr;
+    int* flag = nullptr;
+    int epoch = 0;
   };
   std::map<std::pair<int, int>, TilePlan> tile_plans;
   // LRAC (Section 3.1.2): rank-k pivoted Cholesky factor of Sigma, built on first use
