@@ -995,14 +995,20 @@ struct Engine {
           constexpr int LPV = decltype(Lc)::value, NV = decltype(N)::value, UNR = decltype(U)::value;
           const void* fn = (cand & 2) ? (const void*)sptrsv_tile_kernel<T, FWD, LPV, NV, 2 * UNR>
                                       : (const void*)sptrsv_tile_kernel<T, FWD, LPV, NV, UNR>;
-          const int per_sm = (cand & 1) ? 1 : 2;
-          const int G = per_sm * c->num_sms;
-          const size_t smem = sizeof(int) * (size_t)((n + G - 1) / G);
-          if (smem > kSmemSolveBytes)
-            return fail(c, VL_ERR_INVALID_ARG, "solve form VL_SOLVE_TILE: a tile's flags do not fit shared memory");
           VL_TRY(smem_limit_once(c, fn, kSmemSolveBytes));
-          if (resident_blocks(c, fn, 512, smem) < G)
-            return fail(c, VL_ERR_INVALID_ARG, "solve form VL_SOLVE_TILE: the tiles are not all resident");
+          // 2 or 1 tiles per SM, fewer when the shape's registers or the flags do not allow them
+          int G = 0;
+          size_t smem = 0;
+          for (int per_sm = (cand & 1) ? 1 : 2; per_sm >= 1 && G == 0; --per_sm) {
+            const int g = per_sm * c->num_sms;
+            const size_t sm = sizeof(int) * (size_t)((n + g - 1) / g);
+            if (sm <= kSmemSolveBytes && resident_blocks(c, fn, 512, sm) >= g) {
+              G = g;
+              smem = sm;
+            }
+          }
+          if (G == 0)
+            return fail(c, VL_ERR_INVALID_ARG, "solve form VL_SOLVE_TILE: the tiles do not fit the device");
           Factor::TilePlan* tp = nullptr;
           VL_TRY(tile_plan(c, f, FWD, G, (const Factor::TilePlan**)&tp));
           if (tp->epoch == 0x7fffffff) {   // flags of earlier launches hold older epochs
