@@ -19,10 +19,11 @@ Two more legs run on rank 0 of a single-GPU run, after the timed steps:
   slot contexts on separate streams; reported as evaluations/s.
 * serving: a Poisson stream of fresh problems at 50 requests/s (n log-uniform in
   [1e3, 2e5], Matern-1.5, Bernoulli or Poisson, mode + L^VLA + predictive
-  variances at 1000 points) admitted by device-memory footprint and served by
-  continuous batching (a free slot merges every queued request that fits into one
-  block-diagonal system); reported as p50 / p99 latency (arrival to completion),
-  service time and throughput, with the arrival window stated.
+  variances at 1000 points) admitted by device-memory footprint, each on a slot
+  context of its own with the slots' work overlapping on the device (`--serve-form
+  groups`: a free slot merges every queued request that fits into one block-diagonal
+  system instead); reported as p50 / p99 latency (arrival to completion), service
+  time and throughput, with the arrival window stated.
 
 Multi-GPU (torchrun, one rank per GPU): independent replicas, each rank solving its
 own seeded problem of the same shape (weak scaling); no collective on the data path.
@@ -275,7 +276,7 @@ def pregenerate(kind: str, count: int, procs: int = 12):
 
 
 def serving_leg(vl, problems, arrivals, duration: float, slots: int, device: int, small: int = 0,
-                form: str = "groups", group_slots: int = 2, group_gb: float = 60.0) -> dict:
+                form: str = "slots", group_slots: int = 2, group_gb: float = 60.0) -> dict:
     """The serving stream. form "groups": continuous batching, `group_slots` slot contexts of
     group_gb GiB each, a free slot merging every queued request that fits into one
     block-diagonal system; form "slots": one request per slot context, `slots` of them."""
@@ -645,8 +646,8 @@ def main():
     ap.add_argument("--slots", type=int, default=16, help="slot contexts of the batched and serving legs")
     ap.add_argument("--batch-streams", action="store_true",
                     help="also run the batched problems on slot contexts (one stream each)")
-    ap.add_argument("--serve-form", default="groups", choices=["groups", "slots"],
-                    help="serving by merged groups (continuous batching) or one request per slot context")
+    ap.add_argument("--serve-form", default="slots", choices=["groups", "slots"],
+                    help="serving by one request per slot context, or by merged groups (continuous batching)")
     ap.add_argument("--group-slots", type=int, default=2, help="slot contexts of the merged-group serving form")
     ap.add_argument("--group-gb", type=float, default=60.0, help="workspace GiB of each merged-group slot")
     ap.add_argument("--small-slots", type=int, default=0,

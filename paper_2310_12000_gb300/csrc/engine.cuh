@@ -219,8 +219,8 @@ static __global__ void head_nbr_kernel(int rows, int m, const int32_t* __restric
 // dependency lay outside the head (it cannot: a row depends only on rows of earlier levels).
 // Plan of the tiled solve in one direction over G tiles (tile_plan.h), built on the host from
 // the task list and the dependency lists, and kept on the device.
-inline vl_status tile_plan(Ctx* c, Factor* f, bool fwd, int G, const Factor::TilePlan** out) {
-  const std::pair<int, int> key{fwd ? 1 : 0, G};
+inline vl_status tile_plan(Ctx* c, Factor* f, bool fwd, int G, int first, const Factor::TilePlan** out) {
+  const std::tuple<int, int, int> key{fwd ? 1 : 0, G, first};
   auto it = f->tile_plans.find(key);
   if (it != f->tile_plans.end()) {
     *out = &it->second;
@@ -243,7 +243,7 @@ inline vl_status tile_plan(Ctx* c, Factor* f, bool fwd, int G, const Factor::Til
   }
   VL_CUDA(c, cudaStreamSynchronize(c->stream));
   const TilePlanHost H = build_tile_plan(n, G, task.data(), m, fwd ? nbr.data() : nullptr,
-                                         fwd ? nullptr : rp.data(), fwd ? nullptr : col.data());
+                                         fwd ? nullptr : rp.data(), fwd ? nullptr : col.data(), first);
   Factor::TilePlan plan;
   plan.G = G;
   plan.R = H.R;
@@ -975,14 +975,32 @@ struct Engine {
           const int G = bps * c->num_sms;
           const size_t smem = sizeof(T) * (size_t)((n + G - 1) / G);
           if (smem > kSmemSolveBytes || resident_blocks(c, fn, 1024, smem) < G) continue;
+          // forward: the narrow leading levels first by one block with x in shared memory (their
+          // rows depend on rows far apart, which would make every link a cross-tile hand-off)
+          int first = 0;
+          const Factor::HeadPlan* hp = nullptr;
+          if (FWD) {
+            int l_tail = 0;
+            level_cut(hl, hh, hw, 1, &L.l_head, &l_tail);
+            if (L.l_head > 0 && (size_t)hl[L.l_head] * sizeof(T) <= kSmemSolveBytes) {
+              VL_TRY(head_plan(c, f, L.l_head, &hp));
+              if (hp->usable) first = hl[L.l_head];
+            }
+          }
           Factor::TilePlan* tp = nullptr;
-          VL_TRY(tile_plan(c, f, FWD, G, (const Factor::TilePlan**)&tp));
+          VL_TRY(tile_plan(c, f, FWD, G, first, (const Factor::TilePlan**)&tp));
           TileArgs A = args_of(tp);
           void* args[] = {&A, &mm, &idx, &val, &rp, &rhs, &q, &x};
           // every value starts "unsolved" (all bits set): it is its own ready flag
           VL_CUDA(c, cudaMemsetAsync(x, 0xff, sizeof(T) * (size_t)n, c->stream));
-          ++c->launches;
           ProfScope ps(c, cls, t);
+          if (first > 0) {
+            auto hfn = sptrsv_t1_head_kernel<T, 8>;
+            VL_TRY(smem_limit_once(c, (const void*)hfn, kSmemSolveBytes));
+            hfn<<<1, 1024, sizeof(T) * (size_t)hp->rows, VL_STREAM(c)>>>(L, m, hp->hpos, val, rhs, q, x);
+            VL_CUDA(c, cudaGetLastError());
+          }
+          ++c->launches;
           return cuda_ok(c, cudaLaunchCooperativeKernel(fn, G, 1024, args, smem, c->stream));
         }
         return fail(c, VL_ERR_INVALID_ARG, "solve form VL_SOLVE_TILE: a tile of x does not fit shared memory");
@@ -1010,7 +1028,7 @@ struct Engine {
           if (G == 0)
             return fail(c, VL_ERR_INVALID_ARG, "solve form VL_SOLVE_TILE: the tiles do not fit the device");
           Factor::TilePlan* tp = nullptr;
-          VL_TRY(tile_plan(c, f, FWD, G, (const Factor::TilePlan**)&tp));
+          VL_TRY(tile_plan(c, f, FWD, G, 0, (const Factor::TilePlan**)&tp));
           if (tp->epoch == 0x7fffffff) {   // flags of earlier launches hold older epochs
             VL_CUDA(c, cudaMemsetAsync(tp->flag, 0, sizeof(int) * (size_t)std::max(n, 1), c->stream));
             tp->epoch = 0;

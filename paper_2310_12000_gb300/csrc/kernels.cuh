@@ -1099,8 +1099,8 @@ __device__ __forceinline__ T tile_wait_value(const T* p, DevStatus* st, int row)
 }
 
 // Scalar rows (t = 1): the tile's x in shared memory, every row also stored to x for the other
-// tiles; x starts all "unsolved" (the host sets it before the launch), so a value is its own
-// ready flag and no fence is needed. Team lanes split a row's dependencies (K loads each).
+// tiles; x starts "unsolved" (all bits set by the host before the launch) except on the rows a
+// kernel before this one solved, so a value is its own ready flag and no fence is needed. Team lanes split a row's dependencies (K loads each).
 template <typename T, bool FWD, int LPV>
 __global__ void __launch_bounds__(1024) sptrsv_tile1_kernel(TileArgs A, int m, const int32_t* __restrict__ idx,
                                                             const T* __restrict__ val,
@@ -1115,7 +1115,8 @@ __global__ void __launch_bounds__(1024) sptrsv_tile1_kernel(TileArgs A, int m, c
   const int sl = (threadIdx.x & 31) % LPV;
   const int b = blockIdx.x;
   const int r0 = b * A.R, r1 = min(A.n, r0 + A.R);
-  for (int i = threadIdx.x; i < r1 - r0; i += blockDim.x) xs[i] = unsolved_value(T(0));
+  // x holds "unsolved" everywhere but on the rows solved before the walk (the forward head)
+  for (int i = threadIdx.x; i < r1 - r0; i += blockDim.x) xs[i] = __ldcg(x + r0 + i);
   __syncthreads();
   for (int p = A.toff[b] + tib; p < A.toff[b + 1]; p += tpb) {
     const int s = A.ttask[p];

@@ -17,26 +17,27 @@ namespace vl {
 
 struct TilePlanHost {
   int G = 0, R = 0;
-  std::vector<int32_t> ttask;     // n: each tile's rows in task order, tiles in order
+  std::vector<int32_t> ttask;     // n - first: each tile's rows in task order, tiles in order
   std::vector<int32_t> toff;      // G + 1: tile b's rows are ttask[toff[b] .. toff[b + 1])
   std::vector<uint8_t> exported;  // n: 1 when a row of another tile depends on this row
 };
 
 // Dependencies of storage row s: ELL (nbr[s m .. s m + m), -1 padding) when rp is null, else
-// CSR (col[rp[s] .. rp[s + 1])). task: storage rows sorted by level.
+// CSR (col[rp[s] .. rp[s + 1])). task: storage rows sorted by level; the rows task[0 .. first)
+// are solved before the walk (the leading levels, by another kernel) and are not listed.
 inline TilePlanHost build_tile_plan(int n, int G, const int32_t* task, int m, const int32_t* nbr,
-                                    const int32_t* rp, const int32_t* col) {
+                                    const int32_t* rp, const int32_t* col, int first = 0) {
   TilePlanHost P;
   P.G = G;
   P.R = n > 0 ? (n + G - 1) / G : 1;
   const int R = P.R;
   P.toff.assign(G + 1, 0);
-  for (int p = 0; p < n; ++p) ++P.toff[task[p] / R + 1];
+  for (int p = first; p < n; ++p) ++P.toff[task[p] / R + 1];
   for (int b = 0; b < G; ++b) P.toff[b + 1] += P.toff[b];
-  P.ttask.resize(n);
+  P.ttask.resize(n - first);
   {
     std::vector<int32_t> fill(P.toff.begin(), P.toff.end() - 1);
-    for (int p = 0; p < n; ++p) P.ttask[fill[task[p] / R]++] = task[p];
+    for (int p = first; p < n; ++p) P.ttask[fill[task[p] / R]++] = task[p];
   }
   P.exported.assign(n, 0);
   for (int s = 0; s < n; ++s) {

@@ -6,6 +6,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <map>
+#include <tuple>
 #include <string>
 #include <unordered_map>
 #include <vector>
@@ -189,7 +190,7 @@ struct Factor {
     int* flag = nullptr;
     int epoch = 0;
   };
-  std::map<std::pair<int, int>, TilePlan> tile_plans;
+  std::map<std::tuple<int, int, int>, TilePlan> tile_plans;   // (forward, G, first listed task)
   // LRAC (Section 3.1.2): rank-k pivoted Cholesky factor of Sigma, built on first use
   // and dropped when the covariance parameters change
   Owned lrac_mem;

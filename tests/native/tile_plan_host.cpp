@@ -17,10 +17,10 @@ using vl::TilePlanHost;
 
 static bool replay(const char* name, int n, int G, int teams, const std::vector<int32_t>& task, int m,
                    const std::vector<int32_t>& nbr, const std::vector<int32_t>& rp, const std::vector<int32_t>& col,
-                   const std::vector<double>& w, const std::vector<double>& rhs, unsigned seed) {
+                   const std::vector<double>& w, const std::vector<double>& rhs, unsigned seed, int first) {
   const bool ell = rp.empty();
   TilePlanHost P = vl::build_tile_plan(n, G, task.data(), m, ell ? nbr.data() : nullptr, ell ? nullptr : rp.data(),
-                                       ell ? nullptr : col.data());
+                                       ell ? nullptr : col.data(), first);
   auto deps = [&](int s, auto fn) {
     const int beg = ell ? s * m : rp[s], end = ell ? s * m + m : rp[s + 1];
     for (int k = beg; k < end; ++k) {
@@ -46,9 +46,14 @@ static bool replay(const char* name, int n, int G, int teams, const std::vector<
     printf("%s: exported marks differ\n", name);
     return false;
   }
+  if ((int)P.ttask.size() != n - first || P.toff[G] != n - first) {
+    printf("%s: the tile lists do not hold the rows after the first %d\n", name, first);
+    return false;
+  }
   for (int b = 0; b < G; ++b)
     for (int p = P.toff[b]; p < P.toff[b + 1]; ++p)
-      if (P.ttask[p] / R != b || (p > P.toff[b] && pos[P.ttask[p]] < pos[P.ttask[p - 1]])) {
+      if (P.ttask[p] / R != b || pos[P.ttask[p]] < first ||
+          (p > P.toff[b] && pos[P.ttask[p]] < pos[P.ttask[p - 1]])) {
         printf("%s: tile list of tile %d out of order\n", name, b);
         return false;
       }
@@ -64,7 +69,14 @@ static bool replay(const char* name, int n, int G, int teams, const std::vector<
     }
   std::vector<char> done(n, 0);
   std::vector<double> x(n, 0.0);
-  int left = n;
+  for (int p = 0; p < first; ++p) {   // solved before the walk, in task order
+    const int s = task[p];
+    double acc = 0.0;
+    deps(s, [&](int j, int k) { acc += w[k] * x[j]; });
+    x[s] = rhs[s] + acc;
+    done[s] = 1;
+  }
+  int left = n - first;
   std::vector<int> order(cursor.size());
   for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
   while (left > 0) {
@@ -176,12 +188,13 @@ int main() {
   for (auto& v : wf) v = U(rng);
   for (auto& v : wb) v = U(rng);
   for (auto& v : rhs) v = U(rng);
-  (void)nlevf;
   (void)nlevb;
   bool ok = true;
   for (int teams : {1, 3, 64}) {
-    ok = replay("fwd", n, G, teams, taskf, m, nbr, {}, {}, wf, rhs, seed + teams) && ok;
-    ok = replay("bwd", n, G, teams, taskb, m, nbr, rp, col, wb, rhs, seed + 2 * teams) && ok;
+    // forward: also with the rows of the first levels solved before the walk
+    const int first = teams == 3 ? lptrf[std::min(nlevf, 6)] : 0;
+    ok = replay("fwd", n, G, teams, taskf, m, nbr, {}, {}, wf, rhs, seed + teams, first) && ok;
+    ok = replay("bwd", n, G, teams, taskb, m, nbr, rp, col, wb, rhs, seed + 2 * teams, 0) && ok;
   }
   return ok ? 0 : 1;
 }
