@@ -961,7 +961,12 @@ struct Engine {
       }
       return VL_OK;
     };
-    if (form == VL_SOLVE_TILE) {
+    // the automatic choice takes the tiled walk for backward scalar solves of large systems
+    // (n = 1e6 grid: 1.09 ms against 1.94 ms for the grid walk); forward scalar solves keep the
+    // grid walk with its one-block head (1.09 ms against 1.36 ms), block solves keep the grid
+    // walk (their rows wait on 224-byte gathers: 8.8 / 16.3 ms tiled against 3.0 / 4.6 ms)
+    const bool auto_tile = form == VL_SOLVE_AUTO && t == 1 && !FWD && n > kSharedRows && x != rhs;
+    if (form == VL_SOLVE_TILE || auto_tile) {
       // storage-row tiles, each row waiting only for its own dependencies (see TileArgs)
       if (x == rhs) return fail(c, VL_ERR_STATE, "tiled solve in place");
       auto args_of = [&](const Factor::TilePlan* tp) {
@@ -1003,8 +1008,14 @@ struct Engine {
           ++c->launches;
           return cuda_ok(c, cudaLaunchCooperativeKernel(fn, G, 1024, args, smem, c->stream));
         }
-        return fail(c, VL_ERR_INVALID_ARG, "solve form VL_SOLVE_TILE: a tile of x does not fit shared memory");
+        if (form == VL_SOLVE_TILE)
+          return fail(c, VL_ERR_INVALID_ARG, "solve form VL_SOLVE_TILE: a tile of x does not fit shared memory");
       }
+    }
+    if (form == VL_SOLVE_TILE) {
+      auto args_of = [&](const Factor::TilePlan* tp) {
+        return TileArgs{tp->ttask, tp->toff, tp->exported, tp->flag, c->dstatus, n, tp->R, tp->epoch};
+      };
       if (ld % 8 != 0) return fail(c, VL_ERR_STATE, "block solve with a row width that is not a multiple of 8");
       // candidates (all give the same numbers: a row's sum does not depend on its tile or team):
       // tiles of 512 threads, 2 or 1 per SM, x the shape's UNR or twice it
