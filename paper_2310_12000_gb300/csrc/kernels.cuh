@@ -1133,10 +1133,16 @@ __global__ void __launch_bounds__(1024) sptrsv_tile1_kernel(TileArgs A, int m, c
         j[u] = e < end ? idx[e] : -1;
         a[u] = j[u] >= 0 ? val[e] : T(0);
       }
+      // the K loads go out together; only a value still unsolved is waited for
+      const T* src[K];
+#pragma unroll
+      for (int u = 0; u < K; ++u) {
+        src[u] = j[u] < 0 ? nullptr : ((j[u] >= r0 && j[u] < r1) ? xs + (j[u] - r0) : x + j[u]);
+        xv[u] = src[u] ? *(volatile const T*)src[u] : T(0);
+      }
 #pragma unroll
       for (int u = 0; u < K; ++u)
-        xv[u] = j[u] < 0 ? T(0)
-                         : tile_wait_value((j[u] >= r0 && j[u] < r1) ? xs + (j[u] - r0) : x + j[u], A.st, s);
+        if (src[u] && is_unsolved(xv[u])) xv[u] = tile_wait_value(src[u], A.st, s);
 #pragma unroll
       for (int u = 0; u < K; ++u) acc += a[u] * xv[u];
     }
@@ -1465,82 +1471,114 @@ static __global__ void reduce_partials_kernel(int nblk, int t, const double* __r
 }
 
 // ----------------------------------------------------------------------------- SLQ quadrature
-// e1^T log(T) e1 = sum_j q_{1j}^2 log(theta_j) of the l x l symmetric tridiagonal T (diagonal d,
-// off-diagonal e, both overwritten; z is scratch of length l) by implicit symmetric QR steps with
-// Wilkinson shifts (Golub & Van Loan, Sec. 8.3), rotating only the first row of the eigenvector
-// matrix (kept in z). *bad is set when the iteration did not converge or an eigenvalue is not
-// positive. Host-callable for checks on the CPU.
-__host__ __device__ inline double tridiag_log_quad(int l, double* d, double* e, double* z, bool* bad) {
-  for (int i = 0; i < l; ++i) z[i] = (i == 0) ? 1.0 : 0.0;
-  const double eps = 2.220446049250313e-16;
-  int hi = l - 1;
-  int guard = 0;
-  while (hi > 0 && guard < 60 * l + 60) {
-    if (fabs(e[hi - 1]) <= eps * (fabs(d[hi - 1]) + fabs(d[hi]))) {
-      e[hi - 1] = 0.0;
-      --hi;
-      continue;
-    }
-    int lo = hi - 1;
-    while (lo > 0 && fabs(e[lo - 1]) > eps * (fabs(d[lo - 1]) + fabs(d[lo]))) --lo;
-    if (lo > 0) e[lo - 1] = 0.0;
-    const double dd = 0.5 * (d[hi - 1] - d[hi]);
-    const double ee = e[hi - 1];
-    const double sg = dd >= 0.0 ? 1.0 : -1.0;
-    const double mu = d[hi] - ee * ee / (dd + sg * hypot(dd, ee));
-    double x = d[lo] - mu, y = e[lo];
-    for (int k = lo; k < hi; ++k) {
-      const double rr = hypot(x, y);
-      double cs = 1.0, sn = 0.0;
-      if (rr > 0.0) {
-        cs = x / rr;
-        sn = y / rr;
-      }
-      if (k > lo) e[k - 1] = rr;
-      const double dk = d[k], dk1 = d[k + 1], ek = e[k];
-      d[k] = cs * cs * dk + 2.0 * cs * sn * ek + sn * sn * dk1;
-      d[k + 1] = sn * sn * dk - 2.0 * cs * sn * ek + cs * cs * dk1;
-      e[k] = cs * sn * (dk1 - dk) + (cs * cs - sn * sn) * ek;
-      if (k + 1 < hi) {
-        y = sn * e[k + 1];
-        e[k + 1] = cs * e[k + 1];
-        x = e[k];
-      }
-      const double zk = z[k], zk1 = z[k + 1];
-      z[k] = cs * zk + sn * zk1;
-      z[k + 1] = -sn * zk + cs * zk1;
-    }
-    ++guard;
+// e1^T log(T) e1 for the l x l symmetric positive definite tridiagonal T of one probe (Eq.
+// def_SLQ; the Gauss quadrature sum_j q_{1j}^2 log(theta_j) of its eigenpairs) from the identity
+//   log(theta) = integral over s > 0 of [1 / (1 + s) - 1 / (theta + s)] ds,
+// which gives e1^T log(T) e1 = integral of [1 / (1 + s) - e1^T (T + s I)^{-1} e1] ds with no
+// eigen-decomposition. With s = e^u the integrand is analytic in the strip |Im u| < pi, so the
+// trapezoidal rule in u converges geometrically (error ~ exp(-2 pi^2 / h)); h = 0.4 leaves it far
+// below float64 rounding. e1^T (T + s I)^{-1} e1 = 1 / D_0(s) with the pivots of T + s I taken from
+// the bottom row up, D_{l-1} = d_{l-1} + s, D_k = d_k + s - e_k^2 / D_{k+1}: all positive for a
+// positive definite T and s >= 0, so the recurrence is stable, and clustered or repeated Ritz
+// values (which Lanczos without reorthogonalisation produces) need no special care. Every node
+// is independent: the float64 work spreads over many warps (float64 issues at a small fraction of
+// the float32 rate on this GPU; one thread running implicit QR sweeps over a 519-row T took half
+// a second). The u range covers [log(theta_lo) - 40, log(theta_hi) + 40], where the integrand is
+// below 1e-17: theta_hi a Gershgorin bound, theta_lo within a factor 16 below the smallest
+// eigenvalue (Sturm counts, Wilkinson's sign-count bisection). Host-callable.
+constexpr double kQuadStep = 0.4;
+constexpr int kQuadMaxNodes = 1024;
+
+// Eigenvalues of T below x (the negative pivots of T - x I from the top).
+__host__ __device__ inline int tridiag_count_below(int l, const double* d, const double* e, double x) {
+  const double pivmin = 1e-290;
+  double q = d[0] - x;
+  int cnt = q < 0.0;
+  for (int k = 1; k < l; ++k) {
+    if (fabs(q) < pivmin) q = -pivmin;
+    q = (d[k] - x) - e[k - 1] * e[k - 1] / q;
+    cnt += q < 0.0;
   }
-  double g = 0.0;
-  int nb = 0;
-  for (int i = 0; i < l; ++i) {
-    if (!(d[i] > 0.0)) ++nb;
-    g += z[i] * z[i] * log(d[i]);
-  }
-  *bad = (hi > 0 || nb);
-  return g;
+  return cnt;
 }
 
-// gamma_c = w_c * e1^T log(T_c) e1 for the Lanczos tridiagonal T_c of column c (size iters[c]).
-// One thread per column, float64.
-static __global__ void slq_quad_kernel(int t, int lmax, const double* __restrict__ Tdiag, const double* __restrict__ Toff,
-                                const int* __restrict__ iters, const double* __restrict__ w,
-                                double* __restrict__ work, double* __restrict__ gamma, int* __restrict__ bad) {
+// First node u0 and node count of T's quadrature; false when T is not positive definite (or its
+// eigenvalues span more than the node budget).
+__host__ __device__ inline bool slq_quad_range(int l, const double* d, const double* e, double* u0, int* nodes) {
+  *u0 = 0.0;
+  *nodes = 0;
+  if (l <= 0) return true;
+  double hi = 0.0;
+  for (int k = 0; k < l; ++k) {
+    const double r = (k > 0 ? fabs(e[k - 1]) : 0.0) + (k + 1 < l ? fabs(e[k]) : 0.0);
+    hi = k == 0 ? d[k] + r : fmax(hi, d[k] + r);
+  }
+  if (!(hi > 0.0) || tridiag_count_below(l, d, e, 0.0) > 0) return false;
+  double lo = hi;
+  for (int it = 0; it < 300 && tridiag_count_below(l, d, e, lo) > 0; ++it) lo *= 0.0625;
+  if (!(lo > 0.0)) return false;
+  *u0 = log(lo) - 40.0;
+  const int n = (int)ceil((log(hi) + 40.0 - *u0) / kQuadStep) + 1;
+  if (n > kQuadMaxNodes) return false;
+  *nodes = n;
+  return true;
+}
+
+// Integrand at node u: s / (1 + s) - s e1^T (T + s I)^{-1} e1, s = e^u (the factor s is ds / du).
+__host__ __device__ inline double slq_quad_node(int l, const double* d, const double* e, double u) {
+  const double s = exp(u);
+  double D = d[l - 1] + s;
+  for (int k = l - 2; k >= 0; --k) D = (d[k] + s) - e[k] * e[k] / D;
+  return s / (1.0 + s) - s / D;
+}
+
+// One thread per column: the node range (u0[c], nodes[c]); a T that is not positive definite
+// is counted in *bad.
+static __global__ void slq_range_kernel(int t, int lmax, const double* __restrict__ Tdiag,
+                                        const double* __restrict__ Toff, const int* __restrict__ iters,
+                                        double* __restrict__ u0, int* __restrict__ nodes, int* __restrict__ bad) {
+  const int c = blockIdx.x;
+  if (c >= t || threadIdx.x != 0) return;
+  const int l = min(iters[c], lmax);
+  if (!slq_quad_range(l, Tdiag + (int64_t)c * lmax, Toff + (int64_t)c * lmax, &u0[c], &nodes[c])) {
+    nodes[c] = 0;
+    atomicAdd(bad, 1);
+  }
+}
+
+// Block (x, c): nodes i = x * blockDim.x + threadIdx.x of column c, T_c staged in shared memory
+// when it fits (staged != 0).
+static __global__ void slq_node_kernel(int t, int lmax, const double* __restrict__ Tdiag,
+                                       const double* __restrict__ Toff, const int* __restrict__ iters,
+                                       const double* __restrict__ u0, const int* __restrict__ nodes,
+                                       double* __restrict__ term, int staged) {
+  extern __shared__ double vl_qsh[];
+  const int c = blockIdx.y;
+  if (c >= t || (int)(blockIdx.x * blockDim.x) >= nodes[c]) return;
+  const int l = min(iters[c], lmax);
+  const double* d = Tdiag + (int64_t)c * lmax;
+  const double* e = Toff + (int64_t)c * lmax;
+  if (staged) {
+    for (int k = threadIdx.x; k < l; k += blockDim.x) {
+      vl_qsh[k] = d[k];
+      vl_qsh[lmax + k] = k + 1 < l ? e[k] : 0.0;
+    }
+    __syncthreads();
+    d = vl_qsh;
+    e = vl_qsh + lmax;
+  }
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nodes[c]) term[(int64_t)c * kQuadMaxNodes + i] = slq_quad_node(l, d, e, u0[c] + i * kQuadStep);
+}
+
+// gamma_c = w_c * h * sum_i term[c, i], in node order.
+static __global__ void slq_sum_kernel(int t, const int* __restrict__ nodes, const double* __restrict__ w,
+                                      const double* __restrict__ term, double* __restrict__ gamma) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= t) return;
-  const int l = iters[c];
-  double* d = work + (int64_t)c * 3 * lmax;
-  double* e = d + lmax;
-  double* z = e + lmax;
-  for (int i = 0; i < l; ++i) {
-    d[i] = Tdiag[(int64_t)c * lmax + i];
-    e[i] = (i + 1 < l) ? Toff[(int64_t)c * lmax + i] : 0.0;
-  }
-  bool bad_c = false;
-  const double g = tridiag_log_quad(l, d, e, z, &bad_c);
-  if (bad_c) atomicAdd(bad, 1);
-  gamma[c] = (l > 0) ? w[c] * g : 0.0;
+  double g = 0.0;
+  for (int i = 0; i < nodes[c]; ++i) g += term[(int64_t)c * kQuadMaxNodes + i];
+  gamma[c] = w[c] * kQuadStep * g;
 }
 
 // ----------------------------------------------------------------------------- likelihood

@@ -545,9 +545,12 @@ inline vl_status slq_run(State* st, const vl_opts* o, SlqOut& out) {
   double* sc64 = S.get<double>(n);
   T* sc = S.get<T>(n);
   double* gdev = S.get<double>(ncol);
-  double* work = S.get<double>((size_t)3 * ncol * E.lmax);
+  double* work = S.get<double>((size_t)ncol * kQuadMaxNodes);
+  double* qu0 = S.get<double>(ncol);
+  int* qnodes = S.get<int>(ncol);
   int* bad = S.get<int>(1);
-  if (!Rm || !Zm || !Um || !sc64 || !sc || !gdev || !work || !bad) return fail(c, VL_ERR_OOM, "workspace exhausted (SLQ)");
+  if (!Rm || !Zm || !Um || !sc64 || !sc || !gdev || !work || !qu0 || !qnodes || !bad)
+    return fail(c, VL_ERR_OOM, "workspace exhausted (SLQ)");
   rademacher_kernel<T><<<(n + 127) / 128, 128, 0, VL_STREAM(c)>>>(n, t, E.ld, f->s2u_probe(), o->seed, 0, 0, Rm);
   const int dmode = o->precond == VL_PREC_VADU ? 0 : (o->precond == VL_PREC_LVA ? 1 : 3);
   diag_fn_kernel<<<grid_for(c, n), 256, 0, VL_STREAM(c)>>>(n, dmode, st->W, f->D64, sc64);
@@ -567,20 +570,24 @@ inline vl_status slq_run(State* st, const vl_opts* o, SlqOut& out) {
   int used = 0;
   VL_TRY(E.pcg(Zm, Um, o->cg_tol, o->cg_max_iter, &used));
   VL_CUDA(c, cudaMemsetAsync(bad, 0, sizeof(int), c->stream));
-  // one column per block: the QR sweeps are a serial float64 chain per column, and columns
-  // packed into one block shared that SM's few float64 units (measured 0.7 s for 50 columns of
-  // l = 421 in one block)
   {
+    // the node range of every column, then every (column, node) in its own thread, then the
+    // per-column sums in node order
     ProfScope ps(c, "slq_quad", t);
-    slq_quad_kernel<<<ncol, 1, 0, VL_STREAM(c)>>>(ncol, E.lmax, E.S.Tdiag, E.S.Toff, E.S.iters, E.S.rz0, work, gdev,
-                                                  bad);
+    const size_t qsm = sizeof(double) * 2 * (size_t)E.lmax;
+    const int staged = qsm <= kSmemSolveBytes ? 1 : 0;
+    if (staged) VL_TRY(smem_limit_once(c, (const void*)slq_node_kernel, kSmemSolveBytes));
+    slq_range_kernel<<<ncol, 32, 0, VL_STREAM(c)>>>(ncol, E.lmax, E.S.Tdiag, E.S.Toff, E.S.iters, qu0, qnodes, bad);
+    slq_node_kernel<<<dim3(kQuadMaxNodes / 64, ncol), 64, staged ? qsm : 0, VL_STREAM(c)>>>(
+        ncol, E.lmax, E.S.Tdiag, E.S.Toff, E.S.iters, qu0, qnodes, work, staged);
+    slq_sum_kernel<<<(ncol + 127) / 128, 128, 0, VL_STREAM(c)>>>(ncol, qnodes, E.S.rz0, work, gdev);
   }
   VL_CUDA(c, cudaGetLastError());
   VL_TRY(E.column_stats(out.iters, out.relres));
   std::vector<int> hbad;
   VL_TRY(to_host(c, hbad, (const int*)bad, 1));
   VL_TRY(to_host(c, out.gam, (const double*)gdev, (size_t)ncol));
-  if (hbad[0]) return fail(c, VL_ERR_NOT_CONVERGED, "SLQ: tridiagonal eigen-solve failed (non-positive Ritz value)");
+  if (hbad[0]) return fail(c, VL_ERR_NOT_CONVERGED, "SLQ: a Lanczos tridiagonal is not positive definite (non-positive Ritz value)");
   for (int q = 0; q < ncol; ++q)
     if (out.relres[q] > o->cg_tol && out.iters[q] >= o->cg_max_iter)
       return fail(c, VL_ERR_NOT_CONVERGED, "SLQ probe solves reached cg_max_iter");

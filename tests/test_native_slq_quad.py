@@ -1,8 +1,11 @@
-"""The CUDA side's SLQ quadrature (vl::tridiag_log_quad in csrc/kernels.cuh, the per-column
-body of slq_quad_kernel: e1^T log(T) e1 by implicit-shift QR on the Lanczos tridiagonal of
-Eq. def_SLQ), run on the host against the oracle's dense eigendecomposition (krylov.quad_log)
-over tridiagonals from real PCG runs and random ones, including sizes 1 and 2, deflation
-(a zero off-diagonal), a wide spectrum and an indefinite matrix that must be flagged. No GPU."""
+"""The CUDA side's SLQ quadrature (csrc/kernels.cuh: e1^T log(T) e1 of the Lanczos tridiagonal
+of Eq. def_SLQ through the integral of 1 / (1 + s) - e1^T (T + s I)^{-1} e1 over s > 0, by the
+trapezoidal rule in log s with a continued-fraction evaluation per node: the bodies of
+slq_range_kernel, slq_node_kernel and slq_sum_kernel), run on the host against the oracle's dense
+eigendecomposition (krylov.quad_log) over tridiagonals from real PCG runs (with repeated Ritz
+values), a 519-step Lanczos run with lost orthogonality, and random ones, including sizes 1 and 2,
+deflation (a zero off-diagonal), a wide spectrum, and an indefinite matrix that must be flagged.
+No GPU."""
 import os
 import subprocess
 
@@ -52,6 +55,25 @@ def _pcg_tridiagonals():
     return out
 
 
+def _plain_lanczos(l, cond, seed):
+    """l steps of Lanczos without reorthogonalisation (what CG's coefficients give) on a
+    diagonal matrix with a log-uniform spectrum in [1, cond], from a Rademacher start."""
+    rng = np.random.default_rng(seed)
+    lam = np.exp(rng.uniform(0.0, np.log(cond), 4000))
+    v = rng.choice([-1.0, 1.0], lam.size)
+    v /= np.linalg.norm(v)
+    vp, b, d, e = np.zeros_like(v), 0.0, [], []
+    for _ in range(l):
+        w = lam * v - b * vp
+        a = w @ v
+        w -= a * v
+        b = np.linalg.norm(w)
+        d.append(a)
+        e.append(b)
+        vp, v = v, w / b
+    return np.array(d), np.array(e[:-1])
+
+
 def test_quadrature_matches_the_oracle(harness):
     rng = np.random.default_rng(4)
     cases = _pcg_tridiagonals()
@@ -67,6 +89,7 @@ def test_quadrature_matches_the_oracle(harness):
     e[7] = 0.0                                                     # splits into two blocks
     cases.append((d, e))
     cases.append((np.full(10, 2.0), np.full(9, 1e-20)))           # clustered, deflates at once
+    cases.append(_plain_lanczos(519, 3e3, 5))                      # ghosts of converged Ritz values
     got, bad = harness(cases)
     for (d, e), g, b in zip(cases, got, bad):
         ref = krylov.quad_log(d, e, 1.0)

@@ -67,6 +67,14 @@ def test_gamma_refusals():
     for a in (0.0, -1.0, float("nan")):
         with pytest.raises(vl.VLError):
             fac.find_mode(vl.LIK_GAMMA_LOG, P.y, P.F, vl.Opts.make(lik_shape=a))
+    # a response outside the gamma support (y <= 0, or not finite) is refused before Newton,
+    # naming its caller index
+    for bad in (0.0, -2.0, float("inf")):
+        y = P.y.copy()
+        y[5] = bad
+        with pytest.raises(vl.VLError) as e:
+            fac.find_mode(vl.LIK_GAMMA_LOG, y, P.F, vl.Opts.make(lik_shape=P.xi))
+        assert e.value.status == 1 and "y[5]" in str(e.value), str(e.value)
     st = fac.find_mode(vl.LIK_GAMMA_LOG, P.y, P.F, vl.Opts.make(lik_shape=P.xi, **FP64_TIGHT))
     with pytest.raises(vl.VLError):
         st.lml_grad(vl.Opts.make(t=8, lik_shape=P.xi))
