@@ -755,12 +755,17 @@ struct Engine {
   // out[k * t + c] = sum over segment k's rows of w_s X[s,c] Y[s,c]
   vl_status coldot(const T* X, const T* Y, const T* w, double* out) {
     ProfScope ps(c, "coldot", t);
-    coldot_kernel<T><<<nblk, cb, csh, VL_STREAM(c)>>>(br, t, ld, X, Y, w, partial, tail(EPI_NONE, out));
+    if (vec_sweeps())
+      coldot_vec_kernel<T><<<nblk, 1024, vsh(), VL_STREAM(c)>>>(br, t, ld, X, Y, w, partial, tail(EPI_NONE, out));
+    else
+      coldot_kernel<T><<<nblk, cb, csh, VL_STREAM(c)>>>(br, t, ld, X, Y, w, partial, tail(EPI_NONE, out));
     VL_CUDA(c, cudaGetLastError());
     return VL_OK;
   }
 
   int spmv_grid() const { return std::max(1, std::min((n + 7) / 8, c->num_sms * 8)); }
+  // blocks of the contiguous-range products: per_sm blocks per SM, at least 64 rows each
+  int spmv_chunks(int per_sm) const { return std::max(1, std::min((n + 63) / 64, c->num_sms * per_sm)); }
 
   // Y = ys o (B X)
   vl_status opB(const T* X, const T* ys, T* Yo) {
@@ -768,10 +773,18 @@ struct Engine {
     if (t == 1) {
       spmv_B_t1_kernel<T, 8><<<spmv_grid(), 256, 0, VL_STREAM(c)>>>(n, m, f->nbr, Aval, X, ys, Yo);
     } else {
-      with_shape<T>(ld, [&](auto L, auto N, auto U) {
-        spmv_B_kernel<T, decltype(L)::value, decltype(N)::value, decltype(U)::value>
-            <<<spmv_grid(), 256, 0, VL_STREAM(c)>>>(n, m, f->nbr, Aval, X, ld, ys, Yo);
-        return VL_OK;
+      // candidates (the same numbers): teams interleaved over the grid, or one contiguous range
+      // of rows per block with 4 or 8 blocks per SM
+      return tuned(TuneKey{c->device, 4, (int)sizeof(T), ld, log2_bucket(n)}, 3, [&](int cand) {
+        return with_shape<T>(ld, [&](auto L, auto N, auto U) {
+          constexpr int LPV = decltype(L)::value, NV = decltype(N)::value, UNR = decltype(U)::value;
+          if (cand == 0)
+            spmv_B_kernel<T, LPV, NV, UNR, 0><<<spmv_grid(), 256, 0, VL_STREAM(c)>>>(n, m, f->nbr, Aval, X, ld, ys, Yo);
+          else
+            spmv_B_kernel<T, LPV, NV, UNR, 1><<<spmv_chunks(cand == 1 ? 4 : 8), 256, 0, VL_STREAM(c)>>>(
+                n, m, f->nbr, Aval, X, ld, ys, Yo);
+          return cuda_ok(c, cudaGetLastError());
+        });
       });
     }
     VL_CUDA(c, cudaGetLastError());
@@ -783,10 +796,17 @@ struct Engine {
     if (t == 1) {
       spmv_Bt_t1_kernel<T, 8><<<spmv_grid(), 256, 0, VL_STREAM(c)>>>(n, f->rowptrT, f->colT, valT, Y, ys, X, wx, Zo);
     } else {
-      with_shape<T>(ld, [&](auto L, auto N, auto U) {
-        spmv_Bt_kernel<T, decltype(L)::value, decltype(N)::value, decltype(U)::value>
-            <<<spmv_grid(), 256, 0, VL_STREAM(c)>>>(n, f->rowptrT, f->colT, valT, Y, ys, X, wx, ld, Zo);
-        return VL_OK;
+      return tuned(TuneKey{c->device, 5, (int)sizeof(T), ld, log2_bucket(n)}, 3, [&](int cand) {
+        return with_shape<T>(ld, [&](auto L, auto N, auto U) {
+          constexpr int LPV = decltype(L)::value, NV = decltype(N)::value, UNR = decltype(U)::value;
+          if (cand == 0)
+            spmv_Bt_kernel<T, LPV, NV, UNR, 0><<<spmv_grid(), 256, 0, VL_STREAM(c)>>>(n, f->rowptrT, f->colT, valT,
+                                                                                    Y, ys, X, wx, ld, Zo);
+          else
+            spmv_Bt_kernel<T, LPV, NV, UNR, 1><<<spmv_chunks(cand == 1 ? 4 : 8), 256, 0, VL_STREAM(c)>>>(
+                n, f->rowptrT, f->colT, valT, Y, ys, X, wx, ld, Zo);
+          return cuda_ok(c, cudaGetLastError());
+        });
       });
     }
     VL_CUDA(c, cudaGetLastError());
@@ -1254,27 +1274,45 @@ struct Engine {
   // (fused into the h^T v reduction); u += alpha h, r -= alpha v with the stopping test
   // (fused into the ||r||^2 reduction); z = P^{-1} r; beta, T entries and freezing (fused into
   // the r^T z reduction); h = z + beta h.
+  // block vectors use the 16-byte-word sweeps (VecSweep) when a row has at most 64 words
+  bool vec_sweeps() const { return t > 1 && ld % 8 == 0 && ld / VecT<T>::n <= 64; }
+  size_t vsh() const { return sizeof(double) * 1024 * VecT<T>::n; }
+
   vl_status pcg_step(T* U, double tol2, int max_iter) {
     VL_TRY(opSys(h, v));
     {
       ProfScope ps(c, "coldot", t);
-      coldot_kernel<T><<<nblk, cb, csh, VL_STREAM(c)>>>(br, t, ld, h, v, nullptr, partial, tail(EPI_ALPHA));
+      if (vec_sweeps())
+        coldot_vec_kernel<T><<<nblk, 1024, vsh(), VL_STREAM(c)>>>(br, t, ld, h, v, nullptr, partial, tail(EPI_ALPHA));
+      else
+        coldot_kernel<T><<<nblk, cb, csh, VL_STREAM(c)>>>(br, t, ld, h, v, nullptr, partial, tail(EPI_ALPHA));
     }
     {
       ProfScope ps(c, "pcg_update", t);
-      pcg_update1_kernel<T><<<nblk, cb, csh, VL_STREAM(c)>>>(br, t, ld, U, r, h, v, partial,
-                                                              tail(EPI_STOP, nullptr, tol2));
+      if (vec_sweeps())
+        pcg_update1_vec_kernel<T><<<nblk, 1024, vsh(), VL_STREAM(c)>>>(br, t, ld, U, r, h, v, partial,
+                                                                        tail(EPI_STOP, nullptr, tol2));
+      else
+        pcg_update1_kernel<T><<<nblk, cb, csh, VL_STREAM(c)>>>(br, t, ld, U, r, h, v, partial,
+                                                                tail(EPI_STOP, nullptr, tol2));
     }
     VL_CUDA(c, cudaGetLastError());
     VL_TRY(opPinv(r, z));
     {
       ProfScope ps(c, "coldot", t);
-      coldot_kernel<T><<<nblk, cb, csh, VL_STREAM(c)>>>(br, t, ld, r, z, nullptr, partial,
-                                                         tail(EPI_BETA, nullptr, 0.0, max_iter));
+      if (vec_sweeps())
+        coldot_vec_kernel<T><<<nblk, 1024, vsh(), VL_STREAM(c)>>>(br, t, ld, r, z, nullptr, partial,
+                                                                   tail(EPI_BETA, nullptr, 0.0, max_iter));
+      else
+        coldot_kernel<T><<<nblk, cb, csh, VL_STREAM(c)>>>(br, t, ld, r, z, nullptr, partial,
+                                                           tail(EPI_BETA, nullptr, 0.0, max_iter));
     }
     {
       ProfScope ps(c, "pcg_update", t);
-      pcg_update2_kernel<T><<<nblk, cb, 0, VL_STREAM(c)>>>(br, t, ld, S.beta, S.active, z, h);
+      if (vec_sweeps())
+        pcg_update2_vec_kernel<T><<<nblk, 1024, 0, VL_STREAM(c)>>>(br, t, ld, S.beta, S.active, z, h);
+      else
+        pcg_update2_kernel<T><<<nblk, cb, 0, VL_STREAM(c)>>>(br, t, ld, S.beta, S.active, z, h);
     }
     VL_CUDA(c, cudaGetLastError());
     return VL_OK;

@@ -183,15 +183,39 @@ __device__ __forceinline__ T team_dot1(const int32_t* __restrict__ idx, const T*
 
 // ----------------------------------------------------------------------------- B X
 // Y_s = ys_s (X_s - sum_c A[s,c] X_{nbr[s,c]})   (ys == nullptr: 1)
-template <typename T, int LPV, int NV, int UNR>
+// Rows of a product kernel's team: CH = 0 interleaves the teams of the whole grid over the rows;
+// CH = 1 gives each block one contiguous range of rows, so that the neighbour rows it gathers
+// (near in Morton order) are reused from the SM's L1 across the range. Either way each row is
+// one team's, so the results are the same.
+template <int CH>
+struct TeamRows {
+  int s, end, step;
+  template <int LPV>
+  __device__ __forceinline__ static TeamRows make(int n) {
+    constexpr int RPW = 32 / LPV;
+    TeamRows r;
+    if (CH == 0) {
+      r.s = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * RPW + (threadIdx.x & 31) / LPV;
+      r.end = n;
+      r.step = ((gridDim.x * blockDim.x) >> 5) * RPW;
+    } else {
+      const int per = (n + gridDim.x - 1) / gridDim.x;
+      const int b0 = blockIdx.x * per;
+      r.s = b0 + (threadIdx.x >> 5) * RPW + (threadIdx.x & 31) / LPV;
+      r.end = min(n, b0 + per);
+      r.step = (blockDim.x >> 5) * RPW;
+    }
+    return r;
+  }
+};
+
+template <typename T, int LPV, int NV, int UNR, int CH = 0>
 __global__ void __launch_bounds__(256) spmv_B_kernel(int n, int m, const int32_t* __restrict__ nbr,
                                                      const T* __restrict__ A, const T* __restrict__ X, int ld,
                                                      const T* __restrict__ ys, T* __restrict__ Y) {
-  constexpr int RPW = 32 / LPV;
-  const int G = ((gridDim.x * blockDim.x) >> 5) * RPW;
-  const int g = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * RPW + (threadIdx.x & 31) / LPV;
+  const TeamRows<CH> rows = TeamRows<CH>::template make<LPV>(n);
   T acc[NV * VecT<T>::n];
-  for (int s = g; s < n; s += G) {
+  for (int s = rows.s; s < rows.end; s += rows.step) {
     team_init<T, LPV, NV>(acc, s, ld, T(1), X, T(0), nullptr);
     team_gather<T, LPV, NV, UNR, false>(acc, nbr, A, nullptr, T(-1), s * m, s * m + m, X, ld, nullptr, s);
     team_store<T, LPV, NV>(Y, s, ld, ys ? ys[s] : T(1), acc);
@@ -214,17 +238,15 @@ __global__ void __launch_bounds__(256) spmv_B_t1_kernel(int n, int m, const int3
 // ----------------------------------------------------------------------------- W X + B^T Y
 // Z_s = wx_s X_s + ys_s Y_s - sum_{e in row s of B^T} valT[e] ys_{i} Y_{i},  i = colT[e]
 // (X == nullptr: no diagonal term; ys == nullptr: 1)
-template <typename T, int LPV, int NV, int UNR>
+template <typename T, int LPV, int NV, int UNR, int CH = 0>
 __global__ void __launch_bounds__(256) spmv_Bt_kernel(int n, const int32_t* __restrict__ rowptrT,
                                                       const int32_t* __restrict__ colT, const T* __restrict__ valT,
                                                       const T* __restrict__ Y, const T* __restrict__ ys,
                                                       const T* __restrict__ X, const T* __restrict__ wx, int ld,
                                                       T* __restrict__ Z) {
-  constexpr int RPW = 32 / LPV;
-  const int G = ((gridDim.x * blockDim.x) >> 5) * RPW;
-  const int g = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * RPW + (threadIdx.x & 31) / LPV;
+  const TeamRows<CH> rows = TeamRows<CH>::template make<LPV>(n);
   T acc[NV * VecT<T>::n];
-  for (int s = g; s < n; s += G) {
+  for (int s = rows.s; s < rows.end; s += rows.step) {
     team_init<T, LPV, NV>(acc, s, ld, ys ? ys[s] : T(1), Y, X ? wx[s] : T(0), X);
     team_gather<T, LPV, NV, UNR, false>(acc, colT, valT, ys, T(-1), rowptrT[s], rowptrT[s + 1], Y, ld, nullptr, s);
     team_store<T, LPV, NV>(Z, s, ld, T(1), acc);
@@ -1457,6 +1479,229 @@ __global__ void pcg_update2_kernel(BlockRows br, int t, int ld, const double* __
   for (int s = br.row0(blockIdx.x) + threadIdx.y; s < r1; s += blockDim.y) {
     const int64_t o = (int64_t)s * ld + c;
     h[o] = z[o] + bt * h[o];
+  }
+}
+
+// ----------------------------------------------------------------------------- vector sweeps
+// The column sweeps of block vectors (t > 1, ld a multiple of 8) with 16-byte loads: a thread
+// holds one float4 / double2 word of a row (CX words per row, CX the power of two covering
+// ld / VEC), a 1024-thread block sweeps 1024 / CX rows at a time, two rows per thread in flight.
+// Per-word column sums are float32 partials of 16 rows flushed to float64 (float64 data: float64
+// throughout), then a fixed tree over the block's row lanes in shared memory (1024 * VEC doubles),
+// so the result does not depend on scheduling. The scalar (t = 1) sweeps keep the kernels above.
+template <typename T>
+struct VecSweep {
+  static constexpr int VEC = VecT<T>::n;
+  int cx, ry, w, y;   // words per row lane group, rows per sweep, this thread's word and row lane
+  __device__ __forceinline__ VecSweep(int ld) {
+    const int nw = ld / VEC;
+    cx = nw <= 8 ? 8 : (nw <= 16 ? 16 : (nw <= 32 ? 32 : 64));
+    ry = blockDim.x / cx;
+    w = threadIdx.x % cx;
+    y = threadIdx.x / cx;
+  }
+};
+
+// acc[i] of every thread (its word's VEC columns) -> column sums over the block's row lanes into
+// partial[blockIdx.x * t + c] for c < t. Every thread calls it.
+template <typename T>
+__device__ __forceinline__ void vec_block_sums(const VecSweep<T>& V, const double* acc, int t, double* sh,
+                                               double* __restrict__ partial) {
+  constexpr int VEC = VecSweep<T>::VEC;
+  const int width = V.cx * VEC;
+#pragma unroll
+  for (int i = 0; i < VEC; ++i) sh[V.y * width + V.w * VEC + i] = acc[i];
+  __syncthreads();
+  for (int hh = V.ry >> 1; hh > 0; hh >>= 1) {
+    if (V.y < hh)
+#pragma unroll
+      for (int i = 0; i < VEC; ++i) sh[V.y * width + V.w * VEC + i] += sh[(V.y + hh) * width + V.w * VEC + i];
+    __syncthreads();
+  }
+  for (int c = threadIdx.x; c < t; c += blockDim.x) partial[(int64_t)blockIdx.x * t + c] = sh[c];
+  __threadfence();
+}
+
+template <typename T>
+__device__ __forceinline__ typename VecT<T>::type ld_word(const T* p) {
+  return *reinterpret_cast<const typename VecT<T>::type*>(p);
+}
+template <typename T>
+__device__ __forceinline__ void st_word(T* p, const T* a) {
+  store_vec(p, a);
+}
+__device__ __forceinline__ void unpack(float4 v, float* a) {
+  a[0] = v.x; a[1] = v.y; a[2] = v.z; a[3] = v.w;
+}
+__device__ __forceinline__ void unpack(double2 v, double* a) {
+  a[0] = v.x; a[1] = v.y;
+}
+
+// partial[b * t + c] = sum over block b's rows of w_s X[s,c] Y[s,c] (w == nullptr: 1), then the
+// last block's reduce_tail (as coldot_kernel).
+template <typename T>
+__global__ void __launch_bounds__(1024, 1) coldot_vec_kernel(BlockRows br, int t, int ld, const T* __restrict__ X,
+                                                             const T* __restrict__ Y, const T* __restrict__ w,
+                                                             double* __restrict__ partial, ReduceTail rt) {
+  constexpr int VEC = VecT<T>::n;
+  extern __shared__ double sh[];
+  const VecSweep<T> V(ld);
+  const int r0 = br.row0(blockIdx.x), r1 = br.row1(blockIdx.x);
+  double acc[VEC];
+  T part[VEC];
+#pragma unroll
+  for (int i = 0; i < VEC; ++i) acc[i] = 0.0, part[i] = T(0);
+  if (V.w * VEC < ld) {
+    const int col = V.w * VEC;
+    int cntf = 0;
+    for (int s = r0 + V.y; s < r1; s += 2 * V.ry) {
+      const int s2 = s + V.ry;
+      const bool two = s2 < r1;
+      T x0[VEC], y0[VEC], x1[VEC], y1[VEC];
+      unpack(ld_word(X + (int64_t)s * ld + col), x0);
+      unpack(ld_word(Y + (int64_t)s * ld + col), y0);
+      if (two) {
+        unpack(ld_word(X + (int64_t)s2 * ld + col), x1);
+        unpack(ld_word(Y + (int64_t)s2 * ld + col), y1);
+      }
+      const T w0 = w ? w[s] : T(1), w1 = (w && two) ? w[s2] : T(1);
+#pragma unroll
+      for (int i = 0; i < VEC; ++i) {
+        part[i] += w0 * x0[i] * y0[i];
+        if (two) part[i] += w1 * x1[i] * y1[i];
+      }
+      cntf += two ? 2 : 1;
+      if (cntf >= 16) {
+#pragma unroll
+        for (int i = 0; i < VEC; ++i) acc[i] += (double)part[i], part[i] = T(0);
+        cntf = 0;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < VEC; ++i) acc[i] += (double)part[i];
+  }
+  vec_block_sums<T>(V, acc, t, sh, partial);
+  reduce_tail(br, t, partial, rt);
+}
+
+// u += alpha h, r -= alpha v (alpha = 0 for frozen and padding columns) with ||r||^2 partials,
+// then the stopping test in the last block (as pcg_update1_kernel).
+template <typename T>
+__global__ void __launch_bounds__(1024, 1) pcg_update1_vec_kernel(BlockRows br, int t, int ld, T* __restrict__ u,
+                                                                  T* __restrict__ r, const T* __restrict__ h,
+                                                                  const T* __restrict__ v,
+                                                                  double* __restrict__ partial, ReduceTail rt) {
+  constexpr int VEC = VecT<T>::n;
+  extern __shared__ double sh[];
+  const VecSweep<T> V(ld);
+  const int r0 = br.row0(blockIdx.x), r1 = br.row1(blockIdx.x);
+  const int k = br.segment(blockIdx.x);
+  double acc[VEC];
+  T part[VEC];
+#pragma unroll
+  for (int i = 0; i < VEC; ++i) acc[i] = 0.0, part[i] = T(0);
+  if (V.w * VEC < ld) {
+    const int col = V.w * VEC;
+    T a[VEC];
+    bool any = false;
+#pragma unroll
+    for (int i = 0; i < VEC; ++i) {
+      a[i] = col + i < t ? (T)rt.S.alpha[k * t + col + i] : T(0);
+      any = any || a[i] != T(0);
+    }
+    int cntf = 0;
+    for (int s = r0 + V.y; s < r1; s += 2 * V.ry) {
+      const int s2 = s + V.ry;
+      const bool two = s2 < r1;
+      const int64_t o0 = (int64_t)s * ld + col, o1 = (int64_t)s2 * ld + col;
+      T r0v[VEC], r1v[VEC];
+      unpack(ld_word(r + o0), r0v);
+      if (two) unpack(ld_word(r + o1), r1v);
+      if (any) {
+        T u0[VEC], h0[VEC], v0[VEC], u1[VEC], h1[VEC], v1[VEC];
+        unpack(ld_word(u + o0), u0);
+        unpack(ld_word(h + o0), h0);
+        unpack(ld_word(v + o0), v0);
+        if (two) {
+          unpack(ld_word(u + o1), u1);
+          unpack(ld_word(h + o1), h1);
+          unpack(ld_word(v + o1), v1);
+        }
+#pragma unroll
+        for (int i = 0; i < VEC; ++i) {
+          u0[i] += a[i] * h0[i];
+          r0v[i] -= a[i] * v0[i];
+          if (two) {
+            u1[i] += a[i] * h1[i];
+            r1v[i] -= a[i] * v1[i];
+          }
+        }
+        st_word(u + o0, u0);
+        st_word(r + o0, r0v);
+        if (two) {
+          st_word(u + o1, u1);
+          st_word(r + o1, r1v);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < VEC; ++i) {
+        part[i] += r0v[i] * r0v[i];
+        if (two) part[i] += r1v[i] * r1v[i];
+      }
+      cntf += two ? 2 : 1;
+      if (cntf >= 16) {
+#pragma unroll
+        for (int i = 0; i < VEC; ++i) acc[i] += (double)part[i], part[i] = T(0);
+        cntf = 0;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < VEC; ++i) acc[i] += (double)part[i];
+  }
+  vec_block_sums<T>(V, acc, t, sh, partial);
+  reduce_tail(br, t, partial, rt);
+}
+
+// h = z + beta h on active columns (as pcg_update2_kernel).
+template <typename T>
+__global__ void __launch_bounds__(1024, 1) pcg_update2_vec_kernel(BlockRows br, int t, int ld,
+                                                                  const double* __restrict__ beta,
+                                                                  const int* __restrict__ active,
+                                                                  const T* __restrict__ z, T* __restrict__ h) {
+  constexpr int VEC = VecT<T>::n;
+  const VecSweep<T> V(ld);
+  if (V.w * VEC >= ld) return;
+  const int col = V.w * VEC;
+  const int k = br.segment(blockIdx.x);
+  T bt[VEC];
+  bool act[VEC], any = false;
+#pragma unroll
+  for (int i = 0; i < VEC; ++i) {
+    const int c = col + i;
+    act[i] = c < t && active[k * t + c];
+    bt[i] = act[i] ? (T)beta[k * t + c] : T(0);
+    any = any || act[i];
+  }
+  if (!any) return;
+  const int r0 = br.row0(blockIdx.x), r1 = br.row1(blockIdx.x);
+  for (int s = r0 + V.y; s < r1; s += 2 * V.ry) {
+    const int s2 = s + V.ry;
+    const bool two = s2 < r1;
+    const int64_t o0 = (int64_t)s * ld + col, o1 = (int64_t)s2 * ld + col;
+    T z0[VEC], h0[VEC], z1[VEC], h1[VEC];
+    unpack(ld_word(z + o0), z0);
+    unpack(ld_word(h + o0), h0);
+    if (two) {
+      unpack(ld_word(z + o1), z1);
+      unpack(ld_word(h + o1), h1);
+    }
+#pragma unroll
+    for (int i = 0; i < VEC; ++i) {
+      if (act[i]) h0[i] = z0[i] + bt[i] * h0[i];
+      if (two && act[i]) h1[i] = z1[i] + bt[i] * h1[i];
+    }
+    st_word(h + o0, h0);
+    if (two) st_word(h + o1, h1);
   }
 }
 
