@@ -1217,12 +1217,15 @@ struct Engine {
     if (ld % 8 != 0) return fail(c, VL_ERR_STATE, "block solve with a row width that is not a multiple of 8");
     void* args[] = {&L, &mm, &idx, &val, &rp, &rhs, &q, &x, &l};
     // candidates (all give the same numbers): dependency rows in flight per lane (the shape's
-    // UNR or twice it) x blocks per SM (2 or 1)
-    return tuned(TuneKey{c->device, FWD ? 0 : 1, (int)sizeof(T), ld, log2_bucket(n)}, 5, [&](int cand) {
+    // UNR or twice it) x blocks per SM (2 or 1); clusters of 8 blocks; L2 prefetch of the next
+    // rows' dependencies before each level barrier, 2 or 1 blocks per SM
+    return tuned(TuneKey{c->device, FWD ? 0 : 1, (int)sizeof(T), ld, log2_bucket(n)}, 7, [&](int cand) {
       return with_shape<T>(ld, [&](auto Lc, auto N, auto U) {
         constexpr int LPV = decltype(Lc)::value, NV = decltype(N)::value, UNR = decltype(U)::value;
         if (cand == 4)   // clusters of 8 blocks with the two-stage barrier
           return launch((const void*)sptrsv_kernel<T, FWD, LPV, NV, 2 * UNR, 2>, args, LPV, 1, 8);
+        if (cand >= 5)
+          return launch((const void*)sptrsv_kernel<T, FWD, LPV, NV, UNR, 0, 1>, args, LPV, cand == 5 ? 2 : 1);
         const int bps = (cand & 1) ? 1 : 2;
         if (cand & 2) return launch((const void*)sptrsv_kernel<T, FWD, LPV, NV, 2 * UNR>, args, LPV, bps);
         return launch((const void*)sptrsv_kernel<T, FWD, LPV, NV, UNR>, args, LPV, bps);

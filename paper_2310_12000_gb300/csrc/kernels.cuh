@@ -415,10 +415,19 @@ struct RowPre {
   T acc[NV * VecT<T>::n];
 };
 
+// xpf != nullptr: the lane also asks L2 for the x row of the dependency it holds (every 128-byte
+// line of it). Issued before the level barrier, this turns the DRAM misses of the gathers after
+// it into L2 hits for the dependencies solved at earlier levels; a line a later level rewrites is
+// simply updated in L2, so a prefetch never makes a load see stale data.
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 template <typename T, bool FWD, int LPV, int NV>
 __device__ __forceinline__ void row_pre_s(RowPre<T, LPV, NV>& r, int s, int m, const int32_t* __restrict__ idx,
                                           const T* __restrict__ val, const int32_t* __restrict__ rowptr,
-                                          const T* __restrict__ rhs, const T* __restrict__ q, int ld) {
+                                          const T* __restrict__ rhs, const T* __restrict__ q, int ld,
+                                          const T* xpf = nullptr) {
   const int sl = (threadIdx.x & 31) % LPV;
   r.s = s;
   r.beg = FWD ? r.s * m : rowptr[r.s];
@@ -426,6 +435,12 @@ __device__ __forceinline__ void row_pre_s(RowPre<T, LPV, NV>& r, int s, int m, c
   const int e = r.beg + sl;
   r.jl = e < r.end ? idx[e] : -1;
   r.al = r.jl >= 0 ? val[e] : T(0);
+  if (xpf && r.jl >= 0) {
+    const char* row = reinterpret_cast<const char*>(xpf + (int64_t)r.jl * ld);
+    const int bytes = ld * (int)sizeof(T);
+    for (int o = 0; o < bytes; o += 128) prefetch_l2(row + o);
+    prefetch_l2(row + bytes - 1);
+  }
   team_init<T, LPV, NV>(r.acc, r.s, ld, q ? q[r.s] : T(1), rhs, T(0), nullptr);
 }
 
@@ -433,8 +448,8 @@ template <typename T, bool FWD, int LPV, int NV>
 __device__ __forceinline__ void row_pre(RowPre<T, LPV, NV>& r, int p, int m, const LevelPlan& L,
                                         const int32_t* __restrict__ idx, const T* __restrict__ val,
                                         const int32_t* __restrict__ rowptr, const T* __restrict__ rhs,
-                                        const T* __restrict__ q, int ld) {
-  row_pre_s<T, FWD, LPV, NV>(r, L.task[p], m, idx, val, rowptr, rhs, q, ld);
+                                        const T* __restrict__ q, int ld, const T* xpf = nullptr) {
+  row_pre_s<T, FWD, LPV, NV>(r, L.task[p], m, idx, val, rowptr, rhs, q, ld, xpf);
 }
 
 // Finishes a prefetched row: gathers its dependencies (first chunk already in
@@ -1037,7 +1052,7 @@ __global__ void __launch_bounds__(1024) sptrsv_cluster_kernel(LevelPlan L, int m
   if (tr) L.trace[L.nlev] = clock64();
 }
 
-template <typename T, bool FWD, int LPV, int NV, int UNR, int BAR = 0>
+template <typename T, bool FWD, int LPV, int NV, int UNR, int BAR = 0, int PF = 0>
 __global__ void __launch_bounds__(512) sptrsv_kernel(LevelPlan L, int m, const int32_t* __restrict__ idx,
                                                      const T* __restrict__ val, const int32_t* __restrict__ rowptr,
                                                      const T* __restrict__ rhs, const T* __restrict__ q, T* x, int ld) {
@@ -1045,7 +1060,7 @@ __global__ void __launch_bounds__(512) sptrsv_kernel(LevelPlan L, int m, const i
   T* part = reinterpret_cast<T*>(vl_smem);
   RowPre<T, LPV, NV> r;
   level_walk<LPV, BAR>(
-      L, [&](int p) { row_pre<T, FWD, LPV, NV>(r, p, m, L, idx, val, rowptr, rhs, q, ld); },
+      L, [&](int p) { row_pre<T, FWD, LPV, NV>(r, p, m, L, idx, val, rowptr, rhs, q, ld, PF ? x : nullptr); },
       [&]() { row_run<T, LPV, NV, UNR>(r, idx, val, x, ld); },
       [&](int p) { heavy_row<T, FWD, LPV, NV, UNR>(p, m, L, idx, val, rowptr, rhs, q, x, ld, part); },
       [&](const HeavyChunk& hc) { chunk_run<T, LPV, NV, UNR>(hc, L, idx, val, rhs, q, x, ld); });
