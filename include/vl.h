@@ -198,10 +198,11 @@ typedef enum vl_solve_form {
                            narrow leading and trailing levels in one block (the leading ones of
                            single-column forward solves with x in shared memory)           */
   VL_SOLVE_GRID_ALL = 4, /* cooperative grid with every level on the grid barrier         */
-  VL_SOLVE_TILE = 5      /* cooperative grid of storage-row tiles, one block each, walking
-                            its own rows level by level and waiting only for the progress
-                            of the tiles its rows depend on (t = 1: the tile's x in shared
-                            memory)                                                     */
+  VL_SOLVE_TILE = 5      /* cooperative grid of storage-row tiles, one block each; its teams
+                            take the tile's rows by level and each row waits only for its
+                            own dependencies (t = 1: the tile's x in shared memory). The
+                            automatic choice for backward single-column solves of systems
+                            above 262,144 rows                                          */
 } vl_solve_form;
 /* Sets the form for every later solve on this context (VL_ERR_INVALID_ARG for an
  * unknown form). A solve the forced form cannot run (VL_SOLVE_SHARED with too many

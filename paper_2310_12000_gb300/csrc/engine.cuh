@@ -264,6 +264,55 @@ inline vl_status tile_plan(Ctx* c, Factor* f, bool fwd, int G, int first, const 
   return VL_OK;
 }
 
+// Shared memory a staged product block uses for its rows (two blocks of 256 threads per SM).
+constexpr size_t kHaloBytes = 96 * 1024;
+
+// Plan of the staged products in one direction for rows of row_bytes bytes (build_halo_plan).
+inline vl_status halo_plan(Ctx* c, Factor* f, bool fwd, int row_bytes, const Factor::HaloPlan** out) {
+  const std::pair<int, int> key{fwd ? 1 : 0, row_bytes};
+  auto it = f->halo_plans.find(key);
+  if (it != f->halo_plans.end()) {
+    *out = &it->second;
+    return VL_OK;
+  }
+  const int n = (int)f->n, m = f->m;
+  std::vector<int32_t> nbr, rp, col;
+  if (fwd) {
+    nbr.resize((size_t)n * m);
+    if (m > 0)
+      VL_CUDA(c, cudaMemcpyAsync(nbr.data(), f->nbr, sizeof(int32_t) * nbr.size(), cudaMemcpyDeviceToHost, c->stream));
+  } else {
+    rp.resize(n + 1);
+    col.resize(std::max<int64_t>(f->nnz, 1));
+    VL_CUDA(c, cudaMemcpyAsync(rp.data(), f->rowptrT, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost, c->stream));
+    if (f->nnz > 0)
+      VL_CUDA(c, cudaMemcpyAsync(col.data(), f->colT, sizeof(int32_t) * f->nnz, cudaMemcpyDeviceToHost, c->stream));
+  }
+  VL_CUDA(c, cudaStreamSynchronize(c->stream));
+  Factor::HaloPlan plan;
+  plan.ucap = std::min<int>(65535, (int)(kHaloBytes / row_bytes));
+  const HaloPlanHost H = build_halo_plan(n, m, fwd ? nbr.data() : nullptr, fwd ? nullptr : rp.data(),
+                                         fwd ? nullptr : col.data(), plan.ucap, 512);
+  if (H.ok && n > 0) {
+    plan.nb = (int)H.brow.size() - 1;
+    auto up = [&](const void* h, size_t bytes, void** d) -> vl_status {
+      *d = f->mem.get<uint8_t>(std::max<size_t>(bytes, 16));
+      if (!*d) return fail(c, VL_ERR_OOM, "workspace exhausted (staged product plan)");
+      if (bytes) VL_CUDA(c, cudaMemcpyAsync(*d, h, bytes, cudaMemcpyHostToDevice, c->stream));
+      return VL_OK;
+    };
+    VL_TRY(up(H.brow.data(), sizeof(int32_t) * H.brow.size(), (void**)&plan.brow));
+    VL_TRY(up(H.uoff.data(), sizeof(int32_t) * H.uoff.size(), (void**)&plan.uoff));
+    VL_TRY(up(H.ulist.data(), sizeof(int32_t) * H.ulist.size(), (void**)&plan.ulist));
+    VL_TRY(up(H.lidx.data(), sizeof(uint16_t) * H.lidx.size(), (void**)&plan.lidx));
+    VL_TRY(up(H.lself.data(), sizeof(uint16_t) * H.lself.size(), (void**)&plan.lself));
+    VL_CUDA(c, cudaStreamSynchronize(c->stream));
+    plan.usable = true;
+  }
+  *out = &(f->halo_plans[key] = plan);
+  return VL_OK;
+}
+
 inline vl_status head_plan(Ctx* c, Factor* f, int l_head, const Factor::HeadPlan** out) {
   auto it = f->head_plans.find(l_head);
   if (it != f->head_plans.end()) {
@@ -775,9 +824,19 @@ struct Engine {
     } else {
       // candidates (the same numbers): teams interleaved over the grid, or one contiguous range
       // of rows per block with 4 or 8 blocks per SM
-      return tuned(TuneKey{c->device, 4, (int)sizeof(T), ld, log2_bucket(n)}, 3, [&](int cand) {
+      const Factor::HaloPlan* hp = nullptr;
+      VL_TRY(halo_plan(c, f, true, ld * (int)sizeof(T), &hp));
+      return tuned(TuneKey{c->device, 4, (int)sizeof(T), ld, log2_bucket(n)}, hp->usable ? 4 : 3, [&](int cand) {
         return with_shape<T>(ld, [&](auto L, auto N, auto U) {
           constexpr int LPV = decltype(L)::value, NV = decltype(N)::value, UNR = decltype(U)::value;
+          if (cand == 3 && hp->usable) {   // staged: the block's rows in shared memory
+            const void* fn = (const void*)spmv_B_staged_kernel<T, LPV, NV>;
+            VL_TRY(smem_limit_once(c, fn, kHaloBytes));
+            HaloArgs H{hp->brow, hp->uoff, hp->ulist, hp->lidx, hp->lself};
+            spmv_B_staged_kernel<T, LPV, NV><<<hp->nb, 256, (size_t)hp->ucap * ld * sizeof(T), VL_STREAM(c)>>>(
+                H, m, f->nbr, Aval, X, ld, ys, Yo);
+            return cuda_ok(c, cudaGetLastError());
+          }
           if (cand == 0)
             spmv_B_kernel<T, LPV, NV, UNR, 0><<<spmv_grid(), 256, 0, VL_STREAM(c)>>>(n, m, f->nbr, Aval, X, ld, ys, Yo);
           else
@@ -796,9 +855,19 @@ struct Engine {
     if (t == 1) {
       spmv_Bt_t1_kernel<T, 8><<<spmv_grid(), 256, 0, VL_STREAM(c)>>>(n, f->rowptrT, f->colT, valT, Y, ys, X, wx, Zo);
     } else {
-      return tuned(TuneKey{c->device, 5, (int)sizeof(T), ld, log2_bucket(n)}, 3, [&](int cand) {
+      const Factor::HaloPlan* hp = nullptr;
+      VL_TRY(halo_plan(c, f, false, ld * (int)sizeof(T), &hp));
+      return tuned(TuneKey{c->device, 5, (int)sizeof(T), ld, log2_bucket(n)}, hp->usable ? 4 : 3, [&](int cand) {
         return with_shape<T>(ld, [&](auto L, auto N, auto U) {
           constexpr int LPV = decltype(L)::value, NV = decltype(N)::value, UNR = decltype(U)::value;
+          if (cand == 3 && hp->usable) {   // staged: the block's rows in shared memory
+            const void* fn = (const void*)spmv_Bt_staged_kernel<T, LPV, NV>;
+            VL_TRY(smem_limit_once(c, fn, kHaloBytes));
+            HaloArgs H{hp->brow, hp->uoff, hp->ulist, hp->lidx, hp->lself};
+            spmv_Bt_staged_kernel<T, LPV, NV><<<hp->nb, 256, (size_t)hp->ucap * ld * sizeof(T), VL_STREAM(c)>>>(
+                H, f->rowptrT, f->colT, valT, Y, ys, X, wx, ld, Zo);
+            return cuda_ok(c, cudaGetLastError());
+          }
           if (cand == 0)
             spmv_Bt_kernel<T, LPV, NV, UNR, 0><<<spmv_grid(), 256, 0, VL_STREAM(c)>>>(n, f->rowptrT, f->colT, valT,
                                                                                     Y, ys, X, wx, ld, Zo);

@@ -222,6 +222,127 @@ __global__ void __launch_bounds__(256) spmv_B_kernel(int n, int m, const int32_t
   }
 }
 
+// Staged products (plan: build_halo_plan). Block b copies the rows of its list (its own rows and
+// their dependencies) into shared memory with coalesced 16-byte loads, then each team takes a row
+// of the block and accumulates exactly as team_gather does (entries in order, coefficient
+// sgn * val * dscale), reading the rows from shared memory: the same numbers as the unstaged
+// kernels.
+struct HaloArgs {
+  const int32_t* brow;
+  const int32_t* uoff;
+  const int32_t* ulist;
+  const uint16_t* lidx;
+  const uint16_t* lself;
+};
+
+template <typename T>
+__device__ __forceinline__ void halo_stage(const HaloArgs& H, int b, const T* __restrict__ X, int ld, T* xs) {
+  using V = typename VecT<T>::type;
+  constexpr int VEC = VecT<T>::n;
+  const int nw = ld / VEC;
+  const int u0 = H.uoff[b], U = H.uoff[b + 1] - u0;
+  V* dst = reinterpret_cast<V*>(xs);
+  for (int w = threadIdx.x; w < U * nw; w += blockDim.x) {
+    const int k = w / nw, v = w - k * nw;
+    dst[w] = ldg_vec(X + (int64_t)H.ulist[u0 + k] * ld + v * VEC);
+  }
+  __syncthreads();
+}
+
+// acc (the lane's words) += sum_e sgn * val[e] * dscale[j_e] * xs[lidx[e], :] over [beg, end)
+template <typename T, int LPV, int NV>
+__device__ __forceinline__ void halo_gather(T* acc, const HaloArgs& H, const int32_t* __restrict__ idx,
+                                            const T* __restrict__ val, const T* __restrict__ dscale, T sgn,
+                                            int64_t beg, int64_t end, const T* xs, int ld) {
+  constexpr int VEC = VecT<T>::n;
+  using V = typename VecT<T>::type;
+  const unsigned mask = team_mask<LPV>();
+  const int sl = (threadIdx.x & 31) % LPV;
+  for (int64_t e0 = beg; e0 < end; e0 += LPV) {
+    const int cnt = (int)min((int64_t)LPV, end - e0);
+    int jl = -1, pl = 0;
+    T al = T(0);
+    if (sl < cnt) {
+      jl = idx[e0 + sl];
+      if (jl >= 0) {
+        al = sgn * val[e0 + sl] * (dscale ? dscale[jl] : T(1));
+        pl = H.lidx[e0 + sl];
+      }
+    }
+    for (int q = 0; q < cnt; ++q) {
+      const int j = __shfl_sync(mask, jl, q, LPV);
+      const int pq = __shfl_sync(mask, pl, q, LPV);
+      const T a = __shfl_sync(mask, al, q, LPV);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const int col = (sl + LPV * v) * VEC;
+        const V xv = (j >= 0 && col < ld) ? *reinterpret_cast<const V*>(xs + (int64_t)pq * ld + col) : V{};
+        fma_vec(acc + v * VEC, j >= 0 ? a : T(0), xv);
+      }
+    }
+  }
+}
+
+template <typename T, int LPV, int NV>
+__global__ void __launch_bounds__(256) spmv_B_staged_kernel(HaloArgs H, int m, const int32_t* __restrict__ nbr,
+                                                            const T* __restrict__ A, const T* __restrict__ X, int ld,
+                                                            const T* __restrict__ ys, T* __restrict__ Y) {
+  extern __shared__ __align__(16) unsigned char vl_smem[];
+  T* xs = reinterpret_cast<T*>(vl_smem);
+  constexpr int RPW = 32 / LPV, VEC = VecT<T>::n;
+  const int b = blockIdx.x;
+  halo_stage<T>(H, b, X, ld, xs);
+  const int tpb = (blockDim.x >> 5) * RPW;
+  const int tib = (threadIdx.x >> 5) * RPW + (threadIdx.x & 31) / LPV;
+  const int sl = (threadIdx.x & 31) % LPV;
+  T acc[NV * VEC];
+  for (int s = H.brow[b] + tib; s < H.brow[b + 1]; s += tpb) {
+    const int ps = H.lself[s];
+#pragma unroll
+    for (int i = 0; i < NV * VEC; ++i) acc[i] = T(0);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const int col = (sl + LPV * v) * VEC;
+      if (col < ld) fma_vec(acc + v * VEC, T(1), *reinterpret_cast<const typename VecT<T>::type*>(xs + (int64_t)ps * ld + col));
+    }
+    halo_gather<T, LPV, NV>(acc, H, nbr, A, nullptr, T(-1), (int64_t)s * m, (int64_t)s * m + m, xs, ld);
+    team_store<T, LPV, NV>(Y, s, ld, ys ? ys[s] : T(1), acc);
+  }
+}
+
+template <typename T, int LPV, int NV>
+__global__ void __launch_bounds__(256) spmv_Bt_staged_kernel(HaloArgs H, const int32_t* __restrict__ rowptrT,
+                                                             const int32_t* __restrict__ colT,
+                                                             const T* __restrict__ valT, const T* __restrict__ Y,
+                                                             const T* __restrict__ ys, const T* __restrict__ X,
+                                                             const T* __restrict__ wx, int ld, T* __restrict__ Z) {
+  extern __shared__ __align__(16) unsigned char vl_smem[];
+  T* xs = reinterpret_cast<T*>(vl_smem);
+  constexpr int RPW = 32 / LPV, VEC = VecT<T>::n;
+  const int b = blockIdx.x;
+  halo_stage<T>(H, b, Y, ld, xs);
+  const int tpb = (blockDim.x >> 5) * RPW;
+  const int tib = (threadIdx.x >> 5) * RPW + (threadIdx.x & 31) / LPV;
+  const int sl = (threadIdx.x & 31) % LPV;
+  T acc[NV * VEC];
+  for (int s = H.brow[b] + tib; s < H.brow[b + 1]; s += tpb) {
+    const int ps = H.lself[s];
+    const T s1 = ys ? ys[s] : T(1), s2 = X ? wx[s] : T(0);
+#pragma unroll
+    for (int i = 0; i < NV * VEC; ++i) acc[i] = T(0);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const int col = (sl + LPV * v) * VEC;
+      if (col < ld) {
+        fma_vec(acc + v * VEC, s1, *reinterpret_cast<const typename VecT<T>::type*>(xs + (int64_t)ps * ld + col));
+        if (X) fma_vec(acc + v * VEC, s2, ldg_vec(X + (int64_t)s * ld + col));
+      }
+    }
+    halo_gather<T, LPV, NV>(acc, H, colT, valT, ys, T(-1), rowptrT[s], rowptrT[s + 1], xs, ld);
+    team_store<T, LPV, NV>(Z, s, ld, T(1), acc);
+  }
+}
+
 template <typename T, int LPV>
 __global__ void __launch_bounds__(256) spmv_B_t1_kernel(int n, int m, const int32_t* __restrict__ nbr,
                                                         const T* __restrict__ A, const T* __restrict__ X,

@@ -191,6 +191,18 @@ struct Factor {
     int epoch = 0;
   };
   std::map<std::tuple<int, int, int>, TilePlan> tile_plans;   // (forward, G, first listed task)
+  // staged products (spmv_*_staged_kernel): row blocks and the rows each reads, per (forward,
+  // bytes per row); usable = false when some row reads more rows than shared memory holds
+  struct HaloPlan {
+    int nb = 0, ucap = 0;
+    bool usable = false;
+    int32_t* brow = nullptr;
+    int32_t* uoff = nullptr;
+    int32_t* ulist = nullptr;
+    uint16_t* lidx = nullptr;
+    uint16_t* lself = nullptr;
+  };
+  std::map<std::pair<int, int>, HaloPlan> halo_plans;
   // LRAC (Section 3.1.2): rank-k pivoted Cholesky factor of Sigma, built on first use
   // and dropped when the covariance parameters change
   Owned lrac_mem;

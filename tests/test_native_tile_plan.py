@@ -60,3 +60,30 @@ def test_tile_walk_covers_every_dependency_and_never_stalls(exe, n, m, G):
         inp = f"{n} {m} {G} {seed}\n" + " ".join(map(str, nbr.ravel())) + "\n"
         r = subprocess.run([str(exe)], input=inp, capture_output=True, text=True, timeout=120)
         assert r.returncode == 0 and r.stdout.split() == ["fwd", "ok", "bwd", "ok"] * 3, r.stdout + r.stderr
+
+
+@pytest.fixture(scope="module")
+def halo_exe(tmp_path_factory):
+    out = tmp_path_factory.mktemp("halo") / "halo_plan_host"
+    r = subprocess.run(["g++", "-O2", "-std=c++17", "-I", CSRC, os.path.join(HERE, "native", "halo_plan_host.cpp"),
+                        "-o", str(out)], capture_output=True, text=True)
+    if r.returncode != 0:
+        pytest.fail(r.stdout + r.stderr)
+    return out
+
+
+@pytest.mark.parametrize("n,m,ucap,rmax", [(1500, 10, 438, 512), (2500, 20, 219, 512), (3000, 30, 100, 64),
+                                           (500, 5, 8, 3), (40, 0, 4, 512)])
+def test_staged_product_plan_places_every_row(halo_exe, n, m, ucap, rmax):
+    """The staged products' plan (build_halo_plan): blocks cover the rows in order within the row
+    and shared-memory limits, and every own row and dependency entry finds its row in the block's
+    list. A limit too small for a row's dependencies is refused (the products then stay unstaged)."""
+    nbr = _neighbours(n, m, seed=n + m)
+    inp = f"{n} {m} {ucap} {rmax}\n" + " ".join(map(str, nbr.ravel())) + "\n"
+    r = subprocess.run([str(halo_exe)], input=inp, capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stdout + r.stderr
+    out = r.stdout.split("\n")
+    assert out[0] == "fwd ok" or (out[0] == "fwd refused" and m + 1 > ucap), r.stdout
+    assert out[1] == "bwd ok" or out[1] == "bwd refused", r.stdout
+    if ucap >= 200:
+        assert out[:2] == ["fwd ok", "bwd ok"], r.stdout
