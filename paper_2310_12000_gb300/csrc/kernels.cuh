@@ -235,17 +235,20 @@ struct HaloArgs {
   const uint16_t* lself;
 };
 
+// The block's rows into shared memory by asynchronous 16-byte copies (cp.async: every copy of
+// the thread in flight at once, no registers held), then a wait and a block barrier.
 template <typename T>
 __device__ __forceinline__ void halo_stage(const HaloArgs& H, int b, const T* __restrict__ X, int ld, T* xs) {
-  using V = typename VecT<T>::type;
   constexpr int VEC = VecT<T>::n;
   const int nw = ld / VEC;
   const int u0 = H.uoff[b], U = H.uoff[b + 1] - u0;
-  V* dst = reinterpret_cast<V*>(xs);
+  const unsigned base = (unsigned)__cvta_generic_to_shared(xs);
   for (int w = threadIdx.x; w < U * nw; w += blockDim.x) {
     const int k = w / nw, v = w - k * nw;
-    dst[w] = ldg_vec(X + (int64_t)H.ulist[u0 + k] * ld + v * VEC);
+    const T* src = X + (int64_t)H.ulist[u0 + k] * ld + v * VEC;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(base + 16u * (unsigned)w), "l"(src) : "memory");
   }
+  asm volatile("cp.async.wait_all;" ::: "memory");
   __syncthreads();
 }
 
