@@ -567,15 +567,8 @@ inline vl_status slq_run(State* st, const vl_opts* o, SlqOut& out) {
   } else {
     VL_TRY(E.opBt(Rm, sc, nullptr, nullptr, Zm));
   }
-  // float32 Krylov: the recursive residual of a float32 PCG keeps falling after the true one has
-  // stalled near 1e-5 (rounding of the float32 products), so iterating it down to cg_tol buys
-  // nothing the float64 correction solves below do not have to do again. The float32 walk stops
-  // at 10 cg_tol; the Lanczos quadrature of those coefficients has long converged there (the
-  // paper evaluates likelihoods at a tolerance of 1e-2), and probe_residuals then refines every
-  // probe solve to a float64 residual <= cg_tol.
-  const double tol_main = std::is_same<T, float>::value ? std::min(1e-2, 10.0 * o->cg_tol) : o->cg_tol;
   int used = 0;
-  VL_TRY(E.pcg(Zm, Um, tol_main, o->cg_max_iter, &used));
+  VL_TRY(E.pcg(Zm, Um, o->cg_tol, o->cg_max_iter, &used));
   VL_CUDA(c, cudaMemsetAsync(bad, 0, sizeof(int), c->stream));
   {
     // the node range of every column, then every (column, node) in its own thread, then the
@@ -596,7 +589,7 @@ inline vl_status slq_run(State* st, const vl_opts* o, SlqOut& out) {
   VL_TRY(to_host(c, out.gam, (const double*)gdev, (size_t)ncol));
   if (hbad[0]) return fail(c, VL_ERR_NOT_CONVERGED, "SLQ: a Lanczos tridiagonal is not positive definite (non-positive Ritz value)");
   for (int q = 0; q < ncol; ++q)
-    if (out.relres[q] > tol_main && out.iters[q] >= o->cg_max_iter)
+    if (out.relres[q] > o->cg_tol && out.iters[q] >= o->cg_max_iter)
       return fail(c, VL_ERR_NOT_CONVERGED, "SLQ probe solves reached cg_max_iter");
   out.logdetC = (o->precond == VL_PREC_LRAC) ? E.logdetC : 0.0;
   return probe_residuals<T>(st, o, E, Rm, Zm, Um, r1, out.true_rel, out.passes, &out.extra_iters);
