@@ -826,16 +826,9 @@ struct Engine {
       // of rows per block with 4 or 8 blocks per SM
       const Factor::HaloPlan* hp = nullptr;
       VL_TRY(halo_plan(c, f, true, ld * (int)sizeof(T), &hp));
-      // candidate 4: the interleaved rows with at most 40 registers a thread (6 blocks of 256 per
-      // SM instead of 5: more warps to hide the gathers' latency)
-      return tuned(TuneKey{c->device, 4, (int)sizeof(T), ld, log2_bucket(n)}, 5, [&](int cand) {
+      return tuned(TuneKey{c->device, 4, (int)sizeof(T), ld, log2_bucket(n)}, hp->usable ? 4 : 3, [&](int cand) {
         return with_shape<T>(ld, [&](auto L, auto N, auto U) {
           constexpr int LPV = decltype(L)::value, NV = decltype(N)::value, UNR = decltype(U)::value;
-          if (cand == 4) {
-            spmv_B_kernel<T, LPV, NV, UNR, 0, 6><<<spmv_grid(), 256, 0, VL_STREAM(c)>>>(n, m, f->nbr, Aval, X, ld, ys,
-                                                                                       Yo);
-            return cuda_ok(c, cudaGetLastError());
-          }
           if (cand == 3 && hp->usable) {   // staged: the block's rows in shared memory
             const void* fn = (const void*)spmv_B_staged_kernel<T, LPV, NV>;
             VL_TRY(smem_limit_once(c, fn, kHaloBytes));
@@ -864,14 +857,9 @@ struct Engine {
     } else {
       const Factor::HaloPlan* hp = nullptr;
       VL_TRY(halo_plan(c, f, false, ld * (int)sizeof(T), &hp));
-      return tuned(TuneKey{c->device, 5, (int)sizeof(T), ld, log2_bucket(n)}, 5, [&](int cand) {
+      return tuned(TuneKey{c->device, 5, (int)sizeof(T), ld, log2_bucket(n)}, hp->usable ? 4 : 3, [&](int cand) {
         return with_shape<T>(ld, [&](auto L, auto N, auto U) {
           constexpr int LPV = decltype(L)::value, NV = decltype(N)::value, UNR = decltype(U)::value;
-          if (cand == 4) {
-            spmv_Bt_kernel<T, LPV, NV, UNR, 0, 6><<<spmv_grid(), 256, 0, VL_STREAM(c)>>>(
-                n, f->rowptrT, f->colT, valT, Y, ys, X, wx, ld, Zo);
-            return cuda_ok(c, cudaGetLastError());
-          }
           if (cand == 3 && hp->usable) {   // staged: the block's rows in shared memory
             const void* fn = (const void*)spmv_Bt_staged_kernel<T, LPV, NV>;
             VL_TRY(smem_limit_once(c, fn, kHaloBytes));

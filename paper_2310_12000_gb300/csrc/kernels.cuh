@@ -209,8 +209,8 @@ struct TeamRows {
   }
 };
 
-template <typename T, int LPV, int NV, int UNR, int CH = 0, int MINB = 1>
-__global__ void __launch_bounds__(256, MINB) spmv_B_kernel(int n, int m, const int32_t* __restrict__ nbr,
+template <typename T, int LPV, int NV, int UNR, int CH = 0>
+__global__ void __launch_bounds__(256) spmv_B_kernel(int n, int m, const int32_t* __restrict__ nbr,
                                                      const T* __restrict__ A, const T* __restrict__ X, int ld,
                                                      const T* __restrict__ ys, T* __restrict__ Y) {
   const TeamRows<CH> rows = TeamRows<CH>::template make<LPV>(n);
@@ -362,8 +362,8 @@ __global__ void __launch_bounds__(256) spmv_B_t1_kernel(int n, int m, const int3
 // ----------------------------------------------------------------------------- W X + B^T Y
 // Z_s = wx_s X_s + ys_s Y_s - sum_{e in row s of B^T} valT[e] ys_{i} Y_{i},  i = colT[e]
 // (X == nullptr: no diagonal term; ys == nullptr: 1)
-template <typename T, int LPV, int NV, int UNR, int CH = 0, int MINB = 1>
-__global__ void __launch_bounds__(256, MINB) spmv_Bt_kernel(int n, const int32_t* __restrict__ rowptrT,
+template <typename T, int LPV, int NV, int UNR, int CH = 0>
+__global__ void __launch_bounds__(256) spmv_Bt_kernel(int n, const int32_t* __restrict__ rowptrT,
                                                       const int32_t* __restrict__ colT, const T* __restrict__ valT,
                                                       const T* __restrict__ Y, const T* __restrict__ ys,
                                                       const T* __restrict__ X, const T* __restrict__ wx, int ld,
