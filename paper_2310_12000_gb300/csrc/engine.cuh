@@ -1051,9 +1051,9 @@ struct Engine {
       return VL_OK;
     };
     // the automatic choice takes the tiled walk for backward scalar solves of large systems
-    // (n = 1e6 grid: 1.09 ms against 1.94 ms for the grid walk); forward scalar solves keep the
-    // grid walk with its one-block head (1.09 ms against 1.36 ms), block solves keep the grid
-    // walk (their rows wait on 224-byte gathers: 8.8 / 16.3 ms tiled against 3.0 / 4.6 ms)
+    // (n = 1e6 grid: 1.07 ms against 1.94 ms for the grid walk); forward scalar solves keep the
+    // grid walk with its one-block head (1.05 ms against 1.20 ms), block solves keep the grid
+    // walk (their rows wait on 224-byte gathers: 8.9 / 16.2 ms tiled against 2.9 / 4.5 ms)
     const bool auto_tile = form == VL_SOLVE_AUTO && t == 1 && !FWD && n > kSharedRows && x != rhs;
     if (form == VL_SOLVE_TILE || auto_tile) {
       // storage-row tiles, each row waiting only for its own dependencies (see TileArgs)
@@ -1062,7 +1062,7 @@ struct Engine {
         return TileArgs{tp->ttask, tp->toff, tp->exported, tp->flag, c->dstatus, n, tp->R, tp->epoch};
       };
       if (t == 1) {
-        constexpr int LPVT = FWD ? 8 : 16;
+        constexpr int LPVT = 16;   // forward rows too: 1.20 ms against 1.33 ms with 8 lanes (n = 1e6)
         const void* fn = (const void*)sptrsv_tile1_kernel<T, FWD, LPVT>;
         VL_TRY(smem_limit_once(c, fn, kSmemSolveBytes));
         for (int bps = 1; bps <= 2; ++bps) {
