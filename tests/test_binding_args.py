@@ -107,3 +107,36 @@ def test_context_calls_check_locations():
     f = ctx.build_factor(np.zeros((10, 2)), np.random.default_rng(0).permutation(10).astype(np.int32),
                          0, 1.0, 0.1, 3)
     f.h = None
+
+
+@pytest.fixture
+def batch():
+    ctx = _Ctx()
+    b = _lib.Batch.__new__(_lib.Batch)
+    b.ctx, b.factors, b.h = ctx, [], C.c_void_p(1)
+    b.sizes = [10, 4]
+    b.offsets = np.array([0, 10, 14], np.int64)
+    yield b
+    b.h = None
+
+
+def test_batch_arguments_are_checked_per_problem(batch):
+    lib = batch.ctx.lib
+    with pytest.raises(ValueError, match="expected 2 problems"):
+        batch.find_mode([0], [np.zeros(10)])
+    with pytest.raises(ValueError, match=r"y\[1\]"):
+        batch.find_mode([0, 0], [np.zeros(10), np.zeros(5)])
+    with pytest.raises(ValueError, match=r"F\[0\]"):
+        batch.find_mode([0, 0], [np.zeros(10), np.zeros(4)], [np.zeros(9), np.zeros(4)])
+    with pytest.raises(ValueError, match="expected 2 problems"):
+        batch.pred_var([np.zeros((3, 2))])
+    with pytest.raises(ValueError, match=r"test_locs\[1\]"):
+        batch.pred_var([np.zeros((3, 2)), np.zeros(6)])
+    with pytest.raises(ValueError, match=r"Fp\[1\]"):
+        batch.pred_var([np.zeros((3, 2)), np.zeros((2, 2))], [np.zeros(3), np.zeros(5)])
+    assert "vl_batch_find_mode" not in lib.calls and "vl_batch_pred_var" not in lib.calls
+    modes = batch.find_mode([0, 0], [np.zeros(10), np.zeros(4)])
+    assert [len(v) for v in modes] == [10, 4]
+    means, vars_ = batch.pred_var([np.zeros((3, 2)), np.zeros((0, 2))], [np.zeros(3), np.zeros(0)])
+    assert [len(v) for v in means] == [3, 0] and [len(v) for v in vars_] == [3, 0]
+    assert lib.calls.count("vl_batch_find_mode") == 1 and lib.calls.count("vl_batch_pred_var") == 1
